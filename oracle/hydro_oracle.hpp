@@ -1,0 +1,677 @@
+// hydro_oracle.hpp -- plain, slow, FP64 CPU oracle for the Parthenon-hydro cycle.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+// call this code: only tests/, __graft_entry__.smoke() and bench.py's CPU
+// baseline leg use it.  It shares no code, header, table or constant with the
+// CUDA library; the two meet only through the seeded input generators.
+//
+// What it computes (arXiv:2202.12309, Sec. 5.1 "Parthenon-hydro"): the 3-D
+// Euler equations of an ideal gas, advanced with a two-stage Runge-Kutta
+// integrator, piecewise-linear reconstruction and the HLLE Riemann solver, on
+// a mesh of equal-sized MeshBlocks arranged in an oct-tree (Sec. 2.1), with
+// ghost cells filled from neighbours, restriction/prolongation at level
+// boundaries and flux correction (Sec. 3.6), and a global CFL time step from a
+// min-reduction (Sec. 3.9).  The paper names the methods only; every choice it
+// leaves open is fixed here as one "reading", listed in the comments below and
+// in the design notes.  Everything is written in the order the method defines
+// it, one cell / one face at a time, with no blocking or fusion.
+//
+// The scalar type R is double, or std::complex<double> for complex-step
+// derivatives (Squire & Trapp 1998): every branch (limiter, wave-speed max/min,
+// floors, |x|) is decided on the real part, which freezes branches exactly as
+// the adjoint does.
+//
+// Parity status per function (pins live in tests/test_oracle_*.py):
+//   cons_to_prim, vanleer, hlle_flux, stage update, dt, ghost fill (uniform),
+//   restriction/prolongation, flux correction, tree order, tagging: pinned by
+//   closed forms, invariants, exact Riemann solutions and brute force.
+#pragma once
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace ho {
+
+using cplx = std::complex<double>;
+inline double re(double x) { return x; }
+inline double re(const cplx& x) { return x.real(); }
+using std::sqrt;
+
+// |x|, max, min with branches taken on the real part (identity for double).
+template <class R> inline R rabs(const R& x) { return re(x) < 0.0 ? R(-x) : x; }
+template <class R> inline R rmax(const R& a, const R& b) { return re(a) >= re(b) ? a : b; }
+template <class R> inline R rmin(const R& a, const R& b) { return re(a) <= re(b) ? a : b; }
+
+enum { IDN = 0, IM1 = 1, IM2 = 2, IM3 = 3, IEN = 4, NVAR = 5 };
+constexpr int NG = 2;  // ghost width (PLM needs two cells on each side)
+
+// Mesh / physics configuration.  Plain POD, mirrored field by field by the
+// ctypes wrapper in oracle/__init__.py.
+struct Config {
+  int32_t nx[3];          // interior cells per block along x1,x2,x3
+  int32_t nb[3];          // root-grid blocks along x1,x2,x3
+  double xmin[3], xmax[3];
+  int32_t max_level;      // 0 = uniform, 1 = two levels
+  int32_t adaptive;       // tag + remesh after every cycle
+  double gamma, cfl, dfloor, pfloor;
+  double refine_tol, derefine_tol;
+  int32_t derefine_count;
+  int32_t static_region;  // 1: blocks overlapping [static_lo, static_hi] refined and pinned
+  double static_lo[3], static_hi[3];
+};
+
+// ---------------------------------------------------------------------------
+// Pointwise physics (Sec. 5.1: Euler equations, ideal gas)
+// ---------------------------------------------------------------------------
+
+// Conserved U = (rho, m1, m2, m3, E) -> primitive W = (rho, v1, v2, v3, p).
+// Reading: E = p/(gamma-1) + rho |v|^2 / 2; density and pressure floors are
+// applied here and only here, and every hit is counted.
+template <class R>
+inline void cons_to_prim(const R u[NVAR], R w[NVAR], const R& gamma, double dfloor,
+                         double pfloor, long* floors) {
+  R rho = u[IDN];
+  if (re(rho) < dfloor) { rho = R(dfloor); ++*floors; }
+  w[IDN] = rho;
+  w[IM1] = u[IM1] / rho;
+  w[IM2] = u[IM2] / rho;
+  w[IM3] = u[IM3] / rho;
+  R ke = 0.5 * (u[IM1] * w[IM1] + u[IM2] * w[IM2] + u[IM3] * w[IM3]);
+  R p = (gamma - 1.0) * (u[IEN] - ke);
+  if (re(p) < pfloor) { p = R(pfloor); ++*floors; }
+  w[IEN] = p;
+}
+
+// Piecewise-linear reconstruction slope (Sec. 5.1 "piecewise linear
+// reconstruction").  Reading: van Leer's harmonic limiter applied to each
+// primitive variable: delta = 2 dL dR / (dL + dR) where dL dR > 0, else 0.
+template <class R>
+inline R vanleer(const R& wm, const R& w0, const R& wp) {
+  R dl = w0 - wm;
+  R dr = wp - w0;
+  R prod = dl * dr;
+  if (re(prod) > 0.0) return 2.0 * prod / (dl + dr);
+  return R(0.0);
+}
+
+// HLLE flux through a face with normal along `dir` (0,1,2) from the left and
+// right primitive states (Sec. 5.1 "HLLE Riemann solver").  Reading: Einfeldt's
+// wave-speed bounds with Roe-averaged velocity and enthalpy:
+//   b+ = max(0, vR + cR, v~ + c~),  b- = min(0, vL - cL, v~ - c~),
+//   F  = (b+ FL - b- FR + b+ b- (UR - UL)) / (b+ - b-).
+template <class R>
+inline void hlle_flux(const R wl[NVAR], const R wr[NVAR], int dir, const R& gamma,
+                      R flux[NVAR]) {
+  const int ivn = IM1 + dir;
+  const R gm1 = gamma - 1.0;
+  // left and right conserved states and physical fluxes
+  R ul[NVAR], ur[NVAR], fl[NVAR], fr[NVAR];
+  R v2l = wl[IM1] * wl[IM1] + wl[IM2] * wl[IM2] + wl[IM3] * wl[IM3];
+  R v2r = wr[IM1] * wr[IM1] + wr[IM2] * wr[IM2] + wr[IM3] * wr[IM3];
+  R el = wl[IEN] / gm1 + 0.5 * wl[IDN] * v2l;
+  R er = wr[IEN] / gm1 + 0.5 * wr[IDN] * v2r;
+  ul[IDN] = wl[IDN];
+  ur[IDN] = wr[IDN];
+  for (int a = 0; a < 3; ++a) {
+    ul[IM1 + a] = wl[IDN] * wl[IM1 + a];
+    ur[IM1 + a] = wr[IDN] * wr[IM1 + a];
+  }
+  ul[IEN] = el;
+  ur[IEN] = er;
+  R vnl = wl[ivn], vnr = wr[ivn];
+  fl[IDN] = wl[IDN] * vnl;
+  fr[IDN] = wr[IDN] * vnr;
+  for (int a = 0; a < 3; ++a) {
+    fl[IM1 + a] = wl[IDN] * vnl * wl[IM1 + a];
+    fr[IM1 + a] = wr[IDN] * vnr * wr[IM1 + a];
+  }
+  fl[ivn] = fl[ivn] + wl[IEN];
+  fr[ivn] = fr[ivn] + wr[IEN];
+  fl[IEN] = (el + wl[IEN]) * vnl;
+  fr[IEN] = (er + wr[IEN]) * vnr;
+
+  // sound speeds and Roe averages
+  R cl = sqrt(gamma * wl[IEN] / wl[IDN]);
+  R cr = sqrt(gamma * wr[IEN] / wr[IDN]);
+  R sl = sqrt(wl[IDN]);
+  R sr = sqrt(wr[IDN]);
+  R hl = (el + wl[IEN]) / wl[IDN];
+  R hr = (er + wr[IEN]) / wr[IDN];
+  R vroe[3];
+  for (int a = 0; a < 3; ++a) vroe[a] = (sl * wl[IM1 + a] + sr * wr[IM1 + a]) / (sl + sr);
+  R hroe = (sl * hl + sr * hr) / (sl + sr);
+  R v2roe = vroe[0] * vroe[0] + vroe[1] * vroe[1] + vroe[2] * vroe[2];
+  R a2roe = rmax(R(0.0), R(gm1 * (hroe - 0.5 * v2roe)));
+  R croe = sqrt(a2roe);
+
+  R bp = rmax(R(0.0), rmax(R(vnr + cr), R(vroe[dir] + croe)));
+  R bm = rmin(R(0.0), rmin(R(vnl - cl), R(vroe[dir] - croe)));
+  for (int v = 0; v < NVAR; ++v)
+    flux[v] = (bp * fl[v] - bm * fr[v] + bp * bm * (ur[v] - ul[v])) / (bp - bm);
+}
+
+// minmod of two one-sided differences (used by prolongation).
+template <class R>
+inline R minmod(const R& a, const R& b) {
+  if (re(a * b) > 0.0) return re(rabs(a)) < re(rabs(b)) ? a : b;
+  return R(0.0);
+}
+
+// ---------------------------------------------------------------------------
+// Block tree (Sec. 2.1: oct-tree of MeshBlocks, Z-ordering)
+// ---------------------------------------------------------------------------
+
+struct LeafId {
+  int32_t level;
+  int64_t lx[3];
+};
+
+// Morton (Z-order) key of a block's logical location scaled to the finest
+// level; bit b of x1 goes to bit 3b, x2 to 3b+1, x3 to 3b+2.
+inline uint64_t morton_key(const LeafId& id, int max_level) {
+  uint64_t key = 0;
+  int sh = max_level - id.level;
+  for (int d = 0; d < 3; ++d) {
+    uint64_t c = (uint64_t)id.lx[d] << sh;
+    for (int b = 0; b < 21; ++b) key |= ((c >> b) & 1ull) << (3 * b + d);
+  }
+  return key;
+}
+
+inline bool leaf_less(const LeafId& a, const LeafId& b, int max_level) {
+  uint64_t ka = morton_key(a, max_level), kb = morton_key(b, max_level);
+  if (ka != kb) return ka < kb;
+  return a.level < b.level;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh of leaf blocks with ghost zones
+// ---------------------------------------------------------------------------
+
+template <class R>
+struct Mesh {
+  Config cfg;
+  R gamma;
+  std::vector<LeafId> leaf;
+  std::vector<int32_t> age;            // cycles since the leaf was created
+  std::vector<std::vector<R>> U;       // per leaf: NVAR x S3 x S2 x S1 (ghosts included)
+  std::vector<int32_t> root;           // root-grid slot -> leaf index, or -1 when refined
+  std::vector<std::vector<int32_t>> kids;  // root-grid slot -> 8 child leaf indices
+  double time = 0.0, dt = 0.0;
+  int64_t cycle = 0;
+  long floors = 0;
+
+  int S(int d) const { return cfg.nx[d] + 2 * NG; }
+  size_t block_len() const { return (size_t)NVAR * S(0) * S(1) * S(2); }
+  size_t idx(int v, int k, int j, int i) const {
+    return (((size_t)v * S(2) + k) * S(1) + j) * S(0) + i;
+  }
+  int64_t ncell(int d, int level) const { return ((int64_t)cfg.nb[d] * cfg.nx[d]) << level; }
+  double dx(int d, int level) const {
+    return (cfg.xmax[d] - cfg.xmin[d]) / (double)ncell(d, level);
+  }
+
+  explicit Mesh(const Config& c) : cfg(c), gamma(c.gamma) {
+    for (int64_t k = 0; k < cfg.nb[2]; ++k)
+      for (int64_t j = 0; j < cfg.nb[1]; ++j)
+        for (int64_t i = 0; i < cfg.nb[0]; ++i) leaf.push_back(LeafId{0, {i, j, k}});
+    age.assign(leaf.size(), 0);
+    U.assign(leaf.size(), std::vector<R>(block_len(), R(0.0)));
+    sort_and_index();
+    if (cfg.max_level >= 1 && cfg.static_region) {
+      std::vector<int8_t> flags(leaf.size(), 0);
+      for (size_t b = 0; b < leaf.size(); ++b)
+        if (in_static_region(leaf[b])) flags[b] = 1;
+      remesh(flags);
+    }
+  }
+
+  // Block extent along d: xmin + l * (width of one block at that level).
+  void block_extent(const LeafId& id, int d, double* lo, double* hi) const {
+    double w = (cfg.xmax[d] - cfg.xmin[d]) / (double)((int64_t)cfg.nb[d] << id.level);
+    *lo = cfg.xmin[d] + (double)id.lx[d] * w;
+    *hi = cfg.xmin[d] + (double)(id.lx[d] + 1) * w;
+  }
+  // Reading of "static + adaptive": a block overlapping the open box is refined
+  // at start and never derefined.
+  bool in_static_region(const LeafId& id) const {
+    if (!cfg.static_region) return false;
+    for (int d = 0; d < 3; ++d) {
+      double lo, hi;
+      block_extent(id, d, &lo, &hi);
+      if (!(lo < cfg.static_hi[d] && hi > cfg.static_lo[d])) return false;
+    }
+    return true;
+  }
+
+  int root_slot(int64_t r0, int64_t r1, int64_t r2) const {
+    return (int)((r2 * cfg.nb[1] + r1) * cfg.nb[0] + r0);
+  }
+
+  // Sort leaves in Z-order and rebuild the lookup tables.
+  void sort_and_index() {
+    std::vector<size_t> order(leaf.size());
+    for (size_t b = 0; b < order.size(); ++b) order[b] = b;
+    int ml = cfg.max_level;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+      return leaf_less(leaf[a], leaf[b], ml);
+    });
+    std::vector<LeafId> l2;
+    std::vector<int32_t> a2;
+    std::vector<std::vector<R>> u2;
+    for (size_t b : order) {
+      l2.push_back(leaf[b]);
+      a2.push_back(age[b]);
+      u2.push_back(std::move(U[b]));
+    }
+    leaf.swap(l2);
+    age.swap(a2);
+    U.swap(u2);
+    size_t nroot = (size_t)cfg.nb[0] * cfg.nb[1] * cfg.nb[2];
+    root.assign(nroot, -1);
+    kids.assign(nroot, std::vector<int32_t>(8, -1));
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      const LeafId& id = leaf[b];
+      if (id.level == 0) {
+        root[root_slot(id.lx[0], id.lx[1], id.lx[2])] = (int32_t)b;
+      } else {
+        int s = root_slot(id.lx[0] >> 1, id.lx[1] >> 1, id.lx[2] >> 1);
+        int c = (int)((id.lx[0] & 1) + 2 * (id.lx[1] & 1) + 4 * (id.lx[2] & 1));
+        kids[s][c] = (int32_t)b;
+      }
+    }
+  }
+
+  static int64_t wrap(int64_t i, int64_t n) { return ((i % n) + n) % n; }
+
+  // Interior value of leaf b at global cell (I,J,K) of the leaf's own level.
+  void leaf_value(int b, int64_t I, int64_t J, int64_t K, R out[NVAR]) const {
+    const LeafId& id = leaf[b];
+    int i = (int)(I - id.lx[0] * cfg.nx[0]) + NG;
+    int j = (int)(J - id.lx[1] * cfg.nx[1]) + NG;
+    int k = (int)(K - id.lx[2] * cfg.nx[2]) + NG;
+    for (int v = 0; v < NVAR; ++v) out[v] = U[b][idx(v, k, j, i)];
+  }
+
+  // The composite field: the value of cell (I,J,K) of level L built from the
+  // interior data of the leaves only (periodic wrap).  Same level: copy.
+  // Covered by finer leaves: restriction = mean of the 8 children (Sec. 3.6,
+  // "restricted first").  Covered by a coarser leaf: prolongation (Sec. 3.6,
+  // "interpolated (prolongated)"); reading: u_f = u_c + sum_d s_d minmod(
+  // u_c - u_{c-e_d}, u_{c+e_d} - u_c), s_d = +-1/4, evaluated d = 1,2,3 in
+  // order, with the coarse neighbours taken from the composite field.
+  void composite(int L, int64_t I, int64_t J, int64_t K, R out[NVAR]) const {
+    I = wrap(I, ncell(0, L));
+    J = wrap(J, ncell(1, L));
+    K = wrap(K, ncell(2, L));
+    int64_t r0 = (I >> L) / cfg.nx[0], r1 = (J >> L) / cfg.nx[1], r2 = (K >> L) / cfg.nx[2];
+    int s = root_slot(r0, r1, r2);
+    if (root[s] >= 0) {  // the covering leaf is at level 0
+      if (L == 0) { leaf_value(root[s], I, J, K, out); return; }
+      // prolongation from the coarse leaf (L == 1)
+      int64_t C[3] = {I >> 1, J >> 1, K >> 1};
+      int64_t F[3] = {I, J, K};
+      R uc[NVAR];
+      composite(0, C[0], C[1], C[2], uc);
+      R acc[NVAR];
+      for (int v = 0; v < NVAR; ++v) acc[v] = uc[v];
+      for (int d = 0; d < 3; ++d) {
+        int64_t cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
+        cm[d] -= 1;
+        cp[d] += 1;
+        R um[NVAR], up[NVAR];
+        composite(0, cm[0], cm[1], cm[2], um);
+        composite(0, cp[0], cp[1], cp[2], up);
+        double sgn = (F[d] & 1) ? 0.25 : -0.25;
+        for (int v = 0; v < NVAR; ++v)
+          acc[v] = acc[v] + sgn * minmod(R(uc[v] - um[v]), R(up[v] - uc[v]));
+      }
+      for (int v = 0; v < NVAR; ++v) out[v] = acc[v];
+      return;
+    }
+    // the location is refined: the covering leaves are at level 1
+    if (L == 1) {
+      int c = (int)(((I / cfg.nx[0]) & 1) + 2 * ((J / cfg.nx[1]) & 1) + 4 * ((K / cfg.nx[2]) & 1));
+      leaf_value(kids[s][c], I, J, K, out);
+      return;
+    }
+    // restriction (L == 0): mean of the 8 fine cells, summed c3 outer, c1 inner
+    R sum[NVAR];
+    for (int v = 0; v < NVAR; ++v) sum[v] = R(0.0);
+    for (int c3 = 0; c3 < 2; ++c3)
+      for (int c2 = 0; c2 < 2; ++c2)
+        for (int c1 = 0; c1 < 2; ++c1) {
+          R f[NVAR];
+          composite(1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
+          for (int v = 0; v < NVAR; ++v) sum[v] = sum[v] + f[v];
+        }
+    for (int v = 0; v < NVAR; ++v) out[v] = 0.125 * sum[v];
+  }
+
+  bool is_interior(int i, int j, int k) const {
+    return i >= NG && i < NG + cfg.nx[0] && j >= NG && j < NG + cfg.nx[1] && k >= NG &&
+           k < NG + cfg.nx[2];
+  }
+
+  // Ghost exchange (Sec. 3.6): every ghost cell of every leaf (faces, edges and
+  // corners, all 26 neighbour regions) takes the composite-field value there.
+  void fill_ghosts() {
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      const LeafId& id = leaf[b];
+      for (int k = 0; k < S(2); ++k)
+        for (int j = 0; j < S(1); ++j)
+          for (int i = 0; i < S(0); ++i) {
+            if (is_interior(i, j, k)) continue;
+            R val[NVAR];
+            composite(id.level, id.lx[0] * cfg.nx[0] + i - NG, id.lx[1] * cfg.nx[1] + j - NG,
+                      id.lx[2] * cfg.nx[2] + k - NG, val);
+            for (int v = 0; v < NVAR; ++v) U[b][idx(v, k, j, i)] = val[v];
+          }
+    }
+  }
+
+  void prim_at(const std::vector<R>& u, int k, int j, int i, R w[NVAR]) {
+    R c[NVAR];
+    for (int v = 0; v < NVAR; ++v) c[v] = u[idx(v, k, j, i)];
+    cons_to_prim(c, w, gamma, cfg.dfloor, cfg.pfloor, &floors);
+  }
+
+  // Face fluxes of one leaf along direction d.  Face f lies between interior
+  // cells f-1 and f (0 <= f <= n_d); its left state is reconstructed in cell
+  // f-1 and its right state in cell f.
+  // Layout: flux[((v * n3' + k) * n2' + j) * n1' + i] with n_d' = n_d + (d==dir).
+  struct Fluxes {
+    int n[3];
+    std::vector<R> f;
+    R& at(int v, int k, int j, int i) {
+      return f[(((size_t)v * n[2] + k) * n[1] + j) * n[0] + i];
+    }
+  };
+
+  Fluxes face_fluxes(int b, int dir) {
+    Fluxes F;
+    for (int d = 0; d < 3; ++d) F.n[d] = cfg.nx[d] + (d == dir ? 1 : 0);
+    F.f.assign((size_t)NVAR * F.n[0] * F.n[1] * F.n[2], R(0.0));
+    const std::vector<R>& u = U[b];
+    int e[3] = {dir == 0, dir == 1, dir == 2};
+    for (int k = 0; k < F.n[2]; ++k)
+      for (int j = 0; j < F.n[1]; ++j)
+        for (int i = 0; i < F.n[0]; ++i) {
+          // array indices of cell f (right of the face)
+          int ci = i + NG, cj = j + NG, ck = k + NG;
+          R w[4][NVAR];  // cells f-2, f-1, f, f+1 along dir
+          for (int s = 0; s < 4; ++s)
+            prim_at(u, ck + (s - 2) * e[2], cj + (s - 2) * e[1], ci + (s - 2) * e[0], w[s]);
+          R wl[NVAR], wr[NVAR];
+          for (int v = 0; v < NVAR; ++v) {
+            R dl = vanleer(w[0][v], w[1][v], w[2][v]);
+            R dr = vanleer(w[1][v], w[2][v], w[3][v]);
+            wl[v] = w[1][v] + 0.5 * dl;
+            wr[v] = w[2][v] - 0.5 * dr;
+          }
+          R fl[NVAR];
+          hlle_flux(wl, wr, dir, gamma, fl);
+          for (int v = 0; v < NVAR; ++v) F.at(v, k, j, i) = fl[v];
+        }
+    return F;
+  }
+
+  // Flux correction (Sec. 3.6): at a face shared by a level-0 leaf and
+  // level-1 leaves, the coarse flux is replaced by the mean of the 4 fine
+  // fluxes over it (summed t1 inner, t2 outer).
+  void flux_correct(std::vector<std::array<Fluxes, 3>>& F) {
+    if (cfg.max_level < 1) return;
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      const LeafId& id = leaf[b];
+      if (id.level != 0) continue;
+      for (int d = 0; d < 3; ++d) {
+        int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        for (int side = 0; side < 2; ++side) {
+          int64_t nl[3] = {id.lx[0], id.lx[1], id.lx[2]};
+          nl[d] += side ? 1 : -1;
+          nl[d] = wrap(nl[d], cfg.nb[d]);
+          int s = root_slot(nl[0], nl[1], nl[2]);
+          if (root[s] >= 0) continue;  // same-level neighbour
+          int cface = side ? cfg.nx[d] : 0;  // coarse face index along d
+          int fface = side ? 0 : cfg.nx[d];  // fine face index along d in the fine block
+          int childd = side ? 0 : 1;         // child offset along d adjacent to the face
+          for (int a2 = 0; a2 < cfg.nx[t2]; ++a2)
+            for (int a1 = 0; a1 < cfg.nx[t1]; ++a1) {
+              R sum[NVAR];
+              for (int v = 0; v < NVAR; ++v) sum[v] = R(0.0);
+              for (int q2 = 0; q2 < 2; ++q2)
+                for (int q1 = 0; q1 < 2; ++q1) {
+                  int64_t g1 = 2 * (id.lx[t1] * cfg.nx[t1] + a1) + q1;  // fine global index
+                  int64_t g2 = 2 * (id.lx[t2] * cfg.nx[t2] + a2) + q2;
+                  int c[3];
+                  c[d] = childd;
+                  c[t1] = (int)((g1 / cfg.nx[t1]) & 1);
+                  c[t2] = (int)((g2 / cfg.nx[t2]) & 1);
+                  int fb = kids[s][c[0] + 2 * c[1] + 4 * c[2]];
+                  int l[3];
+                  l[d] = fface;
+                  l[t1] = (int)(g1 % cfg.nx[t1]);
+                  l[t2] = (int)(g2 % cfg.nx[t2]);
+                  for (int v = 0; v < NVAR; ++v)
+                    sum[v] = sum[v] + F[fb][d].at(v, l[2], l[1], l[0]);
+                }
+              int l[3];
+              l[d] = cface;
+              l[t1] = a1;
+              l[t2] = a2;
+              for (int v = 0; v < NVAR; ++v) F[b][d].at(v, l[2], l[1], l[0]) = 0.25 * sum[v];
+            }
+        }
+      }
+    }
+  }
+
+  // One stage of the two-stage Runge-Kutta integrator (Sec. 5.1).  Reading:
+  // SSPRK2 (Heun) in the form
+  //   stage 1: U1 = U0 + dt L(U0)
+  //   stage 2: U  = 0.5 U0 + 0.5 (U1 + dt L(U1))
+  // with L(U) = -[(F1_{i+1/2}-F1_{i-1/2})/dx1 + (F2..)/dx2 + (F3..)/dx3],
+  // summed x1, then x2, then x3 (flux divergence, Sec. 3.6).
+  void stage(int which, const std::vector<std::vector<R>>& U0, double dtv) {
+    std::vector<std::array<Fluxes, 3>> F(leaf.size());
+    for (size_t b = 0; b < leaf.size(); ++b)
+      for (int d = 0; d < 3; ++d) F[b][d] = face_fluxes((int)b, d);
+    flux_correct(F);
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      int lev = leaf[b].level;
+      double h1 = dx(0, lev), h2 = dx(1, lev), h3 = dx(2, lev);
+      for (int k = 0; k < cfg.nx[2]; ++k)
+        for (int j = 0; j < cfg.nx[1]; ++j)
+          for (int i = 0; i < cfg.nx[0]; ++i)
+            for (int v = 0; v < NVAR; ++v) {
+              R L = -((F[b][0].at(v, k, j, i + 1) - F[b][0].at(v, k, j, i)) / h1 +
+                      (F[b][1].at(v, k, j + 1, i) - F[b][1].at(v, k, j, i)) / h2 +
+                      (F[b][2].at(v, k + 1, j, i) - F[b][2].at(v, k, j, i)) / h3);
+              size_t c = idx(v, k + NG, j + NG, i + NG);
+              if (which == 1)
+                U[b][c] = U0[b][c] + dtv * L;
+              else
+                U[b][c] = 0.5 * U0[b][c] + 0.5 * (U[b][c] + dtv * L);
+            }
+    }
+  }
+
+  // CFL time step (Sec. 3.9, global min-reduction).  Reading:
+  // dt = cfl * min over interior cells of all leaves and d of dx_d/(|v_d|+c_s),
+  // c_s = sqrt(gamma p / rho), in FP64, from the real part of the state.
+  double compute_dt() {
+    double m = INFINITY;
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      int lev = leaf[b].level;
+      for (int k = NG; k < NG + cfg.nx[2]; ++k)
+        for (int j = NG; j < NG + cfg.nx[1]; ++j)
+          for (int i = NG; i < NG + cfg.nx[0]; ++i) {
+            double u[NVAR], w[NVAR];
+            for (int v = 0; v < NVAR; ++v) u[v] = re(U[b][idx(v, k, j, i)]);
+            long dummy = 0;
+            cons_to_prim(u, w, re(gamma), cfg.dfloor, cfg.pfloor, &dummy);
+            double cs = std::sqrt(re(gamma) * w[IEN] / w[IDN]);
+            for (int d = 0; d < 3; ++d) {
+              double c = dx(d, lev) / (std::fabs(w[IM1 + d]) + cs);
+              if (c < m) m = c;
+            }
+          }
+    }
+    return cfg.cfl * m;
+  }
+
+  // One full cycle with a given dt: two stages, each followed by ghost exchange.
+  void cycle_with_dt(double dtv) {
+    std::vector<std::vector<R>> U0 = U;
+    stage(1, U0, dtv);
+    fill_ghosts();
+    stage(2, U0, dtv);
+    fill_ghosts();
+    time += dtv;
+    cycle += 1;
+    dt = dtv;
+    for (auto& a : age) a += 1;
+  }
+
+  // Refinement indicator (reading): m_b = max over interior cells and d of
+  // |rho_{i+e_d} - rho_{i-e_d}| / (2 rho_i), using the ghost-filled density.
+  double indicator(int b) const {
+    double m = 0.0;
+    const std::vector<R>& u = U[b];
+    for (int k = NG; k < NG + cfg.nx[2]; ++k)
+      for (int j = NG; j < NG + cfg.nx[1]; ++j)
+        for (int i = NG; i < NG + cfg.nx[0]; ++i) {
+          double r0 = re(u[idx(IDN, k, j, i)]);
+          double g[3] = {
+              std::fabs(re(u[idx(IDN, k, j, i + 1)]) - re(u[idx(IDN, k, j, i - 1)])) / (2.0 * r0),
+              std::fabs(re(u[idx(IDN, k, j + 1, i)]) - re(u[idx(IDN, k, j - 1, i)])) / (2.0 * r0),
+              std::fabs(re(u[idx(IDN, k + 1, j, i)]) - re(u[idx(IDN, k - 1, j, i)])) / (2.0 * r0)};
+          for (int d = 0; d < 3; ++d)
+            if (g[d] > m) m = g[d];
+        }
+    return m;
+  }
+
+  // Flags: +1 refine when m_b > refine_tol and level < max_level; -1 derefine
+  // when m_b < derefine_tol and level > 0 and the block is not pinned by the
+  // static region; 0 otherwise.
+  void tag(std::vector<int8_t>& flags, std::vector<double>* mb) const {
+    flags.assign(leaf.size(), 0);
+    if (mb) mb->assign(leaf.size(), 0.0);
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      double m = indicator((int)b);
+      if (mb) (*mb)[b] = m;
+      if (m > cfg.refine_tol && leaf[b].level < cfg.max_level)
+        flags[b] = 1;
+      else if (m < cfg.derefine_tol && leaf[b].level > 0 && !in_static_region(leaf[b]))
+        flags[b] = -1;
+    }
+  }
+
+  // Rebuild the tree (Sec. 2.1/3.7): refine every +1 leaf into 8 children;
+  // merge 8 siblings that are all -1 and at least derefine_count cycles old
+  // ("derefinement only allowed periodically").  New data is the composite
+  // field of the old mesh at the new leaf's level, i.e. prolongation for new
+  // children and restriction for merged parents.  Returns true if changed.
+  bool remesh(const std::vector<int8_t>& flags, bool check_age = true) {
+    std::vector<LeafId> nl;
+    std::vector<int32_t> na;
+    std::vector<bool> keep_old(leaf.size(), true);
+    bool changed = false;
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      if (flags[b] == 1 && leaf[b].level == 0 && cfg.max_level >= 1) {
+        keep_old[b] = false;
+        changed = true;
+        for (int c = 0; c < 8; ++c) {
+          LeafId k{1, {2 * leaf[b].lx[0] + (c & 1), 2 * leaf[b].lx[1] + ((c >> 1) & 1),
+                       2 * leaf[b].lx[2] + ((c >> 2) & 1)}};
+          nl.push_back(k);
+          na.push_back(0);
+        }
+      }
+    }
+    for (size_t s = 0; s < root.size(); ++s) {
+      if (root[s] >= 0) continue;
+      bool all = true;
+      for (int c = 0; c < 8; ++c) {
+        int b = kids[s][c];
+        if (b < 0 || flags[b] != -1 || (check_age && age[b] < cfg.derefine_count) ||
+            in_static_region(leaf[b])) {
+          all = false;
+          break;
+        }
+      }
+      if (!all) continue;
+      changed = true;
+      for (int c = 0; c < 8; ++c) keep_old[kids[s][c]] = false;
+      const LeafId& k0 = leaf[kids[s][0]];
+      nl.push_back(LeafId{0, {k0.lx[0] >> 1, k0.lx[1] >> 1, k0.lx[2] >> 1}});
+      na.push_back(0);
+    }
+    if (!changed) return false;
+    for (size_t b = 0; b < leaf.size(); ++b)
+      if (keep_old[b]) { nl.push_back(leaf[b]); na.push_back(age[b]); }
+    // new data from the old mesh's composite field
+    std::vector<std::vector<R>> nu(nl.size(), std::vector<R>(block_len(), R(0.0)));
+    for (size_t b = 0; b < nl.size(); ++b) {
+      const LeafId& id = nl[b];
+      for (int k = NG; k < NG + cfg.nx[2]; ++k)
+        for (int j = NG; j < NG + cfg.nx[1]; ++j)
+          for (int i = NG; i < NG + cfg.nx[0]; ++i) {
+            R val[NVAR];
+            composite(id.level, id.lx[0] * cfg.nx[0] + i - NG, id.lx[1] * cfg.nx[1] + j - NG,
+                      id.lx[2] * cfg.nx[2] + k - NG, val);
+            for (int v = 0; v < NVAR; ++v) nu[b][idx(v, k, j, i)] = val[v];
+          }
+    }
+    leaf.swap(nl);
+    age.swap(na);
+    U.swap(nu);
+    sort_and_index();
+    fill_ghosts();
+    return true;
+  }
+
+  // One driver cycle (Sec. 3.8 EvolutionDriver/MultiStageDriver): dt from the
+  // current state, the two stages, then tagging and remesh when adaptive.
+  void step_one() {
+    double dtv = compute_dt();
+    cycle_with_dt(dtv);
+    if (cfg.adaptive && cfg.max_level >= 1) {
+      std::vector<int8_t> flags;
+      tag(flags, nullptr);
+      remesh(flags);
+    }
+  }
+
+  // Conserved totals: sum over interior cells of all leaves of U_v dV, with
+  // Neumaier's compensated summation so that the sum itself adds no
+  // round-off that a conservation check could mistake for a flux error.
+  void totals(double out[NVAR]) const {
+    for (int v = 0; v < NVAR; ++v) {
+      double s = 0.0, comp = 0.0;
+      for (size_t b = 0; b < leaf.size(); ++b) {
+        int lev = leaf[b].level;
+        double dv = dx(0, lev) * dx(1, lev) * dx(2, lev);
+        for (int k = NG; k < NG + cfg.nx[2]; ++k)
+          for (int j = NG; j < NG + cfg.nx[1]; ++j)
+            for (int i = NG; i < NG + cfg.nx[0]; ++i) {
+              double x = re(U[b][idx(v, k, j, i)]) * dv;
+              double t = s + x;
+              if (std::fabs(s) >= std::fabs(x))
+                comp += (s - t) + x;
+              else
+                comp += (x - t) + s;
+              s = t;
+            }
+      }
+      out[v] = s + comp;
+    }
+  }
+};
+
+}  // namespace ho
