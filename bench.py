@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 Parthenon-hydro hot path.
+
+Workload (one "step" = one full cycle: two RK stages, two ghost exchanges,
+the dt reduction): a uniform 256^3-zone periodic mesh carrying a seeded
+linear sound wave of amplitude 1e-4 on rho=1, p=0.6 (gamma=5/3), split into
+blocks of 16^3, 32^3 or 64^3 zones.  The headline is FP64 with 32^3 blocks;
+the other block sizes and the FP32 variant are reported under "variants".
+
+Metric: zone-cycles/s = zones x cycles / device time (CUDA events on the
+mesh's stream around K replays of the captured cycle graph, after W warm-up
+cycles).  The state (671 MB in FP64, 335 MB in FP32) is larger than the
+129 MB L2, so no flush is needed between cycles.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this build
+has) on a bounded sample of the same workload, on the host cores.
+Under torchrun each rank runs an independent replica (replicas only: the
+single-GPU path has no exchange step between meshes); value sums the ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "zone-cycles/s on 1 GB300 (FP64 plain vs batched/FP32) and % of HBM roofline"
+MESH = 256
+GAMMA = 5.0 / 3.0
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe: 2 DFMA per clock per SM (measured 1.20 TFLOP/s at ~1.98 GHz on
+# 152 SMs); FP32: 128 FFMA per clock per SM.
+SMS = 152
+SM_MAX_MHZ = 2070.0
+# Algorithmic work per zone and stage launch ("Roofline"):
+#  bytes: stage 1 reads U0 and writes U1 (10 words), stage 2 reads U1 and U0
+#  and writes U0 (15 words): 25 words per zone-cycle, 12.5 per launch.
+WORDS_PER_ZONE_LAUNCH = 12.5
+#  flops: counted from the method, one flop per add/sub/mul/div/sqrt.
+FLOPS_PER_ZONE_CYCLE = 1235.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def build_mesh(ph, block, precision, nbfac=1):
+    n = MESH // nbfac
+    nb = n // block
+    cfg = ph.make_config((block,) * 3, (nb,) * 3, precision=precision)
+    m = ph.Mesh(cfg)
+    geo = W.Geometry((block,) * 3, (nb,) * 3)
+    return m, geo
+
+
+def wave_state(geo, leaves, dtype):
+    return W.linear_wave(geo, leaves, gamma=GAMMA, seed=0, amp=1e-4, kvec=(1, 0, 0)).astype(dtype)
+
+
+def time_variant(ph, torch, block, precision, steps, warmup):
+    """Device-timed cycles of one variant; returns a dict."""
+    m, geo = build_mesh(ph, block, precision)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    U = wave_state(geo, m.tree(), dtype)
+    m.set_state(U)
+    zones = MESH ** 3
+    stream = torch.cuda.current_stream()
+    m.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # per-launch device times over the same number of cycles (events between launches)
+    prof = m.profile(steps)
+    rc, floors, nonfinite = m.status()
+    res = {
+        "block": block, "precision": precision, "nblocks": m.nblocks, "tile": list(m.tile()),
+        "ms_per_cycle": ms / steps, "zone_cycles_per_s": zones * steps / (ms / 1e3),
+        "stage_ms_avg": float((prof[0] + prof[2]) / (2 * steps)),
+        "ghost_ms_avg": float((prof[1] + prof[3]) / (2 * steps)),
+        "launch_ms": [float(x / steps) for x in prof],
+        "floors": floors, "nonfinite": nonfinite,
+    }
+    m.close()
+    return res
+
+
+def roofline_for(v, pk, peak_kind):
+    zones = MESH ** 3
+    if v["precision"] == "fp32":
+        word = 4
+        achieved = WORDS_PER_ZONE_LAUNCH * word * zones / (v["stage_ms_avg"] / 1e3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}
+    # FP64: bound by the FP64 pipe
+    achieved = FLOPS_PER_ZONE_CYCLE * 0.5 * zones / (v["stage_ms_avg"] / 1e3) / 1e12
+    peak = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)"}
+
+
+def e2e_variant(ph, torch, block, precision, steps, warmup):
+    """Same metric through the public API with pinned host buffers: every step
+    copies the state in (ph_set_state from host), runs one cycle and reads the
+    new state back (ph_get_state to host)."""
+    m, geo = build_mesh(ph, block, precision)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    U = wave_state(geo, m.tree(), dtype)
+    tdt = torch.float32 if precision == "fp32" else torch.float64
+    host_in = torch.from_numpy(U).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(max(1, warmup // 2)):
+        m.set_state(host_in.numpy())
+        m.step(1)
+        m.get_state(host_out.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        m.set_state(host_in.numpy())
+        m.step(1)
+        m.get_state(host_out.numpy())
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nbytes = host_in.numel() * host_in.element_size()
+    m.close()
+    del tdt
+    return {"value": MESH ** 3 * steps / dt, "unit": "zone-cycles/s",
+            "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)}
+
+
+def oracle_rate(block, n_sample, cycles):
+    """FP64 oracle zone-cycles/s on an n_sample^3 mesh of the same workload."""
+    import oracle as O
+    nb = max(1, n_sample // block)
+    blk = min(block, n_sample)
+    cfg = O.make_config((blk,) * 3, (nb,) * 3)
+    om = O.OracleMesh(cfg)
+    geo = W.Geometry((blk,) * 3, (nb,) * 3)
+    om.set_state(wave_state(geo, om.tree(), np.float64))
+    t0 = time.perf_counter()
+    om.step(cycles)
+    dt = time.perf_counter() - t0
+    return (blk * nb) ** 3 * cycles / dt, (blk * nb), dt
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    # each step: one oracle cycle on a 64^3-zone sample (8 blocks of 32^3)
+    block, n_sample = 32, 64
+    import oracle as O
+    cfg = O.make_config((block,) * 3, (n_sample // block,) * 3)
+    om = O.OracleMesh(cfg)
+    geo = W.Geometry((block,) * 3, (n_sample // block,) * 3)
+    om.set_state(wave_state(geo, om.tree(), np.float64))
+    om.step(args.warmup)
+    t0 = time.perf_counter()
+    om.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = n_sample ** 3 * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "zone-cycles/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "FP64 CPU oracle, linear sound wave, 64^3-zone sample of the "
+                               "256^3 workload (8 blocks of 32^3), 1 cycle per step",
+                   "zones_per_step": n_sample ** 3},
+        "cpu_baseline": {"value": value, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
+                         "sample": "64^3 zones (8 blocks of 32^3), %d cycles" % args.steps},
+        "e2e": {"value": value, "unit": "zone-cycles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--block", type=int, default=32)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.quick:
+        args.no_variants = args.no_cpu = True
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2202_12309_gb300 as ph
+    from paper_2202_12309_gb300 import build as B
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or not os.path.exists(ph.LIB_PATH):
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    ph.use_torch_allocator()
+    pk, peak_kind = peaks()
+
+    # headline: timed with clocks sampled; barrier + max over ranks
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    head = time_variant(ph, torch, args.block, args.precision, args.steps, args.warmup)
+    ck = clocks.stop()
+    ms = head["ms_per_cycle"] * args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * MESH ** 3 * args.steps / (ms / 1e3)
+
+    variants = []
+    if not args.no_variants:
+        for prec in ("fp64", "fp32"):
+            for block in (16, 32, 64):
+                if prec == args.precision and block == args.block:
+                    continue
+                v = time_variant(ph, torch, block, prec, args.steps, args.warmup)
+                v["roofline"] = roofline_for(v, pk, peak_kind)
+                variants.append(v)
+                log("variant %s block %d: %.3e zone-cycles/s" % (prec, block, v["zone_cycles_per_s"]))
+
+    e2e = None
+    if not args.quick:
+        e2e = e2e_variant(ph, torch, args.block, args.precision, max(3, args.steps // 4), args.warmup)
+    if world > 1 and e2e is not None:
+        t = torch.tensor([e2e["value"]], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
+        e2e["value"] = float(t.item()) * world
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu:
+        rate, n, secs = oracle_rate(args.block, 128, 1)
+        cpu = {"value": rate, "unit": "zone-cycles/s", "cores": 1, "kind": "oracle",
+               "sample": "%d^3 zones of the same workload (blocks of %d^3), 1 cycle, %.1f s"
+                         % (n, min(args.block, n), secs)}
+
+    roof = roofline_for(head, pk, peak_kind)
+    nb = (MESH // args.block) ** 3
+    line = {
+        "metric": METRIC, "value": value, "unit": "zone-cycles/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_cycle"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+        "config": {"workload": "uniform 256^3-zone periodic linear sound wave (A=1e-4), %d blocks "
+                               "of %d^3, 2 ghost zones, %s, 1 cycle per step"
+                               % (nb, args.block, args.precision.upper()),
+                   "zones": MESH ** 3, "block": args.block, "nblocks": nb, "tile": head["tile"],
+                   "l2": "state %.0f MB > 129 MB L2: no flush needed"
+                         % (MESH ** 3 * 5 * (8 if args.precision == "fp64" else 4) / 1e6 *
+                            (1 + 4.0 / args.block) ** 3),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps,
+        "clocks": ck,
+        "kernel_ms": {"stage_avg": head["stage_ms_avg"], "ghost_avg": head["ghost_ms_avg"],
+                      "per_launch": head["launch_ms"]},
+        "variants": variants,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

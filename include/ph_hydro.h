@@ -1,0 +1,193 @@
+/* ph_hydro.h -- C ABI of the GB300 Parthenon-hydro hot path (libphhydro.so).
+ *
+ * The library advances the 3-D Euler equations of an ideal gas on a mesh of
+ * equal-sized MeshBlocks with ghost zones, one GPU, all work in hand-written
+ * CUDA kernels for sm_103a (arXiv:2202.12309; the method is that of its
+ * Parthenon-hydro miniapp, Sec. 5.1: two-stage Runge-Kutta, piecewise-linear
+ * reconstruction, HLLE Riemann solver; the mesh and its boundary
+ * communication are Sec. 2.1, 3.6 and 3.7; the time step is a global
+ * min-reduction, Sec. 3.9; the call sequence follows the driver pattern of
+ * Sec. 3.10: create a mesh, refine, set the state, step, read state and dt).
+ *
+ * Conventions for every entry point:
+ *  - Return value: PH_OK (0) or a negative PH_ERR_* code.  The message of the
+ *    last failure on the calling thread is ph_last_error().  No C++ exception
+ *    crosses this ABI.
+ *  - Work is enqueued on the stream given at creation; calls that return data
+ *    to host memory synchronise that stream.  ph_step does not synchronise
+ *    (except on two-level meshes, where it reads refinement flags each cycle).
+ *  - Caller buffers are borrowed for the duration of the call only.
+ *  - State arrays are in the mesh's precision (double for PH_FP64, float for
+ *    PH_FP32), conserved variables (rho, m1, m2, m3, E), interior cells only,
+ *    layout U[block][var][k][j][i] with i fastest, blocks in the order of
+ *    ph_tree (Z-order).
+ *  - Device memory of a mesh is owned by the library and comes from the
+ *    allocator installed with ph_set_allocator (cudaMalloc by default).
+ */
+#ifndef PH_HYDRO_H
+#define PH_HYDRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PH_OK 0
+#define PH_ERR_INVALID (-1)     /* bad argument or configuration */
+#define PH_ERR_OOM (-2)         /* device allocation failed */
+#define PH_ERR_NONPHYSICAL (-3) /* non-finite state or density/pressure floor hit */
+#define PH_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define PH_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define PH_ERR_STATE (-6)       /* call not valid in the object's current state */
+
+#define PH_FP64 0
+#define PH_FP32 1
+
+/* Mesh configuration (Sec. 2.1: equal-sized blocks, an integer number of
+ * blocks per dimension; Sec. 5.1: ideal gas).  All fields are read once by
+ * ph_create.
+ *   nx[3]          interior cells per block along x1, x2, x3 (each >= 4)
+ *   nb[3]          root-grid blocks along x1, x2, x3 (each >= 1)
+ *   xmin/xmax      domain extent; boundaries are periodic
+ *   max_level      0 (uniform) or 1 (two levels)
+ *   adaptive       1: tag and remesh after every cycle (max_level 1 only)
+ *   gamma          adiabatic index; cfl: Courant number
+ *   dfloor/pfloor  density and pressure floors applied when converting to
+ *                  primitive variables (every application is counted)
+ *   refine_tol     refine a level-0 block whose indicator exceeds it
+ *   derefine_tol   derefine 8 level-1 siblings whose indicators are all below it
+ *   derefine_count siblings must be at least this many cycles old to merge
+ *   static_region  1: level-0 blocks overlapping the open box
+ *                  (static_lo, static_hi) are refined at creation and pinned
+ *   precision      PH_FP64 or PH_FP32 (state and fluxes; dt and totals stay FP64)
+ *   tile[3]        fused-stage tile (TX, TY, KC); 0,0,0 = pick a default
+ */
+typedef struct ph_config {
+  int32_t nx[3];
+  int32_t nb[3];
+  double xmin[3];
+  double xmax[3];
+  int32_t max_level;
+  int32_t adaptive;
+  double gamma;
+  double cfl;
+  double dfloor;
+  double pfloor;
+  double refine_tol;
+  double derefine_tol;
+  int32_t derefine_count;
+  int32_t static_region;
+  double static_lo[3];
+  double static_hi[3];
+  int32_t precision;
+  int32_t tile[3];
+} ph_config;
+
+typedef struct ph_mesh ph_mesh;
+
+/* Device allocator hook: alloc(bytes, stream, ctx) returns a device pointer
+ * or NULL; release(ptr, stream, ctx) returns it.  Installed process-wide;
+ * NULL, NULL restores cudaMalloc/cudaFree.  Meshes created before the call
+ * keep the allocator they were created with. */
+typedef void* (*ph_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*ph_free_fn)(void* ptr, void* stream, void* ctx);
+int ph_set_allocator(ph_alloc_fn alloc, ph_free_fn release, void* ctx);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* ph_last_error(void);
+
+/* Create a mesh (Sec. 2.1): root grid, oct-tree, Z-order, static refinement
+ * (Sec. 3.7).  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * The state is zero until ph_set_state.  *out receives the handle.
+ * Errors: PH_ERR_INVALID (nx < 4, nb < 1, bad level/precision/tile),
+ * PH_ERR_OOM, PH_ERR_CUDA. */
+int ph_create(const ph_config* cfg, void* stream, ph_mesh** out);
+
+/* Release the mesh and its device memory (synchronises its stream). */
+int ph_destroy(ph_mesh* mesh);
+
+/* Number of leaf blocks. */
+int ph_num_blocks(const ph_mesh* mesh, int32_t* n);
+
+/* Leaves in Z-order (Sec. 2.1), 4 int64 per leaf: level, lx1, lx2, lx3.
+ * `n` is the capacity in leaves; PH_ERR_INVALID if smaller than the count. */
+int ph_tree(const ph_mesh* mesh, int64_t* out, int32_t n);
+
+/* Copy the interior state in (count = blocks*5*nx1*nx2*nx3 elements) and
+ * fill ghosts; computes the first dt.  on_device: 1 if U is a device pointer,
+ * 0 for host memory.  PH_ERR_INVALID if count does not match. */
+int ph_set_state(ph_mesh* mesh, const void* U, int64_t count, int32_t on_device);
+
+/* Copy the interior state out (same layout and count rule). */
+int ph_get_state(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
+
+/* Copy whole blocks out, ghosts included: layout U[block][var][k][j][i] over
+ * (nx+4)^3 cells (count = blocks*5*(nx1+4)*(nx2+4)*(nx3+4)). */
+int ph_get_full(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
+
+/* Advance `ncycles` cycles (Sec. 3.10 MultiStageDriver): per cycle, two RK
+ * stages each followed by the ghost exchange (Sec. 3.6) and, on two-level
+ * meshes, flux correction; then dt for the next cycle (Sec. 3.9) and, when
+ * adaptive, tagging and remesh (Sec. 3.7).  Uniform meshes replay a captured
+ * CUDA graph of one cycle and return without synchronising. */
+int ph_step(ph_mesh* mesh, int32_t ncycles);
+
+/* dt used by the last cycle (the first dt before any cycle); synchronises. */
+int ph_get_dt(ph_mesh* mesh, double* dt);
+/* dt the next cycle will use; synchronises. */
+int ph_get_next_dt(ph_mesh* mesh, double* dt);
+
+/* Simulation time and cycle count; synchronises. */
+int ph_get_time(ph_mesh* mesh, double* time, int64_t* cycle);
+
+/* Conserved totals: sum over interior cells of all leaves of U_v dV, in FP64. */
+int ph_totals(ph_mesh* mesh, double out[5]);
+
+/* Refinement indicator of every leaf (reading of the unspecified criterion:
+ * max over interior cells and directions of |rho_{+1} - rho_{-1}| / (2 rho))
+ * and the flags it implies (+1 refine, -1 derefine, 0 keep) under the
+ * configured tolerances.  Arrays of n entries (n >= ph_num_blocks). */
+int ph_tag(ph_mesh* mesh, int8_t* flags, double* indicator, int32_t n);
+
+/* Rebuild the tree from explicit flags (+1 refine a level-0 leaf, -1 merge
+ * 8 level-1 siblings that are all -1, 0 keep; Sec. 2.1/3.7) and move the data
+ * (prolongation for new children, restriction for merged parents).
+ * check_age: also require derefine_count cycles of age to merge.
+ * *changed (may be NULL) is set to 1 if the tree changed. */
+int ph_refine_where(ph_mesh* mesh, const int8_t* flags, int32_t n, int32_t check_age,
+                    int32_t* changed);
+
+/* One tag + remesh pass on the current state (initial refinement). */
+int ph_refine_by_density(ph_mesh* mesh, int32_t* changed);
+
+/* Health of the state since creation: number of floor applications and 1 if
+ * a non-finite dt was produced.  Returns PH_ERR_NONPHYSICAL when either is
+ * non-zero (outputs are still written). */
+int ph_status(ph_mesh* mesh, int64_t* floor_hits, int32_t* nonfinite);
+
+/* Kernel-level entry points used by tests and benchmarks ------------------ */
+
+/* Ghost exchange alone on the current state (Sec. 3.6). */
+int ph_fill_ghosts(ph_mesh* mesh);
+
+/* Number of kernel launches one uniform-mesh cycle enqueues. */
+int ph_launches_per_cycle(const ph_mesh* mesh, int32_t* n);
+
+/* Fused-stage tile in use (TX, TY, KC). */
+int ph_get_tile(const ph_mesh* mesh, int32_t tile[3]);
+
+/* Run `ncycles` uniform-mesh cycles with the same launches as ph_step but
+ * without the graph, recording a CUDA event on the mesh's stream between
+ * launches; ms_out[s] (s < nslots, nslots <= 5) receives the summed device
+ * time of launch slot s of the cycle: 0 stage 1, 1 ghost exchange, 2 stage 2,
+ * 3 ghost exchange, 4 dt bookkeeping.  Synchronises.  Uniform meshes only
+ * (PH_ERR_INVALID otherwise). */
+int ph_profile_cycles(ph_mesh* mesh, int32_t ncycles, double* ms_out, int32_t nslots);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PH_HYDRO_H */

@@ -1,0 +1,310 @@
+"""Python binding of libphhydro.so (include/ph_hydro.h): argument marshalling only.
+
+Every step of the hydro cycle runs in the library's CUDA kernels; this module
+only converts Python arguments into the C ABI's plain pointers and sizes.
+PyTorch is used for device memory (its caching allocator backs the library's
+allocations) and streams.  There is no CPU fallback: if the shared library is
+missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphhydro.so")
+
+PH_OK = 0
+PH_ERR = {-1: "PH_ERR_INVALID", -2: "PH_ERR_OOM", -3: "PH_ERR_NONPHYSICAL", -4: "PH_ERR_TIMEOUT",
+          -5: "PH_ERR_CUDA", -6: "PH_ERR_STATE"}
+PH_FP64 = 0
+PH_FP32 = 1
+
+EXPORTS = [
+    "ph_set_allocator", "ph_last_error", "ph_create", "ph_destroy", "ph_num_blocks", "ph_tree",
+    "ph_set_state", "ph_get_state", "ph_get_full", "ph_step", "ph_get_dt", "ph_get_next_dt",
+    "ph_get_time", "ph_totals", "ph_tag", "ph_refine_where", "ph_refine_by_density", "ph_status",
+    "ph_fill_ghosts", "ph_launches_per_cycle", "ph_get_tile", "ph_profile_cycles",
+]
+
+
+class PhError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (PH_ERR.get(code, "PH_ERR"), code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    """Mirror of ph_config."""
+    _fields_ = [
+        ("nx", ctypes.c_int32 * 3),
+        ("nb", ctypes.c_int32 * 3),
+        ("xmin", ctypes.c_double * 3),
+        ("xmax", ctypes.c_double * 3),
+        ("max_level", ctypes.c_int32),
+        ("adaptive", ctypes.c_int32),
+        ("gamma", ctypes.c_double),
+        ("cfl", ctypes.c_double),
+        ("dfloor", ctypes.c_double),
+        ("pfloor", ctypes.c_double),
+        ("refine_tol", ctypes.c_double),
+        ("derefine_tol", ctypes.c_double),
+        ("derefine_count", ctypes.c_int32),
+        ("static_region", ctypes.c_int32),
+        ("static_lo", ctypes.c_double * 3),
+        ("static_hi", ctypes.c_double * 3),
+        ("precision", ctypes.c_int32),
+        ("tile", ctypes.c_int32 * 3),
+    ]
+
+
+def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0 / 3.0, cfl=0.3,
+                max_level=0, adaptive=0, dfloor=None, pfloor=None, refine_tol=0.05,
+                derefine_tol=0.0125, derefine_count=10, static_region=0,
+                static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2), precision="fp64",
+                tile=(0, 0, 0)) -> Config:
+    prec = PH_FP32 if precision in ("fp32", PH_FP32) else PH_FP64
+    if dfloor is None:
+        dfloor = 1e-7 if prec == PH_FP32 else 1e-12
+    if pfloor is None:
+        pfloor = 1e-7 if prec == PH_FP32 else 1e-12
+    c = Config()
+    c.nx[:] = list(nx)
+    c.nb[:] = list(nb)
+    c.xmin[:] = list(xmin)
+    c.xmax[:] = list(xmax)
+    c.max_level = max_level
+    c.adaptive = adaptive
+    c.gamma = gamma
+    c.cfl = cfl
+    c.dfloor = dfloor
+    c.pfloor = pfloor
+    c.refine_tol = refine_tol
+    c.derefine_tol = derefine_tol
+    c.derefine_count = derefine_count
+    c.static_region = static_region
+    c.static_lo[:] = list(static_lo)
+    c.static_hi[:] = list(static_hi)
+    c.precision = prec
+    c.tile[:] = list(tile)
+    return c
+
+
+_lib = None
+_alloc_refs = None
+
+
+def lib():
+    """Load libphhydro.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libphhydro.so is missing: run paper_2202_12309_gb300/build.py "
+                              "(or __graft_entry__.build()) first")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.c_void_p
+        i32, i64 = ctypes.c_int32, ctypes.c_int64
+        dp = ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "ph_set_allocator": [P, P, P],
+            "ph_create": [ctypes.POINTER(Config), P, ctypes.POINTER(P)],
+            "ph_destroy": [P],
+            "ph_num_blocks": [P, ctypes.POINTER(i32)],
+            "ph_tree": [P, ctypes.POINTER(i64), i32],
+            "ph_set_state": [P, P, i64, i32],
+            "ph_get_state": [P, P, i64, i32],
+            "ph_get_full": [P, P, i64, i32],
+            "ph_step": [P, i32],
+            "ph_get_dt": [P, dp],
+            "ph_get_next_dt": [P, dp],
+            "ph_get_time": [P, dp, ctypes.POINTER(i64)],
+            "ph_totals": [P, dp],
+            "ph_tag": [P, ctypes.POINTER(ctypes.c_int8), dp, i32],
+            "ph_refine_where": [P, ctypes.POINTER(ctypes.c_int8), i32, i32, ctypes.POINTER(i32)],
+            "ph_refine_by_density": [P, ctypes.POINTER(i32)],
+            "ph_status": [P, ctypes.POINTER(i64), ctypes.POINTER(i32)],
+            "ph_fill_ghosts": [P],
+            "ph_launches_per_cycle": [P, ctypes.POINTER(i32)],
+            "ph_get_tile": [P, ctypes.POINTER(i32)],
+            "ph_profile_cycles": [P, i32, dp, i32],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.ph_last_error.restype = ctypes.c_char_p
+        L.ph_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != PH_OK:
+        raise PhError(rc, lib().ph_last_error().decode())
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    global _alloc_refs
+    import torch
+
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+    def _alloc(nbytes, stream, ctx):
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0)))
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC(_alloc), FREE(_free)
+    check(lib().ph_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
+    _alloc_refs = (a, f)
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    assert x.is_contiguous()
+    return x.data_ptr(), (1 if x.is_cuda else 0)
+
+
+class Mesh:
+    """A GPU mesh (uniform or two-level) with its conserved state."""
+
+    def __init__(self, cfg: Config, stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the GB300 hydro library has no CPU path")
+            stream = torch.cuda.current_stream().cuda_stream
+        self.L = lib()
+        self.cfg = cfg
+        self.h = ctypes.c_void_p()
+        check(self.L.ph_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(self.h)))
+        self.nx = tuple(cfg.nx)
+        self.dtype = np.float32 if cfg.precision == PH_FP32 else np.float64
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.ph_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nblocks(self) -> int:
+        n = ctypes.c_int32()
+        check(self.L.ph_num_blocks(self.h, ctypes.byref(n)))
+        return n.value
+
+    def tree(self) -> np.ndarray:
+        n = self.nblocks
+        out = np.zeros((n, 4), dtype=np.int64)
+        check(self.L.ph_tree(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n))
+        return out
+
+    def state_shape(self):
+        return (self.nblocks, 5, self.nx[2], self.nx[1], self.nx[0])
+
+    def count(self) -> int:
+        return int(np.prod(self.state_shape()))
+
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=self.dtype)
+        p, dev = _ptr(U)
+        check(self.L.ph_set_state(self.h, ctypes.c_void_p(p), self.count(), dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros(self.state_shape(), dtype=self.dtype)
+        p, dev = _ptr(out)
+        check(self.L.ph_get_state(self.h, ctypes.c_void_p(p), self.count(), dev))
+        return out
+
+    def get_full(self) -> np.ndarray:
+        S = [n + 4 for n in self.nx]
+        out = np.zeros((self.nblocks, 5, S[2], S[1], S[0]), dtype=self.dtype)
+        check(self.L.ph_get_full(self.h, ctypes.c_void_p(out.ctypes.data), out.size, 0))
+        return out
+
+    def step(self, n: int = 1):
+        check(self.L.ph_step(self.h, int(n)))
+
+    def dt(self) -> float:
+        v = ctypes.c_double()
+        check(self.L.ph_get_dt(self.h, ctypes.byref(v)))
+        return v.value
+
+    def next_dt(self) -> float:
+        v = ctypes.c_double()
+        check(self.L.ph_get_next_dt(self.h, ctypes.byref(v)))
+        return v.value
+
+    def time(self):
+        t = ctypes.c_double()
+        c = ctypes.c_int64()
+        check(self.L.ph_get_time(self.h, ctypes.byref(t), ctypes.byref(c)))
+        return t.value, c.value
+
+    def totals(self) -> np.ndarray:
+        out = np.zeros(5)
+        check(self.L.ph_totals(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def tag(self):
+        n = self.nblocks
+        flags = np.zeros(n, dtype=np.int8)
+        mb = np.zeros(n, dtype=np.float64)
+        check(self.L.ph_tag(self.h, flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                            mb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n))
+        return flags, mb
+
+    def refine_where(self, flags: Sequence[int], check_age: bool = True) -> bool:
+        f = np.ascontiguousarray(flags, dtype=np.int8)
+        ch = ctypes.c_int32()
+        check(self.L.ph_refine_where(self.h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), len(f),
+                                     1 if check_age else 0, ctypes.byref(ch)))
+        return bool(ch.value)
+
+    def refine_by_density(self) -> bool:
+        ch = ctypes.c_int32()
+        check(self.L.ph_refine_by_density(self.h, ctypes.byref(ch)))
+        return bool(ch.value)
+
+    def status(self):
+        fh = ctypes.c_int64()
+        nf = ctypes.c_int32()
+        rc = self.L.ph_status(self.h, ctypes.byref(fh), ctypes.byref(nf))
+        return rc, fh.value, nf.value
+
+    def fill_ghosts(self):
+        check(self.L.ph_fill_ghosts(self.h))
+
+    def launches_per_cycle(self) -> int:
+        n = ctypes.c_int32()
+        check(self.L.ph_launches_per_cycle(self.h, ctypes.byref(n)))
+        return n.value
+
+    def profile(self, ncycles: int) -> np.ndarray:
+        """Summed device ms per launch slot over ncycles (stage1, ghost, stage2, ghost, dt)."""
+        ms = np.zeros(5)
+        check(self.L.ph_profile_cycles(self.h, int(ncycles),
+                                       ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 5))
+        return ms
+
+    def tile(self):
+        t = (ctypes.c_int32 * 3)()
+        check(self.L.ph_get_tile(self.h, t))
+        return tuple(t)

@@ -1,0 +1,971 @@
+// ph_api.cu -- the C ABI (include/ph_hydro.h): mesh object, host block tree,
+// device tables, the per-cycle launch sequence and its CUDA-graph capture.
+//
+// Host tree (arXiv:2202.12309 Sec. 2.1): root grid of nb1 x nb2 x nb3 blocks,
+// each of which may split into 2^3 children (two levels); leaves are kept in
+// Z-order of their location scaled to the finest level (x1 in the lowest
+// bit).  Leaf b's data lives in slot b of the device pools, so a remesh
+// rebuilds the pool in the new order (Sec. 3.7: the tree is rebuilt first,
+// then populated).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ph_hydro.h"
+#include "ph_internal.h"
+#include "ph_stage.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(PH_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PH_CUDA(expr)                                       \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);     \
+  } while (0)
+
+struct Allocator {
+  ph_alloc_fn alloc = nullptr;
+  ph_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+Allocator g_alloc;
+
+struct Leaf {
+  int level;
+  int64_t lx[3];
+  int age;
+};
+
+// Z-order key: interleave the location scaled to level 1 (x1 lowest bit).
+uint64_t zkey(const Leaf& l, int max_level) {
+  uint64_t key = 0;
+  for (int d = 0; d < 3; ++d) {
+    const uint64_t c = (uint64_t)l.lx[d] << (max_level - l.level);
+    for (int b = 0; b < 21; ++b) key |= ((c >> b) & 1ull) << (3 * b + d);
+  }
+  return key;
+}
+
+}  // namespace
+
+struct ph_mesh {
+  ph_config cfg;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  Allocator alloc;
+  int nx[3], S[3], nb[3];
+  size_t block_elems = 0;  // NV * S1 * S2 * S3
+  size_t esize = 8;
+  bool two_level = false;
+
+  std::vector<Leaf> leaf;
+  std::vector<int> root, kids;  // host copies of the lookup tables
+
+  // device memory
+  void* U0 = nullptr;
+  void* U1 = nullptr;
+  size_t pool_cap = 0;  // leaves the pools can hold
+  ph::DevScalars* sc = nullptr;
+  int* d_nbr = nullptr;
+  int8_t* d_level = nullptr;
+  int* d_root = nullptr;
+  int* d_kids = nullptr;
+  int* d_leaf_id = nullptr;
+  double* d_partial = nullptr;
+  double* d_totals = nullptr;
+  double* d_mb = nullptr;
+  size_t table_cap = 0;
+  // flux correction
+  int* d_face_rec = nullptr;
+  int* d_fine_off = nullptr;
+  int* d_corr_leaf = nullptr;
+  int* d_rec_beg = nullptr;
+  int* d_rec_face = nullptr;
+  void* d_fcc = nullptr;
+  void* d_fcf = nullptr;
+  int nrec = 0, ncorr = 0;
+  // staging for host copies and packed device copies
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+
+  cudaGraphExec_t gexec = nullptr;
+  int tile[3] = {0, 0, 0};
+  bool state_set = false;
+
+  std::vector<void*> owned;  // every device allocation, for destroy
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (alloc.alloc) {
+      p = alloc.alloc(bytes, (void*)stream, alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) owned.push_back(p);
+    return p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    auto it = std::find(owned.begin(), owned.end(), p);
+    if (it != owned.end()) owned.erase(it);
+    if (alloc.release)
+      alloc.release(p, (void*)stream, alloc.ctx);
+    else
+      cudaFree(p);
+  }
+  int nleaf() const { return (int)leaf.size(); }
+  double dx(int d, int level) const {
+    return (cfg.xmax[d] - cfg.xmin[d]) / (double)(((int64_t)nb[d] * nx[d]) << level);
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------- tree logic
+
+bool overlaps_static(const ph_mesh* m, const Leaf& l) {
+  if (!m->cfg.static_region) return false;
+  for (int d = 0; d < 3; ++d) {
+    const double w = (m->cfg.xmax[d] - m->cfg.xmin[d]) / (double)((int64_t)m->nb[d] << l.level);
+    const double lo = m->cfg.xmin[d] + (double)l.lx[d] * w;
+    const double hi = m->cfg.xmin[d] + (double)(l.lx[d] + 1) * w;
+    if (!(lo < m->cfg.static_hi[d] && hi > m->cfg.static_lo[d])) return false;
+  }
+  return true;
+}
+
+int root_slot(const ph_mesh* m, int64_t a, int64_t b, int64_t c) {
+  return (int)((c * m->nb[1] + b) * m->nb[0] + a);
+}
+
+// Sort leaves in Z-order and rebuild the host lookup tables.
+void index_tree(ph_mesh* m) {
+  const int ml = m->cfg.max_level;
+  std::stable_sort(m->leaf.begin(), m->leaf.end(), [ml](const Leaf& a, const Leaf& b) {
+    const uint64_t ka = zkey(a, ml), kb = zkey(b, ml);
+    return ka != kb ? ka < kb : a.level < b.level;
+  });
+  const size_t nroot = (size_t)m->nb[0] * m->nb[1] * m->nb[2];
+  m->root.assign(nroot, -1);
+  m->kids.assign(nroot * 8, -1);
+  for (int b = 0; b < m->nleaf(); ++b) {
+    const Leaf& l = m->leaf[b];
+    if (l.level == 0) {
+      m->root[root_slot(m, l.lx[0], l.lx[1], l.lx[2])] = b;
+    } else {
+      const int s = root_slot(m, l.lx[0] >> 1, l.lx[1] >> 1, l.lx[2] >> 1);
+      m->kids[8 * s + (l.lx[0] & 1) + 2 * (l.lx[1] & 1) + 4 * (l.lx[2] & 1)] = b;
+    }
+  }
+}
+
+// New leaf list from flags: +1 splits a level-0 leaf; a complete set of 8
+// level-1 siblings all flagged -1 (old enough when check_age, none pinned by
+// the static region) merges.  Returns false if nothing changes.
+bool next_tree(const ph_mesh* m, const std::vector<int8_t>& flags, bool check_age,
+               std::vector<Leaf>& out) {
+  out.clear();
+  std::vector<char> keep(m->leaf.size(), 1);
+  bool changed = false;
+  for (size_t b = 0; b < m->leaf.size(); ++b) {
+    const Leaf& l = m->leaf[b];
+    if (flags[b] == 1 && l.level == 0 && m->cfg.max_level >= 1) {
+      keep[b] = 0;
+      changed = true;
+      for (int c = 0; c < 8; ++c)
+        out.push_back(Leaf{1, {2 * l.lx[0] + (c & 1), 2 * l.lx[1] + ((c >> 1) & 1),
+                               2 * l.lx[2] + ((c >> 2) & 1)}, 0});
+    }
+  }
+  for (size_t s = 0; s < m->root.size(); ++s) {
+    if (m->root[s] >= 0) continue;
+    bool merge = true;
+    for (int c = 0; c < 8 && merge; ++c) {
+      const int b = m->kids[8 * s + c];
+      if (b < 0 || flags[b] != -1) merge = false;
+      else if (check_age && m->leaf[b].age < m->cfg.derefine_count) merge = false;
+      else if (overlaps_static(m, m->leaf[b])) merge = false;
+    }
+    if (!merge) continue;
+    changed = true;
+    for (int c = 0; c < 8; ++c) keep[m->kids[8 * s + c]] = 0;
+    const Leaf& k0 = m->leaf[m->kids[8 * s]];
+    out.push_back(Leaf{0, {k0.lx[0] >> 1, k0.lx[1] >> 1, k0.lx[2] >> 1}, 0});
+  }
+  if (!changed) return false;
+  for (size_t b = 0; b < m->leaf.size(); ++b)
+    if (keep[b]) out.push_back(m->leaf[b]);
+  return true;
+}
+
+// ---------------------------------------------------------------- device tables
+
+void free_tables(ph_mesh* m) {
+  void** ptrs[] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_root, (void**)&m->d_kids,
+                   (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
+                   (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
+                   (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
+                   (void**)&m->d_fcf};
+  for (void** p : ptrs) {
+    m->dfree(*p);
+    *p = nullptr;
+  }
+}
+
+template <class V>
+int upload(ph_mesh* m, V** dst, const std::vector<V>& src) {
+  *dst = (V*)m->dalloc(sizeof(V) * std::max<size_t>(src.size(), 1));
+  if (!*dst) return fail(PH_ERR_OOM, "device allocation failed (tables)");
+  if (!src.empty())
+    PH_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(V) * src.size(), cudaMemcpyHostToDevice,
+                            m->stream));
+  return PH_OK;
+}
+
+// Build and upload every per-leaf table for the current tree.
+int build_tables(ph_mesh* m) {
+  free_tables(m);
+  const int n = m->nleaf();
+  std::vector<int8_t> level(n);
+  std::vector<int> leaf_id(4 * n), nbr(27 * n, -1);
+  for (int b = 0; b < n; ++b) {
+    const Leaf& l = m->leaf[b];
+    level[b] = (int8_t)l.level;
+    leaf_id[4 * b] = l.level;
+    for (int d = 0; d < 3; ++d) leaf_id[4 * b + 1 + d] = (int)l.lx[d];
+    if (!m->two_level) {
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int64_t a = (l.lx[0] + ox + m->nb[0]) % m->nb[0];
+            const int64_t bb = (l.lx[1] + oy + m->nb[1]) % m->nb[1];
+            const int64_t c = (l.lx[2] + oz + m->nb[2]) % m->nb[2];
+            nbr[27 * b + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = m->root[root_slot(m, a, bb, c)];
+          }
+    }
+  }
+  int rc;
+  if ((rc = upload(m, &m->d_level, level))) return rc;
+  if ((rc = upload(m, &m->d_leaf_id, leaf_id))) return rc;
+  if ((rc = upload(m, &m->d_nbr, nbr))) return rc;
+  if ((rc = upload(m, &m->d_root, m->root))) return rc;
+  if ((rc = upload(m, &m->d_kids, m->kids))) return rc;
+  m->d_partial = (double*)m->dalloc(sizeof(double) * 5 * std::max(n, 1));
+  m->d_mb = (double*)m->dalloc(sizeof(double) * std::max(n, 1));
+  if (!m->d_partial || !m->d_mb) return fail(PH_ERR_OOM, "device allocation failed (tables)");
+
+  // flux-correction records: one per (level-0 leaf, face) whose neighbour is refined
+  m->nrec = 0;
+  m->ncorr = 0;
+  if (m->two_level) {
+    std::vector<int> face_rec(6 * n, -1), fine_off(12 * n, 0), corr_leaf, rec_beg, rec_face;
+    for (int b = 0; b < n; ++b) {
+      const Leaf& l = m->leaf[b];
+      if (l.level != 0) continue;
+      bool any = false;
+      for (int d = 0; d < 3; ++d)
+        for (int side = 0; side < 2; ++side) {
+          int64_t o[3] = {l.lx[0], l.lx[1], l.lx[2]};
+          o[d] = (o[d] + (side ? 1 : -1) + m->nb[d]) % m->nb[d];
+          const int s = root_slot(m, o[0], o[1], o[2]);
+          if (m->root[s] >= 0) continue;
+          if (!any) {
+            corr_leaf.push_back(b);
+            rec_beg.push_back(m->nrec);
+            any = true;
+          }
+          const int rec = m->nrec++;
+          const int face = 2 * d + side;
+          face_rec[6 * b + face] = rec;
+          rec_face.push_back(face);
+          // the 4 children of slot s adjacent to this face, on their opposite face
+          const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          for (int c = 0; c < 8; ++c) {
+            const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+            if (cb[d] != (side ? 0 : 1)) continue;
+            const int kid = m->kids[8 * s + c];
+            const int kface = 2 * d + (1 - side);
+            face_rec[6 * kid + kface] = rec;
+            fine_off[12 * kid + 2 * kface] = cb[t1];
+            fine_off[12 * kid + 2 * kface + 1] = cb[t2];
+          }
+        }
+    }
+    rec_beg.push_back(m->nrec);
+    m->ncorr = (int)corr_leaf.size();
+    if ((rc = upload(m, &m->d_face_rec, face_rec))) return rc;
+    if ((rc = upload(m, &m->d_fine_off, fine_off))) return rc;
+    if ((rc = upload(m, &m->d_corr_leaf, corr_leaf))) return rc;
+    if ((rc = upload(m, &m->d_rec_beg, rec_beg))) return rc;
+    if ((rc = upload(m, &m->d_rec_face, rec_face))) return rc;
+    const int nmax = std::max(m->nx[0], std::max(m->nx[1], m->nx[2]));
+    const size_t face_elems = (size_t)5 * nmax * nmax;
+    m->d_fcc = m->dalloc(m->esize * face_elems * std::max(m->nrec, 1));
+    m->d_fcf = m->dalloc(m->esize * face_elems * 4 * std::max(m->nrec, 1));
+    if (!m->d_fcc || !m->d_fcf) return fail(PH_ERR_OOM, "device allocation failed (flux records)");
+  }
+  return PH_OK;
+}
+
+int ensure_pools(ph_mesh* m, int n) {
+  if ((size_t)n <= m->pool_cap && m->U0) return PH_OK;
+  m->dfree(m->U0);
+  m->dfree(m->U1);
+  m->U0 = m->U1 = nullptr;
+  const size_t bytes = m->esize * m->block_elems * (size_t)std::max(n, 1);
+  m->U0 = m->dalloc(bytes);
+  m->U1 = m->dalloc(bytes);
+  if (!m->U0 || !m->U1) return fail(PH_ERR_OOM, "device allocation failed (state pools)");
+  PH_CUDA(cudaMemsetAsync(m->U0, 0, bytes, m->stream));
+  PH_CUDA(cudaMemsetAsync(m->U1, 0, bytes, m->stream));
+  m->pool_cap = (size_t)std::max(n, 1);
+  return PH_OK;
+}
+
+int ensure_staging(ph_mesh* m, size_t bytes) {
+  if (bytes <= m->staging_bytes) return PH_OK;
+  m->dfree(m->staging);
+  m->staging = m->dalloc(bytes);
+  if (!m->staging) {
+    m->staging_bytes = 0;
+    return fail(PH_ERR_OOM, "device allocation failed (staging)");
+  }
+  m->staging_bytes = bytes;
+  return PH_OK;
+}
+
+ph::TreeView tree_view(const ph_mesh* m) {
+  ph::TreeView tv;
+  tv.root = m->d_root;
+  tv.kids = m->d_kids;
+  for (int d = 0; d < 3; ++d) {
+    tv.nb[d] = m->nb[d];
+    tv.nx[d] = m->nx[d];
+    tv.S[d] = m->S[d];
+  }
+  return tv;
+}
+
+template <class T>
+ph::Phys<T> phys(const ph_mesh* m) {
+  ph::Phys<T> P;
+  P.gamma = (T)m->cfg.gamma;
+  P.gm1 = (T)(m->cfg.gamma - 1.0);
+  P.igm1 = (T)(1.0 / (m->cfg.gamma - 1.0));
+  P.dfloor = (T)m->cfg.dfloor;
+  P.pfloor = (T)m->cfg.pfloor;
+  return P;
+}
+
+void inv_dx(const ph_mesh* m, double idx[2][3]) {
+  for (int l = 0; l < 2; ++l)
+    for (int d = 0; d < 3; ++d) idx[l][d] = 1.0 / m->dx(d, l);
+}
+
+template <class T>
+int fill_ghosts_t(ph_mesh* m, T* U) {
+  if (m->two_level) {
+    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->nleaf(), m->stream));
+  } else {
+    PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream));
+  }
+  return PH_OK;
+}
+
+template <class T>
+ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
+  ph::StageArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.Uin = (const T*)(stage == 1 ? m->U0 : m->U1);
+  a.U0 = (const T*)m->U0;
+  a.Uout = (T*)(stage == 1 ? m->U1 : m->U0);
+  a.level = m->d_level;
+  inv_dx(m, a.idx);
+  for (int d = 0; d < 3; ++d) {
+    a.nx[d] = m->nx[d];
+    a.S[d] = m->S[d];
+  }
+  a.ntile[0] = (m->nx[0] + m->tile[0] - 1) / m->tile[0];
+  a.ntile[1] = (m->nx[1] + m->tile[1] - 1) / m->tile[1];
+  a.ntile[2] = (m->nx[2] + m->tile[2] - 1) / m->tile[2];
+  a.KC = m->tile[2];
+  a.nleaf = m->nleaf();
+  a.stage = stage;
+  a.want_rate = (stage == 2 && !m->two_level) ? 1 : 0;
+  a.P = phys<T>(m);
+  a.sc = m->sc;
+  if (m->two_level && m->nrec > 0) {
+    a.face_rec = m->d_face_rec;
+    a.fc_coarse = (T*)m->d_fcc;
+    a.fc_fine = (T*)m->d_fcf;
+    a.fine_off = m->d_fine_off;
+  }
+  return a;
+}
+
+// New dt from the current state (K5 + bookkeeping), without committing a cycle.
+template <class T>
+int refresh_dt_t(ph_mesh* m) {
+  double idx[2][3];
+  inv_dx(m, idx);
+  PH_CUDA(ph::launch_rate<T>((const T*)m->U0, m->d_level, idx, m->nx, m->nleaf(), phys<T>(m), m->sc,
+                             m->stream));
+  PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 2, m->stream));
+  return PH_OK;
+}
+
+// Enqueue one uniform-mesh cycle: 5 launches.
+template <class T>
+int enqueue_uniform_cycle(ph_mesh* m, cudaStream_t s) {
+  const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
+  PH_CUDA(ph::launch_stage<T>(a1, m->tile[0], m->tile[1], s));
+  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s));
+  const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
+  PH_CUDA(ph::launch_stage<T>(a2, m->tile[0], m->tile[1], s));
+  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s));
+  PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, s));
+  return PH_OK;
+}
+
+void drop_graph(ph_mesh* m) {
+  if (m->gexec) {
+    cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+  }
+}
+
+template <class T>
+int capture_graph(ph_mesh* m) {
+  drop_graph(m);
+  PH_CUDA(cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_uniform_cycle<T>(m, m->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(m->cap, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&m->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    m->gexec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return PH_OK;
+}
+
+template <class T>
+int remesh_t(ph_mesh* m, std::vector<Leaf>& nl);
+
+// One two-level cycle (host-driven; flux correction after each stage).
+template <class T>
+int two_level_cycle(ph_mesh* m) {
+  int rc;
+  if ((rc = refresh_dt_t<T>(m))) return rc;
+  double idx[2][3];
+  inv_dx(m, idx);
+  for (int stage = 1; stage <= 2; ++stage) {
+    const ph::StageArgs<T> a = stage_args<T>(m, stage);
+    PH_CUDA(ph::launch_stage<T>(a, m->tile[0], m->tile[1], m->stream));
+    T* out = (T*)(stage == 1 ? m->U1 : m->U0);
+    PH_CUDA(ph::launch_flux_correct<T>(out, m->d_corr_leaf, m->d_rec_beg, m->ncorr, m->d_rec_face,
+                                       (const T*)m->d_fcc, (const T*)m->d_fcf, m->nx, idx[0],
+                                       stage == 1 ? 1.0 : 0.5, m->sc, m->stream));
+    if ((rc = fill_ghosts_t<T>(m, out))) return rc;
+  }
+  PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 1, m->stream));
+  for (auto& l : m->leaf) l.age += 1;
+  if (m->cfg.adaptive) {
+    std::vector<int8_t> flags;
+    std::vector<double> mb;
+    PH_CUDA(ph::launch_indicator<T>((const T*)m->U0, m->nx, m->nleaf(), m->d_mb, m->stream));
+    mb.resize(m->nleaf());
+    PH_CUDA(cudaMemcpyAsync(mb.data(), m->d_mb, sizeof(double) * mb.size(), cudaMemcpyDeviceToHost,
+                            m->stream));
+    PH_CUDA(cudaStreamSynchronize(m->stream));
+    flags.assign(m->nleaf(), 0);
+    for (int b = 0; b < m->nleaf(); ++b) {
+      const Leaf& l = m->leaf[b];
+      if (mb[b] > m->cfg.refine_tol && l.level < m->cfg.max_level)
+        flags[b] = 1;
+      else if (mb[b] < m->cfg.derefine_tol && l.level > 0 && !overlaps_static(m, l))
+        flags[b] = -1;
+    }
+    std::vector<Leaf> nl;
+    if (next_tree(m, flags, true, nl))
+      if ((rc = remesh_t<T>(m, nl))) return rc;
+  }
+  return PH_OK;
+}
+
+// Replace the tree by `nl` and move the data: each new leaf's interior is the
+// old mesh's composite field (prolongation for new children, restriction for
+// merged parents, copy otherwise), then ghosts are refilled.
+template <class T>
+int remesh_t(ph_mesh* m, std::vector<Leaf>& nl) {
+  int rc;
+  std::vector<Leaf> old = m->leaf;
+  m->leaf = nl;
+  index_tree(m);  // sorts the new leaves; host tables now describe the new tree
+  const int nnew = m->nleaf();
+  std::vector<int> leaf_id(4 * nnew);
+  for (int b = 0; b < nnew; ++b) {
+    leaf_id[4 * b] = m->leaf[b].level;
+    for (int d = 0; d < 3; ++d) leaf_id[4 * b + 1 + d] = (int)m->leaf[b].lx[d];
+  }
+  // the old device tables and pool stay valid until the copy is enqueued
+  ph::TreeView old_tv = tree_view(m);
+  int* d_new_id = nullptr;
+  if ((rc = upload(m, &d_new_id, leaf_id))) return rc;
+  const size_t bytes = m->esize * m->block_elems * (size_t)std::max(nnew, 1);
+  void* U0n = m->dalloc(bytes);
+  void* U1n = m->dalloc(bytes);
+  if (!U0n || !U1n) return fail(PH_ERR_OOM, "device allocation failed (remesh)");
+  PH_CUDA(cudaMemsetAsync(U0n, 0, bytes, m->stream));
+  PH_CUDA(cudaMemsetAsync(U1n, 0, bytes, m->stream));
+  PH_CUDA(ph::launch_remesh<T>((T*)U0n, d_new_id, nnew, (const T*)m->U0, old_tv, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  m->dfree(d_new_id);
+  m->dfree(m->U0);
+  m->dfree(m->U1);
+  m->U0 = U0n;
+  m->U1 = U1n;
+  m->pool_cap = (size_t)std::max(nnew, 1);
+  (void)old;
+  if ((rc = build_tables(m))) return rc;
+  if ((rc = fill_ghosts_t<T>(m, (T*)m->U0))) return rc;
+  drop_graph(m);
+  return PH_OK;
+}
+
+template <class T>
+int step_t(ph_mesh* m, int n) {
+  int rc;
+  if (m->two_level) {
+    for (int c = 0; c < n; ++c)
+      if ((rc = two_level_cycle<T>(m))) return rc;
+    return PH_OK;
+  }
+  if (!m->gexec)
+    if ((rc = capture_graph<T>(m))) return rc;
+  for (int c = 0; c < n; ++c) PH_CUDA(cudaGraphLaunch(m->gexec, m->stream));
+  return PH_OK;
+}
+
+template <class T>
+int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
+  cudaEvent_t ev[6];
+  for (int e = 0; e < 6; ++e) PH_CUDA(cudaEventCreate(&ev[e]));
+  double acc[5] = {0, 0, 0, 0, 0};
+  int rc = PH_OK;
+  for (int c = 0; c < n && !rc; ++c) {
+    const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
+    const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
+    cudaError_t e = cudaEventRecord(ev[0], m->stream);
+    if (!e) e = ph::launch_stage<T>(a1, m->tile[0], m->tile[1], m->stream);
+    if (!e) e = cudaEventRecord(ev[1], m->stream);
+    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream);
+    if (!e) e = cudaEventRecord(ev[2], m->stream);
+    if (!e) e = ph::launch_stage<T>(a2, m->tile[0], m->tile[1], m->stream);
+    if (!e) e = cudaEventRecord(ev[3], m->stream);
+    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream);
+    if (!e) e = cudaEventRecord(ev[4], m->stream);
+    if (!e) e = ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream);
+    if (!e) e = cudaEventRecord(ev[5], m->stream);
+    if (!e) e = cudaEventSynchronize(ev[5]);
+    for (int s = 0; s < 5 && !e; ++s) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[s], ev[s + 1]);
+      acc[s] += t;
+    }
+    if (e) rc = cuda_fail(e, "profile_cycles");
+  }
+  for (int e = 0; e < 6; ++e) cudaEventDestroy(ev[e]);
+  for (int s = 0; s < nslots && s < 5; ++s) ms[s] = acc[s];
+  return rc;
+}
+
+template <class T>
+int set_state_t(ph_mesh* m, const void* U, int on_device) {
+  int rc;
+  const size_t count = (size_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
+  T* packed;
+  if (on_device) {
+    packed = (T*)U;
+  } else {
+    if ((rc = ensure_staging(m, count * sizeof(T)))) return rc;
+    packed = (T*)m->staging;
+    PH_CUDA(cudaMemcpyAsync(packed, U, count * sizeof(T), cudaMemcpyHostToDevice, m->stream));
+  }
+  PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 0, m->stream));
+  if ((rc = fill_ghosts_t<T>(m, (T*)m->U0))) return rc;
+  ph::DevScalars zero;
+  std::memset(&zero, 0, sizeof(zero));
+  PH_CUDA(cudaMemcpyAsync(m->sc, &zero, sizeof(zero), cudaMemcpyHostToDevice, m->stream));
+  if ((rc = refresh_dt_t<T>(m))) return rc;
+  // the first dt is reported as the "last" dt until a cycle runs
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  ph::DevScalars hs;
+  PH_CUDA(cudaMemcpy(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost));
+  hs.dt_last = hs.dt_next;
+  PH_CUDA(cudaMemcpy(m->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice));
+  m->state_set = true;
+  return PH_OK;
+}
+
+template <class T>
+int get_state_t(ph_mesh* m, void* U, int on_device) {
+  int rc;
+  const size_t count = (size_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
+  T* packed;
+  if (on_device) {
+    packed = (T*)U;
+  } else {
+    if ((rc = ensure_staging(m, count * sizeof(T)))) return rc;
+    packed = (T*)m->staging;
+  }
+  PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 1, m->stream));
+  if (!on_device)
+    PH_CUDA(cudaMemcpyAsync(U, packed, count * sizeof(T), cudaMemcpyDeviceToHost, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  return PH_OK;
+}
+
+template <class T>
+int totals_t(ph_mesh* m, double out[5]) {
+  double vol[2];
+  for (int l = 0; l < 2; ++l) vol[l] = m->dx(0, l) * m->dx(1, l) * m->dx(2, l);
+  PH_CUDA(ph::launch_totals<T>((const T*)m->U0, m->d_level, vol, m->nx, m->nleaf(), m->d_partial,
+                               m->d_totals, m->stream));
+  PH_CUDA(cudaMemcpyAsync(out, m->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  return PH_OK;
+}
+
+template <class T>
+int tag_t(ph_mesh* m, int8_t* flags, double* mb) {
+  PH_CUDA(ph::launch_indicator<T>((const T*)m->U0, m->nx, m->nleaf(), m->d_mb, m->stream));
+  std::vector<double> h(m->nleaf());
+  PH_CUDA(cudaMemcpyAsync(h.data(), m->d_mb, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                          m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  for (int b = 0; b < m->nleaf(); ++b) {
+    const Leaf& l = m->leaf[b];
+    int8_t f = 0;
+    if (h[b] > m->cfg.refine_tol && l.level < m->cfg.max_level)
+      f = 1;
+    else if (h[b] < m->cfg.derefine_tol && l.level > 0 && !overlaps_static(m, l))
+      f = -1;
+    if (flags) flags[b] = f;
+    if (mb) mb[b] = h[b];
+  }
+  return PH_OK;
+}
+
+#define DISPATCH(m, fn, ...) \
+  ((m)->cfg.precision == PH_FP32 ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
+
+bool valid_tile(const ph_config* c, const int t[3]) {
+  return ph::stage_tile_supported(t[0], t[1]) && t[2] >= 1 && t[2] <= c->nx[2];
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+int ph_set_allocator(ph_alloc_fn alloc, ph_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(PH_ERR_INVALID, "ph_set_allocator: give both functions or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.release = release;
+  g_alloc.ctx = ctx;
+  return PH_OK;
+}
+
+const char* ph_last_error(void) { return g_err.c_str(); }
+
+int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
+  if (!cfg || !out) return fail(PH_ERR_INVALID, "ph_create: null argument");
+  *out = nullptr;
+  for (int d = 0; d < 3; ++d) {
+    if (cfg->nx[d] < 2 * ph::NG) return fail(PH_ERR_INVALID, "ph_create: nx must be >= 4");
+    if (cfg->nb[d] < 1) return fail(PH_ERR_INVALID, "ph_create: nb must be >= 1");
+    if (!(cfg->xmax[d] > cfg->xmin[d])) return fail(PH_ERR_INVALID, "ph_create: empty domain");
+  }
+  if (cfg->max_level < 0 || cfg->max_level > 1)
+    return fail(PH_ERR_INVALID, "ph_create: max_level must be 0 or 1");
+  if (cfg->max_level == 1 && (cfg->nx[0] % 2 || cfg->nx[1] % 2 || cfg->nx[2] % 2))
+    return fail(PH_ERR_INVALID, "ph_create: two-level meshes need even nx");
+  if (cfg->precision != PH_FP64 && cfg->precision != PH_FP32)
+    return fail(PH_ERR_INVALID, "ph_create: precision must be PH_FP64 or PH_FP32");
+  if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0))
+    return fail(PH_ERR_INVALID, "ph_create: need gamma > 1 and cfl > 0");
+  ph_mesh* m = new ph_mesh();
+  m->cfg = *cfg;
+  m->stream = (cudaStream_t)stream;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    m->alloc = g_alloc;
+  }
+  for (int d = 0; d < 3; ++d) {
+    m->nx[d] = cfg->nx[d];
+    m->nb[d] = cfg->nb[d];
+    m->S[d] = cfg->nx[d] + 2 * ph::NG;
+  }
+  m->esize = cfg->precision == PH_FP32 ? 4 : 8;
+  m->block_elems = (size_t)5 * m->S[0] * m->S[1] * m->S[2];
+  m->two_level = cfg->max_level >= 1;
+  int t[3] = {cfg->tile[0], cfg->tile[1], cfg->tile[2]};
+  if (t[0] == 0 && t[1] == 0 && t[2] == 0) {
+    t[0] = cfg->nx[0] >= 16 ? 16 : 8;
+    t[1] = (cfg->nx[1] >= 16 && t[0] == 16) ? 16 : 8;
+    t[2] = cfg->nx[2];
+  }
+  if (!valid_tile(cfg, t)) {
+    delete m;
+    return fail(PH_ERR_INVALID, "ph_create: unsupported tile");
+  }
+  for (int d = 0; d < 3; ++d) m->tile[d] = t[d];
+  cudaError_t e = ph::configure_stage_kernels();
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "configure_stage_kernels");
+  }
+  e = cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaStreamCreateWithFlags");
+  }
+  // root grid, then static refinement (Sec. 3.7) before any data exists
+  for (int64_t k = 0; k < cfg->nb[2]; ++k)
+    for (int64_t j = 0; j < cfg->nb[1]; ++j)
+      for (int64_t i = 0; i < cfg->nb[0]; ++i) m->leaf.push_back(Leaf{0, {i, j, k}, 0});
+  index_tree(m);
+  if (m->two_level && cfg->static_region) {
+    std::vector<int8_t> flags(m->nleaf(), 0);
+    for (int b = 0; b < m->nleaf(); ++b)
+      if (overlaps_static(m, m->leaf[b])) flags[b] = 1;
+    std::vector<Leaf> nl;
+    if (next_tree(m, flags, false, nl)) {
+      m->leaf = nl;
+      index_tree(m);
+    }
+  }
+  int rc = PH_OK;
+  m->sc = (ph::DevScalars*)m->dalloc(sizeof(ph::DevScalars));
+  m->d_totals = (double*)m->dalloc(8 * sizeof(double));
+  if (!m->sc || !m->d_totals) rc = fail(PH_ERR_OOM, "device allocation failed");
+  if (!rc) rc = ensure_pools(m, m->nleaf());
+  if (!rc) rc = build_tables(m);
+  if (!rc) {
+    e = cudaMemsetAsync(m->sc, 0, sizeof(ph::DevScalars), m->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (!rc) {
+    e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+  }
+  if (rc) {
+    ph_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return PH_OK;
+}
+
+int ph_destroy(ph_mesh* m) {
+  if (!m) return PH_OK;
+  cudaStreamSynchronize(m->stream);
+  drop_graph(m);
+  std::vector<void*> all = m->owned;
+  for (void* p : all) m->dfree(p);
+  if (m->cap) cudaStreamDestroy(m->cap);
+  delete m;
+  return PH_OK;
+}
+
+int ph_num_blocks(const ph_mesh* m, int32_t* n) {
+  if (!m || !n) return fail(PH_ERR_INVALID, "ph_num_blocks: null argument");
+  *n = m->nleaf();
+  return PH_OK;
+}
+
+int ph_tree(const ph_mesh* m, int64_t* out, int32_t n) {
+  if (!m || !out) return fail(PH_ERR_INVALID, "ph_tree: null argument");
+  if (n < m->nleaf()) return fail(PH_ERR_INVALID, "ph_tree: output too small");
+  for (int b = 0; b < m->nleaf(); ++b) {
+    out[4 * b] = m->leaf[b].level;
+    for (int d = 0; d < 3; ++d) out[4 * b + 1 + d] = m->leaf[b].lx[d];
+  }
+  return PH_OK;
+}
+
+static int64_t interior_count(const ph_mesh* m) {
+  return (int64_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
+}
+
+int ph_set_state(ph_mesh* m, const void* U, int64_t count, int32_t on_device) {
+  if (!m || !U) return fail(PH_ERR_INVALID, "ph_set_state: null argument");
+  if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_set_state: count mismatch");
+  return DISPATCH(m, set_state_t, m, U, on_device);
+}
+
+int ph_get_state(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
+  if (!m || !U) return fail(PH_ERR_INVALID, "ph_get_state: null argument");
+  if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_get_state: count mismatch");
+  return DISPATCH(m, get_state_t, m, U, on_device);
+}
+
+int ph_get_full(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
+  if (!m || !U) return fail(PH_ERR_INVALID, "ph_get_full: null argument");
+  if (count != (int64_t)(m->nleaf() * m->block_elems))
+    return fail(PH_ERR_INVALID, "ph_get_full: count mismatch");
+  PH_CUDA(cudaMemcpyAsync(U, m->U0, count * m->esize,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  return PH_OK;
+}
+
+int ph_step(ph_mesh* m, int32_t ncycles) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_step: null mesh");
+  if (ncycles < 0) return fail(PH_ERR_INVALID, "ph_step: negative cycle count");
+  if (!m->state_set) return fail(PH_ERR_STATE, "ph_step: set the state first");
+  if (ncycles == 0) return PH_OK;
+  return DISPATCH(m, step_t, m, ncycles);
+}
+
+static int read_scalars(ph_mesh* m, ph::DevScalars* hs) {
+  PH_CUDA(cudaMemcpyAsync(hs, m->sc, sizeof(*hs), cudaMemcpyDeviceToHost, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  return PH_OK;
+}
+
+int ph_get_dt(ph_mesh* m, double* dt) {
+  if (!m || !dt) return fail(PH_ERR_INVALID, "ph_get_dt: null argument");
+  ph::DevScalars hs;
+  int rc = read_scalars(m, &hs);
+  if (rc) return rc;
+  *dt = hs.dt_last;
+  return PH_OK;
+}
+
+int ph_get_next_dt(ph_mesh* m, double* dt) {
+  if (!m || !dt) return fail(PH_ERR_INVALID, "ph_get_next_dt: null argument");
+  ph::DevScalars hs;
+  int rc = read_scalars(m, &hs);
+  if (rc) return rc;
+  *dt = hs.dt_next;
+  return PH_OK;
+}
+
+int ph_get_time(ph_mesh* m, double* time, int64_t* cycle) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_get_time: null mesh");
+  ph::DevScalars hs;
+  int rc = read_scalars(m, &hs);
+  if (rc) return rc;
+  if (time) *time = hs.time;
+  if (cycle) *cycle = hs.cycle;
+  return PH_OK;
+}
+
+int ph_totals(ph_mesh* m, double out[5]) {
+  if (!m || !out) return fail(PH_ERR_INVALID, "ph_totals: null argument");
+  return DISPATCH(m, totals_t, m, out);
+}
+
+int ph_tag(ph_mesh* m, int8_t* flags, double* indicator, int32_t n) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_tag: null mesh");
+  if (n < m->nleaf()) return fail(PH_ERR_INVALID, "ph_tag: output too small");
+  return DISPATCH(m, tag_t, m, flags, indicator);
+}
+
+int ph_refine_where(ph_mesh* m, const int8_t* flags, int32_t n, int32_t check_age,
+                    int32_t* changed) {
+  if (!m || !flags) return fail(PH_ERR_INVALID, "ph_refine_where: null argument");
+  if (n != m->nleaf()) return fail(PH_ERR_INVALID, "ph_refine_where: flag count mismatch");
+  if (!m->two_level) return fail(PH_ERR_INVALID, "ph_refine_where: mesh has max_level 0");
+  std::vector<int8_t> f(flags, flags + n);
+  std::vector<Leaf> nl;
+  const bool ch = next_tree(m, f, check_age != 0, nl);
+  if (changed) *changed = ch ? 1 : 0;
+  if (!ch) return PH_OK;
+  int rc = DISPATCH(m, remesh_t, m, nl);
+  if (rc) return rc;
+  if (m->state_set) {
+    rc = m->cfg.precision == PH_FP32 ? refresh_dt_t<float>(m) : refresh_dt_t<double>(m);
+  }
+  return rc;
+}
+
+int ph_refine_by_density(ph_mesh* m, int32_t* changed) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_refine_by_density: null mesh");
+  std::vector<int8_t> flags(m->nleaf());
+  int rc = ph_tag(m, flags.data(), nullptr, m->nleaf());
+  if (rc) return rc;
+  return ph_refine_where(m, flags.data(), m->nleaf(), 1, changed);
+}
+
+int ph_status(ph_mesh* m, int64_t* floor_hits, int32_t* nonfinite) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_status: null mesh");
+  ph::DevScalars hs;
+  int rc = read_scalars(m, &hs);
+  if (rc) return rc;
+  if (floor_hits) *floor_hits = (int64_t)hs.floor_hits;
+  if (nonfinite) *nonfinite = hs.nonfinite;
+  if (hs.error) return fail(PH_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (hs.floor_hits || hs.nonfinite)
+    return fail(PH_ERR_NONPHYSICAL, "floors applied or non-finite dt");
+  return PH_OK;
+}
+
+int ph_fill_ghosts(ph_mesh* m) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_fill_ghosts: null mesh");
+  int rc = m->cfg.precision == PH_FP32 ? fill_ghosts_t<float>(m, (float*)m->U0)
+                                       : fill_ghosts_t<double>(m, (double*)m->U0);
+  if (rc) return rc;
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  return PH_OK;
+}
+
+int ph_launches_per_cycle(const ph_mesh* m, int32_t* n) {
+  if (!m || !n) return fail(PH_ERR_INVALID, "ph_launches_per_cycle: null argument");
+  *n = m->two_level ? 0 : 5;
+  return PH_OK;
+}
+
+int ph_profile_cycles(ph_mesh* m, int32_t ncycles, double* ms_out, int32_t nslots) {
+  if (!m || !ms_out || nslots < 0 || nslots > 5 || ncycles < 0)
+    return fail(PH_ERR_INVALID, "ph_profile_cycles: bad argument");
+  if (m->two_level) return fail(PH_ERR_INVALID, "ph_profile_cycles: uniform meshes only");
+  if (!m->state_set) return fail(PH_ERR_STATE, "ph_profile_cycles: set the state first");
+  return DISPATCH(m, profile_t, m, ncycles, ms_out, nslots);
+}
+
+int ph_get_tile(const ph_mesh* m, int32_t tile[3]) {
+  if (!m || !tile) return fail(PH_ERR_INVALID, "ph_get_tile: null argument");
+  for (int d = 0; d < 3; ++d) tile[d] = m->tile[d];
+  return PH_OK;
+}
+
+}  // extern "C"

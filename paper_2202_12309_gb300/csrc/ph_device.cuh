@@ -1,0 +1,151 @@
+// ph_device.cuh -- device-side building blocks shared by the library's kernels.
+//
+// Pointwise physics of the Parthenon-hydro method (arXiv:2202.12309 Sec. 5.1:
+// ideal-gas Euler equations, piecewise-linear reconstruction, HLLE fluxes)
+// written for throughput on sm_103a: one reciprocal square root gives both
+// sqrt(rho) and 1/rho, Roe weights are formed once, and every division that
+// shares a denominator is a multiplication by one reciprocal.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ph {
+
+constexpr int NV = 5;   // conserved variables: rho, m1, m2, m3, E
+constexpr int NG = 2;   // ghost width: PLM needs two cells on each side
+
+// Device-resident scalars of one mesh.  The cycle's dt never leaves the GPU.
+struct DevScalars {
+  double dt_next;               // dt the next cycle uses
+  double dt_last;               // dt the last cycle used
+  double time;
+  long long cycle;
+  unsigned long long wmax_bits; // max over cells of (|v_d| + c)/dx_d, as bits (>= 0)
+  unsigned long long floor_hits;
+  int nonfinite;                // a non-finite dt was produced
+  int error;                    // bounded device wait gave up
+};
+
+template <class T>
+struct Phys {
+  T gamma, gm1, igm1, dfloor, pfloor;
+};
+
+// Round-to-nearest add/mul that the compiler may not fuse into an FMA: used
+// wherever results must be reproducible operation by operation
+// (restriction, prolongation).
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sq(double x) { return sqrt(x); }
+__device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+
+// Conserved -> primitive in place: (rho, m1, m2, m3, E) -> (rho, v1, v2, v3, p),
+// with density and pressure floors (each application counted).
+template <class T>
+__device__ __forceinline__ void cons_to_prim(T w[NV], const Phys<T>& P, unsigned& floors) {
+  T rho = w[0];
+  if (rho < P.dfloor) { rho = P.dfloor; ++floors; }
+  const T ir = T(1) / rho;
+  const T v1 = w[1] * ir, v2 = w[2] * ir, v3 = w[3] * ir;
+  T p = P.gm1 * (w[4] - T(0.5) * (w[1] * v1 + w[2] * v2 + w[3] * v3));
+  if (p < P.pfloor) { p = P.pfloor; ++floors; }
+  w[0] = rho;
+  w[1] = v1;
+  w[2] = v2;
+  w[3] = v3;
+  w[4] = p;
+}
+
+// van Leer (harmonic) limited slope of a cell from its two neighbours.
+template <class T>
+__device__ __forceinline__ T vanleer(T wm, T w0, T wp) {
+  const T dl = w0 - wm, dr = wp - w0, prod = dl * dr;
+  return prod > T(0) ? (T(2) * prod) / (dl + dr) : T(0);
+}
+
+// HLLE flux with Einfeldt's wave-speed bounds (Roe averages) through a face
+// whose normal is x_{DIR+1}; wl/wr are primitive states.
+template <class T, int DIR>
+__device__ __forceinline__ void hlle(const T wl[NV], const T wr[NV], const Phys<T>& P, T f[NV]) {
+  constexpr int IN = 1 + DIR;
+  const T rl = wl[0], pl = wl[4], rr = wr[0], pr = wr[4];
+  const T vnl = wl[IN], vnr = wr[IN];
+  const T el = pl * P.igm1 + T(0.5) * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  const T er = pr * P.igm1 + T(0.5) * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  const T ql = rsq(rl), qr = rsq(rr);
+  const T sl = rl * ql, sr = rr * qr;          // sqrt(rho)
+  const T irl = ql * ql, irr = qr * qr;        // 1/rho
+  const T cl = sq(P.gamma * pl * irl), cr = sq(P.gamma * pr * irr);
+  const T hl = (el + pl) * irl, hr = (er + pr) * irr;
+  const T isum = T(1) / (sl + sr);
+  const T wsl = sl * isum, wsr = sr * isum;    // Roe weights
+  const T u1 = wsl * wl[1] + wsr * wr[1];
+  const T u2 = wsl * wl[2] + wsr * wr[2];
+  const T u3 = wsl * wl[3] + wsr * wr[3];
+  const T hroe = wsl * hl + wsr * hr;
+  const T a2 = P.gm1 * (hroe - T(0.5) * (u1 * u1 + u2 * u2 + u3 * u3));
+  const T croe = sq(a2 > T(0) ? a2 : T(0));
+  const T un = (IN == 1) ? u1 : ((IN == 2) ? u2 : u3);
+  const T bp = fmax(T(0), fmax(vnr + cr, un + croe));
+  const T bm = fmin(T(0), fmin(vnl - cl, un - croe));
+  const T idb = T(1) / (bp - bm);
+  const T bpbm = bp * bm;
+  const T mfl = rl * vnl, mfr = rr * vnr;
+  f[0] = (bp * mfl - bm * mfr + bpbm * (rr - rl)) * idb;
+#pragma unroll
+  for (int a = 1; a <= 3; ++a) {
+    const T fl = mfl * wl[a] + (a == IN ? pl : T(0));
+    const T fr = mfr * wr[a] + (a == IN ? pr : T(0));
+    f[a] = (bp * fl - bm * fr + bpbm * (rr * wr[a] - rl * wl[a])) * idb;
+  }
+  f[4] = (bp * ((el + pl) * vnl) - bm * ((er + pr) * vnr) + bpbm * (er - el)) * idb;
+}
+
+// Largest signal speed over cell width of one primitive state:
+// max_d (|v_d| + c) / dx_d.  dt = cfl / (max over cells).
+template <class T>
+__device__ __forceinline__ T wave_rate(const T w[NV], const Phys<T>& P, T idx1, T idx2, T idx3) {
+  const T c = sq(P.gamma * w[4] / w[0]);
+  const T a = (fabs(w[1]) + c) * idx1;
+  const T b = (fabs(w[2]) + c) * idx2;
+  const T d = (fabs(w[3]) + c) * idx3;
+  T m = a;
+  if (!(b <= m)) m = b;   // NaN-propagating max
+  if (!(d <= m)) m = d;
+  return m;
+}
+
+// Block-wide NaN-propagating max of a non-negative double, then one atomic
+// max on its bit pattern (for non-negative doubles and NaN, the unsigned bit
+// order is the numeric order, NaN above +inf).
+__device__ __forceinline__ void block_max_to(unsigned long long* dst, double v, double* red) {
+  unsigned long long bits = __double_as_longlong(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = __longlong_as_double(bits);
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long b2 = lane < nwarp ? (unsigned long long)__double_as_longlong(red[lane]) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long ob = __shfl_xor_sync(0xffffffffu, b2, o);
+      b2 = ob > b2 ? ob : b2;
+    }
+    if (lane == 0 && b2 != 0ull) atomicMax(dst, b2);
+  }
+}
+
+}  // namespace ph

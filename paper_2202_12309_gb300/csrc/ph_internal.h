@@ -1,0 +1,81 @@
+// ph_internal.h -- host-side declarations shared by the library's translation
+// units (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ph_device.cuh"
+
+namespace ph {
+
+// Device view of a mesh's block tree, used by the ghost exchange and remesh
+// kernels to find the leaf covering any cell (Sec. 2.1: one leaf covers each
+// location).  root[s] is the level-0 leaf at root slot s, or -1 when that
+// slot is refined, in which case kids[8 s + c] are its children.
+struct TreeView {
+  const int* root;
+  const int* kids;
+  int nb[3];
+  int nx[3];
+  int S[3];
+};
+
+template <class T>
+struct StageArgs;
+
+// K3: fused stage over all leaves.  Returns the launch error.
+template <class T>
+cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s);
+template <class T>
+size_t stage_smem_bytes(int TX, int TY);
+bool stage_tile_supported(int TX, int TY);
+cudaError_t configure_stage_kernels();
+
+// K1 (uniform mesh): every ghost cell of every leaf copied from the
+// same-level neighbour given by nbr[27 * leaf + region].
+template <class T>
+cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s);
+
+// K1 (two-level mesh): every ghost cell of every leaf takes the composite
+// field of the mesh (copy / restriction / prolongation), one launch.
+template <class T>
+cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
+                                   cudaStream_t s);
+
+// K7: interior of every new leaf from the old mesh's composite field.
+template <class T>
+cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uold,
+                          const TreeView& old_tv, cudaStream_t s);
+
+// K5: max over interior cells of (|v_d|+c)/dx_d into sc->wmax_bits.
+template <class T>
+cudaError_t launch_rate(const T* U, const int8_t* level, const double idx[2][3], const int nx[3],
+                        int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s);
+
+// dt bookkeeping: mode bit 1 commits the cycle (time += dt, cycle++),
+// bit 2 computes the next dt = cfl / wmax and clears wmax.
+cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s);
+
+// Interior <-> padded copies.  dir 0: packed -> padded, 1: padded -> packed.
+template <class T>
+cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s);
+
+// Conserved totals: per-leaf FP64 sums into partial[nleaf*5], then one
+// ordered compensated sum into out[5].
+template <class T>
+cudaError_t launch_totals(const T* U, const int8_t* level, const double vol[2], const int nx[3],
+                          int nleaf, double* partial, double* out, cudaStream_t s);
+
+// K6: refinement indicator per leaf (FP64).
+template <class T>
+cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s);
+
+// K4: flux correction at fine-coarse faces, applied after the stage update.
+// One CTA per coarse leaf corr_leaf[c] with records rec_beg[c] .. rec_beg[c+1].
+template <class T>
+cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
+                                const int* rec_face, const T* fc_coarse, const T* fc_fine,
+                                const int nx[3], const double idx0[3], double beta,
+                                const DevScalars* sc, cudaStream_t s);
+
+}  // namespace ph

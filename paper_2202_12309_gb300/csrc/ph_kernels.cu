@@ -1,0 +1,544 @@
+// ph_kernels.cu -- mesh-level kernels: ghost exchange (K1), remesh data
+// movement (K7), signal-speed max for dt (K5), dt bookkeeping, refinement
+// indicator (K6), interior <-> padded copies and conserved totals.
+//
+// Ghost exchange (arXiv:2202.12309 Sec. 3.6, "fill-in-one"): the paper packs
+// every buffer of every block into one kernel, sends, and unpacks with
+// restriction/prolongation.  On one GPU there is nothing to send, so K1 is a
+// single pull: each ghost cell reads the data it needs straight from the
+// interior of the leaf that covers it.  It reads interior cells only and
+// writes ghost cells only, so one launch has no ordering hazard.
+#include "ph_internal.h"
+
+namespace ph {
+
+// --------------------------------------------------------------------------
+// Ghost-shell enumeration: the ghost cells of a padded block, flattened as
+// (A) the 4 x3-ghost planes, (B) the 4 x2-ghost rows of each interior plane,
+// (C) the 4 x1-ghost cells of each interior row.  Rows stay contiguous in x1.
+// --------------------------------------------------------------------------
+struct Shell {
+  int n1, n2, n3, S1, S2, nA, nB, nC;
+  __device__ __forceinline__ Shell(const int nx[3]) {
+    n1 = nx[0]; n2 = nx[1]; n3 = nx[2];
+    S1 = n1 + 2 * NG; S2 = n2 + 2 * NG;
+    nA = 4 * S2 * S1;
+    nB = n3 * 4 * S1;
+    nC = n3 * n2 * 4;
+  }
+  __device__ __forceinline__ int count() const { return nA + nB + nC; }
+  __device__ __forceinline__ void cell(int c, int& i, int& j, int& k) const {
+    if (c < nA) {
+      const int kk = c / (S2 * S1), r = c - kk * S2 * S1;
+      j = r / S1;
+      i = r - j * S1;
+      k = kk < 2 ? kk : n3 + kk;
+    } else if (c < nA + nB) {
+      c -= nA;
+      const int kq = c / (4 * S1), r = c - kq * 4 * S1;
+      const int jj = r / S1;
+      i = r - jj * S1;
+      k = kq + NG;
+      j = jj < 2 ? jj : n2 + jj;
+    } else {
+      c -= nA + nB;
+      const int kq = c / (4 * n2), r = c - kq * 4 * n2;
+      const int jq = r >> 2, ii = r & 3;
+      k = kq + NG;
+      j = jq + NG;
+      i = ii < 2 ? ii : n1 + ii;
+    }
+  }
+};
+
+template <class T>
+__global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx) {
+  const int nxa[3] = {nx.x, nx.y, nx.z};
+  const Shell sh(nxa);
+  const int b = blockIdx.x;
+  const int S1 = sh.S1, S2 = sh.S2, S3 = nx.z + 2 * NG;
+  const size_t vs = (size_t)S1 * S2 * S3;
+  T* dstb = U + (size_t)b * NV * vs;
+  const int* nb = nbr + 27 * b;
+  const int total = sh.count();
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    int i, j, k;
+    sh.cell(c, i, j, k);
+    const int ox = i < NG ? -1 : (i >= NG + nx.x ? 1 : 0);
+    const int oy = j < NG ? -1 : (j >= NG + nx.y ? 1 : 0);
+    const int oz = k < NG ? -1 : (k >= NG + nx.z ? 1 : 0);
+    const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    const T* srcb = U + (size_t)src * NV * vs;
+    const size_t so = ((size_t)(k - oz * nx.z) * S2 + (j - oy * nx.y)) * S1 + (i - ox * nx.x);
+    const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dstb[v * vs + dofs] = srcb[v * vs + so];
+  }
+}
+
+template <class T>
+cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s) {
+  if (nleaf <= 0) return cudaSuccess;
+  ghost_uniform_kernel<T><<<nleaf, 256, 0, s>>>(U, nbr, make_int3(nx[0], nx[1], nx[2]));
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Composite field of a two-level mesh (Sec. 2.1 + Sec. 3.6).
+//   level-0 cell: the level-0 leaf's value, or the mean of its 8 children
+//                 (restriction; summed c3 outer, c1 inner, then x 1/8);
+//   level-1 cell: the level-1 leaf's value, or the coarse value plus
+//                 +-1/4 of the minmod-limited coarse differences in x1, x2,
+//                 x3 in that order (prolongation).
+// Every add/multiply is an unfused round-to-nearest operation so that the
+// result is reproducible operation by operation.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ long long wrapi(long long i, long long n) {
+  long long r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+template <class T>
+__device__ __forceinline__ void read_cell(const T* U, const TreeView& tv, int leaf, int li, int lj,
+                                          int lk, T out[NV]) {
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  const T* p = U + (size_t)leaf * NV * vs + ((size_t)(lk + NG) * tv.S[1] + (lj + NG)) * tv.S[0] + (li + NG);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = p[v * vs];
+}
+
+template <class T>
+__device__ void coarse_value(const T* U, const TreeView& tv, long long I, long long J, long long K,
+                             T out[NV]) {
+  const long long N1 = (long long)tv.nb[0] * tv.nx[0], N2 = (long long)tv.nb[1] * tv.nx[1],
+                  N3 = (long long)tv.nb[2] * tv.nx[2];
+  I = wrapi(I, N1);
+  J = wrapi(J, N2);
+  K = wrapi(K, N3);
+  const int r1 = (int)(I / tv.nx[0]), r2 = (int)(J / tv.nx[1]), r3 = (int)(K / tv.nx[2]);
+  const int s = (r3 * tv.nb[1] + r2) * tv.nb[0] + r1;
+  const int lf = tv.root[s];
+  if (lf >= 0) {
+    read_cell(U, tv, lf, (int)(I - (long long)r1 * tv.nx[0]), (int)(J - (long long)r2 * tv.nx[1]),
+              (int)(K - (long long)r3 * tv.nx[2]), out);
+    return;
+  }
+  T sum[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) sum[v] = T(0);
+  for (int c3 = 0; c3 < 2; ++c3)
+    for (int c2 = 0; c2 < 2; ++c2)
+      for (int c1 = 0; c1 < 2; ++c1) {
+        const long long fi = 2 * I + c1, fj = 2 * J + c2, fk = 2 * K + c3;
+        const int l1 = (int)(fi / tv.nx[0]), l2 = (int)(fj / tv.nx[1]), l3 = (int)(fk / tv.nx[2]);
+        const int kid = tv.kids[8 * s + (l1 & 1) + 2 * (l2 & 1) + 4 * (l3 & 1)];
+        T f[NV];
+        read_cell(U, tv, kid, (int)(fi - (long long)l1 * tv.nx[0]), (int)(fj - (long long)l2 * tv.nx[1]),
+                  (int)(fk - (long long)l3 * tv.nx[2]), f);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sum[v] = add_rn(sum[v], f[v]);
+      }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = mul_rn(T(0.125), sum[v]);
+}
+
+template <class T>
+__device__ __forceinline__ T minmod_dev(T a, T b) {
+  if (mul_rn(a, b) > T(0)) return fabs(a) < fabs(b) ? a : b;
+  return T(0);
+}
+
+template <class T>
+__device__ void fine_value(const T* U, const TreeView& tv, long long I, long long J, long long K,
+                           T out[NV]) {
+  const long long N1 = 2LL * tv.nb[0] * tv.nx[0], N2 = 2LL * tv.nb[1] * tv.nx[1],
+                  N3 = 2LL * tv.nb[2] * tv.nx[2];
+  I = wrapi(I, N1);
+  J = wrapi(J, N2);
+  K = wrapi(K, N3);
+  const int r1 = (int)((I >> 1) / tv.nx[0]), r2 = (int)((J >> 1) / tv.nx[1]),
+            r3 = (int)((K >> 1) / tv.nx[2]);
+  const int s = (r3 * tv.nb[1] + r2) * tv.nb[0] + r1;
+  if (tv.root[s] < 0) {
+    const int l1 = (int)(I / tv.nx[0]), l2 = (int)(J / tv.nx[1]), l3 = (int)(K / tv.nx[2]);
+    const int kid = tv.kids[8 * s + (l1 & 1) + 2 * (l2 & 1) + 4 * (l3 & 1)];
+    read_cell(U, tv, kid, (int)(I - (long long)l1 * tv.nx[0]), (int)(J - (long long)l2 * tv.nx[1]),
+              (int)(K - (long long)l3 * tv.nx[2]), out);
+    return;
+  }
+  const long long C[3] = {I >> 1, J >> 1, K >> 1};
+  const long long F[3] = {I, J, K};
+  T uc[NV], acc[NV];
+  coarse_value(U, tv, C[0], C[1], C[2], uc);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = uc[v];
+  for (int d = 0; d < 3; ++d) {
+    long long cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
+    cm[d] -= 1;
+    cp[d] += 1;
+    T um[NV], up[NV];
+    coarse_value(U, tv, cm[0], cm[1], cm[2], um);
+    coarse_value(U, tv, cp[0], cp[1], cp[2], up);
+    const T sg = (F[d] & 1) ? T(0.25) : T(-0.25);
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      acc[v] = add_rn(acc[v], mul_rn(sg, minmod_dev(sub_rn(uc[v], um[v]), sub_rn(up[v], uc[v]))));
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v] = acc[v];
+}
+
+template <class T>
+__global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id) {
+  const Shell sh(tv.nx);
+  const int b = blockIdx.x;
+  const int lev = leaf_id[4 * b];
+  const long long o1 = (long long)leaf_id[4 * b + 1] * tv.nx[0] - NG;
+  const long long o2 = (long long)leaf_id[4 * b + 2] * tv.nx[1] - NG;
+  const long long o3 = (long long)leaf_id[4 * b + 3] * tv.nx[2] - NG;
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  T* dst = U + (size_t)b * NV * vs;
+  const int total = sh.count();
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    int i, j, k;
+    sh.cell(c, i, j, k);
+    T val[NV];
+    if (lev == 0)
+      coarse_value(U, tv, o1 + i, o2 + j, o3 + k, val);
+    else
+      fine_value(U, tv, o1 + i, o2 + j, o3 + k, val);
+    const size_t d = ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * vs + d] = val[v];
+  }
+}
+
+template <class T>
+cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
+                                   cudaStream_t s) {
+  if (nleaf <= 0) return cudaSuccess;
+  ghost_composite_kernel<T><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+  return cudaGetLastError();
+}
+
+template <class T>
+__global__ void remesh_kernel(T* Unew, const int* __restrict__ leaf_id, const T* Uold,
+                              const TreeView tv) {
+  const int b = blockIdx.x;
+  const int lev = leaf_id[4 * b];
+  const int n1 = tv.nx[0], n2 = tv.nx[1], n3 = tv.nx[2];
+  const long long o1 = (long long)leaf_id[4 * b + 1] * n1;
+  const long long o2 = (long long)leaf_id[4 * b + 2] * n2;
+  const long long o3 = (long long)leaf_id[4 * b + 3] * n3;
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  T* dst = Unew + (size_t)b * NV * vs;
+  const int total = n1 * n2 * n3;
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    const int k = c / (n1 * n2), r = c - k * n1 * n2, j = r / n1, i = r - j * n1;
+    T val[NV];
+    if (lev == 0)
+      coarse_value(Uold, tv, o1 + i, o2 + j, o3 + k, val);
+    else
+      fine_value(Uold, tv, o1 + i, o2 + j, o3 + k, val);
+    const size_t d = ((size_t)(k + NG) * tv.S[1] + (j + NG)) * tv.S[0] + (i + NG);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * vs + d] = val[v];
+  }
+}
+
+template <class T>
+cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uold,
+                          const TreeView& old_tv, cudaStream_t s) {
+  if (nnew <= 0) return cudaSuccess;
+  remesh_kernel<T><<<nnew, 256, 0, s>>>(Unew, new_leaf_id, Uold, old_tv);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// K5: signal-speed max for the CFL dt (Sec. 3.9), from interior cells.
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level, double4 ia,
+                            double4 ib, int3 nx, Phys<T> P, DevScalars* sc) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
+  const size_t vs = (size_t)S1 * S2 * S3;
+  const T* Ub = U + (size_t)b * NV * vs;
+  const int lev = level ? (int)level[b] : 0;
+  const T i1 = (T)(lev ? ib.x : ia.x), i2 = (T)(lev ? ib.y : ia.y), i3 = (T)(lev ? ib.z : ia.z);
+  unsigned floors = 0;
+  double m = 0.0;
+  const int total = nx.x * nx.y * nx.z;
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
+    const size_t o = ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
+    T w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = Ub[v * vs + o];
+    cons_to_prim(w, P, floors);
+    const double r8 = (double)wave_rate(w, P, i1, i2, i3);
+    if (!(r8 <= m)) m = r8;
+  }
+  block_max_to(&sc->wmax_bits, m, red);
+  if (floors) atomicAdd(&sc->floor_hits, (unsigned long long)floors);
+}
+
+template <class T>
+cudaError_t launch_rate(const T* U, const int8_t* level, const double idx[2][3], const int nx[3],
+                        int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s) {
+  if (nleaf <= 0) return cudaSuccess;
+  rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, make_double4(idx[0][0], idx[0][1], idx[0][2], 0),
+                                        make_double4(idx[1][0], idx[1][1], idx[1][2], 0),
+                                        make_int3(nx[0], nx[1], nx[2]), P, sc);
+  return cudaGetLastError();
+}
+
+__global__ void advance_kernel(DevScalars* sc, double cfl, int mode) {
+  if (mode & 1) {
+    sc->dt_last = sc->dt_next;
+    sc->time += sc->dt_next;
+    sc->cycle += 1;
+  }
+  if (mode & 2) {
+    const double w = __longlong_as_double((long long)sc->wmax_bits);
+    const double dt = cfl / w;
+    sc->dt_next = dt;
+    if (!isfinite(dt) || !(dt > 0.0)) sc->nonfinite = 1;
+    sc->wmax_bits = 0ull;
+  }
+}
+
+cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s) {
+  advance_kernel<<<1, 1, 0, s>>>(sc, cfl, mode);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Interior <-> padded copies
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir) {
+  const int b = blockIdx.y;
+  const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
+  const size_t per = (size_t)NV * nx.x * nx.y * nx.z;
+  const size_t vs = (size_t)S1 * S2 * S3;
+  const int cells = nx.x * nx.y * nx.z;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int v = (int)(e / cells);
+    const int c = (int)(e - (size_t)v * cells);
+    const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
+    T* pp = padded + (size_t)b * NV * vs + v * vs + ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
+    T* qq = packed + (size_t)b * per + e;
+    if (dir == 0)
+      *pp = *qq;
+    else
+      *qq = *pp;
+  }
+}
+
+template <class T>
+cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s) {
+  if (nleaf <= 0) return cudaSuccess;
+  const size_t per = (size_t)NV * nx[0] * nx[1] * nx[2];
+  int gx = (int)((per + 255) / 256);
+  if (gx > 64) gx = 64;
+  pack_kernel<T><<<dim3(gx, nleaf), 256, 0, s>>>(padded, packed, make_int3(nx[0], nx[1], nx[2]), dir);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Conserved totals in FP64
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void totals_block_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
+                                    double2 vol, int3 nx, double* partial) {
+  __shared__ double red[NV][256];
+  const int b = blockIdx.x;
+  const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
+  const size_t vs = (size_t)S1 * S2 * S3;
+  const T* Ub = U + (size_t)b * NV * vs;
+  double acc[NV] = {0, 0, 0, 0, 0};
+  const int total = nx.x * nx.y * nx.z;
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
+    const size_t o = ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += (double)Ub[v * vs + o];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) red[v][threadIdx.x] = acc[v];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < NV) {
+    const double dv = (level && level[b]) ? vol.y : vol.x;
+    partial[(size_t)b * NV + threadIdx.x] = red[threadIdx.x][0] * dv;
+  }
+}
+
+__global__ void totals_final_kernel(const double* __restrict__ partial, int nleaf, double* out) {
+  const int v = threadIdx.x;
+  if (v >= NV) return;
+  double s = 0.0, comp = 0.0;  // Neumaier compensated sum over leaves in order
+  for (int b = 0; b < nleaf; ++b) {
+    const double x = partial[(size_t)b * NV + v];
+    const double t = s + x;
+    if (fabs(s) >= fabs(x))
+      comp += (s - t) + x;
+    else
+      comp += (x - t) + s;
+    s = t;
+  }
+  out[v] = s + comp;
+}
+
+template <class T>
+cudaError_t launch_totals(const T* U, const int8_t* level, const double vol[2], const int nx[3],
+                          int nleaf, double* partial, double* out, cudaStream_t s) {
+  if (nleaf > 0)
+    totals_block_kernel<T><<<nleaf, 256, 0, s>>>(U, level, make_double2(vol[0], vol[1]),
+                                                  make_int3(nx[0], nx[1], nx[2]), partial);
+  totals_final_kernel<<<1, 32, 0, s>>>(partial, nleaf, out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// K6: refinement indicator, max over interior cells and d of
+// |rho_{+e_d} - rho_{-e_d}| / (2 rho), in FP64 (IEEE division).
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void indicator_kernel(const T* __restrict__ U, int3 nx, double* mb) {
+  __shared__ unsigned long long red[32];
+  const int b = blockIdx.x;
+  const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
+  const T* r = U + (size_t)b * NV * S1 * S2 * S3;  // density is variable 0
+  double m = 0.0;
+  const int total = nx.x * nx.y * nx.z;
+  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+    const int k = c / (nx.x * nx.y), q = c - k * nx.x * nx.y, j = q / nx.x, i = q - j * nx.x;
+    const size_t o = ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
+    const double r0 = (double)r[o];
+    const double den = __dmul_rn(2.0, r0);
+    const double g1 = __ddiv_rn(fabs(__dsub_rn((double)r[o + 1], (double)r[o - 1])), den);
+    const double g2 = __ddiv_rn(fabs(__dsub_rn((double)r[o + S1], (double)r[o - S1])), den);
+    const double g3 = __ddiv_rn(
+        fabs(__dsub_rn((double)r[o + (size_t)S1 * S2], (double)r[o - (size_t)S1 * S2])), den);
+    if (g1 > m) m = g1;
+    if (g2 > m) m = g2;
+    if (g3 > m) m = g3;
+  }
+  unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = bits;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long best = 0ull;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) best = red[w] > best ? red[w] : best;
+    mb[b] = __longlong_as_double((long long)best);
+  }
+}
+
+template <class T>
+cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s) {
+  if (nleaf <= 0) return cudaSuccess;
+  indicator_kernel<T><<<nleaf, 256, 0, s>>>(U, make_int3(nx[0], nx[1], nx[2]), mb);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// K4: flux correction (Sec. 3.6).  A record is one face of one level-0 leaf
+// whose neighbour across the face is refined.  During the stage the coarse
+// leaf stored its own face flux Fc and the 4 fine leaves stored theirs; the
+// coarse cell next to the face is corrected by the difference between Fc and
+// the mean of the 4 fine fluxes over it, which equals replacing the flux
+// before the update:  U += beta dt (Fc - <Ff>) / dx  on a high face,
+//                     U -= beta dt (Fc - <Ff>) / dx  on a low face.
+// One CTA per corrected coarse leaf walks its records in order (faces x1-,
+// x1+, x2-, ...), so a cell on an edge of the block is corrected face by
+// face, deterministically and without atomics.
+// rec_face: 2*d + side (side 1 = high face).
+// --------------------------------------------------------------------------
+template <class T>
+__global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
+                                    const int* __restrict__ rec_beg,
+                                    const int* __restrict__ rec_face, const T* __restrict__ fcc,
+                                    const T* __restrict__ fcf, int3 nx, double3 idx0, double beta,
+                                    const DevScalars* sc) {
+  const int leaf = corr_leaf[blockIdx.x];
+  const int n[3] = {nx.x, nx.y, nx.z};
+  const int S[3] = {nx.x + 2 * NG, nx.y + 2 * NG, nx.z + 2 * NG};
+  const size_t vs = (size_t)S[0] * S[1] * S[2];
+  T* Ub = U + (size_t)leaf * NV * vs;
+  for (int r = rec_beg[blockIdx.x]; r < rec_beg[blockIdx.x + 1]; ++r) {
+    const int face = rec_face[r];
+    const int d = face >> 1, side = face & 1;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const int m1 = n[t1], m2 = n[t2];
+    const double id = d == 0 ? idx0.x : (d == 1 ? idx0.y : idx0.z);
+    const T coef = (T)(beta * sc->dt_next * id) * (side ? T(1) : T(-1));
+    const T* Fc = fcc + (size_t)r * NV * m1 * m2;
+    const T* Ff = fcf + (size_t)r * NV * 4 * m1 * m2;
+    for (int c = threadIdx.x; c < m1 * m2; c += blockDim.x) {
+      const int a2 = c / m1, a1 = c - a2 * m1;
+      int l[3];
+      l[d] = side ? n[d] - 1 : 0;
+      l[t1] = a1;
+      l[t2] = a2;
+      const size_t o = ((size_t)(l[2] + NG) * S[1] + (l[1] + NG)) * S[0] + (l[0] + NG);
+      const int w = 2 * m1;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T* f = Ff + (size_t)v * 4 * m1 * m2;
+        const T fmean = T(0.25) * (f[(2 * a2) * w + 2 * a1] + f[(2 * a2) * w + 2 * a1 + 1] +
+                                   f[(2 * a2 + 1) * w + 2 * a1] + f[(2 * a2 + 1) * w + 2 * a1 + 1]);
+        const T fc = Fc[(size_t)v * m1 * m2 + c];
+        Ub[v * vs + o] += coef * (fc - fmean);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
+                                const int* rec_face, const T* fc_coarse, const T* fc_fine,
+                                const int nx[3], const double idx0[3], double beta,
+                                const DevScalars* sc, cudaStream_t s) {
+  if (ncorr <= 0) return cudaSuccess;
+  flux_correct_kernel<T><<<ncorr, 256, 0, s>>>(U, corr_leaf, rec_beg, rec_face, fc_coarse, fc_fine,
+                                                make_int3(nx[0], nx[1], nx[2]),
+                                                make_double3(idx0[0], idx0[1], idx0[2]), beta, sc);
+  return cudaGetLastError();
+}
+
+// explicit instantiations
+#define PH_INST(T)                                                                              \
+  template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t); \
+  template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, int,          \
+                                                 cudaStream_t);                                 \
+  template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
+                                        cudaStream_t);                                          \
+  template cudaError_t launch_rate<T>(const T*, const int8_t*, const double[2][3], const int*, \
+                                      int, Phys<T>, DevScalars*, cudaStream_t);                 \
+  template cudaError_t launch_pack<T>(T*, T*, const int*, int, int, cudaStream_t);              \
+  template cudaError_t launch_totals<T>(const T*, const int8_t*, const double*, const int*, int, \
+                                        double*, double*, cudaStream_t);                        \
+  template cudaError_t launch_indicator<T>(const T*, const int*, int, double*, cudaStream_t);   \
+  template cudaError_t launch_flux_correct<T>(T*, const int*, const int*, int, const int*,      \
+                                              const T*, const T*, const int*, const double*,    \
+                                              double, const DevScalars*, cudaStream_t);
+PH_INST(double)
+PH_INST(float)
+#undef PH_INST
+
+}  // namespace ph

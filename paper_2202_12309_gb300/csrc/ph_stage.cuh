@@ -1,0 +1,291 @@
+// ph_stage.cuh -- the fused per-block stage kernel (K3).
+//
+// One launch covers every leaf block of the mesh ("pack all blocks into one
+// kernel", arXiv:2202.12309 Sec. 3.5/6.1).  A CTA owns a TX x TY column tile
+// of one block and marches along x3 over KC planes.  For each plane it:
+//   (A) stages the next conserved plane (tile + 2 ghost cells in x1, x2)
+//       into a 4-slot shared-memory ring and converts it to primitives;
+//   (C) computes van Leer slopes: x1 and x2 for the plane, x3 for its own
+//       column (x3 slopes roll through registers, each computed once);
+//   (E) computes HLLE fluxes on all x1 and x2 faces of the plane into shared
+//       memory and the x3 face above its cell in registers;
+//   (G) forms the flux divergence and the SSPRK2 combination and writes the
+//       new conserved state (stage 2 also folds the cell's signal speed into
+//       the block-wide max that becomes the next dt, Sec. 3.9).
+// Every face flux is computed once per tile (twice only on tile borders),
+// every slope once per tile (plus one halo column/row), every primitive
+// once per tile plus halo.
+#pragma once
+#include "ph_device.cuh"
+
+namespace ph {
+
+template <class T>
+struct StageArgs {
+  const T* Uin;        // stencil input, padded blocks [slot][v][k][j][i]
+  const T* U0;         // stage 2: state at the start of the cycle (pointwise)
+  T* Uout;             // stage 1: U1; stage 2: U0 (in place)
+  const int8_t* level; // per leaf (null: all level 0)
+  double idx[2][3];    // 1/dx per level and direction
+  int nx[3];           // interior cells per block
+  int S[3];            // padded extents nx + 4
+  int ntile[3];        // tiles per block along x1, x2 and k-chunks along x3
+  int KC;              // planes per chunk
+  int nleaf;
+  int stage;           // 1 or 2
+  int want_rate;       // stage 2 on uniform meshes: fold the next dt's max
+  Phys<T> P;
+  DevScalars* sc;
+  // flux-correction capture (two-level meshes): per leaf 6 records (-1: none)
+  const int* face_rec;
+  T* fc_coarse;        // [rec][v][n_t2][n_t1] flux of the coarse block on the face
+  T* fc_fine;          // [rec][v][2 n_t2][2 n_t1] fluxes of the fine blocks on the face
+  const int* fine_off; // per leaf 6 x 2: offset of the fine block's quadrant (t1, t2)
+};
+
+// Store one face flux of a leaf on a fine-coarse face (Sec. 3.6 flux
+// correction).  face = 2 d + side; (a1, a2) are the cell's indices along
+// t1 = d+1 and t2 = d+2 (mod 3).  A level-0 leaf writes the record's coarse
+// flux; a level-1 leaf writes its quadrant (q1, q2) of the record's fine
+// fluxes, which are 2 n_t1 x 2 n_t2 per variable.
+template <class T>
+__device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int face, int a1, int a2,
+                                        int v, T val) {
+  const int rec = a.face_rec[6 * leaf + face];
+  const int d = face >> 1;
+  const int m1 = a.nx[(d + 1) % 3], m2 = a.nx[(d + 2) % 3];
+  if (a.level[leaf] == 0) {
+    a.fc_coarse[(((size_t)rec * NV + v) * m2 + a2) * m1 + a1] = val;
+  } else {
+    const int q1 = a.fine_off[12 * leaf + 2 * face], q2 = a.fine_off[12 * leaf + 2 * face + 1];
+    a.fc_fine[(((size_t)rec * NV + v) * (2 * m2) + q2 * m2 + a2) * (2 * m1) + q1 * m1 + a1] = val;
+  }
+}
+
+template <class T, int TX, int TY>
+struct StageSmem {
+  static constexpr int WX = TX + 4, WY = TY + 4;
+  static constexpr int PLANE = NV * WX * WY;          // one primitive plane
+  static constexpr int DXN = NV * TY * (TX + 2);      // x1 slopes
+  static constexpr int DYN = NV * (TY + 2) * TX;      // x2 slopes
+  static constexpr int FXN = NV * TY * (TX + 1);      // x1 face fluxes
+  static constexpr int FYN = NV * (TY + 1) * TX;      // x2 face fluxes
+  static constexpr size_t body = sizeof(T) * (size_t)(4 * PLANE + DXN + DYN + FXN + FYN);
+  static constexpr size_t red_off = (body + 15) / 16 * 16;
+  static constexpr size_t bytes = red_off + 32 * sizeof(double);
+};
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+stage_kernel(const StageArgs<T> a) {
+  using SM = StageSmem<T, TX, TY>;
+  constexpr int NT = TX * TY;
+  constexpr int WX = SM::WX, WY = SM::WY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  T* sdx = ring + 4 * SM::PLANE;
+  T* sdy = sdx + SM::DXN;
+  T* sfx = sdy + SM::DYN;
+  T* sfy = sfx + SM::FXN;
+  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int tiles_per_block = a.ntile[0] * a.ntile[1] * a.ntile[2];
+  const int leaf = blockIdx.x / tiles_per_block;
+  if (leaf >= a.nleaf) return;
+  int t = blockIdx.x - leaf * tiles_per_block;
+  const int tk = t / (a.ntile[0] * a.ntile[1]);
+  t -= tk * a.ntile[0] * a.ntile[1];
+  const int tj = t / a.ntile[0];
+  const int ti = t - tj * a.ntile[0];
+  const int n1 = a.nx[0], n2 = a.nx[1], n3 = a.nx[2];
+  const int S1 = a.S[0], S2 = a.S[1], S3 = a.S[2];
+  const int i0 = ti * TX, j0 = tj * TY;        // interior origin of the tile
+  const int k0 = tk * a.KC;
+  const int k1 = min(k0 + a.KC, n3);
+  const int lev = a.level ? (int)a.level[leaf] : 0;
+  const T idx1 = (T)a.idx[lev][0], idx2 = (T)a.idx[lev][1], idx3 = (T)a.idx[lev][2];
+  const size_t vstride = (size_t)S1 * S2 * S3;
+  const size_t bbase = (size_t)leaf * NV * vstride;
+  const T* __restrict__ Ub = a.Uin + bbase;
+  const Phys<T> P = a.P;
+  unsigned floors = 0;
+
+  // Stage plane p (interior index, -2..n3+1) into its ring slot as primitives.
+  // Cells past a ragged block edge are clamped to the edge (never used).
+  auto load_plane = [&](int p) {
+    T* dst = ring + ((p + 4) & 3) * SM::PLANE;
+    const size_t kofs = (size_t)(p + NG) * S2 * S1;
+    for (int c = tid; c < WX * WY; c += NT) {
+      const int jj = c / WX, ii = c - jj * WX;
+      const int jp = min(j0 + jj, S2 - 1), ip = min(i0 + ii, S1 - 1);
+      const T* src = Ub + kofs + (size_t)jp * S1 + ip;
+      T w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = __ldg(src + v * vstride);
+      cons_to_prim(w, P, floors);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
+    }
+  };
+  auto col = [&](int p, T w[NV]) {  // own column's primitive at plane p
+    const T* s = ring + ((p + 4) & 3) * SM::PLANE;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = s[(v * WY + ty + 2) * WX + tx + 2];
+  };
+
+  // Priming: planes k0-2 .. k0+1 give the x3 slope at k0 and the flux at k0-1/2.
+  load_plane(k0 - 2);
+  load_plane(k0 - 1);
+  load_plane(k0);
+  load_plane(k0 + 1);
+  __syncthreads();
+  T dz[NV], fzm[NV];
+  {
+    T wa[NV], wb[NV], wc[NV], wd[NV], wl[NV], wr[NV];
+    col(k0 - 2, wa);
+    col(k0 - 1, wb);
+    col(k0, wc);
+    col(k0 + 1, wd);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T d0 = vanleer(wa[v], wb[v], wc[v]);
+      dz[v] = vanleer(wb[v], wc[v], wd[v]);
+      wl[v] = wb[v] + T(0.5) * d0;
+      wr[v] = wc[v] - T(0.5) * dz[v];
+    }
+    hlle<T, 2>(wl, wr, P, fzm);
+  }
+  __syncthreads();
+
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = (i < n1) && (j < n2);
+  const double dt = a.sc->dt_next;
+  const T tdt = (T)dt;
+  double rate = 0.0;
+
+  for (int k = k0; k < k1; ++k) {
+    // (A) next plane in
+    load_plane(k + 2);
+    __syncthreads();
+    // (C) slopes; own x3 flux
+    T fzlo[NV];  // x3 flux below the cell; fzm becomes the flux above it
+    {
+      T wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], f[NV];
+      col(k, wa);
+      col(k + 1, wb);
+      col(k + 2, wc);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T d1 = vanleer(wa[v], wb[v], wc[v]);
+        wl[v] = wa[v] + T(0.5) * dz[v];
+        wr[v] = wb[v] - T(0.5) * d1;
+        dz[v] = d1;
+      }
+      hlle<T, 2>(wl, wr, P, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        fzlo[v] = fzm[v];
+        fzm[v] = f[v];
+      }
+    }
+    {
+      const T* W = ring + ((k + 4) & 3) * SM::PLANE;
+      for (int c = tid; c < (TX + 2) * TY; c += NT) {   // x1 slopes, cells -1..TX
+        const int jj = c / (TX + 2), ii = c - jj * (TX + 2);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* r = W + (v * WY + jj + 2) * WX + ii;
+          sdx[(v * TY + jj) * (TX + 2) + ii] = vanleer(r[0], r[1], r[2]);
+        }
+      }
+      for (int c = tid; c < TX * (TY + 2); c += NT) {   // x2 slopes, rows -1..TY
+        const int jj = c / TX, ii = c - jj * TX;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* r = W + (v * WY + jj) * WX + ii + 2;
+          sdy[(v * (TY + 2) + jj) * TX + ii] = vanleer(r[0], r[WX], r[2 * WX]);
+        }
+      }
+    }
+    __syncthreads();
+    // (E) x1 and x2 face fluxes of the plane
+    {
+      const T* W = ring + ((k + 4) & 3) * SM::PLANE;
+      for (int c = tid; c < (TX + 1) * TY; c += NT) {
+        const int jj = c / (TX + 1), f = c - jj * (TX + 1);  // face between cells f-1, f
+        T wl[NV], wr[NV], fl[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* r = W + (v * WY + jj + 2) * WX + f + 1;
+          const T* s = sdx + (v * TY + jj) * (TX + 2) + f;
+          wl[v] = r[0] + T(0.5) * s[0];
+          wr[v] = r[1] - T(0.5) * s[1];
+        }
+        hlle<T, 0>(wl, wr, P, fl);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sfx[(v * TY + jj) * (TX + 1) + f] = fl[v];
+      }
+      for (int c = tid; c < TX * (TY + 1); c += NT) {
+        const int g = c / TX, ii = c - g * TX;   // face between rows g-1, g
+        T wl[NV], wr[NV], fl[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const T* r = W + (v * WY + g + 1) * WX + ii + 2;
+          const T* s = sdy + (v * (TY + 2) + g) * TX + ii;
+          wl[v] = r[0] + T(0.5) * s[0];
+          wr[v] = r[WX] - T(0.5) * s[TX];
+        }
+        hlle<T, 1>(wl, wr, P, fl);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sfy[(v * (TY + 1) + g) * TX + ii] = fl[v];
+      }
+    }
+    __syncthreads();
+    // (G) flux divergence + SSPRK2 combination
+    if (own) {
+      const size_t cell = bbase + (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
+      T unew[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T dfx = sfx[(v * TY + ty) * (TX + 1) + tx + 1] - sfx[(v * TY + ty) * (TX + 1) + tx];
+        const T dfy = sfy[(v * (TY + 1) + ty + 1) * TX + tx] - sfy[(v * (TY + 1) + ty) * TX + tx];
+        const T L = -(dfx * idx1 + dfy * idx2 + (fzm[v] - fzlo[v]) * idx3);
+        const T ucur = a.Uin[cell + v * vstride];
+        if (a.stage == 1) {
+          unew[v] = ucur + tdt * L;
+        } else {
+          const T u0 = a.U0[cell + v * vstride];
+          unew[v] = T(0.5) * u0 + T(0.5) * (ucur + tdt * L);
+        }
+        a.Uout[cell + v * vstride] = unew[v];
+      }
+      if (a.face_rec) {  // two-level mesh: keep fluxes on fine-coarse faces
+        const int* fr = a.face_rec + 6 * leaf;
+        if (i == 0 && fr[0] >= 0)
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 0, j, k, v, sfx[(v * TY + ty) * (TX + 1) + tx]);
+        if (i == n1 - 1 && fr[1] >= 0)
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 1, j, k, v, sfx[(v * TY + ty) * (TX + 1) + tx + 1]);
+        if (j == 0 && fr[2] >= 0)
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 2, k, i, v, sfy[(v * (TY + 1) + ty) * TX + tx]);
+        if (j == n2 - 1 && fr[3] >= 0)
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 3, k, i, v, sfy[(v * (TY + 1) + ty + 1) * TX + tx]);
+        if (k == 0 && fr[4] >= 0)
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 4, i, j, v, fzlo[v]);
+        if (k == n3 - 1 && fr[5] >= 0)
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 5, i, j, v, fzm[v]);
+      }
+      if (a.want_rate) {
+        cons_to_prim(unew, P, floors);
+        const T r = wave_rate(unew, P, idx1, idx2, idx3);
+        const double rd = (double)r;
+        if (!(rd <= rate)) rate = rd;
+      }
+    }
+  }
+  if (a.want_rate) block_max_to(&a.sc->wmax_bits, rate, red);
+  if (floors) atomicAdd(&a.sc->floor_hits, (unsigned long long)floors);
+}
+
+}  // namespace ph
