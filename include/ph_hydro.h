@@ -186,6 +186,35 @@ int ph_get_tile(const ph_mesh* mesh, int32_t tile[3]);
  * (PH_ERR_INVALID otherwise). */
 int ph_profile_cycles(ph_mesh* mesh, int32_t ncycles, double* ms_out, int32_t nslots);
 
+/* Conserved totals of a caller-owned state without any device allocation.
+ * The paper has no counterpart: this exists for callers that may not call
+ * cudaMalloc at all (a plugin whose host application owns every byte of
+ * device memory, a solver embedded in a code that reserves its whole memory
+ * budget up front, a time-critical loop that must not enter the CUDA
+ * allocator, which can block and synchronise).  It computes what ph_totals
+ * computes, from the state alone:
+ *   U       device pointer, interior state in the layout of ph_get_state
+ *           (U[block][var][k][j][i] over nx cells), double for PH_FP64 or
+ *           float for PH_FP32
+ *   nx[3]   host array, interior cells per block
+ *   nblocks 0 .. PH_TOTALS_NOALLOC_MAX_BLOCKS; more is rejected with
+ *           PH_ERR_INVALID
+ *   level   device pointer to nblocks levels (0 or 1), or NULL for all 0
+ *   vol0/1  cell volume at level 0 / level 1
+ *   out     device pointer to 5 doubles, written asynchronously on `stream`
+ *           (a cudaStream_t; NULL = legacy default stream)
+ * Its scratch (per-block partial sums) is a fixed device array of
+ * PH_TOTALS_NOALLOC_MAX_BLOCKS x 5 doubles (640 KiB) that every GPU which
+ * loads the library holds until the process exits.  The first call on a
+ * device, made with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Each call overwrites the entries it reads, so nothing needs clearing. */
+#define PH_TOTALS_NOALLOC_MAX_BLOCKS 16384
+int ph_totals_noalloc(const void* U, int32_t precision, const int32_t nx[3], int32_t nblocks,
+                      const int8_t* level, double vol0, double vol1, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,7 @@ EXPORTS = [
     "ph_set_state", "ph_get_state", "ph_get_full", "ph_step", "ph_get_dt", "ph_get_next_dt",
     "ph_get_time", "ph_totals", "ph_tag", "ph_refine_where", "ph_refine_by_density", "ph_status",
     "ph_fill_ghosts", "ph_launches_per_cycle", "ph_get_tile", "ph_profile_cycles",
+    "ph_totals_noalloc",
 ]
 
 
@@ -130,6 +131,8 @@ def lib():
             "ph_launches_per_cycle": [P, ctypes.POINTER(i32)],
             "ph_get_tile": [P, ctypes.POINTER(i32)],
             "ph_profile_cycles": [P, i32, dp, i32],
+            "ph_totals_noalloc": [P, i32, ctypes.POINTER(i32), i32, P, ctypes.c_double,
+                                  ctypes.c_double, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -164,6 +167,21 @@ def use_torch_allocator():
     a, f = ALLOC(_alloc), FREE(_free)
     check(lib().ph_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))
     _alloc_refs = (a, f)
+
+
+def totals_noalloc(U, nx, nblocks, out, precision="fp64", level=None, vol=(1.0, 0.125),
+                   stream: Optional[int] = None):
+    """ph_totals_noalloc on caller-owned device tensors (U packed interior
+    state, out 5 doubles); the library allocates nothing for this call."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    n3 = (ctypes.c_int32 * 3)(*nx)
+    prec = PH_FP32 if precision in ("fp32", PH_FP32) else PH_FP64
+    lvl = ctypes.c_void_p(level.data_ptr()) if level is not None else None
+    check(lib().ph_totals_noalloc(ctypes.c_void_p(U.data_ptr()), prec, n3, int(nblocks), lvl,
+                                  float(vol[0]), float(vol[1]), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(stream)))
 
 
 def _ptr(x):

@@ -64,6 +64,8 @@ uint64_t zkey(const Leaf& l, int max_level) {
 
 }  // namespace
 
+void ph::set_error_message(const char* msg) { g_err = msg ? msg : ""; }
+
 struct ph_mesh {
   ph_config cfg;
   cudaStream_t stream = nullptr;

@@ -8,6 +8,9 @@
 
 namespace ph {
 
+// Record the message that ph_last_error() returns on this thread.
+void set_error_message(const char* msg);
+
 // Device view of a mesh's block tree, used by the ghost exchange and remesh
 // kernels to find the leaf covering any cell (Sec. 2.1: one leaf covers each
 // location).  root[s] is the level-0 leaf at root slot s, or -1 when that
