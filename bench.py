@@ -165,20 +165,38 @@ def time_variant(ph, torch, block, precision, steps, warmup):
     return res
 
 
+def measured_traffic(precision):
+    """DRAM bytes of one stage launch at this mesh size, from the committed ncu
+    capture (profiles/stage_kernel_traffic.json, per zone, scaled by zones), or
+    None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
+        h = hashlib.sha256()
+        for f in ("ph_stage.cuh", "ph_device.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2202_12309_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() != rec["kernel_source_sha256"]:
+            return None
+        return rec[precision]["bytes_per_zone"] * MESH ** 3
+    except Exception:
+        return None
+
+
 def roofline_for(v, pk, peak_kind):
     zones = MESH ** 3
+    traffic = measured_traffic(v["precision"])
     if v["precision"] == "fp32":
         word = 4
         achieved = WORDS_PER_ZONE_LAUNCH * word * zones / (v["stage_ms_avg"] / 1e3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_launch": "stage 1 (ncu)",
                 "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}
     # FP64: bound by the FP64 pipe
     achieved = FLOPS_PER_ZONE_CYCLE * 0.5 * zones / (v["stage_ms_avg"] / 1e3) / 1e12
     peak = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "traffic_launch": "stage 1 (ncu)",
             "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)"}
 
 
@@ -277,8 +295,11 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
+    ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global MESH
+    MESH = args.mesh
     if args.quick:
         args.no_variants = args.no_cpu = True
     if args.impl == "reference":
