@@ -3,11 +3,11 @@
  * The library advances the 3-D Euler equations of an ideal gas on a mesh of
  * equal-sized MeshBlocks with ghost zones, one GPU, all work in hand-written
  * CUDA kernels for sm_103a (arXiv:2202.12309; the method is that of its
- * Parthenon-hydro miniapp, Sec. 5.1: two-stage Runge-Kutta, piecewise-linear
+ * Parthenon-hydro miniapp, Sec. 4.1: two-stage Runge-Kutta, piecewise-linear
  * reconstruction, HLLE Riemann solver; the mesh and its boundary
  * communication are Sec. 2.1, 3.6 and 3.7; the time step is a global
- * min-reduction, Sec. 3.9; the call sequence follows the driver pattern of
- * Sec. 3.10: create a mesh, refine, set the state, step, read state and dt).
+ * min-reduction, Sec. 3.10; the call sequence follows the driver pattern of
+ * Sec. 3.11: create a mesh, refine, set the state, step, read state and dt).
  *
  * Conventions for every entry point:
  *  - Return value: PH_OK (0) or a negative PH_ERR_* code.  The message of the
@@ -46,7 +46,7 @@ extern "C" {
 #define PH_FP32 1
 
 /* Mesh configuration (Sec. 2.1: equal-sized blocks, an integer number of
- * blocks per dimension; Sec. 5.1: ideal gas).  All fields are read once by
+ * blocks per dimension; Sec. 4.1: ideal gas).  All fields are read once by
  * ph_create.
  *   nx[3]          interior cells per block along x1, x2, x3 (each >= 4)
  *   nb[3]          root-grid blocks along x1, x2, x3 (each >= 1)
@@ -99,7 +99,7 @@ int ph_set_allocator(ph_alloc_fn alloc, ph_free_fn release, void* ctx);
 const char* ph_last_error(void);
 
 /* Create a mesh (Sec. 2.1): root grid, oct-tree, Z-order, static refinement
- * (Sec. 3.7).  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * (Sec. 3.8).  `stream` is a cudaStream_t (NULL = legacy default stream).
  * The state is zero until ph_set_state.  *out receives the handle.
  * Errors: PH_ERR_INVALID (nx < 4, nb < 1, bad level/precision/tile),
  * PH_ERR_OOM, PH_ERR_CUDA. */
@@ -127,10 +127,10 @@ int ph_get_state(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
  * (nx+4)^3 cells (count = blocks*5*(nx1+4)*(nx2+4)*(nx3+4)). */
 int ph_get_full(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
 
-/* Advance `ncycles` cycles (Sec. 3.10 MultiStageDriver): per cycle, two RK
- * stages each followed by the ghost exchange (Sec. 3.6) and, on two-level
- * meshes, flux correction; then dt for the next cycle (Sec. 3.9) and, when
- * adaptive, tagging and remesh (Sec. 3.7).  Uniform meshes replay a captured
+/* Advance `ncycles` cycles (Sec. 3.11 MultiStageDriver): per cycle, two RK
+ * stages each followed by the ghost exchange (Sec. 3.7) and, on two-level
+ * meshes, flux correction; then dt for the next cycle (Sec. 3.10) and, when
+ * adaptive, tagging and remesh (Sec. 3.8).  Uniform meshes replay a captured
  * CUDA graph of one cycle and return without synchronising. */
 int ph_step(ph_mesh* mesh, int32_t ncycles);
 
@@ -152,7 +152,7 @@ int ph_totals(ph_mesh* mesh, double out[5]);
 int ph_tag(ph_mesh* mesh, int8_t* flags, double* indicator, int32_t n);
 
 /* Rebuild the tree from explicit flags (+1 refine a level-0 leaf, -1 merge
- * 8 level-1 siblings that are all -1, 0 keep; Sec. 2.1/3.7) and move the data
+ * 8 level-1 siblings that are all -1, 0 keep; Sec. 2.1/3.8) and move the data
  * (prolongation for new children, restriction for merged parents).
  * check_age: also require derefine_count cycles of age to merge.
  * *changed (may be NULL) is set to 1 if the tree changed. */
@@ -169,7 +169,7 @@ int ph_status(ph_mesh* mesh, int64_t* floor_hits, int32_t* nonfinite);
 
 /* Kernel-level entry points used by tests and benchmarks ------------------ */
 
-/* Ghost exchange alone on the current state (Sec. 3.6). */
+/* Ghost exchange alone on the current state (Sec. 3.7). */
 int ph_fill_ghosts(ph_mesh* mesh);
 
 /* Number of kernel launches one uniform-mesh cycle enqueues. */
@@ -185,6 +185,53 @@ int ph_get_tile(const ph_mesh* mesh, int32_t tile[3]);
  * 3 ghost exchange, 4 dt bookkeeping.  Synchronises.  Uniform meshes only
  * (PH_ERR_INVALID otherwise). */
 int ph_profile_cycles(ph_mesh* mesh, int32_t ncycles, double* ms_out, int32_t nslots);
+
+/* ---------------------------------------------------------------------------
+ * Batched independent meshes (one persistent launch per cycle).
+ *
+ * `nsim` uniform periodic meshes (max_level 0), each with its own block size,
+ * block count, state and dt, all in one precision, advanced together: one
+ * cooperative kernel per cycle runs stage 1, the ghost exchange, stage 2 and
+ * the ghost exchange for every block of every member (a work list of
+ * (block, tile) items, four grid barriers with bounded spins) and updates each
+ * member's dt; the cycle is captured in a CUDA graph.  This is the paper's
+ * "all blocks in one kernel" (Sec. 3.6, 5.1) taken to one launch per cycle
+ * across independent problems.  Member s's state uses the layout of
+ * ph_get_state for its own mesh (blocks in Z-order).
+ * ------------------------------------------------------------------------- */
+typedef struct ph_batch ph_batch;
+
+/* Create from nsim configurations (uniform, same precision; tile ignored). */
+int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch** out);
+int ph_batch_destroy(ph_batch* batch);
+int ph_batch_num_blocks(const ph_batch* batch, int32_t sim, int32_t* n);
+/* Copy member `sim`'s interior state in (fills its ghosts, computes its dt)
+ * or out; count = its blocks * 5 * nx1 * nx2 * nx3. */
+int ph_batch_set_state(ph_batch* batch, int32_t sim, const void* U, int64_t count,
+                       int32_t on_device);
+int ph_batch_get_state(ph_batch* batch, int32_t sim, void* U, int64_t count,
+                       int32_t on_device);
+/* Advance every member by ncycles (graph replays; does not synchronise). */
+int ph_batch_step(ph_batch* batch, int32_t ncycles);
+/* Per-member dt of the last cycle, time and cycle count (arrays of nsim);
+ * synchronise; PH_ERR_TIMEOUT if a grid barrier gave up. */
+int ph_batch_get_dt(ph_batch* batch, double* dt);
+int ph_batch_get_time(ph_batch* batch, double* time, int64_t* cycle);
+int ph_batch_status(ph_batch* batch, int64_t* floor_hits, int32_t* nonfinite);
+/* Launch choice {TX, TY, KC, CTAs per SM}: read, set, or pick by timing
+ * trial_cycles cycles of every candidate (tile 8x8/16x8/16x16/32x8, chunk
+ * 8/16/32 planes, 1..max CTAs per SM) on the current state, which is restored
+ * afterwards. */
+int ph_batch_get_launch(const ph_batch* batch, int32_t choice[4]);
+int ph_batch_set_launch(ph_batch* batch, const int32_t choice[4]);
+int ph_batch_autotune(ph_batch* batch, int32_t trial_cycles, int32_t chosen[4]);
+
+/* Failure-detection self test of the bounded grid barrier: launches nctas
+ * (1..64) CTAs whose barrier can never complete; each gives up after
+ * spin_limit polls (<= 2^26).  *gave_up = CTAs that reported it; returns
+ * PH_ERR_TIMEOUT when any did (the expected outcome), with the GPU context
+ * still usable. */
+int ph_debug_barrier_timeout(void* stream, int32_t nctas, int64_t spin_limit, int32_t* gave_up);
 
 /* Conserved totals of a caller-owned state without any device allocation.
  * The paper has no counterpart: this exists for callers that may not call

@@ -29,6 +29,10 @@ EXPORTS = [
     "ph_get_time", "ph_totals", "ph_tag", "ph_refine_where", "ph_refine_by_density", "ph_status",
     "ph_fill_ghosts", "ph_launches_per_cycle", "ph_get_tile", "ph_profile_cycles",
     "ph_totals_noalloc",
+    "ph_batch_create", "ph_batch_destroy", "ph_batch_num_blocks", "ph_batch_set_state",
+    "ph_batch_get_state", "ph_batch_step", "ph_batch_get_dt", "ph_batch_get_time",
+    "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
+    "ph_debug_barrier_timeout",
 ]
 
 
@@ -133,6 +137,19 @@ def lib():
             "ph_profile_cycles": [P, i32, dp, i32],
             "ph_totals_noalloc": [P, i32, ctypes.POINTER(i32), i32, P, ctypes.c_double,
                                   ctypes.c_double, P, P],
+            "ph_batch_create": [ctypes.POINTER(Config), i32, P, ctypes.POINTER(P)],
+            "ph_batch_destroy": [P],
+            "ph_batch_num_blocks": [P, i32, ctypes.POINTER(i32)],
+            "ph_batch_set_state": [P, i32, P, i64, i32],
+            "ph_batch_get_state": [P, i32, P, i64, i32],
+            "ph_batch_step": [P, i32],
+            "ph_batch_get_dt": [P, dp],
+            "ph_batch_get_time": [P, dp, ctypes.POINTER(i64)],
+            "ph_batch_status": [P, ctypes.POINTER(i64), ctypes.POINTER(i32)],
+            "ph_batch_get_launch": [P, ctypes.POINTER(i32)],
+            "ph_batch_set_launch": [P, ctypes.POINTER(i32)],
+            "ph_batch_autotune": [P, i32, ctypes.POINTER(i32)],
+            "ph_debug_barrier_timeout": [P, i32, i64, ctypes.POINTER(i32)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -326,3 +343,102 @@ class Mesh:
         t = (ctypes.c_int32 * 3)()
         check(self.L.ph_get_tile(self.h, t))
         return tuple(t)
+
+
+class Batch:
+    """Independent uniform meshes advanced together by one persistent launch per cycle."""
+
+    def __init__(self, cfgs, stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the GB300 hydro library has no CPU path")
+            stream = torch.cuda.current_stream().cuda_stream
+        self.L = lib()
+        arr = (Config * len(cfgs))(*cfgs)
+        self.cfgs = list(cfgs)
+        self.nsim = len(cfgs)
+        self.h = ctypes.c_void_p()
+        check(self.L.ph_batch_create(arr, self.nsim, ctypes.c_void_p(stream), ctypes.byref(self.h)))
+        self.dtype = np.float32 if cfgs[0].precision == PH_FP32 else np.float64
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.ph_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nblocks(self, sim: int) -> int:
+        n = ctypes.c_int32()
+        check(self.L.ph_batch_num_blocks(self.h, sim, ctypes.byref(n)))
+        return n.value
+
+    def state_shape(self, sim: int):
+        nx = tuple(self.cfgs[sim].nx)
+        return (self.nblocks(sim), 5, nx[2], nx[1], nx[0])
+
+    def set_state(self, sim: int, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=self.dtype)
+        p, dev = _ptr(U)
+        check(self.L.ph_batch_set_state(self.h, sim, ctypes.c_void_p(p),
+                                        int(np.prod(self.state_shape(sim))), dev))
+
+    def get_state(self, sim: int, out=None):
+        if out is None:
+            out = np.zeros(self.state_shape(sim), dtype=self.dtype)
+        p, dev = _ptr(out)
+        check(self.L.ph_batch_get_state(self.h, sim, ctypes.c_void_p(p),
+                                        int(np.prod(self.state_shape(sim))), dev))
+        return out
+
+    def step(self, n: int = 1):
+        check(self.L.ph_batch_step(self.h, int(n)))
+
+    def dt(self) -> np.ndarray:
+        out = np.zeros(self.nsim)
+        check(self.L.ph_batch_get_dt(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def time(self):
+        t = np.zeros(self.nsim)
+        c = np.zeros(self.nsim, dtype=np.int64)
+        check(self.L.ph_batch_get_time(self.h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return t, c
+
+    def status(self):
+        fh = ctypes.c_int64()
+        nf = ctypes.c_int32()
+        rc = self.L.ph_batch_status(self.h, ctypes.byref(fh), ctypes.byref(nf))
+        return rc, fh.value, nf.value
+
+    def launch(self):
+        c = (ctypes.c_int32 * 4)()
+        check(self.L.ph_batch_get_launch(self.h, c))
+        return tuple(c)
+
+    def set_launch(self, choice):
+        c = (ctypes.c_int32 * 4)(*choice)
+        check(self.L.ph_batch_set_launch(self.h, c))
+
+    def autotune(self, trial_cycles: int = 2):
+        c = (ctypes.c_int32 * 4)()
+        check(self.L.ph_batch_autotune(self.h, int(trial_cycles), c))
+        return tuple(c)
+
+
+def debug_barrier_timeout(nctas: int = 4, spin_limit: int = 1 << 16, stream: Optional[int] = None):
+    """Run the barrier self test; returns (return code, CTAs that gave up)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    g = ctypes.c_int32()
+    rc = lib().ph_debug_barrier_timeout(ctypes.c_void_p(stream), int(nctas), int(spin_limit),
+                                        ctypes.byref(g))
+    return rc, g.value

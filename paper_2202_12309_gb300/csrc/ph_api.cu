@@ -5,7 +5,7 @@
 // each of which may split into 2^3 children (two levels); leaves are kept in
 // Z-order of their location scaled to the finest level (x1 in the lowest
 // bit).  Leaf b's data lives in slot b of the device pools, so a remesh
-// rebuilds the pool in the new order (Sec. 3.7: the tree is rebuilt first,
+// rebuilds the pool in the new order (Sec. 3.8: the tree is rebuilt first,
 // then populated).
 #include <algorithm>
 #include <cmath>
@@ -759,7 +759,7 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     delete m;
     return cuda_fail(e, "cudaStreamCreateWithFlags");
   }
-  // root grid, then static refinement (Sec. 3.7) before any data exists
+  // root grid, then static refinement (Sec. 3.8) before any data exists
   for (int64_t k = 0; k < cfg->nb[2]; ++k)
     for (int64_t j = 0; j < cfg->nb[1]; ++j)
       for (int64_t i = 0; i < cfg->nb[0]; ++i) m->leaf.push_back(Leaf{0, {i, j, k}, 0});

@@ -1,6 +1,6 @@
 // ph_device.cuh -- device-side building blocks shared by the library's kernels.
 //
-// Pointwise physics of the Parthenon-hydro method (arXiv:2202.12309 Sec. 5.1:
+// Pointwise physics of the Parthenon-hydro method (arXiv:2202.12309 Sec. 4.1:
 // ideal-gas Euler equations, piecewise-linear reconstruction, HLLE fluxes)
 // written for throughput on sm_103a: one reciprocal square root gives both
 // sqrt(rho) and 1/rho, Roe weights are formed once, and every division that
@@ -63,11 +63,13 @@ __device__ __forceinline__ void cons_to_prim(T w[NV], const Phys<T>& P, unsigned
   w[4] = p;
 }
 
-// van Leer (harmonic) limited slope of a cell from its two neighbours.
+// Half of the van Leer (harmonic) limited slope of a cell from its two
+// neighbours: dL dR / (dL + dR) where dL dR > 0, else 0.  The face states are
+// w -+ this value (the factors 2 and 1/2 of the slope cancel exactly).
 template <class T>
-__device__ __forceinline__ T vanleer(T wm, T w0, T wp) {
+__device__ __forceinline__ T vanleer_half(T wm, T w0, T wp) {
   const T dl = w0 - wm, dr = wp - w0, prod = dl * dr;
-  return prod > T(0) ? (T(2) * prod) / (dl + dr) : T(0);
+  return prod > T(0) ? prod / (dl + dr) : T(0);
 }
 
 // HLLE flux with Einfeldt's wave-speed bounds (Roe averages) through a face
@@ -147,5 +149,44 @@ __device__ __forceinline__ void block_max_to(unsigned long long* dst, double v, 
     if (lane == 0 && b2 != 0ull) atomicMax(dst, b2);
   }
 }
+
+// --------------------------------------------------------------------------
+// Ghost-shell enumeration: the ghost cells of a padded block, flattened as
+// (A) the 4 x3-ghost planes, (B) the 4 x2-ghost rows of each interior plane,
+// (C) the 4 x1-ghost cells of each interior row.  Rows stay contiguous in x1.
+// --------------------------------------------------------------------------
+struct Shell {
+  int n1, n2, n3, S1, S2, nA, nB, nC;
+  __device__ __forceinline__ Shell(const int nx[3]) {
+    n1 = nx[0]; n2 = nx[1]; n3 = nx[2];
+    S1 = n1 + 2 * NG; S2 = n2 + 2 * NG;
+    nA = 4 * S2 * S1;
+    nB = n3 * 4 * S1;
+    nC = n3 * n2 * 4;
+  }
+  __device__ __forceinline__ int count() const { return nA + nB + nC; }
+  __device__ __forceinline__ void cell(int c, int& i, int& j, int& k) const {
+    if (c < nA) {
+      const int kk = c / (S2 * S1), r = c - kk * S2 * S1;
+      j = r / S1;
+      i = r - j * S1;
+      k = kk < 2 ? kk : n3 + kk;
+    } else if (c < nA + nB) {
+      c -= nA;
+      const int kq = c / (4 * S1), r = c - kq * 4 * S1;
+      const int jj = r / S1;
+      i = r - jj * S1;
+      k = kq + NG;
+      j = jj < 2 ? jj : n2 + jj;
+    } else {
+      c -= nA + nB;
+      const int kq = c / (4 * n2), r = c - kq * 4 * n2;
+      const int jq = r >> 2, ii = r & 3;
+      k = kq + NG;
+      j = jq + NG;
+      i = ii < 2 ? ii : n1 + ii;
+    }
+  }
+};
 
 }  // namespace ph

@@ -2,7 +2,7 @@
 // movement (K7), signal-speed max for dt (K5), dt bookkeeping, refinement
 // indicator (K6), interior <-> padded copies and conserved totals.
 //
-// Ghost exchange (arXiv:2202.12309 Sec. 3.6, "fill-in-one"): the paper packs
+// Ghost exchange (arXiv:2202.12309 Sec. 3.7, "fill-in-one"): the paper packs
 // every buffer of every block into one kernel, sends, and unpacks with
 // restriction/prolongation.  On one GPU there is nothing to send, so K1 is a
 // single pull: each ghost cell reads the data it needs straight from the
@@ -11,45 +11,6 @@
 #include "ph_internal.h"
 
 namespace ph {
-
-// --------------------------------------------------------------------------
-// Ghost-shell enumeration: the ghost cells of a padded block, flattened as
-// (A) the 4 x3-ghost planes, (B) the 4 x2-ghost rows of each interior plane,
-// (C) the 4 x1-ghost cells of each interior row.  Rows stay contiguous in x1.
-// --------------------------------------------------------------------------
-struct Shell {
-  int n1, n2, n3, S1, S2, nA, nB, nC;
-  __device__ __forceinline__ Shell(const int nx[3]) {
-    n1 = nx[0]; n2 = nx[1]; n3 = nx[2];
-    S1 = n1 + 2 * NG; S2 = n2 + 2 * NG;
-    nA = 4 * S2 * S1;
-    nB = n3 * 4 * S1;
-    nC = n3 * n2 * 4;
-  }
-  __device__ __forceinline__ int count() const { return nA + nB + nC; }
-  __device__ __forceinline__ void cell(int c, int& i, int& j, int& k) const {
-    if (c < nA) {
-      const int kk = c / (S2 * S1), r = c - kk * S2 * S1;
-      j = r / S1;
-      i = r - j * S1;
-      k = kk < 2 ? kk : n3 + kk;
-    } else if (c < nA + nB) {
-      c -= nA;
-      const int kq = c / (4 * S1), r = c - kq * 4 * S1;
-      const int jj = r / S1;
-      i = r - jj * S1;
-      k = kq + NG;
-      j = jj < 2 ? jj : n2 + jj;
-    } else {
-      c -= nA + nB;
-      const int kq = c / (4 * n2), r = c - kq * 4 * n2;
-      const int jq = r >> 2, ii = r & 3;
-      k = kq + NG;
-      j = jq + NG;
-      i = ii < 2 ? ii : n1 + ii;
-    }
-  }
-};
 
 template <class T>
 __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx) {
@@ -84,7 +45,7 @@ cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nlea
 }
 
 // --------------------------------------------------------------------------
-// Composite field of a two-level mesh (Sec. 2.1 + Sec. 3.6).
+// Composite field of a two-level mesh (Sec. 2.1 + Sec. 3.7).
 //   level-0 cell: the level-0 leaf's value, or the mean of its 8 children
 //                 (restriction; summed c3 outer, c1 inner, then x 1/8);
 //   level-1 cell: the level-1 leaf's value, or the coarse value plus
@@ -255,7 +216,7 @@ cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uo
 }
 
 // --------------------------------------------------------------------------
-// K5: signal-speed max for the CFL dt (Sec. 3.9), from interior cells.
+// K5: signal-speed max for the CFL dt (Sec. 3.10), from interior cells.
 // --------------------------------------------------------------------------
 template <class T>
 __global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level, double4 ia,
@@ -456,7 +417,7 @@ cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb,
 }
 
 // --------------------------------------------------------------------------
-// K4: flux correction (Sec. 3.6).  A record is one face of one level-0 leaf
+// K4: flux correction (Sec. 3.7).  A record is one face of one level-0 leaf
 // whose neighbour across the face is refined.  During the stage the coarse
 // leaf stored its own face flux Fc and the 4 fine leaves stored theirs; the
 // coarse cell next to the face is corrected by the difference between Fc and

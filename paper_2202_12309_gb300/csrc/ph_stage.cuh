@@ -1,17 +1,17 @@
 // ph_stage.cuh -- the fused per-block stage kernel (K3).
 //
 // One launch covers every leaf block of the mesh ("pack all blocks into one
-// kernel", arXiv:2202.12309 Sec. 3.5/6.1).  A CTA owns a TX x TY column tile
+// kernel", arXiv:2202.12309 Sec. 3.6/5.1).  A CTA owns a TX x TY column tile
 // of one block and marches along x3 over KC planes.  For each plane it:
 //   (A) stages the next conserved plane (tile + 2 ghost cells in x1, x2)
 //       into a 4-slot shared-memory ring and converts it to primitives;
-//   (C) computes van Leer slopes: x1 and x2 for the plane, x3 for its own
+//   (C) computes van Leer half-slopes: x1 and x2 for the plane, x3 for its own
 //       column (x3 slopes roll through registers, each computed once);
 //   (E) computes HLLE fluxes on all x1 and x2 faces of the plane into shared
 //       memory and the x3 face above its cell in registers;
 //   (G) forms the flux divergence and the SSPRK2 combination and writes the
 //       new conserved state (stage 2 also folds the cell's signal speed into
-//       the block-wide max that becomes the next dt, Sec. 3.9).
+//       the block-wide max that becomes the next dt, Sec. 3.10).
 // Every face flux is computed once per tile (twice only on tile borders),
 // every slope once per tile (plus one halo column/row), every primitive
 // once per tile plus halo.
@@ -43,7 +43,7 @@ struct StageArgs {
   const int* fine_off; // per leaf 6 x 2: offset of the fine block's quadrant (t1, t2)
 };
 
-// Store one face flux of a leaf on a fine-coarse face (Sec. 3.6 flux
+// Store one face flux of a leaf on a fine-coarse face (Sec. 3.7 flux
 // correction).  face = 2 d + side; (a1, a2) are the cell's indices along
 // t1 = d+1 and t2 = d+2 (mod 3).  A level-0 leaf writes the record's coarse
 // flux; a level-1 leaf writes its quadrant (q1, q2) of the record's fine
@@ -75,42 +75,46 @@ struct StageSmem {
   static constexpr size_t bytes = red_off + 32 * sizeof(double);
 };
 
+// One tile of one block for one stage.  J holds the block's data pointers,
+// geometry, the tile's origin and the k-range; returns the max over the
+// tile's own cells of the signal rate (|v_d|+c)/dx_d of the new state when
+// J.want_rate (else 0).  Uses the whole CTA; smem as laid out by StageSmem.
+template <class T>
+struct TileJob {
+  const T* Ub;     // stencil input block (padded)
+  const T* U0b;    // stage 2: the block at the start of the cycle
+  T* Uoutb;        // output block
+  int nx[3], S[3];
+  int i0, j0, k0, k1;
+  T idx1, idx2, idx3;
+  T dt;
+  int stage;
+  int want_rate;
+  int leaf;        // leaf index for flux capture (two-level meshes)
+};
+
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
-stage_kernel(const StageArgs<T> a) {
+__device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>& P,
+                                             const StageArgs<T>& a, unsigned char* smem_raw,
+                                             unsigned& floors) {
   using SM = StageSmem<T, TX, TY>;
   constexpr int NT = TX * TY;
   constexpr int WX = SM::WX, WY = SM::WY;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);
   T* sdx = ring + 4 * SM::PLANE;
   T* sdy = sdx + SM::DXN;
   T* sfx = sdy + SM::DYN;
   T* sfy = sfx + SM::FXN;
-  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int tiles_per_block = a.ntile[0] * a.ntile[1] * a.ntile[2];
-  const int leaf = blockIdx.x / tiles_per_block;
-  if (leaf >= a.nleaf) return;
-  int t = blockIdx.x - leaf * tiles_per_block;
-  const int tk = t / (a.ntile[0] * a.ntile[1]);
-  t -= tk * a.ntile[0] * a.ntile[1];
-  const int tj = t / a.ntile[0];
-  const int ti = t - tj * a.ntile[0];
-  const int n1 = a.nx[0], n2 = a.nx[1], n3 = a.nx[2];
-  const int S1 = a.S[0], S2 = a.S[1], S3 = a.S[2];
-  const int i0 = ti * TX, j0 = tj * TY;        // interior origin of the tile
-  const int k0 = tk * a.KC;
-  const int k1 = min(k0 + a.KC, n3);
-  const int lev = a.level ? (int)a.level[leaf] : 0;
-  const T idx1 = (T)a.idx[lev][0], idx2 = (T)a.idx[lev][1], idx3 = (T)a.idx[lev][2];
+  const int n1 = J.nx[0], n2 = J.nx[1], n3 = J.nx[2];
+  const int S1 = J.S[0], S2 = J.S[1], S3 = J.S[2];
+  const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
+  const T idx1 = J.idx1, idx2 = J.idx2, idx3 = J.idx3;
   const size_t vstride = (size_t)S1 * S2 * S3;
-  const size_t bbase = (size_t)leaf * NV * vstride;
-  const T* __restrict__ Ub = a.Uin + bbase;
-  const Phys<T> P = a.P;
-  unsigned floors = 0;
+  const T* __restrict__ Ub = J.Ub;
+  const int leaf = J.leaf;
 
   // Stage plane p (interior index, -2..n3+1) into its ring slot as primitives.
   // Cells past a ragged block edge are clamped to the edge (never used).
@@ -150,10 +154,10 @@ stage_kernel(const StageArgs<T> a) {
     col(k0 + 1, wd);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const T d0 = vanleer(wa[v], wb[v], wc[v]);
-      dz[v] = vanleer(wb[v], wc[v], wd[v]);
-      wl[v] = wb[v] + T(0.5) * d0;
-      wr[v] = wc[v] - T(0.5) * dz[v];
+      const T d0 = vanleer_half(wa[v], wb[v], wc[v]);
+      dz[v] = vanleer_half(wb[v], wc[v], wd[v]);
+      wl[v] = wb[v] + d0;
+      wr[v] = wc[v] - dz[v];
     }
     hlle<T, 2>(wl, wr, P, fzm);
   }
@@ -161,8 +165,7 @@ stage_kernel(const StageArgs<T> a) {
 
   const int i = i0 + tx, j = j0 + ty;
   const bool own = (i < n1) && (j < n2);
-  const double dt = a.sc->dt_next;
-  const T tdt = (T)dt;
+  const T tdt = J.dt;
   double rate = 0.0;
 
   for (int k = k0; k < k1; ++k) {
@@ -178,9 +181,9 @@ stage_kernel(const StageArgs<T> a) {
       col(k + 2, wc);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T d1 = vanleer(wa[v], wb[v], wc[v]);
-        wl[v] = wa[v] + T(0.5) * dz[v];
-        wr[v] = wb[v] - T(0.5) * d1;
+        const T d1 = vanleer_half(wa[v], wb[v], wc[v]);
+        wl[v] = wa[v] + dz[v];
+        wr[v] = wb[v] - d1;
         dz[v] = d1;
       }
       hlle<T, 2>(wl, wr, P, f);
@@ -197,7 +200,7 @@ stage_kernel(const StageArgs<T> a) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const T* r = W + (v * WY + jj + 2) * WX + ii;
-          sdx[(v * TY + jj) * (TX + 2) + ii] = vanleer(r[0], r[1], r[2]);
+          sdx[(v * TY + jj) * (TX + 2) + ii] = vanleer_half(r[0], r[1], r[2]);
         }
       }
       for (int c = tid; c < TX * (TY + 2); c += NT) {   // x2 slopes, rows -1..TY
@@ -205,7 +208,7 @@ stage_kernel(const StageArgs<T> a) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const T* r = W + (v * WY + jj) * WX + ii + 2;
-          sdy[(v * (TY + 2) + jj) * TX + ii] = vanleer(r[0], r[WX], r[2 * WX]);
+          sdy[(v * (TY + 2) + jj) * TX + ii] = vanleer_half(r[0], r[WX], r[2 * WX]);
         }
       }
     }
@@ -220,8 +223,8 @@ stage_kernel(const StageArgs<T> a) {
         for (int v = 0; v < NV; ++v) {
           const T* r = W + (v * WY + jj + 2) * WX + f + 1;
           const T* s = sdx + (v * TY + jj) * (TX + 2) + f;
-          wl[v] = r[0] + T(0.5) * s[0];
-          wr[v] = r[1] - T(0.5) * s[1];
+          wl[v] = r[0] + s[0];
+          wr[v] = r[1] - s[1];
         }
         hlle<T, 0>(wl, wr, P, fl);
 #pragma unroll
@@ -234,8 +237,8 @@ stage_kernel(const StageArgs<T> a) {
         for (int v = 0; v < NV; ++v) {
           const T* r = W + (v * WY + g + 1) * WX + ii + 2;
           const T* s = sdy + (v * (TY + 2) + g) * TX + ii;
-          wl[v] = r[0] + T(0.5) * s[0];
-          wr[v] = r[WX] - T(0.5) * s[TX];
+          wl[v] = r[0] + s[0];
+          wr[v] = r[WX] - s[TX];
         }
         hlle<T, 1>(wl, wr, P, fl);
 #pragma unroll
@@ -245,21 +248,21 @@ stage_kernel(const StageArgs<T> a) {
     __syncthreads();
     // (G) flux divergence + SSPRK2 combination
     if (own) {
-      const size_t cell = bbase + (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
+      const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
       T unew[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const T dfx = sfx[(v * TY + ty) * (TX + 1) + tx + 1] - sfx[(v * TY + ty) * (TX + 1) + tx];
         const T dfy = sfy[(v * (TY + 1) + ty + 1) * TX + tx] - sfy[(v * (TY + 1) + ty) * TX + tx];
         const T L = -(dfx * idx1 + dfy * idx2 + (fzm[v] - fzlo[v]) * idx3);
-        const T ucur = a.Uin[cell + v * vstride];
-        if (a.stage == 1) {
+        const T ucur = Ub[cell + v * vstride];
+        if (J.stage == 1) {
           unew[v] = ucur + tdt * L;
         } else {
-          const T u0 = a.U0[cell + v * vstride];
+          const T u0 = J.U0b[cell + v * vstride];
           unew[v] = T(0.5) * u0 + T(0.5) * (ucur + tdt * L);
         }
-        a.Uout[cell + v * vstride] = unew[v];
+        J.Uoutb[cell + v * vstride] = unew[v];
       }
       if (a.face_rec) {  // two-level mesh: keep fluxes on fine-coarse faces
         const int* fr = a.face_rec + 6 * leaf;
@@ -276,7 +279,7 @@ stage_kernel(const StageArgs<T> a) {
         if (k == n3 - 1 && fr[5] >= 0)
           for (int v = 0; v < NV; ++v) capture(a, leaf, 5, i, j, v, fzm[v]);
       }
-      if (a.want_rate) {
+      if (J.want_rate) {
         cons_to_prim(unew, P, floors);
         const T r = wave_rate(unew, P, idx1, idx2, idx3);
         const double rd = (double)r;
@@ -284,6 +287,46 @@ stage_kernel(const StageArgs<T> a) {
       }
     }
   }
+  return rate;
+}
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+stage_kernel(const StageArgs<T> a) {
+  using SM = StageSmem<T, TX, TY>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+  const int tiles_per_block = a.ntile[0] * a.ntile[1] * a.ntile[2];
+  const int leaf = blockIdx.x / tiles_per_block;
+  if (leaf >= a.nleaf) return;
+  int t = blockIdx.x - leaf * tiles_per_block;
+  const int tk = t / (a.ntile[0] * a.ntile[1]);
+  t -= tk * a.ntile[0] * a.ntile[1];
+  const int tj = t / a.ntile[0];
+  const int ti = t - tj * a.ntile[0];
+  TileJob<T> J;
+  const size_t bsize = (size_t)NV * a.S[0] * a.S[1] * a.S[2];
+  J.Ub = a.Uin + (size_t)leaf * bsize;
+  J.U0b = a.U0 + (size_t)leaf * bsize;
+  J.Uoutb = a.Uout + (size_t)leaf * bsize;
+  for (int d = 0; d < 3; ++d) {
+    J.nx[d] = a.nx[d];
+    J.S[d] = a.S[d];
+  }
+  J.i0 = ti * TX;
+  J.j0 = tj * TY;
+  J.k0 = tk * a.KC;
+  J.k1 = min(J.k0 + a.KC, a.nx[2]);
+  const int lev = a.level ? (int)a.level[leaf] : 0;
+  J.idx1 = (T)a.idx[lev][0];
+  J.idx2 = (T)a.idx[lev][1];
+  J.idx3 = (T)a.idx[lev][2];
+  J.dt = (T)a.sc->dt_next;
+  J.stage = a.stage;
+  J.want_rate = a.want_rate;
+  J.leaf = leaf;
+  unsigned floors = 0;
+  const double rate = stage_tile<T, TX, TY>(J, a.P, a, smem_raw, floors);
   if (a.want_rate) block_max_to(&a.sc->wmax_bits, rate, red);
   if (floors) atomicAdd(&a.sc->floor_hits, (unsigned long long)floors);
 }
