@@ -122,6 +122,8 @@ def lib():
                                                 ctypes.c_int64, ctypes.c_int]),
                 "or_jvp": (None, [cfgp, dp, dp, ctypes.c_double, dp, ctypes.c_int, dp,
                                   ctypes.c_double, dp, dp]),
+                "or_jvp_state": (None, [cfgp, dp, dp, ctypes.c_double, ctypes.c_int, dp,
+                                        ctypes.c_double, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -256,6 +258,18 @@ def hlle(wl, wr, direction: int, gamma: float) -> np.ndarray:
 
 def morton(level, l1, l2, l3, max_level) -> int:
     return int(lib().or_morton(level, l1, l2, l3, max_level))
+
+
+def jvp_state(cfg: Config, U0, V, dgamma, dts, h=1e-30):
+    """Complex-step tangent J V of the final state (and the final state itself)."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    Uo = np.zeros_like(U0)
+    JV = np.zeros_like(U0)
+    lib().or_jvp_state(ctypes.byref(cfg), _dp(U0), _dp(V), dgamma, len(dts), _dp(dts), h, _dp(Uo),
+                       _dp(JV))
+    return Uo, JV
 
 
 def jvp(cfg: Config, U0, V, dgamma, rho_target, dts, h=1e-30):

@@ -176,4 +176,28 @@ void or_jvp(const Config* cfg, const double* U0, const double* V, double dgamma,
   *dJ = acc.imag() / h;
 }
 
+// Complex-step tangent of the whole final state: runs the uniform mesh for
+// ncycles with the frozen dt schedule from U0 + i h V (gamma + i h dgamma)
+// and writes the final interior state (real part) and J V (imaginary / h),
+// both in the interior layout [b][v][k][j][i].
+void or_jvp_state(const Config* cfg, const double* U0, const double* V, double dgamma,
+                  int ncycles, const double* dts, double h, double* U_out, double* JV_out) {
+  Mesh<cplx> m(*cfg);
+  m.gamma = cplx(cfg->gamma, h * dgamma);
+  copy_interior_in(m, U0, V, h);
+  for (int c = 0; c < ncycles; ++c) m.cycle_with_dt(dts[c]);
+  size_t n1 = cfg->nx[0], n2 = cfg->nx[1], n3 = cfg->nx[2];
+  size_t per = NVAR * n1 * n2 * n3;
+  for (size_t b = 0; b < m.leaf.size(); ++b)
+    for (int v = 0; v < NVAR; ++v)
+      for (size_t k = 0; k < n3; ++k)
+        for (size_t j = 0; j < n2; ++j)
+          for (size_t i = 0; i < n1; ++i) {
+            const cplx z = m.U[b][m.idx(v, (int)k + NG, (int)j + NG, (int)i + NG)];
+            const size_t s = b * per + ((v * n3 + k) * n2 + j) * n1 + i;
+            U_out[s] = z.real();
+            JV_out[s] = z.imag() / h;
+          }
+}
+
 }  // extern "C"

@@ -5,13 +5,13 @@
 // baseline leg use it.  It shares no code, header, table or constant with the
 // CUDA library; the two meet only through the seeded input generators.
 //
-// What it computes (arXiv:2202.12309, Sec. 5.1 "Parthenon-hydro"): the 3-D
+// What it computes (arXiv:2202.12309, Sec. 4.1 "Parthenon-hydro"): the 3-D
 // Euler equations of an ideal gas, advanced with a two-stage Runge-Kutta
 // integrator, piecewise-linear reconstruction and the HLLE Riemann solver, on
 // a mesh of equal-sized MeshBlocks arranged in an oct-tree (Sec. 2.1), with
 // ghost cells filled from neighbours, restriction/prolongation at level
-// boundaries and flux correction (Sec. 3.6), and a global CFL time step from a
-// min-reduction (Sec. 3.9).  The paper names the methods only; every choice it
+// boundaries and flux correction (Sec. 3.7), and a global CFL time step from a
+// min-reduction (Sec. 3.10).  The paper names the methods only; every choice it
 // leaves open is fixed here as one "reading", listed in the comments below and
 // in the design notes.  Everything is written in the order the method defines
 // it, one cell / one face at a time, with no blocking or fusion.
@@ -65,7 +65,7 @@ struct Config {
 };
 
 // ---------------------------------------------------------------------------
-// Pointwise physics (Sec. 5.1: Euler equations, ideal gas)
+// Pointwise physics (Sec. 4.1: Euler equations, ideal gas)
 // ---------------------------------------------------------------------------
 
 // Conserved U = (rho, m1, m2, m3, E) -> primitive W = (rho, v1, v2, v3, p).
@@ -86,7 +86,7 @@ inline void cons_to_prim(const R u[NVAR], R w[NVAR], const R& gamma, double dflo
   w[IEN] = p;
 }
 
-// Piecewise-linear reconstruction slope (Sec. 5.1 "piecewise linear
+// Piecewise-linear reconstruction slope (Sec. 4.1 "piecewise linear
 // reconstruction").  Reading: van Leer's harmonic limiter applied to each
 // primitive variable: delta = 2 dL dR / (dL + dR) where dL dR > 0, else 0.
 template <class R>
@@ -94,12 +94,14 @@ inline R vanleer(const R& wm, const R& w0, const R& wp) {
   R dl = w0 - wm;
   R dr = wp - w0;
   R prod = dl * dr;
-  if (re(prod) > 0.0) return 2.0 * prod / (dl + dr);
+  // branch on the real parts (for doubles this is prod > 0): with complex
+  // arguments Re(dl dr) would also carry -Im(dl) Im(dr)
+  if (re(dl) * re(dr) > 0.0) return 2.0 * prod / (dl + dr);
   return R(0.0);
 }
 
 // HLLE flux through a face with normal along `dir` (0,1,2) from the left and
-// right primitive states (Sec. 5.1 "HLLE Riemann solver").  Reading: Einfeldt's
+// right primitive states (Sec. 4.1 "HLLE Riemann solver").  Reading: Einfeldt's
 // wave-speed bounds with Roe-averaged velocity and enthalpy:
 //   b+ = max(0, vR + cR, v~ + c~),  b- = min(0, vL - cL, v~ - c~),
 //   F  = (b+ FL - b- FR + b+ b- (UR - UL)) / (b+ - b-).
@@ -157,7 +159,7 @@ inline void hlle_flux(const R wl[NVAR], const R wr[NVAR], int dir, const R& gamm
 // minmod of two one-sided differences (used by prolongation).
 template <class R>
 inline R minmod(const R& a, const R& b) {
-  if (re(a * b) > 0.0) return re(rabs(a)) < re(rabs(b)) ? a : b;
+  if (re(a) * re(b) > 0.0) return re(rabs(a)) < re(rabs(b)) ? a : b;
   return R(0.0);
 }
 
@@ -299,8 +301,8 @@ struct Mesh {
 
   // The composite field: the value of cell (I,J,K) of level L built from the
   // interior data of the leaves only (periodic wrap).  Same level: copy.
-  // Covered by finer leaves: restriction = mean of the 8 children (Sec. 3.6,
-  // "restricted first").  Covered by a coarser leaf: prolongation (Sec. 3.6,
+  // Covered by finer leaves: restriction = mean of the 8 children (Sec. 3.7,
+  // "restricted first").  Covered by a coarser leaf: prolongation (Sec. 3.7,
   // "interpolated (prolongated)"); reading: u_f = u_c + sum_d s_d minmod(
   // u_c - u_{c-e_d}, u_{c+e_d} - u_c), s_d = +-1/4, evaluated d = 1,2,3 in
   // order, with the coarse neighbours taken from the composite field.
@@ -357,7 +359,7 @@ struct Mesh {
            k < NG + cfg.nx[2];
   }
 
-  // Ghost exchange (Sec. 3.6): every ghost cell of every leaf (faces, edges and
+  // Ghost exchange (Sec. 3.7): every ghost cell of every leaf (faces, edges and
   // corners, all 26 neighbour regions) takes the composite-field value there.
   void fill_ghosts() {
     for (size_t b = 0; b < leaf.size(); ++b) {
@@ -420,7 +422,7 @@ struct Mesh {
     return F;
   }
 
-  // Flux correction (Sec. 3.6): at a face shared by a level-0 leaf and
+  // Flux correction (Sec. 3.7): at a face shared by a level-0 leaf and
   // level-1 leaves, the coarse flux is replaced by the mean of the 4 fine
   // fluxes over it (summed t1 inner, t2 outer).
   void flux_correct(std::vector<std::array<Fluxes, 3>>& F) {
@@ -470,12 +472,12 @@ struct Mesh {
     }
   }
 
-  // One stage of the two-stage Runge-Kutta integrator (Sec. 5.1).  Reading:
+  // One stage of the two-stage Runge-Kutta integrator (Sec. 4.1).  Reading:
   // SSPRK2 (Heun) in the form
   //   stage 1: U1 = U0 + dt L(U0)
   //   stage 2: U  = 0.5 U0 + 0.5 (U1 + dt L(U1))
   // with L(U) = -[(F1_{i+1/2}-F1_{i-1/2})/dx1 + (F2..)/dx2 + (F3..)/dx3],
-  // summed x1, then x2, then x3 (flux divergence, Sec. 3.6).
+  // summed x1, then x2, then x3 (flux divergence, Sec. 3.7).
   void stage(int which, const std::vector<std::vector<R>>& U0, double dtv) {
     std::vector<std::array<Fluxes, 3>> F(leaf.size());
     for (size_t b = 0; b < leaf.size(); ++b)
@@ -500,7 +502,7 @@ struct Mesh {
     }
   }
 
-  // CFL time step (Sec. 3.9, global min-reduction).  Reading:
+  // CFL time step (Sec. 3.10, global min-reduction).  Reading:
   // dt = cfl * min over interior cells of all leaves and d of dx_d/(|v_d|+c_s),
   // c_s = sqrt(gamma p / rho), in FP64, from the real part of the state.
   double compute_dt() {
@@ -572,7 +574,7 @@ struct Mesh {
     }
   }
 
-  // Rebuild the tree (Sec. 2.1/3.7): refine every +1 leaf into 8 children;
+  // Rebuild the tree (Sec. 2.1/3.8): refine every +1 leaf into 8 children;
   // merge 8 siblings that are all -1 and at least derefine_count cycles old
   // ("derefinement only allowed periodically").  New data is the composite
   // field of the old mesh at the new leaf's level, i.e. prolongation for new
@@ -636,7 +638,7 @@ struct Mesh {
     return true;
   }
 
-  // One driver cycle (Sec. 3.8 EvolutionDriver/MultiStageDriver): dt from the
+  // One driver cycle (Sec. 3.11 EvolutionDriver/MultiStageDriver): dt from the
   // current state, the two stages, then tagging and remesh when adaptive.
   void step_one() {
     double dtv = compute_dt();
