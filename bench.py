@@ -50,7 +50,7 @@ SM_MAX_MHZ = 2070.0
 #  and writes U0 (15 words): 25 words per zone-cycle, 12.5 per launch.
 WORDS_PER_ZONE_LAUNCH = 12.5
 #  flops: counted from the method, one flop per add/sub/mul/div/sqrt.
-FLOPS_PER_ZONE_CYCLE = 1235.0
+FLOPS_PER_ZONE_CYCLE = 1078.0
 
 
 def log(*a):
@@ -200,6 +200,74 @@ def roofline_for(v, pk, peak_kind):
             "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)"}
 
 
+def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0):
+    """64 independent blast-wave meshes, sizes 32^3..128^3 zones in 16^3 or
+    32^3 blocks (seeded), one persistent launch per cycle; autotuned."""
+    members = W.batch_members(seed=seed, nsim=nsim)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    cfgs, states, zones = [], [], 0
+    for mb in members:
+        nb = mb.n // mb.block
+        cfg = ph.make_config((mb.block,) * 3, (nb,) * 3, precision=precision)
+        cfgs.append(cfg)
+        geo = W.Geometry((mb.block,) * 3, (nb,) * 3)
+        m = ph.Mesh(cfg)
+        states.append(W.blast(geo, m.tree(), seed=mb.seed, center=mb.center, p_in=mb.p_in).astype(dtype))
+        m.close()
+        zones += mb.n ** 3
+    B = ph.Batch(cfgs)
+    for s, U in enumerate(states):
+        B.set_state(s, U)
+    t0 = time.perf_counter()
+    choice = B.autotune(1)
+    tune_s = time.perf_counter() - t0
+    B.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    B.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rc, floors, nonfinite = B.status()
+    B.close()
+    return {"workload": "batched: %d independent blast-wave meshes (sizes 32^3-128^3, blocks 16^3/32^3), "
+                        "one persistent launch per cycle" % nsim,
+            "precision": precision, "zones": zones, "ms_per_cycle": ms / steps,
+            "zone_cycles_per_s": zones * steps / (ms / 1e3), "launch": list(choice),
+            "autotune_s": tune_s, "status": rc, "floors": floors, "nonfinite": nonfinite}
+
+
+def adjoint_variant(ph, torch, precision, cycles=20, ckpt=5):
+    """Gradient of the L2 density loss after 20 cycles on 64^3 zones (8 blocks
+    of 32^3), checkpoint every 5: forward + recompute + reverse time."""
+    nx, nb = (32, 32, 32), (2, 2, 2)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    cfg = ph.make_config(nx, nb, precision=precision)
+    geo = W.Geometry(nx, nb)
+    m = ph.Mesh(cfg)
+    U0 = W.smooth_random_density(geo, m.tree(), seed=21).astype(dtype)
+    target = W.density_target(geo, m.tree(), seed=22)
+    m.set_state(U0)
+    m.step(cycles)
+    Uf = m.get_state()
+    dLdU = np.zeros_like(U0)
+    dLdU[:, 0] = 2.0 * (Uf[:, 0] - target)
+    m.adjoint(U0, dLdU, cycles, ckpt)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.adjoint(U0, dLdU, cycles, ckpt)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    m.close()
+    zones = 64 ** 3
+    return {"workload": "adjoint: 64^3 zones (8 blocks of 32^3), %d cycles, checkpoint every %d" % (cycles, ckpt),
+            "precision": precision, "seconds_per_gradient": dt,
+            "zone_cycles_per_s": zones * cycles / dt, "note": "forward + recomputation + reverse"}
+
+
 def e2e_variant(ph, torch, block, precision, steps, warmup):
     """Same metric through the public API with pinned host buffers: every step
     copies the state in (ph_set_state from host), runs one cycle and reads the
@@ -347,6 +415,14 @@ def main():
                 v["roofline"] = roofline_for(v, pk, peak_kind)
                 variants.append(v)
                 log("variant %s block %d: %.3e zone-cycles/s" % (prec, block, v["zone_cycles_per_s"]))
+        for prec in ("fp32", "fp64"):
+            v = batch_variant(ph, torch, prec, args.steps, args.warmup)
+            variants.append(v)
+            log("batched %s: %.3e zone-cycles/s, launch %s" % (prec, v["zone_cycles_per_s"], v["launch"]))
+        for prec in ("fp64", "fp32"):
+            v = adjoint_variant(ph, torch, prec)
+            variants.append(v)
+            log("adjoint %s: %.3f s per gradient" % (prec, v["seconds_per_gradient"]))
 
     e2e = None
     if not args.quick:

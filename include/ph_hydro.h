@@ -186,6 +186,29 @@ int ph_get_tile(const ph_mesh* mesh, int32_t tile[3]);
  * (PH_ERR_INVALID otherwise). */
 int ph_profile_cycles(ph_mesh* mesh, int32_t ncycles, double* ms_out, int32_t nslots);
 
+/* Advance a uniform mesh by ncycles with a prescribed dt per cycle (host
+ * array dts[ncycles]) instead of the CFL dt; synchronises every cycle. */
+int ph_step_dt(ph_mesh* mesh, int32_t ncycles, const double* dts);
+
+/* Gradient of a loss of the final state with respect to the initial
+ * conserved state and the adiabatic index (uniform meshes).  The paper has
+ * no adjoint; this is the reverse of the cycle described above (Sec. 4.1),
+ * with the dt schedule held fixed and the limiter / wave-speed / floor
+ * branches frozen at their forward values.
+ *   U0       initial interior state (layout of ph_set_state)
+ *   ncycles  cycles of the forward run; ckpt_every: keep every k-th state
+ *            and recompute the k cycles in between (memory ~ ncycles/k + 2k
+ *            states)
+ *   dts      host array of ncycles dts, or NULL to use (and freeze) the CFL
+ *            dts of the forward run
+ *   dLdU     dL/dU_final (interior layout); dLdU0 receives dL/dU0
+ *   dLdgamma receives dL/dgamma (may be NULL)
+ *   on_device: 1 if U0, dLdU and dLdU0 are device pointers
+ * The mesh is left at the final state of the forward run. */
+int ph_adjoint(ph_mesh* mesh, const void* U0, int32_t ncycles, int32_t ckpt_every,
+               const double* dts, const void* dLdU, void* dLdU0, double* dLdgamma,
+               int32_t on_device);
+
 /* ---------------------------------------------------------------------------
  * Batched independent meshes (one persistent launch per cycle).
  *

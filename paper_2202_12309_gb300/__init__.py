@@ -32,7 +32,7 @@ EXPORTS = [
     "ph_batch_create", "ph_batch_destroy", "ph_batch_num_blocks", "ph_batch_set_state",
     "ph_batch_get_state", "ph_batch_step", "ph_batch_get_dt", "ph_batch_get_time",
     "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
-    "ph_debug_barrier_timeout",
+    "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint",
 ]
 
 
@@ -150,6 +150,8 @@ def lib():
             "ph_batch_set_launch": [P, ctypes.POINTER(i32)],
             "ph_batch_autotune": [P, i32, ctypes.POINTER(i32)],
             "ph_debug_barrier_timeout": [P, i32, i64, ctypes.POINTER(i32)],
+            "ph_step_dt": [P, i32, dp],
+            "ph_adjoint": [P, P, i32, i32, dp, P, P, dp, i32],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -339,6 +341,37 @@ class Mesh:
                                        ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 5))
         return ms
 
+    def step_dt(self, dts):
+        """Cycles with prescribed dts (host array)."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        check(self.L.ph_step_dt(self.h, len(d), d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def adjoint(self, U0, dLdU, ncycles: int, ckpt_every: int = 5, dts=None, out=None):
+        """(dL/dU0, dL/dgamma) for a loss of the state after ncycles from U0.
+        U0, dLdU (and out) are numpy arrays or CUDA tensors in the interior
+        layout; dts fixes the dt schedule (None: the forward run's CFL dts)."""
+        if isinstance(U0, np.ndarray):
+            U0 = np.ascontiguousarray(U0, dtype=self.dtype)
+            dLdU = np.ascontiguousarray(dLdU, dtype=self.dtype)
+            if out is None:
+                out = np.zeros_like(U0)
+        elif out is None:
+            import torch
+            out = torch.empty_like(U0)
+        p0, dev = _ptr(U0)
+        pg, dev2 = _ptr(dLdU)
+        po, dev3 = _ptr(out)
+        assert dev == dev2 == dev3
+        dptr = None
+        if dts is not None:
+            dts = np.ascontiguousarray(dts, dtype=np.float64)
+            assert len(dts) == ncycles
+            dptr = dts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        g = ctypes.c_double()
+        check(self.L.ph_adjoint(self.h, ctypes.c_void_p(p0), int(ncycles), int(ckpt_every), dptr,
+                                ctypes.c_void_p(pg), ctypes.c_void_p(po), ctypes.byref(g), dev))
+        return out, g.value
+
     def tile(self):
         t = (ctypes.c_int32 * 3)()
         check(self.L.ph_get_tile(self.h, t))
@@ -442,3 +475,54 @@ def debug_barrier_timeout(nctas: int = 4, spin_limit: int = 1 << 16, stream: Opt
     rc = lib().ph_debug_barrier_timeout(ctypes.c_void_p(stream), int(nctas), int(spin_limit),
                                         ctypes.byref(g))
     return rc, g.value
+
+
+def _hydro_run_function():
+    import torch
+
+    class HydroRun(torch.autograd.Function):
+        """U_final = hydro(U0, gamma) over `ncycles` cycles of a uniform mesh.
+
+        forward: set_state + ncycles cycles (the CFL dts are recorded);
+        backward: ph_adjoint with that dt schedule (frozen) and
+        checkpoint-every-k recomputation: gradients w.r.t. U0 and gamma."""
+
+        @staticmethod
+        def forward(ctx, U0, gamma, cfg, ncycles, ckpt_every):
+            import copy
+            c = copy.copy(cfg)
+            c.gamma = float(gamma)
+            m = Mesh(c)
+            U0c = U0.detach().contiguous()
+            m.set_state(U0c)
+            dts = []
+            for _ in range(int(ncycles)):
+                m.step(1)
+                dts.append(m.dt())
+            out = torch.empty_like(U0c)
+            m.get_state(out)
+            ctx.save_for_backward(U0c)
+            ctx.cfg = c
+            ctx.ncycles = int(ncycles)
+            ctx.ckpt = int(ckpt_every)
+            ctx.dts = np.asarray(dts)
+            m.close()
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            (U0,) = ctx.saved_tensors
+            m = Mesh(ctx.cfg)
+            gU0, gg = m.adjoint(U0, gout.contiguous(), ctx.ncycles, ctx.ckpt, dts=ctx.dts)
+            m.close()
+            return gU0, torch.tensor(gg, dtype=torch.float64), None, None, None
+
+    return HydroRun
+
+
+def hydro_run(U0, gamma, cfg: Config, ncycles: int, ckpt_every: int = 5):
+    """Differentiable hydro run: see HydroRun (torch.autograd.Function)."""
+    global _HydroRun
+    if "_HydroRun" not in globals():
+        _HydroRun = _hydro_run_function()
+    return _HydroRun.apply(U0, gamma, cfg, ncycles, ckpt_every)

@@ -1,0 +1,757 @@
+// ph_adjoint.cu -- reverse mode of the uniform-mesh cycle: hand-written
+// adjoints of the fused stage (cons->prim, PLM, HLLE, divergence, SSPRK2) and
+// of the ghost exchange, with checkpoint-every-k recomputation.
+//
+// The paper has no adjoint; this follows the forward method of Sec. 4.1 line
+// by line in reverse.  Readings: the dt schedule of the forward run is held
+// fixed (not differentiated); limiter, wave-speed and floor branches are
+// frozen at their forward values (decided on the forward state exactly as
+// the forward decides them).
+//
+// For a stage  U_out = a U0 + b (U + dt L(U))  the reverse needs the
+// vector-Jacobian product of L.  L_i = -sum_d (F_{i+1/2} - F_{i-1/2}) / dx_d,
+// so the adjoint of the face flux F_f between cells a (left) and b (right) is
+//   Fbar_f = (mu_b - mu_a) / dx_d,
+// which flows back through HLLE to the face states, through
+// W_L = W_a + h_a, W_R = W_b - h_b to the cells and their half-slopes h, and
+// through each half-slope h_k = vl(W_{k-1}, W_k, W_{k+1}) to three cells;
+// finally W -> U by the transpose of the primitive Jacobian.  Three kernels
+// per direction/stage: faces (HLLE reverse), cells (gather of face and slope
+// contributions), primitives (W -> U).  The transpose of the ghost exchange
+// is a gather: an interior cell next to a block face receives the adjoint of
+// the face-ghost cell that copied it in the neighbouring block.  Everything
+// is a gather with one writer per output, so results are reproducible run to
+// run except for the gamma derivative, which is summed with atomics.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ph_hydro.h"
+#include "ph_internal.h"
+
+namespace ph {
+
+// ---------------------------------------------------------------------------
+// pointwise reverses
+// ---------------------------------------------------------------------------
+
+// Forward cons->prim with the branch flags the reverse needs.
+template <class T>
+__device__ __forceinline__ void prim_fwd(const T u[NV], const Phys<T>& P, T w[NV], bool& rf, bool& pf) {
+  T rho = u[0];
+  rf = rho < P.dfloor;
+  if (rf) rho = P.dfloor;
+  const T ir = T(1) / rho;
+  w[0] = rho;
+  w[1] = u[1] * ir;
+  w[2] = u[2] * ir;
+  w[3] = u[3] * ir;
+  T p = P.gm1 * (u[4] - T(0.5) * (u[1] * w[1] + u[2] * w[2] + u[3] * w[3]));
+  pf = p < P.pfloor;
+  if (pf) p = P.pfloor;
+  w[4] = p;
+}
+
+// Ubar = (dW/dU)^T Wbar; gamma adjoint of p = (gamma-1)(E - |m|^2/(2 rho)).
+template <class T>
+__device__ __forceinline__ void prim_rev(const T u[NV], const Phys<T>& P, const T wb[NV], T ub[NV],
+                                         double& gbar) {
+  bool rf, pf;
+  T w[NV];
+  prim_fwd(u, P, w, rf, pf);
+  const T rho = w[0], ir = T(1) / rho;
+  const T pb = pf ? T(0) : wb[4];
+  const T v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
+  // p = gm1 * (E - 0.5 rho_u |v|^2) with v = m / rho_used
+  T rb = rf ? T(0) : wb[0];
+  T mb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // dv_a/dm_a = 1/rho ; dp/dm_a = -gm1 v_a
+    mb[a] = wb[1 + a] * ir - pb * P.gm1 * w[1 + a];
+    // dv_a/drho = -v_a/rho ; only if rho is not floored
+    if (!rf) rb -= wb[1 + a] * w[1 + a] * ir;
+  }
+  if (!rf) rb += pb * P.gm1 * T(0.5) * v2;  // dp/drho = gm1 |v|^2 / 2
+  ub[0] = rb;
+  ub[1] = mb[0];
+  ub[2] = mb[1];
+  ub[3] = mb[2];
+  ub[4] = pb * P.gm1;
+  if (!pf) gbar += (double)pb * (double)(u[4] - T(0.5) * rho * v2);
+}
+
+// Half-slope and its partial derivatives (frozen branch dL dR > 0).
+template <class T>
+__device__ __forceinline__ T vl_half_d(T wm, T w0, T wp, T& dm, T& d0, T& dp) {
+  const T dl = w0 - wm, dr = wp - w0, prod = dl * dr;
+  if (!(prod > T(0))) {
+    dm = d0 = dp = T(0);
+    return T(0);
+  }
+  const T s = dl + dr, is2 = T(1) / (s * s);
+  const T ddl = dr * dr * is2, ddr = dl * dl * is2;
+  dm = -ddl;
+  d0 = ddl - ddr;
+  dp = ddr;
+  return prod / s;
+}
+
+// Reverse of the HLLE flux (same formulation as the forward kernel), with
+// Einfeldt's max/min and the Roe sound-speed clip frozen at their forward
+// choices.  Accumulates wlb, wrb (primitive adjoints) and gbar.
+template <class T, int DIR>
+__device__ void hlle_rev(const T wl[NV], const T wr[NV], const Phys<T>& P, const T fb[NV], T wlb[NV],
+                         T wrb[NV], double& gbar) {
+  constexpr int IN = 1 + DIR;
+  // ---- forward
+  const T rl = wl[0], pl = wl[4], rr = wr[0], pr = wr[4];
+  const T vnl = wl[IN], vnr = wr[IN];
+  const T v2l = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
+  const T v2r = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
+  const T el = pl * P.igm1 + T(0.5) * rl * v2l;
+  const T er = pr * P.igm1 + T(0.5) * rr * v2r;
+  const T ql = rsq(rl), qr = rsq(rr);
+  const T sl = rl * ql, sr = rr * qr;
+  const T irl = ql * ql, irr = qr * qr;
+  const T xl = P.gamma * pl * irl, xr = P.gamma * pr * irr;
+  const T cl = sq(xl), cr = sq(xr);
+  const T hl = (el + pl) * irl, hr = (er + pr) * irr;
+  const T isum = T(1) / (sl + sr);
+  const T wsl = sl * isum, wsr = sr * isum;
+  T u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) u[a] = wsl * wl[1 + a] + wsr * wr[1 + a];
+  const T hroe = wsl * hl + wsr * hr;
+  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T a2raw = P.gm1 * (hroe - T(0.5) * usq);
+  const bool a2pos = a2raw > T(0);
+  const T croe = sq(a2pos ? a2raw : T(0));
+  const T un = u[IN - 1];
+  const T A = vnr + cr, B = un + croe, C = vnl - cl, D = un - croe;
+  const bool AgeB = A >= B;
+  const T m1 = AgeB ? A : B;
+  const bool bp0 = T(0) >= m1;
+  const T bp = bp0 ? T(0) : m1;
+  const bool CleD = C <= D;
+  const T m2 = CleD ? C : D;
+  const bool bm0 = T(0) <= m2;
+  const T bm = bm0 ? T(0) : m2;
+  const T idb = T(1) / (bp - bm);
+  const T bpbm = bp * bm;
+  const T mfl = rl * vnl, mfr = rr * vnr;
+  T FL[NV], FR[NV], UL[NV], UR[NV];
+  FL[0] = mfl;
+  FR[0] = mfr;
+  UL[0] = rl;
+  UR[0] = rr;
+#pragma unroll
+  for (int a = 1; a <= 3; ++a) {
+    FL[a] = mfl * wl[a] + (a == IN ? pl : T(0));
+    FR[a] = mfr * wr[a] + (a == IN ? pr : T(0));
+    UL[a] = rl * wl[a];
+    UR[a] = rr * wr[a];
+  }
+  FL[4] = (el + pl) * vnl;
+  FR[4] = (er + pr) * vnr;
+  UL[4] = el;
+  UR[4] = er;
+  // ---- reverse
+  T bpb = 0, bmb = 0, bpbmb = 0, idbb = 0;
+  T FLb[NV], FRb[NV], ULb[NV], URb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T N = bp * FL[v] - bm * FR[v] + bpbm * (UR[v] - UL[v]);
+    idbb += fb[v] * N;
+    const T Nb = fb[v] * idb;
+    bpb += Nb * FL[v];
+    FLb[v] = Nb * bp;
+    bmb -= Nb * FR[v];
+    FRb[v] = -Nb * bm;
+    bpbmb += Nb * (UR[v] - UL[v]);
+    URb[v] = Nb * bpbm;
+    ULb[v] = -Nb * bpbm;
+  }
+  bpb += bpbmb * bm;
+  bmb += bpbmb * bp;
+  {
+    const T diffb = -idb * idb * idbb;
+    bpb += diffb;
+    bmb -= diffb;
+  }
+  T Ab = 0, Bb = 0, Cb = 0, Db = 0;
+  if (!bp0) {
+    if (AgeB) Ab = bpb; else Bb = bpb;
+  }
+  if (!bm0) {
+    if (CleD) Cb = bmb; else Db = bmb;
+  }
+  T vnrb = Ab, crb = Ab, unb = Bb + Db, croeb = Bb - Db, vnlb = Cb, clb = -Cb;
+  // fluxes and conserved states back to primitives
+  T rlb = 0, rrb = 0, plb = 0, prb = 0, elb = 0, erb = 0;
+  T vlb[3] = {0, 0, 0}, vrb[3] = {0, 0, 0};
+  T mflb = FLb[0], mfrb = FRb[0];
+  rlb += ULb[0];
+  rrb += URb[0];
+#pragma unroll
+  for (int a = 1; a <= 3; ++a) {
+    mflb += FLb[a] * wl[a];
+    vlb[a - 1] += FLb[a] * mfl;
+    mfrb += FRb[a] * wr[a];
+    vrb[a - 1] += FRb[a] * mfr;
+    if (a == IN) {
+      plb += FLb[a];
+      prb += FRb[a];
+    }
+    rlb += ULb[a] * wl[a];
+    vlb[a - 1] += ULb[a] * rl;
+    rrb += URb[a] * wr[a];
+    vrb[a - 1] += URb[a] * rr;
+  }
+  elb += FLb[4] * vnl + ULb[4];
+  plb += FLb[4] * vnl;
+  vnlb += FLb[4] * (el + pl);
+  erb += FRb[4] * vnr + URb[4];
+  prb += FRb[4] * vnr;
+  vnrb += FRb[4] * (er + pr);
+  rlb += mflb * vnl;
+  vnlb += mflb * rl;
+  rrb += mfrb * vnr;
+  vnrb += mfrb * rr;
+  // Roe sound speed
+  T a2b = (a2pos && croe > T(0)) ? croeb / (T(2) * croe) : T(0);
+  T hroeb = a2b * P.gm1;
+  const T usqb = -T(0.5) * P.gm1 * a2b;
+  gbar += (double)a2b * (double)(hroe - T(0.5) * usq);
+  T ub[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ub[a] = usqb * T(2) * u[a];
+  ub[IN - 1] += unb;
+  T wslb = hroeb * hl, wsrb = hroeb * hr;
+  T hlb = hroeb * wsl, hrb = hroeb * wsr;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    wslb += ub[a] * wl[1 + a];
+    vlb[a] += ub[a] * wsl;
+    wsrb += ub[a] * wr[1 + a];
+    vrb[a] += ub[a] * wsr;
+  }
+  T slb = wslb * isum, srb = wsrb * isum;
+  const T isumb = wslb * sl + wsrb * sr;
+  {
+    const T s_b = -isum * isum * isumb;
+    slb += s_b;
+    srb += s_b;
+  }
+  elb += hlb * irl;
+  plb += hlb * irl;
+  T irlb = hlb * (el + pl);
+  erb += hrb * irr;
+  prb += hrb * irr;
+  T irrb = hrb * (er + pr);
+  {
+    const T xlb = clb / (T(2) * cl), xrb = crb / (T(2) * cr);
+    gbar += (double)xlb * (double)(pl * irl) + (double)xrb * (double)(pr * irr);
+    plb += xlb * P.gamma * irl;
+    irlb += xlb * P.gamma * pl;
+    prb += xrb * P.gamma * irr;
+    irrb += xrb * P.gamma * pr;
+  }
+  T qlb = irlb * T(2) * ql + slb * rl;
+  rlb += slb * ql;
+  T qrb = irrb * T(2) * qr + srb * rr;
+  rrb += srb * qr;
+  rlb += qlb * (-T(0.5) * ql * ql * ql);
+  rrb += qrb * (-T(0.5) * qr * qr * qr);
+  // el = pl igm1 + rl v2l / 2
+  plb += elb * P.igm1;
+  rlb += elb * T(0.5) * v2l;
+  prb += erb * P.igm1;
+  rrb += erb * T(0.5) * v2r;
+  gbar += -(double)(elb * pl + erb * pr) * (double)(P.igm1 * P.igm1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    vlb[a] += elb * rl * wl[1 + a];
+    vrb[a] += erb * rr * wr[1 + a];
+  }
+  vlb[IN - 1] += vnlb;
+  vrb[IN - 1] += vnrb;
+  wlb[0] += rlb;
+  wrb[0] += rrb;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    wlb[1 + a] += vlb[a];
+    wrb[1 + a] += vrb[a];
+  }
+  wlb[4] += plb;
+  wrb[4] += prb;
+}
+
+// ---------------------------------------------------------------------------
+// kernels (uniform mesh, padded layout [leaf][v][k][j][i])
+// ---------------------------------------------------------------------------
+
+struct AdjGeom {
+  int nx[3], S[3];
+  int nleaf;
+  double idx[3];
+};
+
+__device__ __forceinline__ size_t cell_index(const AdjGeom& g, int k, int j, int i) {
+  return ((size_t)k * g.S[1] + j) * g.S[0] + i;
+}
+
+template <class T>
+__device__ __forceinline__ void load_u(const T* Ub, size_t vs, size_t c, T u[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) u[v] = Ub[v * vs + c];
+}
+
+__device__ __forceinline__ void block_sum_add(double v, double* dst) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+    if (s != 0.0) atomicAdd(dst, s);
+  }
+}
+
+// Faces along DIR: one thread per face (f in 0..n_d, other axes interior).
+// Writes the adjoints of the face's left and right primitive states at the
+// padded index of the right cell.
+template <class T, int DIR>
+__global__ void adj_faces_kernel(const T* __restrict__ U, const T* __restrict__ mu, T* FLb, T* FRb,
+                                 AdjGeom g, Phys<T> P, double* gbar_out) {
+  constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
+  const size_t per_leaf = (size_t)(g.nx[DIR] + 1) * g.nx[t1] * g.nx[t2];
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  double gbar = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_leaf * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int leaf = (int)(e / per_leaf);
+    size_t r = e - (size_t)leaf * per_leaf;
+    // face box: n_d + 1 faces along DIR, interior cells along the others, x1 fastest
+    int dims[3] = {g.nx[0], g.nx[1], g.nx[2]};
+    dims[DIR] += 1;
+    int bx[3];
+    bx[0] = (int)(r % dims[0]);
+    r /= dims[0];
+    bx[1] = (int)(r % dims[1]);
+    bx[2] = (int)(r / dims[1]);
+    const int f = bx[DIR];
+    int pos[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) pos[d] = (d == DIR) ? f : bx[d] + NG;  // along DIR: padded start of the stencil
+    const T* Ub = U + (size_t)leaf * NV * vs;
+    const T* mub = mu + (size_t)leaf * NV * vs;
+    size_t c[4];
+    for (int s = 0; s < 4; ++s) {
+      int q[3] = {pos[0], pos[1], pos[2]};
+      q[DIR] = f + s;
+      c[s] = cell_index(g, q[2], q[1], q[0]);
+    }
+    // c[1] = left cell a, c[2] = right cell b
+    T fb[NV];
+    bool any = false;
+    const T idx = (T)g.idx[DIR];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fb[v] = (mub[v * vs + c[2]] - mub[v * vs + c[1]]) * idx;
+      any |= fb[v] != T(0);
+    }
+    T wlb[NV] = {0, 0, 0, 0, 0}, wrb[NV] = {0, 0, 0, 0, 0};
+    if (any) {
+      T w[4][NV];
+      for (int s = 0; s < 4; ++s) {
+        T u[NV];
+        bool rf, pf;
+        load_u(Ub, vs, c[s], u);
+        prim_fwd(u, P, w[s], rf, pf);
+      }
+      T wl[NV], wr[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T d0, d1, d2;
+        wl[v] = w[1][v] + vl_half_d(w[0][v], w[1][v], w[2][v], d0, d1, d2);
+        wr[v] = w[2][v] - vl_half_d(w[1][v], w[2][v], w[3][v], d0, d1, d2);
+      }
+      hlle_rev<T, DIR>(wl, wr, P, fb, wlb, wrb, gbar);
+    }
+    T* FLo = FLb + (size_t)leaf * NV * vs;
+    T* FRo = FRb + (size_t)leaf * NV * vs;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      FLo[v * vs + c[2]] = wlb[v];
+      FRo[v * vs + c[2]] = wrb[v];
+    }
+  }
+  block_sum_add(gbar, gbar_out);
+}
+
+// Cells along DIR (padded 0..S-1, other axes interior): gather the face and
+// half-slope contributions into Wbar.  Face k+1/2 lives at padded index k+1
+// when 2 <= k+1 <= n+2.
+template <class T, int DIR>
+__global__ void adj_cells_kernel(const T* __restrict__ U, const T* __restrict__ FLb,
+                                 const T* __restrict__ FRb, T* Wbar, AdjGeom g, Phys<T> P) {
+  constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
+  const int Sd = g.S[DIR], n = g.nx[DIR];
+  const size_t per_leaf = (size_t)Sd * g.nx[t1] * g.nx[t2];
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_leaf * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int leaf = (int)(e / per_leaf);
+    size_t r = e - (size_t)leaf * per_leaf;
+    // cell box: the S_d padded cells along DIR, interior cells along the others
+    int dims[3] = {g.nx[0], g.nx[1], g.nx[2]};
+    dims[DIR] = Sd;
+    int bx[3];
+    bx[0] = (int)(r % dims[0]);
+    r /= dims[0];
+    bx[1] = (int)(r % dims[1]);
+    bx[2] = (int)(r / dims[1]);
+    const int p = bx[DIR];
+    int pos[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) pos[d] = (d == DIR) ? p : bx[d] + NG;
+    auto at = [&](int q) {
+      int qq[3] = {pos[0], pos[1], pos[2]};
+      qq[DIR] = q;
+      return cell_index(g, qq[2], qq[1], qq[0]);
+    };
+    const T* Ub = U + (size_t)leaf * NV * vs;
+    const T* FL = FLb + (size_t)leaf * NV * vs;
+    const T* FR = FRb + (size_t)leaf * NV * vs;
+    auto face_ok = [&](int q) { return q >= NG && q <= n + NG; };  // face stored at q
+    // primitives of cells p-2 .. p+2 that exist
+    T w[5][NV];
+    for (int s = 0; s < 5; ++s) {
+      const int q = p - 2 + s;
+      if (q < 0 || q >= Sd) continue;
+      T u[NV];
+      bool rf, pf;
+      load_u(Ub, vs, at(q), u);
+      prim_fwd(u, P, w[s], rf, pf);
+    }
+    T acc[NV] = {0, 0, 0, 0, 0};
+    // direct: left state of face p+1/2, right state of face p-1/2
+    if (face_ok(p + 1))
+      for (int v = 0; v < NV; ++v) acc[v] += FL[v * vs + at(p + 1)];
+    if (face_ok(p))
+      for (int v = 0; v < NV; ++v) acc[v] += FR[v * vs + at(p)];
+    // slopes of cells k = p-1, p, p+1 (each needs k-1 and k+1 in range)
+    for (int dk = -1; dk <= 1; ++dk) {
+      const int k = p + dk;
+      if (k < 1 || k > Sd - 2) continue;
+      T hb[NV];
+      bool nz = false;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        hb[v] = (face_ok(k + 1) ? FL[v * vs + at(k + 1)] : T(0)) - (face_ok(k) ? FR[v * vs + at(k)] : T(0));
+        nz |= hb[v] != T(0);
+      }
+      if (!nz) continue;
+      const int s = dk + 2;  // index of cell k in w[]
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T dm, d0, dp;
+        vl_half_d(w[s - 1][v], w[s][v], w[s + 1][v], dm, d0, dp);
+        // cell p is k+1 (dk=-1), k (dk=0) or k-1 (dk=+1) relative to slope k
+        acc[v] += hb[v] * (dk == -1 ? dp : (dk == 0 ? d0 : dm));
+      }
+    }
+    T* Wb = Wbar + (size_t)leaf * NV * vs;
+    const size_t cp = at(p);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wb[v * vs + cp] += acc[v];
+  }
+}
+
+// W -> U for every padded cell: acc += J^T Wbar; Wbar cleared.
+template <class T>
+__global__ void adj_prim_kernel(const T* __restrict__ U, T* Wbar, T* acc, AdjGeom g, Phys<T> P,
+                                double* gbar_out) {
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  double gbar = 0.0;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < vs * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int leaf = (int)(e / vs);
+    const size_t c = e - (size_t)leaf * vs;
+    const size_t base = (size_t)leaf * NV * vs + c;
+    T wb[NV];
+    bool nz = false;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wb[v] = Wbar[base + v * vs];
+      nz |= wb[v] != T(0);
+    }
+    if (!nz) continue;
+    T u[NV], ub[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = U[base + v * vs];
+    prim_rev(u, P, wb, ub, gbar);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      acc[base + v * vs] += ub[v];
+      Wbar[base + v * vs] = T(0);
+    }
+  }
+  block_sum_add(gbar, gbar_out);
+}
+
+// Transpose of the uniform ghost exchange: out = in on interior cells plus the
+// adjoints of the face-ghost images in the neighbouring blocks; 0 on ghosts.
+template <class T>
+__global__ void adj_ghost_t_kernel(const T* __restrict__ in, T* out, const int* __restrict__ nbr,
+                                   AdjGeom g) {
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  const int n1 = g.nx[0], n2 = g.nx[1], n3 = g.nx[2];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < vs * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int leaf = (int)(e / vs);
+    const size_t c = e - (size_t)leaf * vs;
+    const int i = (int)(c % g.S[0]);
+    const int j = (int)((c / g.S[0]) % g.S[1]);
+    const int k = (int)(c / ((size_t)g.S[0] * g.S[1]));
+    const bool interior = i >= NG && i < NG + n1 && j >= NG && j < NG + n2 && k >= NG && k < NG + n3;
+    T* o = out + (size_t)leaf * NV * vs + c;
+    if (!interior) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) o[v * vs] = T(0);
+      continue;
+    }
+    const T* ib = in + (size_t)leaf * NV * vs + c;
+    T s[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s[v] = ib[v * vs];
+    const int* nb = nbr + 27 * leaf;
+    // (offset to the neighbour, index of the image cell there) per axis
+    auto add = [&](int region, int ii, int jj, int kk) {
+      const T* src = in + (size_t)nb[region] * NV * vs + ((size_t)kk * g.S[1] + jj) * g.S[0] + ii;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s[v] += src[v * vs];
+    };
+    // region index (oz+1)*9 + (oy+1)*3 + (ox+1)
+    if (i < NG + 2) add(1 * 9 + 1 * 3 + 0, i + n1, j, k);            // -x neighbour's high ghosts
+    if (i >= n1) add(1 * 9 + 1 * 3 + 2, i - n1, j, k);               // +x neighbour's low ghosts
+    if (j < NG + 2) add(1 * 9 + 0 * 3 + 1, i, j + n2, k);
+    if (j >= n2) add(1 * 9 + 2 * 3 + 1, i, j - n2, k);
+    if (k < NG + 2) add(0 * 9 + 1 * 3 + 1, i, j, k + n3);
+    if (k >= n3) add(2 * 9 + 1 * 3 + 1, i, j, k - n3);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) o[v * vs] = s[v];
+  }
+}
+
+// out = alpha * x + beta * y (y may be null)
+template <class T>
+__global__ void adj_axpby_kernel(T* out, const T* x, T alpha, const T* y, T beta, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = alpha * x[e] + (y ? beta * y[e] : T(0));
+}
+
+}  // namespace ph
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int afail(int code, const std::string& msg) {
+  ph::set_error_message(msg.c_str());
+  return code;
+}
+#define PA_CUDA(expr)                                                              \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) return afail(PH_ERR_CUDA, std::string(#expr) + ": " +   \
+                                                         cudaGetErrorString(_e)); \
+  } while (0)
+
+int grid_for(size_t n) {
+  size_t g = (n + 255) / 256;
+  return (int)std::min<size_t>(std::max<size_t>(g, 1), 152 * 16);
+}
+
+}  // namespace
+
+namespace ph {
+
+
+template <class T>
+int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, T* Wbar, double* gbar) {
+  AdjGeom g;
+  for (int d = 0; d < 3; ++d) {
+    g.nx[d] = A.nx[d];
+    g.S[d] = A.nx[d] + 2 * NG;
+    g.idx[d] = A.idx[d];
+  }
+  g.nleaf = A.nleaf;
+  Phys<T> P;
+  P.gamma = (T)A.gamma;
+  P.gm1 = (T)(A.gamma - 1.0);
+  P.igm1 = (T)(1.0 / (A.gamma - 1.0));
+  P.dfloor = (T)A.dfloor;
+  P.pfloor = (T)A.pfloor;
+  cudaStream_t s = A.stream;
+  const size_t nfaces0 = (size_t)(A.nx[0] + 1) * A.nx[1] * A.nx[2] * A.nleaf;
+  const size_t ncell = (size_t)(A.nx[0] + 4) * A.nx[1] * A.nx[2] * A.nleaf;
+  const size_t all = A.block_elems / NV * A.nleaf;
+  adj_faces_kernel<T, 0><<<grid_for(nfaces0), 256, 0, s>>>(U, mu, FLb, FRb, g, P, gbar);
+  adj_cells_kernel<T, 0><<<grid_for(ncell), 256, 0, s>>>(U, FLb, FRb, Wbar, g, P);
+  adj_faces_kernel<T, 1><<<grid_for(nfaces0), 256, 0, s>>>(U, mu, FLb, FRb, g, P, gbar);
+  adj_cells_kernel<T, 1><<<grid_for(ncell), 256, 0, s>>>(U, FLb, FRb, Wbar, g, P);
+  adj_faces_kernel<T, 2><<<grid_for(nfaces0), 256, 0, s>>>(U, mu, FLb, FRb, g, P, gbar);
+  adj_cells_kernel<T, 2><<<grid_for(ncell), 256, 0, s>>>(U, FLb, FRb, Wbar, g, P);
+  adj_prim_kernel<T><<<grid_for(all), 256, 0, s>>>(U, Wbar, acc, g, P, gbar);
+  PA_CUDA(cudaGetLastError());
+  return PH_OK;
+}
+
+template <class T>
+int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* dts_in,
+              const void* dLdU, void* dLdU0, double* dLdgamma, int on_device) {
+  MeshAccess A;
+  int rc = mesh_access(m, &A);
+  if (rc) return rc;
+  cudaStream_t s = A.stream;
+  const size_t elems = A.block_elems * A.nleaf;  // padded state
+  const size_t bytes = elems * sizeof(T);
+  const int nseg = (ncycles + ckpt - 1) / ckpt;
+  std::vector<void*> bufs;
+  auto alloc = [&](size_t b) -> T* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, b ? b : 16) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return (T*)p;
+  };
+  auto cleanup = [&]() {
+    for (void* p : bufs) cudaFree(p);
+  };
+  T* lam = alloc(bytes);
+  T* acc0 = alloc(bytes);
+  T* acc1 = alloc(bytes);
+  T* tmp = alloc(bytes);
+  T* mu = alloc(bytes);
+  T* FLb = alloc(bytes);
+  T* FRb = alloc(bytes);
+  T* Wbar = alloc(bytes);
+  T* ufinal = alloc(bytes);
+  T* ck = alloc(bytes * nseg);
+  T* seg0 = alloc(bytes * ckpt);
+  T* seg1 = alloc(bytes * ckpt);
+  double* gbar = (double*)alloc(sizeof(double) * 2);
+  T* packed = alloc(sizeof(T) * (size_t)A.nleaf * NV * A.nx[0] * A.nx[1] * A.nx[2]);
+  for (void* p : bufs)
+    if (!p) {
+      cleanup();
+      return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
+    }
+  if (bufs.size() != 14) {
+    cleanup();
+    return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
+  }
+  const size_t count = (size_t)A.nleaf * NV * A.nx[0] * A.nx[1] * A.nx[2];
+  auto fail_clean = [&](int code) {
+    cleanup();
+    return code;
+  };
+  // ---- forward with checkpoints (records the dt schedule when not given)
+  if ((rc = mesh_set_state(m, U0, on_device))) return fail_clean(rc);
+  std::vector<double> dts(ncycles);
+  for (int c = 0; c < ncycles; ++c) {
+    if (c % ckpt == 0)
+      PA_CUDA(cudaMemcpyAsync(ck + (size_t)(c / ckpt) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+    if (dts_in) {
+      dts[c] = dts_in[c];
+      if ((rc = mesh_cycle_fixed_dt(m, dts[c]))) return fail_clean(rc);
+    } else if ((rc = mesh_cycle_read_dt(m, &dts[c]))) {
+      return fail_clean(rc);
+    }
+  }
+  PA_CUDA(cudaMemcpyAsync(ufinal, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+  // ---- seed: dL/dU_final on interior cells, zero ghosts
+  PA_CUDA(cudaMemsetAsync(lam, 0, bytes, s));
+  if (on_device) {
+    PA_CUDA(launch_pack<T>(lam, (T*)dLdU, A.nx, A.nleaf, 0, s));
+  } else {
+    PA_CUDA(cudaMemcpyAsync(packed, dLdU, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    PA_CUDA(launch_pack<T>(lam, packed, A.nx, A.nleaf, 0, s));
+  }
+  PA_CUDA(cudaMemsetAsync(gbar, 0, 2 * sizeof(double), s));
+  PA_CUDA(cudaMemsetAsync(FLb, 0, bytes, s));
+  PA_CUDA(cudaMemsetAsync(FRb, 0, bytes, s));
+  PA_CUDA(cudaMemsetAsync(Wbar, 0, bytes, s));
+  const int gE = grid_for(elems);
+  AdjGeom g;
+  for (int d = 0; d < 3; ++d) {
+    g.nx[d] = A.nx[d];
+    g.S[d] = A.nx[d] + 2 * NG;
+    g.idx[d] = A.idx[d];
+  }
+  g.nleaf = A.nleaf;
+  // ---- backward, segment by segment
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int c0 = sg * ckpt, c1 = std::min(c0 + ckpt, ncycles);
+    PA_CUDA(cudaMemcpyAsync(A.U0, ck + (size_t)sg * elems, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int c = c0; c < c1; ++c) {
+      PA_CUDA(cudaMemcpyAsync(seg0 + (size_t)(c - c0) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+      if ((rc = mesh_cycle_fixed_dt(m, dts[c]))) return fail_clean(rc);
+      PA_CUDA(cudaMemcpyAsync(seg1 + (size_t)(c - c0) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int c = c1 - 1; c >= c0; --c) {
+      const T* Un = seg0 + (size_t)(c - c0) * elems;
+      const T* U1n = seg1 + (size_t)(c - c0) * elems;
+      const T dt = (T)dts[c];
+      // stage 2: U = 1/2 U0 + 1/2 (U1 + dt L(U1))
+      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, T(0.5), nullptr, T(0), elems);
+      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc1, lam, T(0.5), nullptr, T(0), elems);
+      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, lam, T(0.5) * dt, nullptr, T(0), elems);
+      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, gbar))) return fail_clean(rc);
+      adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc1, tmp, A.nbr, g);
+      // stage 1: U1 = U0 + dt L(U0)
+      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, acc0, T(1), tmp, T(1), elems);
+      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, tmp, dt, nullptr, T(0), elems);
+      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, gbar))) return fail_clean(rc);
+      adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, A.nbr, g);
+      PA_CUDA(cudaGetLastError());
+    }
+  }
+  // ---- outputs; leave the mesh at the final state of the forward run
+  if (on_device) {
+    PA_CUDA(launch_pack<T>(lam, (T*)dLdU0, A.nx, A.nleaf, 1, s));
+  } else {
+    PA_CUDA(launch_pack<T>(lam, packed, A.nx, A.nleaf, 1, s));
+    PA_CUDA(cudaMemcpyAsync(dLdU0, packed, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+  }
+  double hg = 0.0;
+  PA_CUDA(cudaMemcpyAsync(&hg, gbar, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(cudaMemcpyAsync(A.U0, ufinal, bytes, cudaMemcpyDeviceToDevice, s));
+  PA_CUDA(cudaStreamSynchronize(s));
+  if (dLdgamma) *dLdgamma = hg;
+  cleanup();
+  return PH_OK;
+}
+
+}  // namespace ph
+
+extern "C" int ph_adjoint(ph_mesh* m, const void* U0, int32_t ncycles, int32_t ckpt_every,
+                          const double* dts, const void* dLdU, void* dLdU0, double* dLdgamma,
+                          int32_t on_device) {
+  if (!m || !U0 || !dLdU || !dLdU0 || ncycles < 1 || ckpt_every < 1)
+    return afail(PH_ERR_INVALID, "ph_adjoint: bad argument");
+  ph::MeshAccess A;
+  int rc = ph::mesh_access(m, &A);
+  if (rc) return rc;
+  return A.precision == PH_FP32
+             ? ph::adjoint_t<float>(m, U0, ncycles, ckpt_every, dts, dLdU, dLdU0, dLdgamma, on_device)
+             : ph::adjoint_t<double>(m, U0, ncycles, ckpt_every, dts, dLdU, dLdU0, dLdgamma, on_device);
+}

@@ -682,6 +682,19 @@ int tag_t(ph_mesh* m, int8_t* flags, double* mb) {
   return PH_OK;
 }
 
+// One uniform-mesh cycle with a prescribed dt (written into the device
+// scalars before the captured cycle runs).
+template <class T>
+int cycle_fixed_dt_t(ph_mesh* m, double dt) {
+  int rc;
+  if (!m->gexec)
+    if ((rc = capture_graph<T>(m))) return rc;
+  PH_CUDA(cudaMemcpyAsync(&m->sc->dt_next, &dt, sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  PH_CUDA(cudaGraphLaunch(m->gexec, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));  // dt lives on this stack frame
+  return PH_OK;
+}
+
 #define DISPATCH(m, fn, ...) \
   ((m)->cfg.precision == PH_FP32 ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
 
@@ -691,9 +704,63 @@ bool valid_tile(const ph_config* c, const int t[3]) {
 
 }  // namespace
 
+// ============================================================== adjoint access
+
+namespace ph {
+
+
+int mesh_access(ph_mesh* m, MeshAccess* out) {
+  if (m->two_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
+  out->U0 = m->U0;
+  out->U1 = m->U1;
+  out->nbr = m->d_nbr;
+  out->sc = m->sc;
+  out->stream = m->stream;
+  for (int d = 0; d < 3; ++d) {
+    out->nx[d] = m->nx[d];
+    out->idx[d] = 1.0 / m->dx(d, 0);
+  }
+  out->nleaf = m->nleaf();
+  out->block_elems = m->block_elems;
+  out->precision = m->cfg.precision;
+  out->gamma = m->cfg.gamma;
+  out->dfloor = m->cfg.dfloor;
+  out->pfloor = m->cfg.pfloor;
+  return PH_OK;
+}
+
+int mesh_set_state(ph_mesh* m, const void* U, int on_device) {
+  return DISPATCH(m, set_state_t, m, U, on_device);
+}
+
+int mesh_cycle_fixed_dt(ph_mesh* m, double dt) { return DISPATCH(m, cycle_fixed_dt_t, m, dt); }
+
+int mesh_cycle_read_dt(ph_mesh* m, double* dt) {
+  int rc = DISPATCH(m, step_t, m, 1);
+  if (rc) return rc;
+  DevScalars hs;
+  PH_CUDA(cudaMemcpyAsync(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost, m->stream));
+  PH_CUDA(cudaStreamSynchronize(m->stream));
+  *dt = hs.dt_last;
+  return PH_OK;
+}
+
+}  // namespace ph
+
 // ============================================================== C ABI
 
 extern "C" {
+
+int ph_step_dt(ph_mesh* m, int32_t ncycles, const double* dts) {
+  if (!m || (!dts && ncycles > 0) || ncycles < 0) return fail(PH_ERR_INVALID, "ph_step_dt: bad argument");
+  if (m->two_level) return fail(PH_ERR_INVALID, "ph_step_dt: uniform meshes only");
+  if (!m->state_set) return fail(PH_ERR_STATE, "ph_step_dt: set the state first");
+  for (int c = 0; c < ncycles; ++c) {
+    int rc = ph::mesh_cycle_fixed_dt(m, dts[c]);
+    if (rc) return rc;
+  }
+  return PH_OK;
+}
 
 int ph_set_allocator(ph_alloc_fn alloc, ph_free_fn release, void* ctx) {
   if ((alloc == nullptr) != (release == nullptr))

@@ -6,7 +6,29 @@
 
 #include "ph_device.cuh"
 
+struct ph_mesh;
+
 namespace ph {
+
+// What the adjoint needs of a uniform mesh (filled by ph_api.cu).
+struct MeshAccess {
+  void* U0;
+  void* U1;
+  const int* nbr;
+  DevScalars* sc;
+  cudaStream_t stream;
+  int nx[3];
+  int nleaf;
+  size_t block_elems;
+  int precision;
+  double gamma, dfloor, pfloor;
+  double idx[3];
+};
+int mesh_access(ph_mesh* m, MeshAccess* out);
+int mesh_set_state(ph_mesh* m, const void* U, int on_device);
+int mesh_cycle_fixed_dt(ph_mesh* m, double dt);   // one cycle with a prescribed dt
+int mesh_cycle_read_dt(ph_mesh* m, double* dt);   // one CFL cycle, returns its dt
+
 
 // Record the message that ph_last_error() returns on this thread.
 void set_error_message(const char* msg);
