@@ -3,7 +3,8 @@
 
 Workload (one "step" = one full cycle: two RK stages, two ghost exchanges,
 the dt reduction): a uniform 256^3-zone periodic mesh carrying a seeded
-linear sound wave of amplitude 1e-4 on rho=1, p=0.6 (gamma=5/3), split into
+linear sound wave of amplitude 1e-4 on rho=1, p=0.6 (gamma=5/3), travelling
+along the (1,1,1) diagonal, split into
 blocks of 16^3, 32^3 or 64^3 zones.  The headline is FP64 with 32^3 blocks;
 the other block sizes and the FP32 variant are reported under "variants".
 
@@ -129,15 +130,21 @@ def build_mesh(ph, block, precision, nbfac=1):
     return m, geo
 
 
-def wave_state(geo, leaves, dtype):
-    return W.linear_wave(geo, leaves, gamma=GAMMA, seed=0, amp=1e-4, kvec=(1, 0, 0)).astype(dtype)
+# Oblique wave vector: every variable varies along every axis, so no slope is
+# trivially zero (a wave along x1 leaves v2, v3 and every x2/x3 difference
+# exactly 0, which skips most limiter divisions).
+WAVE_K = (1, 1, 1)
 
 
-def time_variant(ph, torch, block, precision, steps, warmup):
+def wave_state(geo, leaves, dtype, kvec=WAVE_K):
+    return W.linear_wave(geo, leaves, gamma=GAMMA, seed=0, amp=1e-4, kvec=kvec).astype(dtype)
+
+
+def time_variant(ph, torch, block, precision, steps, warmup, kvec=WAVE_K):
     """Device-timed cycles of one variant; returns a dict."""
     m, geo = build_mesh(ph, block, precision)
     dtype = np.float32 if precision == "fp32" else np.float64
-    U = wave_state(geo, m.tree(), dtype)
+    U = wave_state(geo, m.tree(), dtype, kvec)
     m.set_state(U)
     zones = MESH ** 3
     stream = torch.cuda.current_stream()
@@ -155,6 +162,7 @@ def time_variant(ph, torch, block, precision, steps, warmup):
     rc, floors, nonfinite = m.status()
     res = {
         "block": block, "precision": precision, "nblocks": m.nblocks, "tile": list(m.tile()),
+        "wave_k": list(kvec),
         "ms_per_cycle": ms / steps, "zone_cycles_per_s": zones * steps / (ms / 1e3),
         "stage_ms_avg": float((prof[0] + prof[2]) / (2 * steps)),
         "ghost_ms_avg": float((prof[1] + prof[3]) / (2 * steps)),
@@ -238,6 +246,33 @@ def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0):
             "precision": precision, "zones": zones, "ms_per_cycle": ms / steps,
             "zone_cycles_per_s": zones * steps / (ms / 1e3), "launch": list(choice),
             "autotune_s": tune_s, "status": rc, "floors": floors, "nonfinite": nonfinite}
+
+
+def two_level_variant(ph, torch, steps, warmup):
+    """Blast wave on a two-level mesh: root 128^3 zones in 16^3 blocks, the
+    central cube of side 0.4 refined (static) plus adaptive refinement at a
+    density-gradient threshold of 0.05; FP64.  Each cycle reads the refinement
+    flags on the host, so the time is wall-clock around the cycles."""
+    nx, nb = (16, 16, 16), (8, 8, 8)
+    cfg = ph.make_config(nx, nb, max_level=1, static_region=1, adaptive=1)
+    m = ph.Mesh(cfg)
+    geo = W.Geometry(nx, nb)
+    m.set_state(W.blast(geo, m.tree(), seed=0))
+    m.step(warmup)
+    torch.cuda.synchronize()
+    zones = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        zones += m.nblocks * 16 ** 3
+        m.step(1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rc, floors, nonfinite = m.status()
+    nblocks = m.nblocks
+    m.close()
+    return {"workload": "two-level blast: root 128^3 in 16^3 blocks, static cube 0.4 + adaptive (0.05)",
+            "precision": "fp64", "leaves": nblocks, "zone_cycles_per_s": zones / dt,
+            "ms_per_cycle": dt / steps * 1e3, "status": rc, "floors": floors}
 
 
 def adjoint_variant(ph, torch, precision, cycles=20, ckpt=5):
@@ -415,10 +450,19 @@ def main():
                 v["roofline"] = roofline_for(v, pk, peak_kind)
                 variants.append(v)
                 log("variant %s block %d: %.3e zone-cycles/s" % (prec, block, v["zone_cycles_per_s"]))
+        for prec in ("fp64", "fp32"):
+            v = time_variant(ph, torch, args.block, prec, args.steps, args.warmup, kvec=(1, 0, 0))
+            v["roofline"] = roofline_for(v, pk, peak_kind)
+            v["workload"] = "wave along x1 only (v2, v3 and all x2/x3 differences exactly 0)"
+            variants.append(v)
+            log("variant %s x1-wave: %.3e zone-cycles/s" % (prec, v["zone_cycles_per_s"]))
         for prec in ("fp32", "fp64"):
             v = batch_variant(ph, torch, prec, args.steps, args.warmup)
             variants.append(v)
             log("batched %s: %.3e zone-cycles/s, launch %s" % (prec, v["zone_cycles_per_s"], v["launch"]))
+        v = two_level_variant(ph, torch, args.steps, args.warmup)
+        variants.append(v)
+        log("two-level: %.3e zone-cycles/s (%d leaves)" % (v["zone_cycles_per_s"], v["leaves"]))
         for prec in ("fp64", "fp32"):
             v = adjoint_variant(ph, torch, prec)
             variants.append(v)
@@ -451,8 +495,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_cycle"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": "uniform 256^3-zone periodic linear sound wave (A=1e-4), %d blocks "
-                               "of %d^3, 2 ghost zones, %s, 1 cycle per step"
+        "config": {"workload": "uniform 256^3-zone periodic linear sound wave (A=1e-4, k=2pi(1,1,1)), "
+                               "%d blocks of %d^3, 2 ghost zones, %s, 1 cycle per step"
                                % (nb, args.block, args.precision.upper()),
                    "zones": MESH ** 3, "block": args.block, "nblocks": nb, "tile": head["tile"],
                    "l2": "state %.0f MB > 129 MB L2: no flush needed"

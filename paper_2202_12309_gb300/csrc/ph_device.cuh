@@ -46,16 +46,42 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sq(double x) { return sqrt(x); }
 __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
 
+// Branch tests on FP64 values done with integer instructions: on GB300 an
+// FP64 compare occupies the FP64 pipe (1/64 of the FP32 rate), an integer
+// compare the ALU pipe.
+//   below_floor(x, f): x < f for a positive floor f (the bit patterns of
+//     doubles order like signed integers for f > 0; NaN is never below).
+//   same_sign_nonzero(a, b): a b > 0 (up to underflow of the product).
+__device__ __forceinline__ bool below_floor(double x, double f) {
+  return __double_as_longlong(x) < __double_as_longlong(f);
+}
+__device__ __forceinline__ bool below_floor(float x, float f) { return x < f; }
+__device__ __forceinline__ bool same_sign_nonzero(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return ((ia ^ ib) >= 0) && ((ia << 1) != 0) && ((ib << 1) != 0);
+}
+__device__ __forceinline__ bool same_sign_nonzero(float a, float b) { return a * b > 0.f; }
+// |x| within [2^-150, 2^150] (so that a product of five such values is a
+// normal number); integer test on the exponent field.
+__device__ __forceinline__ bool mid_range(double x) {
+  const int e = (__double2hiint(x) >> 20) & 0x7ff;
+  return e >= 1023 - 150 && e <= 1023 + 150;
+}
+__device__ __forceinline__ bool mid_range(float x) {
+  const int e = (__float_as_int(x) >> 23) & 0xff;
+  return e >= 127 - 20 && e <= 127 + 20;
+}
+
 // Conserved -> primitive in place: (rho, m1, m2, m3, E) -> (rho, v1, v2, v3, p),
 // with density and pressure floors (each application counted).
 template <class T>
 __device__ __forceinline__ void cons_to_prim(T w[NV], const Phys<T>& P, unsigned& floors) {
   T rho = w[0];
-  if (rho < P.dfloor) { rho = P.dfloor; ++floors; }
+  if (below_floor(rho, P.dfloor)) { rho = P.dfloor; ++floors; }
   const T ir = T(1) / rho;
   const T v1 = w[1] * ir, v2 = w[2] * ir, v3 = w[3] * ir;
   T p = P.gm1 * (w[4] - T(0.5) * (w[1] * v1 + w[2] * v2 + w[3] * v3));
-  if (p < P.pfloor) { p = P.pfloor; ++floors; }
+  if (below_floor(p, P.pfloor)) { p = P.pfloor; ++floors; }
   w[0] = rho;
   w[1] = v1;
   w[2] = v2;
@@ -70,6 +96,53 @@ template <class T>
 __device__ __forceinline__ T vanleer_half(T wm, T w0, T wp) {
   const T dl = w0 - wm, dr = wp - w0, prod = dl * dr;
   return prod > T(0) ? prod / (dl + dr) : T(0);
+}
+
+// The five half-slopes of one cell along one direction with one division:
+// 1/(dL+dR) of every variable comes from the reciprocal of their product
+// (Montgomery's simultaneous-inversion trick: prefix products, one
+// reciprocal, then one multiply back per factor).  Variables with dL dR <= 0
+// take the factor 1 and a zero slope.  If any factor is outside
+// [2^-150, 2^150] the product could leave the normal range, and the slopes
+// are divided one by one instead.  The reciprocals carry a few ulp of
+// rounding more than separate divisions.
+template <class T>
+__device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], const T wp[NV],
+                                              T h[NV]) {
+  T dl[NV], dr[NV], s[NV];
+  bool on[NV];
+  bool ok = true, any = false;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    dl[v] = w0[v] - wm[v];
+    dr[v] = wp[v] - w0[v];
+    on[v] = same_sign_nonzero(dl[v], dr[v]);
+    any = any || on[v];
+    s[v] = on[v] ? dl[v] + dr[v] : T(1);
+    ok = ok && mid_range(s[v]);
+  }
+  if (!any) {  // flat or extremal in every variable: no division at all
+#pragma unroll
+    for (int v = 0; v < NV; ++v) h[v] = T(0);
+  } else if (ok) {
+    T p[NV];
+    p[0] = s[0];
+#pragma unroll
+    for (int v = 1; v < NV; ++v) p[v] = p[v - 1] * s[v];
+    T inv = T(1) / p[NV - 1];
+    T is[NV];
+#pragma unroll
+    for (int v = NV - 1; v > 0; --v) {
+      is[v] = inv * p[v - 1];
+      inv = inv * s[v];
+    }
+    is[0] = inv;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) h[v] = on[v] ? (dl[v] * dr[v]) * is[v] : T(0);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) h[v] = on[v] ? (dl[v] * dr[v]) / s[v] : T(0);
+  }
 }
 
 // HLLE flux with Einfeldt's wave-speed bounds (Roe averages) through a face

@@ -152,11 +152,12 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     col(k0 - 1, wb);
     col(k0, wc);
     col(k0 + 1, wd);
+    T d0[NV];
+    vanleer_half5(wa, wb, wc, d0);
+    vanleer_half5(wb, wc, wd, dz);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const T d0 = vanleer_half(wa[v], wb[v], wc[v]);
-      dz[v] = vanleer_half(wb[v], wc[v], wd[v]);
-      wl[v] = wb[v] + d0;
+      wl[v] = wb[v] + d0[v];
       wr[v] = wc[v] - dz[v];
     }
     hlle<T, 2>(wl, wr, P, fzm);
@@ -179,12 +180,13 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       col(k, wa);
       col(k + 1, wb);
       col(k + 2, wc);
+      T d1[NV];
+      vanleer_half5(wa, wb, wc, d1);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T d1 = vanleer_half(wa[v], wb[v], wc[v]);
         wl[v] = wa[v] + dz[v];
-        wr[v] = wb[v] - d1;
-        dz[v] = d1;
+        wr[v] = wb[v] - d1[v];
+        dz[v] = d1[v];
       }
       hlle<T, 2>(wl, wr, P, f);
 #pragma unroll
@@ -197,19 +199,31 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       const T* W = ring + ((k + 4) & 3) * SM::PLANE;
       for (int c = tid; c < (TX + 2) * TY; c += NT) {   // x1 slopes, cells -1..TX
         const int jj = c / (TX + 2), ii = c - jj * (TX + 2);
+        T a[NV], b[NV], q[NV], h[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const T* r = W + (v * WY + jj + 2) * WX + ii;
-          sdx[(v * TY + jj) * (TX + 2) + ii] = vanleer_half(r[0], r[1], r[2]);
+          a[v] = r[0];
+          b[v] = r[1];
+          q[v] = r[2];
         }
+        vanleer_half5(a, b, q, h);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sdx[(v * TY + jj) * (TX + 2) + ii] = h[v];
       }
       for (int c = tid; c < TX * (TY + 2); c += NT) {   // x2 slopes, rows -1..TY
         const int jj = c / TX, ii = c - jj * TX;
+        T a[NV], b[NV], q[NV], h[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const T* r = W + (v * WY + jj) * WX + ii + 2;
-          sdy[(v * (TY + 2) + jj) * TX + ii] = vanleer_half(r[0], r[WX], r[2 * WX]);
+          a[v] = r[0];
+          b[v] = r[WX];
+          q[v] = r[2 * WX];
         }
+        vanleer_half5(a, b, q, h);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sdy[(v * (TY + 2) + jj) * TX + ii] = h[v];
       }
     }
     __syncthreads();

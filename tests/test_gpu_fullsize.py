@@ -1,0 +1,119 @@
+"""Parity at the workloads' full sizes, in the launch configurations the
+benchmark times.
+
+* uniform 256^3 zones in 512 blocks of 32^3 (the benchmark mesh, default
+  tile): one full cycle against the FP64 oracle, FP64 and FP32;
+* two-level blast, root 128^3 zones in 16^3 blocks with the static cube and
+  adaptive refinement (960 leaves): two cycles against the oracle, then 50
+  cycles of invariants (conservation, no floors, leaves tile the domain);
+* the 64-member batch as the benchmark autotunes it: a member of every size
+  matches its own single-mesh run bit for bit (single meshes are pinned to
+  the oracle above and in test_gpu_uniform)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from parity import describe, field_errors
+
+pytestmark = pytest.mark.gpu
+
+
+def _ph():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2202_12309_gb300 as ph
+    return ph
+
+
+@pytest.fixture(scope="module")
+def oracle_256():
+    nx, nb = (32, 32, 32), (8, 8, 8)
+    om = O.OracleMesh(O.make_config(nx, nb))
+    geo = W.Geometry(nx, nb)
+    U0 = W.linear_wave(geo, om.tree(), seed=0, amp=1e-4, kvec=(1, 1, 1))
+    om.set_state(U0)
+    dt = om.step(1)[0]
+    return U0, om.get_state(), dt, om.tree()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_uniform_256cube_one_cycle(oracle_256, precision):
+    ph = _ph()
+    U0, ref, odt, tree = oracle_256
+    m = ph.Mesh(ph.make_config((32, 32, 32), (8, 8, 8), precision=precision))
+    assert np.array_equal(m.tree(), tree)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    m.set_state(U0.astype(dtype))
+    m.step(1)
+    err = field_errors(m.get_state(), ref)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert err.max() <= tol, describe(err)
+    assert abs(m.dt() - odt) <= (1e-12 if precision == "fp64" else 1e-6) * odt
+    assert m.status()[0] == 0
+
+
+def test_two_level_blast_full_size():
+    ph = _ph()
+    nx, nb = (16, 16, 16), (8, 8, 8)
+    kw = dict(max_level=1, static_region=1, adaptive=1)
+    om = O.OracleMesh(O.make_config(nx, nb, **kw))
+    m = ph.Mesh(ph.make_config(nx, nb, **kw))
+    tree = m.tree()
+    assert np.array_equal(tree, om.tree())
+    assert len(tree) == 512 - 64 + 512
+    geo = W.Geometry(nx, nb)
+    U0 = W.blast(geo, tree, seed=0)
+    om.set_state(U0)
+    m.set_state(U0)
+    for c in range(2):
+        om.step(1)
+        m.step(1)
+        assert np.array_equal(m.tree(), om.tree())
+        err = field_errors(m.get_state(), om.get_state())
+        assert err.max() <= 1e-12, "cycle %d: %s" % (c, describe(err))
+    t0 = m.totals()
+    m.step(48)
+    t1 = m.totals()
+    assert np.all(np.abs(t1 - t0) <= 1e-12 * np.abs(t0).max()), t1 - t0
+    rc, floors, nonfinite = m.status()
+    assert rc == 0 and floors == 0 and nonfinite == 0
+    t, cyc = m.time()
+    assert cyc == 50
+    tree = m.tree()
+    cover = np.zeros((16, 16, 16), dtype=int)
+    for l, a, b, c in tree:
+        s = 2 if l == 0 else 1
+        a, b, c = (int(v) * s for v in (a, b, c))
+        cover[c:c + s, b:b + s, a:a + s] += 1
+    assert np.all(cover == 1)
+
+
+def test_batch_full_members_match_single_meshes():
+    ph = _ph()
+    mem = W.batch_members(seed=0, nsim=64)
+    cfgs, states = [], []
+    for mb in mem:
+        nb = mb.n // mb.block
+        cfg = ph.make_config((mb.block,) * 3, (nb,) * 3, precision="fp64")
+        cfgs.append(cfg)
+        geo = W.Geometry((mb.block,) * 3, (nb,) * 3)
+        states.append(W.blast(geo, ph.Mesh(cfg).tree(), seed=mb.seed, center=mb.center, p_in=mb.p_in))
+    B = ph.Batch(cfgs)
+    for s, U in enumerate(states):
+        B.set_state(s, U)
+    B.autotune(1)
+    B.step(3)
+    seen = set()
+    for s, mb in enumerate(mem):
+        key = (mb.n, mb.block)
+        if key in seen:
+            continue
+        seen.add(key)
+        m = ph.Mesh(cfgs[s])
+        m.set_state(states[s])
+        m.step(3)
+        assert np.array_equal(B.get_state(s), m.get_state()), key
+        m.close()
+    assert len(seen) >= 4
