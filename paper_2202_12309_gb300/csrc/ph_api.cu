@@ -109,6 +109,9 @@ struct ph_mesh {
   cudaGraphExec_t gexec = nullptr;
   int tile[3] = {0, 0, 0};
   bool state_set = false;
+  // tensor maps of the U0 and U1 pools for TMA plane staging (tma: usable)
+  CUtensorMap tm[2];
+  bool tma = false;
 
   std::vector<void*> owned;  // every device allocation, for destroy
 
@@ -326,6 +329,17 @@ int build_tables(ph_mesh* m) {
   return PH_OK;
 }
 
+// (Re)build the tensor maps after the pools change.
+void build_tmaps(ph_mesh* m) {
+  m->tma = ph::stage_tma_wanted() &&
+           ph::make_stage_tmap(&m->tm[0], m->U0, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1]) &&
+           ph::make_stage_tmap(&m->tm[1], m->U1, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1]);
+}
+
+const CUtensorMap* tmap_for(const ph_mesh* m, int stage) {
+  return m->tma ? &m->tm[stage == 1 ? 0 : 1] : nullptr;
+}
+
 int ensure_pools(ph_mesh* m, int n) {
   if ((size_t)n <= m->pool_cap && m->U0) return PH_OK;
   m->dfree(m->U0);
@@ -338,6 +352,7 @@ int ensure_pools(ph_mesh* m, int n) {
   PH_CUDA(cudaMemsetAsync(m->U0, 0, bytes, m->stream));
   PH_CUDA(cudaMemsetAsync(m->U1, 0, bytes, m->stream));
   m->pool_cap = (size_t)std::max(n, 1);
+  build_tmaps(m);
   return PH_OK;
 }
 
@@ -437,10 +452,10 @@ int refresh_dt_t(ph_mesh* m) {
 template <class T>
 int enqueue_uniform_cycle(ph_mesh* m, cudaStream_t s) {
   const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
-  PH_CUDA(ph::launch_stage<T>(a1, m->tile[0], m->tile[1], s));
+  PH_CUDA(ph::launch_stage<T>(a1, m->tile[0], m->tile[1], s, tmap_for(m, 1)));
   PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s));
   const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
-  PH_CUDA(ph::launch_stage<T>(a2, m->tile[0], m->tile[1], s));
+  PH_CUDA(ph::launch_stage<T>(a2, m->tile[0], m->tile[1], s, tmap_for(m, 2)));
   PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s));
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, s));
   return PH_OK;
@@ -486,7 +501,7 @@ int two_level_cycle(ph_mesh* m) {
   inv_dx(m, idx);
   for (int stage = 1; stage <= 2; ++stage) {
     const ph::StageArgs<T> a = stage_args<T>(m, stage);
-    PH_CUDA(ph::launch_stage<T>(a, m->tile[0], m->tile[1], m->stream));
+    PH_CUDA(ph::launch_stage<T>(a, m->tile[0], m->tile[1], m->stream, tmap_for(m, stage)));
     T* out = (T*)(stage == 1 ? m->U1 : m->U0);
     PH_CUDA(ph::launch_flux_correct<T>(out, m->d_corr_leaf, m->d_rec_beg, m->ncorr, m->d_rec_face,
                                        (const T*)m->d_fcc, (const T*)m->d_fcf, m->nx, idx[0],
@@ -551,6 +566,7 @@ int remesh_t(ph_mesh* m, std::vector<Leaf>& nl) {
   m->U0 = U0n;
   m->U1 = U1n;
   m->pool_cap = (size_t)std::max(nnew, 1);
+  build_tmaps(m);
   (void)old;
   if ((rc = build_tables(m))) return rc;
   if ((rc = fill_ghosts_t<T>(m, (T*)m->U0))) return rc;
@@ -582,11 +598,11 @@ int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
     const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
     const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
     cudaError_t e = cudaEventRecord(ev[0], m->stream);
-    if (!e) e = ph::launch_stage<T>(a1, m->tile[0], m->tile[1], m->stream);
+    if (!e) e = ph::launch_stage<T>(a1, m->tile[0], m->tile[1], m->stream, tmap_for(m, 1));
     if (!e) e = cudaEventRecord(ev[1], m->stream);
     if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream);
     if (!e) e = cudaEventRecord(ev[2], m->stream);
-    if (!e) e = ph::launch_stage<T>(a2, m->tile[0], m->tile[1], m->stream);
+    if (!e) e = ph::launch_stage<T>(a2, m->tile[0], m->tile[1], m->stream, tmap_for(m, 2));
     if (!e) e = cudaEventRecord(ev[3], m->stream);
     if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream);
     if (!e) e = cudaEventRecord(ev[4], m->stream);

@@ -136,7 +136,7 @@ __device__ void batch_stage_phase(const BatchArgs<T>& a, int stage, const StageA
     J.stage = stage;
     J.want_rate = stage == 2;
     J.leaf = g;
-    const double rate = stage_tile<T, TX, TY>(J, member_phys<T>(M), nocap, smem, floors);
+    const double rate = stage_tile<T, TX, TY, false>(J, member_phys<T>(M), nocap, smem, floors);
     if (stage == 2) block_max_to(&a.sc[m].wmax_bits, rate, red);
     __syncthreads();  // the next item's priming overwrites the ring
   }

@@ -1,6 +1,7 @@
 // ph_internal.h -- host-side declarations shared by the library's translation
 // units (not part of the public ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,8 +50,14 @@ template <class T>
 struct StageArgs;
 
 // K3: fused stage over all leaves.  Returns the launch error.
+// tmap: tensor map of the stencil input pool (TMA plane staging), or null
+// for plain loads.
 template <class T>
-cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s);
+cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s,
+                         const CUtensorMap* tmap = nullptr);
+bool make_stage_tmap(CUtensorMap* out, const void* base, size_t esize, const int S[3], int nleaf, int TX,
+                     int TY);
+bool stage_tma_wanted();  // false when PH_STAGE_LOADS=plain
 template <class T>
 size_t stage_smem_bytes(int TX, int TY);
 bool stage_tile_supported(int TX, int TY);

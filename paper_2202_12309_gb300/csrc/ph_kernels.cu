@@ -8,10 +8,15 @@
 // single pull: each ghost cell reads the data it needs straight from the
 // interior of the leaf that covers it.  It reads interior cells only and
 // writes ghost cells only, so one launch has no ordering hazard.
+#include <algorithm>
+
 #include "ph_internal.h"
 
 namespace ph {
 
+// blockIdx.x = leaf, blockIdx.y = chunk of the leaf's ghost shell (each CTA
+// copies about 1024 ghost cells, so that small meshes of large blocks still
+// fill the GPU).
 template <class T>
 __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx) {
   const int nxa[3] = {nx.x, nx.y, nx.z};
@@ -22,7 +27,9 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx)
   T* dstb = U + (size_t)b * NV * vs;
   const int* nb = nbr + 27 * b;
   const int total = sh.count();
-  for (int c = threadIdx.x; c < total; c += blockDim.x) {
+  const int per = (total + gridDim.y - 1) / gridDim.y;
+  const int c0 = blockIdx.y * per, c1 = min(total, c0 + per);
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     int i, j, k;
     sh.cell(c, i, j, k);
     const int ox = i < NG ? -1 : (i >= NG + nx.x ? 1 : 0);
@@ -40,7 +47,10 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx)
 template <class T>
 cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s) {
   if (nleaf <= 0) return cudaSuccess;
-  ghost_uniform_kernel<T><<<nleaf, 256, 0, s>>>(U, nbr, make_int3(nx[0], nx[1], nx[2]));
+  const long long S1 = nx[0] + 2 * NG, S2 = nx[1] + 2 * NG, S3 = nx[2] + 2 * NG;
+  const long long shell = S1 * S2 * S3 - (long long)nx[0] * nx[1] * nx[2];
+  const int chunks = (int)std::min<long long>(64, std::max<long long>(1, (shell + 1023) / 1024));
+  ghost_uniform_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(U, nbr, make_int3(nx[0], nx[1], nx[2]));
   return cudaGetLastError();
 }
 

@@ -1,4 +1,11 @@
-// ph_stage.cu -- instantiations and launcher of the fused stage kernel (K3).
+// ph_stage.cu -- instantiations and launchers of the fused stage kernel (K3),
+// and the tensor maps its TMA variant copies planes with.
+#include <cuda.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
 #include "ph_internal.h"
 #include "ph_stage.cuh"
 
@@ -20,7 +27,10 @@ size_t stage_smem_bytes(int TX, int TY) {
 
 template <class T, int TX, int TY>
 static cudaError_t configure_tile() {
-  return cudaFuncSetAttribute(stage_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)StageSmem<T, TX, TY>::bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(stage_kernel_tma<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)StageSmem<T, TX, TY>::bytes);
 }
 
@@ -40,25 +50,81 @@ cudaError_t configure_stage_kernels() {
 }
 
 template <class T, int TX, int TY>
-static cudaError_t launch_tile(const StageArgs<T>& a, cudaStream_t s) {
+static cudaError_t launch_tile(const StageArgs<T>& a, const CUtensorMap* tmap, cudaStream_t s) {
   const size_t smem = StageSmem<T, TX, TY>::bytes;
   const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
   if (grid == 0) return cudaSuccess;
-  stage_kernel<T, TX, TY><<<grid, TX * TY, smem, s>>>(a);
+  if (tmap)
+    stage_kernel_tma<T, TX, TY><<<grid, TX * TY, smem, s>>>(a, *tmap);
+  else
+    stage_kernel<T, TX, TY><<<grid, TX * TY, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s) {
-  if (TX == 8 && TY == 8) return launch_tile<T, 8, 8>(a, s);
-  if (TX == 16 && TY == 8) return launch_tile<T, 16, 8>(a, s);
-  if (TX == 16 && TY == 16) return launch_tile<T, 16, 16>(a, s);
-  if (TX == 32 && TY == 8) return launch_tile<T, 32, 8>(a, s);
+cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s, const CUtensorMap* tmap) {
+  if (TX == 8 && TY == 8) return launch_tile<T, 8, 8>(a, tmap, s);
+  if (TX == 16 && TY == 8) return launch_tile<T, 16, 8>(a, tmap, s);
+  if (TX == 16 && TY == 16) return launch_tile<T, 16, 16>(a, tmap, s);
+  if (TX == 32 && TY == 8) return launch_tile<T, 32, 8>(a, tmap, s);
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, cudaStream_t);
-template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t);
+// ---------------------------------------------------------------- tensor maps
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+}  // namespace
+
+bool stage_tma_wanted() {
+  const char* e = std::getenv("PH_STAGE_LOADS");
+  return !(e && std::strcmp(e, "plain") == 0);
+}
+
+// Tensor map over a pool of padded blocks [leaf][v][k][j][i] seen as a 4-D
+// tensor (S1, S2, S3, 5 * nleaf) with box (TX+4, TY+4, 1, 5).  Returns false
+// (and the stage kernel keeps its plain loads) when the layout breaks a TMA
+// rule: rows of S1 elements must be a multiple of 16 bytes, as must the box
+// rows and the base address.
+bool make_stage_tmap(CUtensorMap* out, const void* base, size_t esize, const int S[3], int nleaf, int TX,
+                     int TY) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !base || nleaf <= 0) return false;
+  if (((size_t)S[0] * esize) % 16 || ((size_t)(TX + 4) * esize) % 16) return false;
+  if (reinterpret_cast<uintptr_t>(base) % 16) return false;
+  if (TY + 4 > 256 || TX + 4 > 256) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)S[0], (cuuint64_t)S[1], (cuuint64_t)S[2], (cuuint64_t)NV * nleaf};
+  cuuint64_t strides[3] = {(cuuint64_t)S[0] * esize, (cuuint64_t)S[0] * S[1] * esize,
+                           (cuuint64_t)S[0] * S[1] * S[2] * esize};
+  cuuint32_t box[4] = {(cuuint32_t)(TX + 4), (cuuint32_t)(TY + 4), 1, (cuuint32_t)NV};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  std::memset(out, 0, sizeof(*out));
+  CUresult r = fn(out, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, cudaStream_t,
+                                          const CUtensorMap*);
+template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t,
+                                         const CUtensorMap*);
 template size_t stage_smem_bytes<double>(int, int);
 template size_t stage_smem_bytes<float>(int, int);
 

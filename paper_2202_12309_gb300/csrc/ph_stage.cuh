@@ -17,6 +17,7 @@
 // once per tile plus halo.
 #pragma once
 #include "ph_device.cuh"
+#include "ph_tma.cuh"
 
 namespace ph {
 
@@ -65,14 +66,18 @@ __device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int fac
 template <class T, int TX, int TY>
 struct StageSmem {
   static constexpr int WX = TX + 4, WY = TY + 4;
-  static constexpr int PLANE = NV * WX * WY;          // one primitive plane
+  static constexpr int PLANE = NV * WX * WY;          // one plane of 5 variables with halo
+  static constexpr int SLOT = (PLANE * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
+  static constexpr unsigned PLANE_BYTES = PLANE * sizeof(T);  // one TMA box
   static constexpr int DXN = NV * TY * (TX + 2);      // x1 slopes
   static constexpr int DYN = NV * (TY + 2) * TX;      // x2 slopes
   static constexpr int FXN = NV * TY * (TX + 1);      // x1 face fluxes
   static constexpr int FYN = NV * (TY + 1) * TX;      // x2 face fluxes
-  static constexpr size_t body = sizeof(T) * (size_t)(4 * PLANE + DXN + DYN + FXN + FYN);
+  static constexpr size_t body = sizeof(T) * (size_t)(4 * SLOT + DXN + DYN + FXN + FYN);
   static constexpr size_t red_off = (body + 15) / 16 * 16;
-  static constexpr size_t bytes = red_off + 32 * sizeof(double);
+  static constexpr size_t bar_off = red_off + 32 * sizeof(double);
+  // + 4 mbarriers, + slack to align the base to 128 bytes (TMA destinations)
+  static constexpr size_t bytes = bar_off + 4 * sizeof(uint64_t) + 128;
 };
 
 // One tile of one block for one stage.  J holds the block's data pointers,
@@ -93,15 +98,21 @@ struct TileJob {
   int leaf;        // leaf index for flux capture (two-level meshes)
 };
 
-template <class T, int TX, int TY>
+// TMA = true: planes arrive by one tensor copy each (tmap over the stencil
+// input pool, box (TX+4, TY+4, 1, 5) at (i0, j0, plane, vz0)), issued one plane
+// ahead on the slot's mbarrier, and are converted to primitives in place.
+// Returns with *failed set (and every thread leaving) if a wait gave up.
+template <class T, int TX, int TY, bool TMA>
 __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>& P,
                                              const StageArgs<T>& a, unsigned char* smem_raw,
-                                             unsigned& floors) {
+                                             unsigned& floors, const CUtensorMap* tmap = nullptr,
+                                             int vz0 = 0, uint64_t* bars = nullptr,
+                                             int* failed = nullptr) {
   using SM = StageSmem<T, TX, TY>;
   constexpr int NT = TX * TY;
   constexpr int WX = SM::WX, WY = SM::WY;
   T* ring = reinterpret_cast<T*>(smem_raw);
-  T* sdx = ring + 4 * SM::PLANE;
+  T* sdx = ring + 4 * SM::SLOT;
   T* sdy = sdx + SM::DXN;
   T* sfx = sdy + SM::DYN;
   T* sfy = sfx + SM::FXN;
@@ -119,7 +130,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   // Stage plane p (interior index, -2..n3+1) into its ring slot as primitives.
   // Cells past a ragged block edge are clamped to the edge (never used).
   auto load_plane = [&](int p) {
-    T* dst = ring + ((p + 4) & 3) * SM::PLANE;
+    T* dst = ring + ((p + 4) & 3) * SM::SLOT;
     const size_t kofs = (size_t)(p + NG) * S2 * S1;
     for (int c = tid; c < WX * WY; c += NT) {
       const int jj = c / WX, ii = c - jj * WX;
@@ -133,18 +144,62 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       for (int v = 0; v < NV; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
     }
   };
+  // TMA path: issue the copy of plane p (one thread), then convert it in
+  // place once its barrier completes (all threads).  Cells of a ragged tile
+  // outside the padded block arrive as zeros and are left alone (no valid
+  // cell's stencil reaches them).
+  unsigned parity = 0;  // bit s: parity of the next completion of slot s
+  auto issue = [&](int p) {
+    if (TMA && tid == 0) {
+      const int sl = (p + 4) & 3;
+      mbar_expect_tx(bars + sl, SM::PLANE_BYTES);
+      tma_load_4d(ring + sl * SM::SLOT, tmap, bars + sl, J.i0, J.j0, p + NG, vz0);
+    }
+  };
+  auto convert = [&](int p) -> bool {
+    const int sl = (p + 4) & 3;
+    const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
+    parity ^= 1u << sl;
+    T* dst = ring + sl * SM::SLOT;
+    const int vi = min(WX, S1 - i0), vj = min(WY, S2 - j0);
+    for (int c = tid; c < WX * WY; c += NT) {
+      const int jj = c / WX, ii = c - jj * WX;
+      if (ii >= vi || jj >= vj) continue;
+      T w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = dst[(v * WY + jj) * WX + ii];
+      cons_to_prim(w, P, floors);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
+    }
+    return ok;
+  };
+  // every thread reports a failed wait; all leave together after a barrier
+  auto check_failed = [&](bool ok) -> bool {
+    if (!ok) atomicExch(failed, 1);
+    __syncthreads();
+    return *(volatile int*)failed != 0;
+  };
   auto col = [&](int p, T w[NV]) {  // own column's primitive at plane p
-    const T* s = ring + ((p + 4) & 3) * SM::PLANE;
+    const T* s = ring + ((p + 4) & 3) * SM::SLOT;
 #pragma unroll
     for (int v = 0; v < NV; ++v) w[v] = s[(v * WY + ty + 2) * WX + tx + 2];
   };
 
   // Priming: planes k0-2 .. k0+1 give the x3 slope at k0 and the flux at k0-1/2.
-  load_plane(k0 - 2);
-  load_plane(k0 - 1);
-  load_plane(k0);
-  load_plane(k0 + 1);
-  __syncthreads();
+  if (TMA) {
+    for (int p = k0 - 2; p <= k0 + 1; ++p) issue(p);
+    bool ok = true;
+    for (int p = k0 - 2; p <= k0 + 1; ++p) ok = convert(p) && ok;
+    fence_proxy_async_smem();
+    if (check_failed(ok)) return 0.0;
+  } else {
+    load_plane(k0 - 2);
+    load_plane(k0 - 1);
+    load_plane(k0);
+    load_plane(k0 + 1);
+    __syncthreads();
+  }
   T dz[NV], fzm[NV];
   {
     T wa[NV], wb[NV], wc[NV], wd[NV], wl[NV], wr[NV];
@@ -163,6 +218,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     hlle<T, 2>(wl, wr, P, fzm);
   }
   __syncthreads();
+  if (TMA && k0 + 2 <= k1 + 1) issue(k0 + 2);  // into the slot of plane k0-2, read above
 
   const int i = i0 + tx, j = j0 + ty;
   const bool own = (i < n1) && (j < n2);
@@ -171,8 +227,16 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 
   for (int k = k0; k < k1; ++k) {
     // (A) next plane in
-    load_plane(k + 2);
-    __syncthreads();
+    if (TMA) {
+      const bool ok = convert(k + 2);
+      fence_proxy_async_smem();
+      if (check_failed(ok)) return 0.0;
+      // plane k+3 goes to the slot of plane k-1, which step k no longer reads
+      if (k + 3 <= k1 + 1) issue(k + 3);
+    } else {
+      load_plane(k + 2);
+      __syncthreads();
+    }
     // (C) slopes; own x3 flux
     T fzlo[NV];  // x3 flux below the cell; fzm becomes the flux above it
     {
@@ -196,7 +260,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       }
     }
     {
-      const T* W = ring + ((k + 4) & 3) * SM::PLANE;
+      const T* W = ring + ((k + 4) & 3) * SM::SLOT;
       for (int c = tid; c < (TX + 2) * TY; c += NT) {   // x1 slopes, cells -1..TX
         const int jj = c / (TX + 2), ii = c - jj * (TX + 2);
         T a[NV], b[NV], q[NV], h[NV];
@@ -229,7 +293,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     __syncthreads();
     // (E) x1 and x2 face fluxes of the plane
     {
-      const T* W = ring + ((k + 4) & 3) * SM::PLANE;
+      const T* W = ring + ((k + 4) & 3) * SM::SLOT;
       for (int c = tid; c < (TX + 1) * TY; c += NT) {
         const int jj = c / (TX + 1), f = c - jj * (TX + 1);  // face between cells f-1, f
         T wl[NV], wr[NV], fl[NV];
@@ -305,20 +369,15 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 }
 
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
-stage_kernel(const StageArgs<T> a) {
-  using SM = StageSmem<T, TX, TY>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+__device__ __forceinline__ bool make_job(const StageArgs<T>& a, TileJob<T>& J) {
   const int tiles_per_block = a.ntile[0] * a.ntile[1] * a.ntile[2];
   const int leaf = blockIdx.x / tiles_per_block;
-  if (leaf >= a.nleaf) return;
+  if (leaf >= a.nleaf) return false;
   int t = blockIdx.x - leaf * tiles_per_block;
   const int tk = t / (a.ntile[0] * a.ntile[1]);
   t -= tk * a.ntile[0] * a.ntile[1];
   const int tj = t / a.ntile[0];
   const int ti = t - tj * a.ntile[0];
-  TileJob<T> J;
   const size_t bsize = (size_t)NV * a.S[0] * a.S[1] * a.S[2];
   J.Ub = a.Uin + (size_t)leaf * bsize;
   J.U0b = a.U0 + (size_t)leaf * bsize;
@@ -339,8 +398,50 @@ stage_kernel(const StageArgs<T> a) {
   J.stage = a.stage;
   J.want_rate = a.want_rate;
   J.leaf = leaf;
+  return true;
+}
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+stage_kernel(const StageArgs<T> a) {
+  using SM = StageSmem<T, TX, TY>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+  TileJob<T> J;
+  if (!make_job<T, TX, TY>(a, J)) return;
   unsigned floors = 0;
-  const double rate = stage_tile<T, TX, TY>(J, a.P, a, smem_raw, floors);
+  const double rate = stage_tile<T, TX, TY, false>(J, a.P, a, smem_raw, floors);
+  if (a.want_rate) block_max_to(&a.sc->wmax_bits, rate, red);
+  if (floors) atomicAdd(&a.sc->floor_hits, (unsigned long long)floors);
+}
+
+// The same stage with planes staged by TMA from the tensor map of the stencil
+// input pool.
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__ CUtensorMap tmap) {
+  using SM = StageSmem<T, TX, TY>;
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + SM::bar_off);
+  __shared__ int failed;
+  TileJob<T> J;
+  if (!make_job<T, TX, TY>(a, J)) return;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int s = 0; s < 4; ++s) mbar_init(bars + s, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  unsigned floors = 0;
+  const double rate =
+      stage_tile<T, TX, TY, true>(J, a.P, a, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
+  if (failed) {
+    if (threadIdx.x == 0) atomicExch(&a.sc->error, 1);
+    return;
+  }
   if (a.want_rate) block_max_to(&a.sc->wmax_bits, rate, red);
   if (floors) atomicAdd(&a.sc->floor_hits, (unsigned long long)floors);
 }
