@@ -181,7 +181,7 @@ def measured_traffic(precision):
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
         h = hashlib.sha256()
-        for f in ("ph_stage.cuh", "ph_device.cuh"):
+        for f in ("ph_stage.cuh", "ph_device.cuh", "ph_tma.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2202_12309_gb300", "csrc", f), "rb").read())
         if h.hexdigest() != rec["kernel_source_sha256"]:
             return None
@@ -399,6 +399,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
     ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
+    ap.add_argument("--only", choices=["batch", "two_level", "adjoint"],
+                    help="run one variant workload only and print its record (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     global MESH
@@ -423,6 +425,16 @@ def main():
         torch.distributed.barrier()
     ph.use_torch_allocator()
     pk, peak_kind = peaks()
+    if args.only:
+        if args.only == "batch":
+            rec = batch_variant(ph, torch, args.precision, args.steps, args.warmup)
+        elif args.only == "two_level":
+            rec = two_level_variant(ph, torch, args.steps, args.warmup)
+        else:
+            rec = adjoint_variant(ph, torch, args.precision)
+        if rank == 0:
+            print(json.dumps(rec), flush=True)
+        return 0
 
     # headline: timed with clocks sampled; barrier + max over ranks
     clocks = Clocks(local)

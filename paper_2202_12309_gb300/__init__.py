@@ -197,6 +197,11 @@ def totals_noalloc(U, nx, nblocks, out, precision="fp64", level=None, vol=(1.0, 
         stream = torch.cuda.current_stream().cuda_stream
     n3 = (ctypes.c_int32 * 3)(*nx)
     prec = PH_FP32 if precision in ("fp32", PH_FP32) else PH_FP64
+    if 0 <= int(nblocks) <= 16384:  # larger counts are rejected by the library itself
+        _check_buffer(U, int(nblocks) * 5 * nx[0] * nx[1] * nx[2], 4 if prec == PH_FP32 else 8, "U")
+        _check_buffer(out, 5, 8, "out")
+    if not (U.is_cuda and out.is_cuda):
+        raise ValueError("U and out must be device tensors")
     lvl = ctypes.c_void_p(level.data_ptr()) if level is not None else None
     check(lib().ph_totals_noalloc(ctypes.c_void_p(U.data_ptr()), prec, n3, int(nblocks), lvl,
                                   float(vol[0]), float(vol[1]), ctypes.c_void_p(out.data_ptr()),
@@ -206,10 +211,28 @@ def totals_noalloc(U, nx, nblocks, out, precision="fp64", level=None, vol=(1.0, 
 def _ptr(x):
     """(pointer, on_device) of a numpy array or a torch tensor."""
     if isinstance(x, np.ndarray):
-        assert x.flags["C_CONTIGUOUS"]
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
         return x.ctypes.data, 0
-    assert x.is_contiguous()
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
     return x.data_ptr(), (1 if x.is_cuda else 0)
+
+
+def _count(x) -> int:
+    """Number of elements actually held by x (passed to the C ABI, which
+    rejects a count that does not match the mesh)."""
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+def _itemsize(x) -> int:
+    return int(x.itemsize) if isinstance(x, np.ndarray) else int(x.element_size())
+
+
+def _check_buffer(x, count: int, itemsize: int, what: str):
+    if _count(x) != count or _itemsize(x) != itemsize:
+        raise ValueError("%s: expected %d elements of %d bytes, got %d of %d"
+                         % (what, count, itemsize, _count(x), _itemsize(x)))
 
 
 class Mesh:
@@ -261,13 +284,14 @@ class Mesh:
         if isinstance(U, np.ndarray):
             U = np.ascontiguousarray(U, dtype=self.dtype)
         p, dev = _ptr(U)
-        check(self.L.ph_set_state(self.h, ctypes.c_void_p(p), self.count(), dev))
+        # the element count of the buffer itself: the ABI rejects a mismatch
+        check(self.L.ph_set_state(self.h, ctypes.c_void_p(p), _count(U), dev))
 
     def get_state(self, out=None):
         if out is None:
             out = np.zeros(self.state_shape(), dtype=self.dtype)
         p, dev = _ptr(out)
-        check(self.L.ph_get_state(self.h, ctypes.c_void_p(p), self.count(), dev))
+        check(self.L.ph_get_state(self.h, ctypes.c_void_p(p), _count(out), dev))
         return out
 
     def get_full(self) -> np.ndarray:
@@ -358,10 +382,14 @@ class Mesh:
         elif out is None:
             import torch
             out = torch.empty_like(U0)
+        isz = np.dtype(self.dtype).itemsize
+        for buf, what in ((U0, "U0"), (dLdU, "dLdU"), (out, "out")):
+            _check_buffer(buf, self.count(), isz, what)
         p0, dev = _ptr(U0)
         pg, dev2 = _ptr(dLdU)
         po, dev3 = _ptr(out)
-        assert dev == dev2 == dev3
+        if not dev == dev2 == dev3:
+            raise ValueError("U0, dLdU and out must all be host arrays or all device tensors")
         dptr = None
         if dts is not None:
             dts = np.ascontiguousarray(dts, dtype=np.float64)
@@ -419,15 +447,13 @@ class Batch:
         if isinstance(U, np.ndarray):
             U = np.ascontiguousarray(U, dtype=self.dtype)
         p, dev = _ptr(U)
-        check(self.L.ph_batch_set_state(self.h, sim, ctypes.c_void_p(p),
-                                        int(np.prod(self.state_shape(sim))), dev))
+        check(self.L.ph_batch_set_state(self.h, sim, ctypes.c_void_p(p), _count(U), dev))
 
     def get_state(self, sim: int, out=None):
         if out is None:
             out = np.zeros(self.state_shape(sim), dtype=self.dtype)
         p, dev = _ptr(out)
-        check(self.L.ph_batch_get_state(self.h, sim, ctypes.c_void_p(p),
-                                        int(np.prod(self.state_shape(sim))), dev))
+        check(self.L.ph_batch_get_state(self.h, sim, ctypes.c_void_p(p), _count(out), dev))
         return out
 
     def step(self, n: int = 1):

@@ -170,7 +170,7 @@ __device__ void batch_ghost_phase(const BatchArgs<T>& a, T* U) {
 }
 
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) batch_cycle_kernel(const BatchArgs<T> a) {
+__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT) batch_cycle_kernel(const BatchArgs<T> a) {
   using SM = StageSmem<T, TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
@@ -311,7 +311,7 @@ int occupancy(int* per_sm) {
   cudaError_t e = set_attr<T, TX, TY>();
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ph::batch_cycle_kernel<T, TX, TY>,
-                                                    TX * TY, ph::batch_smem<T, TX, TY>());
+                                                    ph::StageSmem<T, TX, TY>::NT, ph::batch_smem<T, TX, TY>());
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   return PH_OK;
 }
@@ -343,7 +343,7 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   cudaLaunchConfig_t lc;
   std::memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(b->grid);
-  lc.blockDim = dim3(TX * TY);
+  lc.blockDim = dim3(ph::StageSmem<T, TX, TY>::NT);
   lc.dynamicSmemBytes = ph::batch_smem<T, TX, TY>();
   lc.stream = s;
   cudaLaunchAttribute attr[1];

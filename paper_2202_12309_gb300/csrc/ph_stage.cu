@@ -55,9 +55,9 @@ static cudaError_t launch_tile(const StageArgs<T>& a, const CUtensorMap* tmap, c
   const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
   if (grid == 0) return cudaSuccess;
   if (tmap)
-    stage_kernel_tma<T, TX, TY><<<grid, TX * TY, smem, s>>>(a, *tmap);
+    stage_kernel_tma<T, TX, TY><<<grid, StageSmem<T, TX, TY>::NT, smem, s>>>(a, *tmap);
   else
-    stage_kernel<T, TX, TY><<<grid, TX * TY, smem, s>>>(a);
+    stage_kernel<T, TX, TY><<<grid, StageSmem<T, TX, TY>::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -83,7 +83,8 @@ EncodeTiledFn encode_fn() {
   std::call_once(once, [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = reinterpret_cast<EncodeTiledFn>(p);
   });

@@ -66,19 +66,55 @@ __device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int fac
 template <class T, int TX, int TY>
 struct StageSmem {
   static constexpr int WX = TX + 4, WY = TY + 4;
+  // threads.  FP32 (issue-bound): enough for the largest per-plane work list
+  // (x1 or x2 slopes) in one round, so no warp works a second round while the
+  // others wait at the barrier, with registers capped for 3 CTAs per SM.
+  // FP64 (bound by the FP64 pipe): one thread per cell, no cap (the extra warp
+  // and the cap cost more FP64 pipe time in spills than the balance saves).
+  static constexpr int NT0 = (TX + 2) * TY > TX * (TY + 2) ? (TX + 2) * TY : TX * (TY + 2);
+  static constexpr int NT = sizeof(T) == 4 ? (NT0 + 31) / 32 * 32 : TX * TY;
+  // resident CTAs per SM the registers are allocated for (FP32: 3; FP64: left
+  // to the compiler, which keeps 2 CTAs of 256 threads without spills)
+  static constexpr int MINB = sizeof(T) == 4 ? 3 : 0;
   static constexpr int PLANE = NV * WX * WY;          // one plane of 5 variables with halo
   static constexpr int SLOT = (PLANE * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
   static constexpr unsigned PLANE_BYTES = PLANE * sizeof(T);  // one TMA box
+  // row pitch of the face-flux arrays: TX+4 keeps the FP32 warps of own_cell
+  // on distinct banks; FP64 keeps the dense TX+1
+  static constexpr int FP = sizeof(T) == 4 ? TX + 4 : TX + 1;
   static constexpr int DXN = NV * TY * (TX + 2);      // x1 slopes
   static constexpr int DYN = NV * (TY + 2) * TX;      // x2 slopes
-  static constexpr int FXN = NV * TY * (TX + 1);      // x1 face fluxes
-  static constexpr int FYN = NV * (TY + 1) * TX;      // x2 face fluxes
+  static constexpr int FXN = NV * TY * FP;            // x1 face fluxes (TX+1 used per row)
+  static constexpr int FYN = NV * (TY + 1) * FP;      // x2 face fluxes (TX used per row)
   static constexpr size_t body = sizeof(T) * (size_t)(4 * SLOT + DXN + DYN + FXN + FYN);
   static constexpr size_t red_off = (body + 15) / 16 * 16;
   static constexpr size_t bar_off = red_off + 32 * sizeof(double);
   // + 4 mbarriers, + slack to align the base to 128 bytes (TMA destinations)
   static constexpr size_t bytes = bar_off + 4 * sizeof(uint64_t) + 128;
 };
+
+// Cell owned by thread tid < TX*TY.  The rows a warp touches are chosen so
+// that its 32 lanes hit distinct shared-memory banks for 4-byte data with row
+// pitch TX+4: a 16-wide warp covers rows r and r+4 (4 (16+4) = 16 mod 32), an
+// 8-wide warp rows r, r+2, r+4, r+6, a 32-wide warp one row.
+template <class T, int TX, int TY>
+__device__ __forceinline__ void own_cell(int tid, int& tx, int& ty) {
+  if (sizeof(T) == 8) {  // a half-warp of doubles already fills all 32 banks
+    tx = tid % TX;
+    ty = tid / TX;
+  } else if (TX == 16 && TY % 8 == 0) {
+    const int w = tid >> 5, h = (tid >> 4) & 1;
+    tx = tid & 15;
+    ty = (w & 3) + 8 * (w >> 2) + 4 * h;
+  } else if (TX == 8 && TY % 8 == 0) {
+    const int w = tid >> 5, q = (tid >> 3) & 3;
+    tx = tid & 7;
+    ty = (w & 1) + 8 * (w >> 1) + 2 * q;
+  } else {
+    tx = tid % TX;
+    ty = tid / TX;
+  }
+}
 
 // One tile of one block for one stage.  J holds the block's data pointers,
 // geometry, the tile's origin and the k-range; returns the max over the
@@ -109,7 +145,9 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
                                              int vz0 = 0, uint64_t* bars = nullptr,
                                              int* failed = nullptr) {
   using SM = StageSmem<T, TX, TY>;
-  constexpr int NT = TX * TY;
+  constexpr int NT = SM::NT;        // threads of the CTA
+  constexpr int NC = TX * TY;       // threads that own a cell of the tile
+  constexpr int FP = SM::FP;
   constexpr int WX = SM::WX, WY = SM::WY;
   T* ring = reinterpret_cast<T*>(smem_raw);
   T* sdx = ring + 4 * SM::SLOT;
@@ -118,7 +156,9 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   T* sfy = sfx + SM::FXN;
 
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+  const bool has_cell = (NT == NC) || tid < NC;  // compile-time true when every thread owns one
+  int tx = 0, ty = 0;
+  if (has_cell) own_cell<T, TX, TY>(tid, tx, ty);
   const int n1 = J.nx[0], n2 = J.nx[1], n3 = J.nx[2];
   const int S1 = J.S[0], S2 = J.S[1], S3 = J.S[2];
   const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
@@ -201,7 +241,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     __syncthreads();
   }
   T dz[NV], fzm[NV];
-  {
+  if (has_cell) {  // x3 work is per owned column
     T wa[NV], wb[NV], wc[NV], wd[NV], wl[NV], wr[NV];
     col(k0 - 2, wa);
     col(k0 - 1, wb);
@@ -221,7 +261,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   if (TMA && k0 + 2 <= k1 + 1) issue(k0 + 2);  // into the slot of plane k0-2, read above
 
   const int i = i0 + tx, j = j0 + ty;
-  const bool own = (i < n1) && (j < n2);
+  const bool own = has_cell && (i < n1) && (j < n2);
   const T tdt = J.dt;
   double rate = 0.0;
 
@@ -239,7 +279,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     }
     // (C) slopes; own x3 flux
     T fzlo[NV];  // x3 flux below the cell; fzm becomes the flux above it
-    {
+    if (has_cell) {
       T wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], f[NV];
       col(k, wa);
       col(k + 1, wb);
@@ -306,7 +346,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         }
         hlle<T, 0>(wl, wr, P, fl);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sfx[(v * TY + jj) * (TX + 1) + f] = fl[v];
+        for (int v = 0; v < NV; ++v) sfx[(v * TY + jj) * FP + f] = fl[v];
       }
       for (int c = tid; c < TX * (TY + 1); c += NT) {
         const int g = c / TX, ii = c - g * TX;   // face between rows g-1, g
@@ -320,7 +360,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         }
         hlle<T, 1>(wl, wr, P, fl);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sfy[(v * (TY + 1) + g) * TX + ii] = fl[v];
+        for (int v = 0; v < NV; ++v) sfy[(v * (TY + 1) + g) * FP + ii] = fl[v];
       }
     }
     __syncthreads();
@@ -330,8 +370,8 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       T unew[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const T dfx = sfx[(v * TY + ty) * (TX + 1) + tx + 1] - sfx[(v * TY + ty) * (TX + 1) + tx];
-        const T dfy = sfy[(v * (TY + 1) + ty + 1) * TX + tx] - sfy[(v * (TY + 1) + ty) * TX + tx];
+        const T dfx = sfx[(v * TY + ty) * FP + tx + 1] - sfx[(v * TY + ty) * FP + tx];
+        const T dfy = sfy[(v * (TY + 1) + ty + 1) * FP + tx] - sfy[(v * (TY + 1) + ty) * FP + tx];
         const T L = -(dfx * idx1 + dfy * idx2 + (fzm[v] - fzlo[v]) * idx3);
         const T ucur = Ub[cell + v * vstride];
         if (J.stage == 1) {
@@ -345,13 +385,13 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       if (a.face_rec) {  // two-level mesh: keep fluxes on fine-coarse faces
         const int* fr = a.face_rec + 6 * leaf;
         if (i == 0 && fr[0] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 0, j, k, v, sfx[(v * TY + ty) * (TX + 1) + tx]);
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 0, j, k, v, sfx[(v * TY + ty) * FP + tx]);
         if (i == n1 - 1 && fr[1] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 1, j, k, v, sfx[(v * TY + ty) * (TX + 1) + tx + 1]);
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 1, j, k, v, sfx[(v * TY + ty) * FP + tx + 1]);
         if (j == 0 && fr[2] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 2, k, i, v, sfy[(v * (TY + 1) + ty) * TX + tx]);
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 2, k, i, v, sfy[(v * (TY + 1) + ty) * FP + tx]);
         if (j == n2 - 1 && fr[3] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 3, k, i, v, sfy[(v * (TY + 1) + ty + 1) * TX + tx]);
+          for (int v = 0; v < NV; ++v) capture(a, leaf, 3, k, i, v, sfy[(v * (TY + 1) + ty + 1) * FP + tx]);
         if (k == 0 && fr[4] >= 0)
           for (int v = 0; v < NV; ++v) capture(a, leaf, 4, i, j, v, fzlo[v]);
         if (k == n3 - 1 && fr[5] >= 0)
@@ -402,7 +442,7 @@ __device__ __forceinline__ bool make_job(const StageArgs<T>& a, TileJob<T>& J) {
 }
 
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, StageSmem<T, TX, TY>::MINB)
 stage_kernel(const StageArgs<T> a) {
   using SM = StageSmem<T, TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -418,7 +458,7 @@ stage_kernel(const StageArgs<T> a) {
 // The same stage with planes staged by TMA from the tensor map of the stencil
 // input pool.
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, StageSmem<T, TX, TY>::MINB)
 stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__ CUtensorMap tmap) {
   using SM = StageSmem<T, TX, TY>;
   extern __shared__ __align__(128) unsigned char smem_dyn[];

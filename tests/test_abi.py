@@ -46,3 +46,63 @@ def test_invalid_config_rejected_without_gpu_work():
     rc = L.ph_create(ctypes.byref(cfg), None, ctypes.byref(h))
     assert rc == -1
     assert b"nx" in L.ph_last_error()
+
+
+BAD_CONFIGS = [
+    dict(nx=(16, 16, 16), nb=(0, 1, 1)),                       # no blocks
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), xmin=(0, 0, 0), xmax=(0, 1, 1)),  # empty domain
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), max_level=2),          # more than two levels
+    dict(nx=(15, 16, 16), nb=(1, 1, 1), max_level=1),          # odd block on a two-level mesh
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), gamma=1.0),            # gamma must exceed 1
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), cfl=0.0),
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), tile=(24, 8, 16)),     # unsupported tile
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), tile=(16, 16, 17)),    # chunk deeper than the block
+]
+
+
+@pytest.mark.parametrize("kw", BAD_CONFIGS)
+def test_invalid_configs_rejected_before_any_cuda_call(kw):
+    import paper_2202_12309_gb300 as ph
+    L = ph.lib()
+    kw = dict(kw)
+    nx, nb = kw.pop("nx"), kw.pop("nb")
+    cfg = ph.make_config(nx, nb, **kw)
+    h = ctypes.c_void_p()
+    assert L.ph_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    assert h.value is None
+    assert len(L.ph_last_error()) > 0
+
+
+def test_bad_precision_and_batch_arguments_rejected():
+    import paper_2202_12309_gb300 as ph
+    L = ph.lib()
+    cfg = ph.make_config((16, 16, 16), (1, 1, 1))
+    cfg.precision = 7
+    h = ctypes.c_void_p()
+    assert L.ph_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1
+    # batches: mixed precision, two-level member
+    a = ph.make_config((16, 16, 16), (1, 1, 1))
+    b = ph.make_config((16, 16, 16), (1, 1, 1), precision="fp32")
+    arr = (ph.Config * 2)(a, b)
+    assert L.ph_batch_create(arr, 2, None, ctypes.byref(h)) == -1
+    c = ph.make_config((16, 16, 16), (1, 1, 1), max_level=1)
+    arr = (ph.Config * 1)(c)
+    assert L.ph_batch_create(arr, 1, None, ctypes.byref(h)) == -1
+    assert L.ph_batch_create(arr, 0, None, ctypes.byref(h)) == -1
+
+
+def test_null_handles_rejected():
+    import paper_2202_12309_gb300 as ph
+    L = ph.lib()
+    assert L.ph_step(None, 1) == -1
+    assert L.ph_num_blocks(None, None) == -1
+    assert L.ph_destroy(None) == 0
+    assert L.ph_batch_destroy(None) == 0
+    # allocator hooks come in pairs
+    assert L.ph_set_allocator(ctypes.c_void_p(1), None, None) == -1
+    # no-allocation totals: checks happen before any device work
+    out = ctypes.c_void_p(8)
+    n3 = (ctypes.c_int32 * 3)(4, 4, 4)
+    assert L.ph_totals_noalloc(None, 0, n3, 1, None, 1.0, 1.0, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 3, n3, 1, None, 1.0, 1.0, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 1 << 20, None, 1.0, 1.0, out, None) == -1

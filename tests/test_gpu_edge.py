@@ -1,0 +1,100 @@
+"""Edge and degenerate cases of the GPU path: no-op and out-of-order calls,
+wrong sizes, a non-finite state planted on the host, a vacuum region that
+trips the floors, a maximum-size mesh, and the torch allocator hook."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _ph():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2202_12309_gb300 as ph
+    return torch, ph
+
+
+def test_call_order_and_sizes():
+    torch, ph = _ph()
+    m = ph.Mesh(ph.make_config((8, 8, 8), (2, 2, 2)))
+    with pytest.raises(ph.PhError) as e:
+        m.step(1)                                   # no state yet
+    assert e.value.code == -6
+    # a buffer of the wrong size: the binding passes its real element count
+    # and the ABI rejects it before touching it
+    with pytest.raises(ph.PhError) as e:
+        m.set_state(np.zeros((8, 5, 8, 8, 7)))
+    assert e.value.code == -1
+    with pytest.raises(ph.PhError) as e:
+        m.get_state(np.zeros((8, 5, 8, 8, 7)))
+    assert e.value.code == -1
+    geo = W.Geometry((8, 8, 8), (2, 2, 2))
+    U = W.blast(geo, m.tree(), seed=0)
+    m.set_state(U)
+    m.step(0)                                       # no-op
+    assert m.time() == (0.0, 0)
+    assert np.array_equal(m.get_state(), U)
+    with pytest.raises(ph.PhError):
+        m.step(-1)
+
+
+def test_non_finite_state_is_reported():
+    torch, ph = _ph()
+    m = ph.Mesh(ph.make_config((8, 8, 8), (2, 2, 2)))
+    geo = W.Geometry((8, 8, 8), (2, 2, 2))
+    U = W.blast(geo, m.tree(), seed=0)
+    U[3, 4, 2, 2, 2] = np.nan                      # planted on the host
+    m.set_state(U)
+    m.step(2)
+    rc, floors, nonfinite = m.status()
+    assert rc == -3 and nonfinite == 1
+
+
+def test_vacuum_region_hits_floors_and_is_counted():
+    torch, ph = _ph()
+    m = ph.Mesh(ph.make_config((8, 8, 8), (2, 2, 2)))
+    geo = W.Geometry((8, 8, 8), (2, 2, 2))
+    U = W.blast(geo, m.tree(), seed=0)
+    U[0, 0, 3:5, 3:5, 3:5] = 1e-14                 # density below the 1e-12 floor
+    m.set_state(U)
+    m.step(1)
+    rc, floors, nonfinite = m.status()
+    assert rc == -3 and floors > 0 and nonfinite == 0
+    assert np.all(np.isfinite(m.get_state()))
+
+
+def test_maximum_size_mesh_conserves():
+    """512^3 zones in 512 blocks of 64^3 (FP64, ~14 GB of state pools)."""
+    torch, ph = _ph()
+    nx, nb = (64, 64, 64), (8, 8, 8)
+    m = ph.Mesh(ph.make_config(nx, nb))
+    geo = W.Geometry(nx, nb)
+    U = W.linear_wave(geo, m.tree(), seed=2, kvec=(1, 2, 3))
+    m.set_state(U)
+    t0 = m.totals()
+    m.step(2)
+    t1 = m.totals()
+    assert np.all(np.abs(t1 - t0) <= 1e-13 * np.abs(t0).max())
+    assert m.status()[0] == 0
+    del U
+    m.close()
+
+
+def test_torch_allocator_hook():
+    torch, ph = _ph()
+    ph.use_torch_allocator()
+    try:
+        before = torch.cuda.memory_allocated()
+        m = ph.Mesh(ph.make_config((16, 16, 16), (2, 2, 2)))
+        assert torch.cuda.memory_allocated() > before + 2 * 8 * 5 * 20 ** 3 * 8
+        geo = W.Geometry((16, 16, 16), (2, 2, 2))
+        m.set_state(W.blast(geo, m.tree(), seed=1))
+        m.step(2)
+        assert m.status()[0] == 0
+        m.close()
+        assert torch.cuda.memory_allocated() <= before + 1024
+    finally:
+        ph.lib().ph_set_allocator(None, None, None)

@@ -1,8 +1,8 @@
-"""Seeded synthetic inputs: the problem generators of arXiv:2202.12309 Sec. 5.1.
+"""Seeded synthetic inputs: the problem generators of arXiv:2202.12309 Sec. 4.1.
 
 The paper's Parthenon-hydro runs three problem generators (a linear wave, a
 spherical blast wave, Kelvin-Helmholtz) and times uniform and static/adaptive
-multilevel meshes built from them (Sec. 6).  No dataset is involved.  This
+multilevel meshes built from them (Sec. 5).  No dataset is involved.  This
 module builds the initial *conserved* state of such problems on any list of
 leaf blocks, from cell-centre coordinates and a counter-based random generator,
 so that the result does not depend on how the mesh is split into blocks.
