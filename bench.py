@@ -15,8 +15,9 @@ cycles).  The state (671 MB in FP64, 335 MB in FP32) is larger than the
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the only reference this build
-has) on a bounded sample of the same workload, on the host cores.
+--impl reference times the FP64 CPU oracle (written from the paper; there is
+no reference program to run) on a bounded sample of the same workload, on
+the host cores.
 Under torchrun each rank runs an independent replica (replicas only: the
 single-GPU path has no exchange step between meshes); value sums the ranks.
 """
@@ -29,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -46,7 +48,7 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 152 SMs); FP32: 128 FFMA per clock per SM.
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# Algorithmic work per zone and stage launch ("Roofline"):
+# Algorithmic work per zone and stage launch:
 #  bytes: stage 1 reads U0 and writes U1 (10 words), stage 2 reads U1 and U0
 #  and writes U0 (15 words): 25 words per zone-cycle, 12.5 per launch.
 WORDS_PER_ZONE_LAUNCH = 12.5
@@ -77,7 +79,7 @@ class Clocks:
     def __init__(self, device_index=0):
         self.dev = device_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "ph_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -173,17 +175,18 @@ def time_variant(ph, torch, block, precision, steps, warmup, kvec=WAVE_K):
     return res
 
 
-def measured_traffic(precision):
+def measured_traffic(precision, block):
     """DRAM bytes of one stage launch at this mesh size, from the committed ncu
-    capture (profiles/stage_kernel_traffic.json, per zone, scaled by zones), or
-    None when the kernel source changed since the capture."""
+    capture (profiles/stage_kernel_traffic.json: mean of the stage-1 and stage-2
+    launches, per zone, scaled by zones), or None when the kernel source changed
+    since the capture or the block size differs from the captured one."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
         h = hashlib.sha256()
         for f in ("ph_stage.cuh", "ph_device.cuh", "ph_tma.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2202_12309_gb300", "csrc", f), "rb").read())
-        if h.hexdigest() != rec["kernel_source_sha256"]:
+        if h.hexdigest() != rec["kernel_source_sha256"] or rec[precision]["block"] != block:
             return None
         return rec[precision]["bytes_per_zone"] * MESH ** 3
     except Exception:
@@ -192,23 +195,23 @@ def measured_traffic(precision):
 
 def roofline_for(v, pk, peak_kind):
     zones = MESH ** 3
-    traffic = measured_traffic(v["precision"])
+    traffic = measured_traffic(v["precision"], v["block"])
     if v["precision"] == "fp32":
         word = 4
         achieved = WORDS_PER_ZONE_LAUNCH * word * zones / (v["stage_ms_avg"] / 1e3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_launch": "stage 1 (ncu)",
+                "frac": achieved / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
                 "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}
     # FP64: bound by the FP64 pipe
     achieved = FLOPS_PER_ZONE_CYCLE * 0.5 * zones / (v["stage_ms_avg"] / 1e3) / 1e12
     peak = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "traffic_launch": "stage 1 (ncu)",
+            "frac": achieved / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
             "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)"}
 
 
-def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0):
+def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0, launch=None):
     """64 independent blast-wave meshes, sizes 32^3..128^3 zones in 16^3 or
     32^3 blocks (seeded), one persistent launch per cycle; autotuned."""
     members = W.batch_members(seed=seed, nsim=nsim)
@@ -227,7 +230,11 @@ def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0):
     for s, U in enumerate(states):
         B.set_state(s, U)
     t0 = time.perf_counter()
-    choice = B.autotune(1)
+    if launch:
+        B.set_launch(launch)
+        choice = B.launch()
+    else:
+        choice = B.autotune(1)
     tune_s = time.perf_counter() - t0
     B.step(warmup)
     torch.cuda.synchronize()
@@ -399,6 +406,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
     ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
+    ap.add_argument("--batch-launch", help="TX,TY,KC,CTAS: skip the batch autotuner (profiling runs)")
     ap.add_argument("--only", choices=["batch", "two_level", "adjoint"],
                     help="run one variant workload only and print its record (profiling runs)")
     args = ap.parse_args()
@@ -427,7 +435,8 @@ def main():
     pk, peak_kind = peaks()
     if args.only:
         if args.only == "batch":
-            rec = batch_variant(ph, torch, args.precision, args.steps, args.warmup)
+            launch = [int(x) for x in args.batch_launch.split(",")] if args.batch_launch else None
+            rec = batch_variant(ph, torch, args.precision, args.steps, args.warmup, launch=launch)
         elif args.only == "two_level":
             rec = two_level_variant(ph, torch, args.steps, args.warmup)
         else:

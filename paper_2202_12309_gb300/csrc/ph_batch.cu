@@ -170,7 +170,8 @@ __device__ void batch_ghost_phase(const BatchArgs<T>& a, T* U) {
 }
 
 template <class T, int TX, int TY>
-__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT) batch_cycle_kernel(const BatchArgs<T> a) {
+__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, (sizeof(T) == 4 ? 3 : 0))
+batch_cycle_kernel(const BatchArgs<T> a) {
   using SM = StageSmem<T, TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
