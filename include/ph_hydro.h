@@ -256,6 +256,26 @@ int ph_batch_autotune(ph_batch* batch, int32_t trial_cycles, int32_t chosen[4]);
  * still usable. */
 int ph_debug_barrier_timeout(void* stream, int32_t nctas, int64_t spin_limit, int32_t* gave_up);
 
+/* Accuracy check of the stage kernels' reciprocal and root routines.  The
+ * paper has no counterpart: the kernels compute 1/x, 1/sqrt(x) and sqrt(x)
+ * (Sec. 4.1's HLLE wave speeds and Roe weights, the primitive variables, the
+ * limiter) from the hardware approximation plus one Newton-Raphson step
+ * instead of the correctly rounded operations; this entry evaluates those
+ * routines on caller data so that tests can bound their error.
+ *   fn         PH_MATH_RCP, PH_MATH_RSQRT or PH_MATH_SQRT (the routines),
+ *              PH_MATH_RCP_APPROX or PH_MATH_RSQRT_APPROX (the raw hardware
+ *              approximations they start from; PH_FP64 only)
+ *   precision  PH_FP64 (x, y double) or PH_FP32 (float)
+ *   x, y       device pointers to n elements; y[i] = fn(x[i]); may not overlap
+ *   stream     cudaStream_t the kernel is queued on (asynchronous)
+ * Returns PH_ERR_INVALID for a bad argument, PH_ERR_CUDA if the launch fails. */
+#define PH_MATH_RCP 0
+#define PH_MATH_RSQRT 1
+#define PH_MATH_SQRT 2
+#define PH_MATH_RCP_APPROX 3
+#define PH_MATH_RSQRT_APPROX 4
+int ph_debug_math(int32_t fn, int32_t precision, const void* x, void* y, int64_t n, void* stream);
+
 /* Conserved totals of a caller-owned state without any device allocation.
  * The paper has no counterpart: this exists for callers that may not call
  * cudaMalloc at all (a plugin whose host application owns every byte of

@@ -32,7 +32,7 @@ EXPORTS = [
     "ph_batch_create", "ph_batch_destroy", "ph_batch_num_blocks", "ph_batch_set_state",
     "ph_batch_get_state", "ph_batch_step", "ph_batch_get_dt", "ph_batch_get_time",
     "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
-    "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint",
+    "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint", "ph_debug_math",
 ]
 
 
@@ -152,6 +152,7 @@ def lib():
             "ph_debug_barrier_timeout": [P, i32, i64, ctypes.POINTER(i32)],
             "ph_step_dt": [P, i32, dp],
             "ph_adjoint": [P, P, i32, i32, dp, P, P, dp, i32],
+            "ph_debug_math": [i32, i32, P, P, i64, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -501,6 +502,23 @@ def debug_barrier_timeout(nctas: int = 4, spin_limit: int = 1 << 16, stream: Opt
     rc = lib().ph_debug_barrier_timeout(ctypes.c_void_p(stream), int(nctas), int(spin_limit),
                                         ctypes.byref(g))
     return rc, g.value
+
+
+MATH_FN = {"rcp": 0, "rsqrt": 1, "sqrt": 2, "rcp_approx": 3, "rsqrt_approx": 4}
+
+
+def debug_math(fn: str, x):
+    """Evaluate the stage kernels' reciprocal / root routine `fn` on the CUDA
+    tensor x (float64 or float32); returns a new tensor on x's stream."""
+    import torch
+    if not (x.is_cuda and x.is_contiguous() and x.dtype in (torch.float64, torch.float32)):
+        raise ValueError("x must be a contiguous float64/float32 CUDA tensor")
+    y = torch.empty_like(x)
+    prec = PH_FP64 if x.dtype == torch.float64 else PH_FP32
+    check(lib().ph_debug_math(MATH_FN[fn], prec, ctypes.c_void_p(x.data_ptr()),
+                              ctypes.c_void_p(y.data_ptr()), x.numel(),
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return y
 
 
 def _hydro_run_function():

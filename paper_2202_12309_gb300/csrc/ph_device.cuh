@@ -41,10 +41,85 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+// --------------------------------------------------------------------------
+// Reciprocal, reciprocal square root and square root for the stage kernels.
+// GB300 retires two FP64 FMAs per clock per SM, and a correctly rounded FP64
+// division or square root costs about ten of them.  These routines start from
+// the hardware's approximate value (PTX rcp.approx.ftz / rsqrt.approx.ftz, on
+// the special-function unit) and take one higher-order Newton-Raphson
+// (Householder) step in FP64:
+//   reciprocal:  e = 1 - x y,   y' = y (1 + e + e^2)        error e^3
+//   rsqrt:       e = 1 - x y^2, y' = y (1 + e/2 + 3e^2/8)   error 5e^3/16
+// (the truncated binomial series of (1-e)^-1 and (1-e)^-1/2).  With the
+// approximation good to ~2^-20 the truncation error is below 2^-56, so the
+// reciprocal and rsqrt are within one ulp of the exact values and
+// sqrt = x rsqrt(x) within two (tested against them).  Arguments outside [2^-1000, 2^1000] in magnitude (zero,
+// subnormals, infinities, NaN; negative ones for the roots) take the
+// correctly rounded path instead.  FP32: the approximation plus one Newton
+// step for the reciprocal, the approximate rsqrt as is.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ bool nr_range(double x) {  // 2^-1000 <= |x| <= 2^1000
+  const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  return hi - (23u << 20) < (2001u << 20);
+}
+__device__ __forceinline__ bool nr_range_pos(double x) {  // 2^-1000 <= x <= 2^1000
+  return (unsigned)__double2hiint(x) - (23u << 20) < (2001u << 20);
+}
+__device__ __forceinline__ double rcp_approx(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+__device__ __forceinline__ double rsqrt_approx(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+__device__ __forceinline__ double rcp(double x) {
+  if (!nr_range(x)) return 1.0 / x;
+  const double y = rcp_approx(x);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return fmaf(y, fmaf(-x, y, 1.f), y);
+}
+__device__ __forceinline__ double rsq(double x) {
+  if (!nr_range_pos(x)) return rsqrt(x);
+  const double y = rsqrt_approx(x);
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
+}
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double sq(double x) { return sqrt(x); }
-__device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sq(double x) {
+  if (!nr_range_pos(x)) return sqrt(x);
+  const double y = rsqrt_approx(x);
+  const double e = fma(-(x * y), y, 1.0);
+  return x * fma(y * e, fma(0.375, e, 0.5), y);
+}
+__device__ __forceinline__ float sq(float x) { return x > 1e-30f ? x * rsqrtf(x) : sqrtf(x); }
+
+// HLLE wave-speed bounds max(0, a, b) and min(0, a, b).  For doubles with
+// integer instructions: the bit patterns of non-negative doubles order like
+// signed 64-bit integers and every negative double is below them, so the
+// integer max of (0, a, b) is the numeric max(0, a, b) (a positive NaN
+// propagates); min(0, a, b) = -max(0, -a, -b) with the sign bit flipped.
+__device__ __forceinline__ double max0(double a, double b) {
+  const long long m = max(__double_as_longlong(a), __double_as_longlong(b));
+  return __longlong_as_double(max(m, 0ll));
+}
+__device__ __forceinline__ float max0(float a, float b) { return fmaxf(0.f, fmaxf(a, b)); }
+__device__ __forceinline__ double min0(double a, double b) {
+  constexpr long long S = (long long)0x8000000000000000ull;
+  const long long m = max(__double_as_longlong(a) ^ S, __double_as_longlong(b) ^ S);
+  return __longlong_as_double(max(m, 0ll) ^ S);
+}
+__device__ __forceinline__ float min0(float a, float b) { return fminf(0.f, fminf(a, b)); }
+// x > 0 (integer test for doubles; NaN with the sign bit clear counts as > 0).
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(float x) { return x > 0.f; }
 
 // Branch tests on FP64 values done with integer instructions: on GB300 an
 // FP64 compare occupies the FP64 pipe (1/64 of the FP32 rate), an integer
@@ -78,7 +153,7 @@ template <class T>
 __device__ __forceinline__ void cons_to_prim(T w[NV], const Phys<T>& P, unsigned& floors) {
   T rho = w[0];
   if (below_floor(rho, P.dfloor)) { rho = P.dfloor; ++floors; }
-  const T ir = T(1) / rho;
+  const T ir = rcp(rho);
   const T v1 = w[1] * ir, v2 = w[2] * ir, v3 = w[3] * ir;
   T p = P.gm1 * (w[4] - T(0.5) * (w[1] * v1 + w[2] * v2 + w[3] * v3));
   if (below_floor(p, P.pfloor)) { p = P.pfloor; ++floors; }
@@ -129,7 +204,7 @@ __device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], co
     p[0] = s[0];
 #pragma unroll
     for (int v = 1; v < NV; ++v) p[v] = p[v - 1] * s[v];
-    T inv = T(1) / p[NV - 1];
+    T inv = rcp(p[NV - 1]);
     T is[NV];
 #pragma unroll
     for (int v = NV - 1; v > 0; --v) {
@@ -147,50 +222,61 @@ __device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], co
 
 // HLLE flux with Einfeldt's wave-speed bounds (Roe averages) through a face
 // whose normal is x_{DIR+1}; wl/wr are primitive states.
+//   F = (b+ F_L - b- F_R + b+ b- (U_R - U_L)) / (b+ - b-)
+// is evaluated as F = cL F_L + cR F_R + cD (U_R - U_L) with cL = b+/(b+ - b-),
+// cR = -b-/(b+ - b-), cD = b+ b-/(b+ - b-).  Every conserved component except
+// the energy is a density times a velocity component, so with
+// aL = cL rho_L v_nL - cD rho_L and aR = cR rho_R v_nR + cD rho_R the mass flux
+// is aL + aR and the momentum flux aL v_L + aR v_R plus the pressure term on
+// the normal component: two FP64 operations per momentum component instead
+// of eight.  Roe averages use sqrt(rho) v and h sqrt(rho) = (E + p)/sqrt(rho).
 template <class T, int DIR>
 __device__ __forceinline__ void hlle(const T wl[NV], const T wr[NV], const Phys<T>& P, T f[NV]) {
+  // Every multiply-add is an explicit fma, so that the rounding is the same
+  // in every kernel this is inlined into (the single-mesh and the batched
+  // kernels agree bit for bit).
   constexpr int IN = 1 + DIR;
   const T rl = wl[0], pl = wl[4], rr = wr[0], pr = wr[4];
   const T vnl = wl[IN], vnr = wr[IN];
-  const T el = pl * P.igm1 + T(0.5) * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
-  const T er = pr * P.igm1 + T(0.5) * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
-  const T ql = rsq(rl), qr = rsq(rr);
-  const T sl = rl * ql, sr = rr * qr;          // sqrt(rho)
-  const T irl = ql * ql, irr = qr * qr;        // 1/rho
-  const T cl = sq(P.gamma * pl * irl), cr = sq(P.gamma * pr * irr);
-  const T hl = (el + pl) * irl, hr = (er + pr) * irr;
-  const T isum = T(1) / (sl + sr);
-  const T wsl = sl * isum, wsr = sr * isum;    // Roe weights
-  const T u1 = wsl * wl[1] + wsr * wr[1];
-  const T u2 = wsl * wl[2] + wsr * wr[2];
-  const T u3 = wsl * wl[3] + wsr * wr[3];
-  const T hroe = wsl * hl + wsr * hr;
-  const T a2 = P.gm1 * (hroe - T(0.5) * (u1 * u1 + u2 * u2 + u3 * u3));
-  const T croe = sq(a2 > T(0) ? a2 : T(0));
+  const T kl = fma(wl[1], wl[1], fma(wl[2], wl[2], wl[3] * wl[3]));
+  const T kr = fma(wr[1], wr[1], fma(wr[2], wr[2], wr[3] * wr[3]));
+  const T el = fma(pl, P.igm1, (T(0.5) * rl) * kl);
+  const T er = fma(pr, P.igm1, (T(0.5) * rr) * kr);
+  const T ql = rsq(rl), qr = rsq(rr);            // 1/sqrt(rho)
+  const T sl = rl * ql, sr = rr * qr;            // sqrt(rho)
+  const T gl = sq(P.gamma * pl), gr = sq(P.gamma * pr);  // c = g / sqrt(rho)
+  const T hl = el + pl, hr = er + pr;            // rho h
+  const T isum = rcp(add_rn(sl, sr));
+  const T wsl = sl * isum, wsr = sr * isum;      // Roe weights
+  const T u1 = fma(wsl, wl[1], wsr * wr[1]);
+  const T u2 = fma(wsl, wl[2], wsr * wr[2]);
+  const T u3 = fma(wsl, wl[3], wsr * wr[3]);
+  const T hroe = fma(hl, ql, hr * qr) * isum;
+  const T a2 = P.gm1 * fma(T(-0.5), fma(u1, u1, fma(u2, u2, u3 * u3)), hroe);
+  const T croe = positive(a2) ? sq(a2) : T(0);
   const T un = (IN == 1) ? u1 : ((IN == 2) ? u2 : u3);
-  const T bp = fmax(T(0), fmax(vnr + cr, un + croe));
-  const T bm = fmin(T(0), fmin(vnl - cl, un - croe));
-  const T idb = T(1) / (bp - bm);
-  const T bpbm = bp * bm;
-  const T mfl = rl * vnl, mfr = rr * vnr;
-  f[0] = (bp * mfl - bm * mfr + bpbm * (rr - rl)) * idb;
+  const T bp = max0(fma(gr, qr, vnr), add_rn(un, croe));
+  const T bm = min0(fma(-gl, ql, vnl), sub_rn(un, croe));
+  const T idb = rcp(bp - bm);
+  const T cL = bp * idb, cR = -bm * idb, cD = (bp * bm) * idb;
+  const T aL = fma(cL, rl * vnl, -(cD * rl));
+  const T aR = fma(cR, rr * vnr, cD * rr);
+  f[0] = aL + aR;
 #pragma unroll
-  for (int a = 1; a <= 3; ++a) {
-    const T fl = mfl * wl[a] + (a == IN ? pl : T(0));
-    const T fr = mfr * wr[a] + (a == IN ? pr : T(0));
-    f[a] = (bp * fl - bm * fr + bpbm * (rr * wr[a] - rl * wl[a])) * idb;
-  }
-  f[4] = (bp * ((el + pl) * vnl) - bm * ((er + pr) * vnr) + bpbm * (er - el)) * idb;
+  for (int a = 1; a <= 3; ++a) f[a] = fma(aL, wl[a], aR * wr[a]);
+  f[IN] += fma(cL, pl, cR * pr);
+  f[4] = fma(cL * vnl, hl, fma(cR * vnr, hr, cD * (er - el)));
 }
 
 // Largest signal speed over cell width of one primitive state:
 // max_d (|v_d| + c) / dx_d.  dt = cfl / (max over cells).
 template <class T>
 __device__ __forceinline__ T wave_rate(const T w[NV], const Phys<T>& P, T idx1, T idx2, T idx3) {
-  const T c = sq(P.gamma * w[4] / w[0]);
-  const T a = (fabs(w[1]) + c) * idx1;
-  const T b = (fabs(w[2]) + c) * idx2;
-  const T d = (fabs(w[3]) + c) * idx3;
+  const T g = P.gamma * w[4];
+  const T c = g * rsq(g * w[0]);   // sqrt(gamma p / rho)
+  const T a = add_rn(fabs(w[1]), c) * idx1;
+  const T b = add_rn(fabs(w[2]), c) * idx2;
+  const T d = add_rn(fabs(w[3]), c) * idx3;
   T m = a;
   if (!(b <= m)) m = b;   // NaN-propagating max
   if (!(d <= m)) m = d;
