@@ -2,13 +2,17 @@
 //
 // One launch covers every leaf block of the mesh ("pack all blocks into one
 // kernel", arXiv:2202.12309 Sec. 3.6/5.1).  A CTA owns a TX x TY column tile
-// of one block and marches along x3 over KC planes.  For each plane it:
-//   (A) stages the next conserved plane (tile + 2 ghost cells in x1, x2)
-//       into a 4-slot shared-memory ring and converts it to primitives;
+// of one block and marches along x3 over KC planes, holding four planes of
+// primitives (tile + 2 ghost cells in x1, x2) in a shared-memory ring.  For
+// plane k it:
 //   (C) computes van Leer half-slopes: x1 and x2 for the plane, x3 for its own
-//       column (x3 slopes roll through registers, each computed once);
+//       column (x3 slopes roll through registers, each computed once), and
+//       the HLLE flux on the x3 face above its cell;
 //   (E) computes HLLE fluxes on all x1 and x2 faces of the plane into shared
-//       memory and the x3 face above its cell in registers;
+//       memory;
+//   (F) converts plane k+3, staged in the ring slot of plane k-1 while (C)
+//       and (E) ran, to primitives, and stages plane k+4 into the slot of
+//       plane k;
 //   (G) forms the flux divergence and the SSPRK2 combination and writes the
 //       new conserved state (stage 2 also folds the cell's signal speed into
 //       the block-wide max that becomes the next dt, Sec. 3.10).
@@ -156,6 +160,10 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   T* sfy = sfx + SM::FXN;
 
   const int tid = threadIdx.x;
+  // The x2 work lists are walked from warp 1 on: when a list leaves a second,
+  // partial round, the x1 list's falls to warp 0 and the x2 list's to warp 1,
+  // which run on different SM sub-partitions, instead of both to warp 0.
+  const int trot = (tid + NT - 32) % NT;
   const bool has_cell = (NT == NC) || tid < NC;  // compile-time true when every thread owns one
   int tx = 0, ty = 0;
   if (has_cell) own_cell<T, TX, TY>(tid, tx, ty);
@@ -258,7 +266,18 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     hlle<T, 2>(wl, wr, P, fzm);
   }
   __syncthreads();
-  if (TMA && k0 + 2 <= k1 + 1) issue(k0 + 2);  // into the slot of plane k0-2, read above
+  // Plane k0+2 into the slot of plane k0-2 (read above); the loop's step k
+  // then brings in plane k+3 while it computes the fluxes of plane k.
+  if (TMA) {
+    issue(k0 + 2);
+    const bool ok = convert(k0 + 2);
+    fence_proxy_async_smem();
+    if (check_failed(ok)) return 0.0;
+    if (k0 + 3 <= k1 + 1) issue(k0 + 3);  // slot of plane k0-1, read above
+  } else {
+    load_plane(k0 + 2);
+    __syncthreads();
+  }
 
   const int i = i0 + tx, j = j0 + ty;
   const bool own = has_cell && (i < n1) && (j < n2);
@@ -266,18 +285,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   double rate = 0.0;
 
   for (int k = k0; k < k1; ++k) {
-    // (A) next plane in
-    if (TMA) {
-      const bool ok = convert(k + 2);
-      fence_proxy_async_smem();
-      if (check_failed(ok)) return 0.0;
-      // plane k+3 goes to the slot of plane k-1, which step k no longer reads
-      if (k + 3 <= k1 + 1) issue(k + 3);
-    } else {
-      load_plane(k + 2);
-      __syncthreads();
-    }
-    // (C) slopes; own x3 flux
+    // (C) slopes; own x3 flux (planes k, k+1, k+2 are in the ring)
     T fzlo[NV];  // x3 flux below the cell; fzm becomes the flux above it
     if (has_cell) {
       T wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], f[NV];
@@ -315,7 +323,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 #pragma unroll
         for (int v = 0; v < NV; ++v) sdx[(v * TY + jj) * (TX + 2) + ii] = h[v];
       }
-      for (int c = tid; c < TX * (TY + 2); c += NT) {   // x2 slopes, rows -1..TY
+      for (int c = trot; c < TX * (TY + 2); c += NT) {  // x2 slopes, rows -1..TY
         const int jj = c / TX, ii = c - jj * TX;
         T a[NV], b[NV], q[NV], h[NV];
 #pragma unroll
@@ -348,7 +356,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 #pragma unroll
         for (int v = 0; v < NV; ++v) sfx[(v * TY + jj) * FP + f] = fl[v];
       }
-      for (int c = tid; c < TX * (TY + 1); c += NT) {
+      for (int c = trot; c < TX * (TY + 1); c += NT) {
         const int g = c / TX, ii = c - g * TX;   // face between rows g-1, g
         T wl[NV], wr[NV], fl[NV];
 #pragma unroll
@@ -363,7 +371,17 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         for (int v = 0; v < NV; ++v) sfy[(v * (TY + 1) + g) * FP + ii] = fl[v];
       }
     }
-    __syncthreads();
+    // (F) plane k+3 into the slot of plane k-1, which step k does not read
+    if (TMA) {
+      const bool ok = k + 3 <= k1 + 1 ? convert(k + 3) : true;
+      fence_proxy_async_smem();  // this thread's reads of plane k before its slot is refilled
+      if (check_failed(ok)) return 0.0;
+      // plane k+4 into the slot of plane k, read for the last time above
+      if (k + 4 <= k1 + 1) issue(k + 4);
+    } else {
+      if (k + 3 <= k1 + 1) load_plane(k + 3);
+      __syncthreads();
+    }
     // (G) flux divergence + SSPRK2 combination
     if (own) {
       const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
