@@ -255,6 +255,37 @@ def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0, launch=N
             "autotune_s": tune_s, "status": rc, "floors": floors, "nonfinite": nonfinite}
 
 
+def restart_variant(ph, torch, block=32):
+    """Write and read a restart file of the 256^3 FP64 benchmark mesh (state,
+    tree, scalars) in the system's temporary directory: GB/s of file bytes,
+    each direction timed once after one untimed round."""
+    m, geo = build_mesh(ph, block, "fp64")
+    m.set_state(wave_state(geo, m.tree(), np.float64))
+    m.step(1)
+    path = os.path.join(tempfile.gettempdir(), "ph_restart_%d.phr" % os.getpid())
+    try:
+        m.save(path)
+        r = ph.Mesh.load(path)
+        r.close()
+        t0 = time.perf_counter()
+        m.save(path)
+        t1 = time.perf_counter()
+        r = ph.Mesh.load(path)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        same = bool(np.array_equal(r.get_state(), m.get_state()))
+        r.close()
+        nbytes = os.path.getsize(path)
+    finally:
+        if os.path.exists(path):
+            os.remove(path)
+    m.close()
+    return {"workload": "restart file of the 256^3 FP64 mesh (%d blocks of %d^3)" % ((MESH // block) ** 3, block),
+            "bytes": nbytes, "save_s": t1 - t0, "load_s": t2 - t1,
+            "save_gbs": nbytes / (t1 - t0) / 1e9, "load_gbs": nbytes / (t2 - t1) / 1e9,
+            "bitwise_state": same}
+
+
 def two_level_variant(ph, torch, steps, warmup):
     """Blast wave on a two-level mesh: root 128^3 zones in 16^3 blocks, the
     central cube of side 0.4 refined (static) plus adaptive refinement at a
@@ -431,7 +462,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
     ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
     ap.add_argument("--batch-launch", help="TX,TY,KC,CTAS: skip the batch autotuner (profiling runs)")
-    ap.add_argument("--only", choices=["batch", "two_level", "adjoint"],
+    ap.add_argument("--only", choices=["batch", "two_level", "adjoint", "restart"],
                     help="run one variant workload only and print its record (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -463,6 +494,8 @@ def main():
             rec = batch_variant(ph, torch, args.precision, args.steps, args.warmup, launch=launch)
         elif args.only == "two_level":
             rec = two_level_variant(ph, torch, args.steps, args.warmup)
+        elif args.only == "restart":
+            rec = restart_variant(ph, torch)
         else:
             rec = adjoint_variant(ph, torch, args.precision)
         if rank == 0:
@@ -512,6 +545,9 @@ def main():
             v = adjoint_variant(ph, torch, prec)
             variants.append(v)
             log("adjoint %s: %.3f s per gradient" % (prec, v["seconds_per_gradient"]))
+        v = restart_variant(ph, torch)
+        variants.append(v)
+        log("restart: save %.2f GB/s, load %.2f GB/s (%.0f MB)" % (v["save_gbs"], v["load_gbs"], v["bytes"] / 1e6))
 
     e2e = None
     if not args.quick:

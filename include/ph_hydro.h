@@ -41,6 +41,7 @@ extern "C" {
 #define PH_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
 #define PH_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define PH_ERR_STATE (-6)       /* call not valid in the object's current state */
+#define PH_ERR_IO (-7)          /* a file could not be opened, read or written */
 
 #define PH_FP64 0
 #define PH_FP32 1
@@ -255,6 +256,30 @@ int ph_batch_autotune(ph_batch* batch, int32_t trial_cycles, int32_t chosen[4]);
  * PH_ERR_TIMEOUT when any did (the expected outcome), with the GPU context
  * still usable. */
 int ph_debug_barrier_timeout(void* stream, int32_t nctas, int64_t spin_limit, int32_t* gave_up);
+
+/* Outputs and restarts (Sec. 3.9: outputs of single or double precision, and
+ * a restart type from which a run continues bitwise identically).
+ *
+ * ph_save writes the mesh to the file `path` (created or truncated): its
+ * configuration, block tree (levels, locations and the per-leaf ages that set
+ * the derefinement cadence), time, cycle, current and next dt, status
+ * counters, and the interior state in the layout of ph_get_state, stored in
+ * `precision` (PH_FP64 or PH_FP32).  A file whose precision is at least the
+ * mesh's is a restart file: ph_load of it followed by ph_step(n) gives the
+ * state, dt, time and tree that n more cycles of the saved mesh give, bit for
+ * bit.  An FP64 mesh saved as PH_FP32 is an output (each value rounded to
+ * nearest); it loads, but the continuation is not bitwise.  Synchronises the
+ * mesh's stream.  Errors: PH_ERR_INVALID (bad argument), PH_ERR_STATE (no
+ * state yet), PH_ERR_IO (the file could not be written).
+ *
+ * ph_load reads such a file and creates a new mesh on `stream` (as
+ * ph_create), owned by the caller (ph_destroy).  The file is validated before
+ * any device work: PH_ERR_IO if it cannot be opened or is truncated,
+ * PH_ERR_INVALID if it is not a file of this format or its tree does not tile
+ * the domain; *out is NULL on any error.  The file's format is native byte
+ * order, not portable across machines of different endianness. */
+int ph_save(ph_mesh* m, const char* path, int32_t precision);
+int ph_load(const char* path, void* stream, ph_mesh** out);
 
 /* Accuracy check of the stage kernels' reciprocal and root routines.  The
  * paper has no counterpart: the kernels compute 1/x, 1/sqrt(x) and sqrt(x)

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libphhydro.so")
 
 PH_OK = 0
 PH_ERR = {-1: "PH_ERR_INVALID", -2: "PH_ERR_OOM", -3: "PH_ERR_NONPHYSICAL", -4: "PH_ERR_TIMEOUT",
-          -5: "PH_ERR_CUDA", -6: "PH_ERR_STATE"}
+          -5: "PH_ERR_CUDA", -6: "PH_ERR_STATE", -7: "PH_ERR_IO"}
 PH_FP64 = 0
 PH_FP32 = 1
 
@@ -33,6 +33,7 @@ EXPORTS = [
     "ph_batch_get_state", "ph_batch_step", "ph_batch_get_dt", "ph_batch_get_time",
     "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
     "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint", "ph_debug_math",
+    "ph_save", "ph_load",
 ]
 
 
@@ -153,6 +154,8 @@ def lib():
             "ph_step_dt": [P, i32, dp],
             "ph_adjoint": [P, P, i32, i32, dp, P, P, dp, i32],
             "ph_debug_math": [i32, i32, P, P, i64, P],
+            "ph_save": [P, ctypes.c_char_p, i32],
+            "ph_load": [ctypes.c_char_p, P, ctypes.POINTER(P)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -251,6 +254,40 @@ class Mesh:
         check(self.L.ph_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(self.h)))
         self.nx = tuple(cfg.nx)
         self.dtype = np.float32 if cfg.precision == PH_FP32 else np.float64
+
+    @classmethod
+    def load(cls, path: str, stream: Optional[int] = None) -> "Mesh":
+        """ph_load: a new mesh from a file written by save()."""
+        if stream is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the GB300 hydro library has no CPU path")
+            stream = torch.cuda.current_stream().cuda_stream
+        L = lib()
+        h = ctypes.c_void_p()
+        check(L.ph_load(os.fsencode(path), ctypes.c_void_p(stream), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.L = L
+        self.h = h
+        cfg = Config()
+        # the configuration lives in the file's header, after magic, version
+        # and precision (8 + 4 + 4 bytes)
+        with open(path, "rb") as f:
+            f.seek(16)
+            f.readinto(cfg)
+        self.cfg = cfg
+        self.nx = tuple(cfg.nx)
+        self.dtype = np.float32 if cfg.precision == PH_FP32 else np.float64
+        return self
+
+    def save(self, path: str, precision: Optional[str] = None):
+        """ph_save: restart file (default: the mesh's own precision) or an
+        output of the given precision ("fp64" / "fp32")."""
+        if precision is None:
+            prec = self.cfg.precision
+        else:
+            prec = PH_FP32 if precision == "fp32" else PH_FP64
+        check(self.L.ph_save(self.h, os.fsencode(path), prec))
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -1053,4 +1053,204 @@ int ph_get_tile(const ph_mesh* m, int32_t tile[3]) {
   return PH_OK;
 }
 
+// ------------------------------------------------------------ restart files
+// Sec. 3.9: outputs of selectable precision, and a restart type from which a
+// run continues bitwise identically.  Layout (native byte order):
+//   char magic[8] "PHYDRST1"; int32 version (1); int32 data precision;
+//   ph_config; int32 nleaf; int32 pad; double time, dt_next, dt_last;
+//   int64 cycle; uint64 floor_hits; int32 nonfinite, error;
+//   per leaf: int32 level, int32 age, int64 lx[3];
+//   interior state in the layout of ph_get_state, in the data precision.
+namespace {
+
+constexpr char kMagic[8] = {'P', 'H', 'Y', 'D', 'R', 'S', 'T', '1'};
+
+struct FileHead {
+  char magic[8];
+  int32_t version;
+  int32_t data_precision;
+  ph_config cfg;
+  int32_t nleaf;
+  int32_t pad;
+  double time, dt_next, dt_last;
+  int64_t cycle;
+  uint64_t floor_hits;
+  int32_t nonfinite, error;
+};
+
+struct FileLeaf {
+  int32_t level, age;
+  int64_t lx[3];
+};
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) fclose(f);
+  }
+};
+
+}  // namespace
+
+int ph_save(ph_mesh* m, const char* path, int32_t precision) {
+  if (!m || !path) return fail(PH_ERR_INVALID, "ph_save: null argument");
+  if (precision != PH_FP64 && precision != PH_FP32)
+    return fail(PH_ERR_INVALID, "ph_save: precision must be PH_FP64 or PH_FP32");
+  if (!m->state_set) return fail(PH_ERR_STATE, "ph_save: set the state first");
+  ph::DevScalars hs;
+  int rc = read_scalars(m, &hs);
+  if (rc) return rc;
+  const int64_t count = interior_count(m);
+  std::vector<unsigned char> buf((size_t)count * m->esize);
+  if ((rc = ph_get_state(m, buf.data(), count, 0))) return rc;
+  FileHead h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.data_precision = precision;
+  h.cfg = m->cfg;
+  h.nleaf = m->nleaf();
+  h.time = hs.time;
+  h.dt_next = hs.dt_next;
+  h.dt_last = hs.dt_last;
+  h.cycle = hs.cycle;
+  h.floor_hits = hs.floor_hits;
+  h.nonfinite = hs.nonfinite;
+  h.error = hs.error;
+  std::vector<FileLeaf> lv(m->nleaf());
+  for (int b = 0; b < m->nleaf(); ++b) {
+    lv[b].level = m->leaf[b].level;
+    lv[b].age = m->leaf[b].age;
+    for (int d = 0; d < 3; ++d) lv[b].lx[d] = m->leaf[b].lx[d];
+  }
+  // data in the requested precision (a narrowing conversion rounds to nearest)
+  std::vector<unsigned char> out;
+  const unsigned char* data = buf.data();
+  size_t data_bytes = buf.size();
+  const int mp = m->cfg.precision;
+  if (precision != mp) {
+    out.resize((size_t)count * (precision == PH_FP32 ? 4 : 8));
+    if (precision == PH_FP32) {
+      const double* src = (const double*)buf.data();
+      float* dst = (float*)out.data();
+      for (int64_t i = 0; i < count; ++i) dst[i] = (float)src[i];
+    } else {
+      const float* src = (const float*)buf.data();
+      double* dst = (double*)out.data();
+      for (int64_t i = 0; i < count; ++i) dst[i] = (double)src[i];
+    }
+    data = out.data();
+    data_bytes = out.size();
+  }
+  FileCloser fc{fopen(path, "wb")};
+  if (!fc.f) return fail(PH_ERR_IO, std::string("ph_save: cannot open ") + path);
+  bool ok = fwrite(&h, sizeof(h), 1, fc.f) == 1;
+  if (ok && !lv.empty()) ok = fwrite(lv.data(), sizeof(FileLeaf), lv.size(), fc.f) == lv.size();
+  if (ok && data_bytes) ok = fwrite(data, 1, data_bytes, fc.f) == data_bytes;
+  if (fclose(fc.f) != 0) ok = false;
+  fc.f = nullptr;
+  if (!ok) return fail(PH_ERR_IO, std::string("ph_save: write failed: ") + path);
+  return PH_OK;
+}
+
+int ph_load(const char* path, void* stream, ph_mesh** out) {
+  if (!path || !out) return fail(PH_ERR_INVALID, "ph_load: null argument");
+  *out = nullptr;
+  FileCloser fc{fopen(path, "rb")};
+  if (!fc.f) return fail(PH_ERR_IO, std::string("ph_load: cannot open ") + path);
+  FileHead h;
+  if (fread(&h, sizeof(h), 1, fc.f) != 1) return fail(PH_ERR_IO, "ph_load: truncated header");
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
+    return fail(PH_ERR_INVALID, "ph_load: not a restart file of this library");
+  if (h.data_precision != PH_FP64 && h.data_precision != PH_FP32)
+    return fail(PH_ERR_INVALID, "ph_load: bad data precision");
+  for (int d = 0; d < 3; ++d)
+    if (h.cfg.nx[d] < 1 || h.cfg.nx[d] > (1 << 16) || h.cfg.nb[d] < 1 || h.cfg.nb[d] > (1 << 16))
+      return fail(PH_ERR_INVALID, "ph_load: bad block or grid size");
+  const int64_t nroot = (int64_t)h.cfg.nb[0] * h.cfg.nb[1] * h.cfg.nb[2];
+  const int64_t cells = (int64_t)h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
+  if (nroot > (1 << 24) || cells > (1 << 30) || h.nleaf < 1 || (int64_t)h.nleaf > 8 * nroot)
+    return fail(PH_ERR_INVALID, "ph_load: bad leaf count");
+  {  // the file must hold exactly the tree and the state its header announces
+    const int64_t want = (int64_t)sizeof(FileHead) + (int64_t)h.nleaf * sizeof(FileLeaf) +
+                         (int64_t)h.nleaf * 5 * cells * (h.data_precision == PH_FP32 ? 4 : 8);
+    if (fseek(fc.f, 0, SEEK_END) != 0) return fail(PH_ERR_IO, "ph_load: cannot seek");
+    const long have = ftell(fc.f);
+    if (have < 0 || (int64_t)have != want)
+      return fail(PH_ERR_IO, "ph_load: file size does not match its header (truncated?)");
+    if (fseek(fc.f, (long)sizeof(FileHead), SEEK_SET) != 0)
+      return fail(PH_ERR_IO, "ph_load: cannot seek");
+  }
+  std::vector<FileLeaf> lv(h.nleaf);
+  if (fread(lv.data(), sizeof(FileLeaf), lv.size(), fc.f) != lv.size())
+    return fail(PH_ERR_IO, "ph_load: truncated tree");
+  // the tree must tile the root grid with leaves of level 0 or 1
+  std::vector<int> cover(nroot, 0);
+  for (const FileLeaf& l : lv) {
+    if (l.level < 0 || l.level > h.cfg.max_level)
+      return fail(PH_ERR_INVALID, "ph_load: bad leaf level");
+    int64_t r[3];
+    for (int d = 0; d < 3; ++d) {
+      r[d] = l.lx[d] >> l.level;
+      if (l.lx[d] < 0 || r[d] >= h.cfg.nb[d]) return fail(PH_ERR_INVALID, "ph_load: leaf outside the domain");
+    }
+    cover[(r[2] * h.cfg.nb[1] + r[1]) * h.cfg.nb[0] + r[0]] += l.level ? 1 : 8;
+  }
+  for (int c : cover)
+    if (c != 8) return fail(PH_ERR_INVALID, "ph_load: leaves do not tile the domain");
+  const int64_t count = (int64_t)h.nleaf * 5 * h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
+  const size_t fbytes = (size_t)count * (h.data_precision == PH_FP32 ? 4 : 8);
+  std::vector<unsigned char> data(fbytes);
+  if (fbytes && fread(data.data(), 1, fbytes, fc.f) != fbytes)
+    return fail(PH_ERR_IO, "ph_load: truncated state");
+  ph_mesh* m = nullptr;
+  int rc = ph_create(&h.cfg, stream, &m);
+  if (rc) return rc;
+  // install the saved tree (ages included: they set the derefinement cadence)
+  m->leaf.clear();
+  for (const FileLeaf& l : lv) m->leaf.push_back(Leaf{l.level, {l.lx[0], l.lx[1], l.lx[2]}, l.age});
+  index_tree(m);
+  drop_graph(m);
+  if (!rc) rc = ensure_pools(m, m->nleaf());
+  if (!rc) rc = build_tables(m);
+  // state in the mesh's precision (widening is exact)
+  std::vector<unsigned char> conv;
+  const void* U = data.data();
+  if (!rc && h.data_precision != h.cfg.precision) {
+    conv.resize((size_t)count * (h.cfg.precision == PH_FP32 ? 4 : 8));
+    if (h.cfg.precision == PH_FP32) {
+      const double* src = (const double*)data.data();
+      float* dst = (float*)conv.data();
+      for (int64_t i = 0; i < count; ++i) dst[i] = (float)src[i];
+    } else {
+      const float* src = (const float*)data.data();
+      double* dst = (double*)conv.data();
+      for (int64_t i = 0; i < count; ++i) dst[i] = (double)src[i];
+    }
+    U = conv.data();
+  }
+  if (!rc) rc = ph_set_state(m, U, count, 0);
+  if (!rc) {
+    ph::DevScalars hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.time = h.time;
+    hs.dt_next = h.dt_next;
+    hs.dt_last = h.dt_last;
+    hs.cycle = h.cycle;
+    hs.floor_hits = h.floor_hits;
+    hs.nonfinite = h.nonfinite;
+    hs.error = h.error;
+    cudaError_t e = cudaMemcpyAsync(m->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, m->stream);
+    if (!e) e = cudaStreamSynchronize(m->stream);
+    if (e) rc = cuda_fail(e, "ph_load");
+  }
+  if (rc) {
+    ph_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return PH_OK;
+}
+
 }  // extern "C"
+

@@ -106,3 +106,19 @@ def test_null_handles_rejected():
     assert L.ph_totals_noalloc(None, 0, n3, 1, None, 1.0, 1.0, out, None) == -1
     assert L.ph_totals_noalloc(ctypes.c_void_p(8), 3, n3, 1, None, 1.0, 1.0, out, None) == -1
     assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 1 << 20, None, 1.0, 1.0, out, None) == -1
+
+
+def test_load_validates_the_file_before_any_device_work(tmp_path):
+    import paper_2202_12309_gb300 as ph
+    L = ph.lib()
+    h = ctypes.c_void_p()
+    assert L.ph_load(os.fsencode(str(tmp_path / "missing.phr")), None, ctypes.byref(h)) == -7
+    assert not h.value
+    junk = tmp_path / "junk.phr"
+    junk.write_bytes(b"not a restart file" * 64)
+    assert L.ph_load(os.fsencode(str(junk)), None, ctypes.byref(h)) == -1
+    short = tmp_path / "short.phr"
+    short.write_bytes(b"PHYDRST1")
+    assert L.ph_load(os.fsencode(str(short)), None, ctypes.byref(h)) == -7
+    assert L.ph_load(None, None, ctypes.byref(h)) == -1
+    assert L.ph_save(None, os.fsencode(str(junk)), 0) == -1
