@@ -43,13 +43,20 @@ class Config(ctypes.Structure):
         ("static_region", ctypes.c_int32),
         ("static_lo", ctypes.c_double * 3),
         ("static_hi", ctypes.c_double * 3),
+        ("bc", ctypes.c_int32 * 6),
+        ("pad", ctypes.c_int32),
     ]
+
+
+BC = {"periodic": 0, "outflow": 1, "reflect": 2}
 
 
 def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0 / 3.0, cfl=0.3,
                 max_level=0, adaptive=0, dfloor=1e-12, pfloor=1e-12, refine_tol=0.05,
                 derefine_tol=0.0125, derefine_count=10, static_region=0,
-                static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2)) -> Config:
+                static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2), bc=None) -> Config:
+    """bc: None (all periodic) or 6 entries, names or codes, for the faces
+    x1 inner, x1 outer, x2 inner, x2 outer, x3 inner, x3 outer."""
     c = Config()
     c.nx[:] = list(nx)
     c.nb[:] = list(nb)
@@ -67,6 +74,7 @@ def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0
     c.static_region = static_region
     c.static_lo[:] = list(static_lo)
     c.static_hi[:] = list(static_hi)
+    c.bc[:] = [BC[b] if isinstance(b, str) else int(b) for b in (bc or ["periodic"] * 6)]
     return c
 
 

@@ -62,7 +62,21 @@ struct Config {
   int32_t derefine_count;
   int32_t static_region;  // 1: blocks overlapping [static_lo, static_hi] refined and pinned
   double static_lo[3], static_hi[3];
+  int32_t bc[6];          // physical boundary per face (x1 inner, x1 outer, x2 ..., x3 ...):
+                          // BC_PERIODIC, BC_OUTFLOW or BC_REFLECT; both faces of an axis
+                          // periodic or neither
+  int32_t pad;
 };
+
+// Physical boundary conditions.  Reading (the paper's reflective boundaries
+// mirror the vector component normal to the boundary, Sec. 3.4; outflow is the
+// usual zero-gradient copy): a location outside the domain along axis d takes
+// the value at its image inside the domain at the same level --
+//   periodic:   shifted by the domain length;
+//   outflow:    the nearest cell inside (the first interior layer);
+//   reflecting: mirrored about the boundary face (ghost layer g takes interior
+//               layer g), with the momentum component along d negated.
+constexpr int BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2;
 
 // ---------------------------------------------------------------------------
 // Pointwise physics (Sec. 4.1: Euler equations, ideal gas)
@@ -307,9 +321,34 @@ struct Mesh {
   // u_c - u_{c-e_d}, u_{c+e_d} - u_c), s_d = +-1/4, evaluated d = 1,2,3 in
   // order, with the coarse neighbours taken from the composite field.
   void composite(int L, int64_t I, int64_t J, int64_t K, R out[NVAR]) const {
-    I = wrap(I, ncell(0, L));
-    J = wrap(J, ncell(1, L));
-    K = wrap(K, ncell(2, L));
+    int64_t X[3] = {I, J, K};
+    bool flip[3] = {false, false, false};
+    bool outside = false;
+    for (int d = 0; d < 3; ++d) {
+      const int64_t n = ncell(d, L);
+      if (X[d] >= 0 && X[d] < n) continue;
+      const int side = X[d] < 0 ? 0 : 1;
+      const int bc = cfg.bc[2 * d + side];
+      if (bc == BC_PERIODIC) {
+        X[d] = wrap(X[d], n);
+      } else if (bc == BC_OUTFLOW) {
+        X[d] = side ? n - 1 : 0;
+        outside = true;
+      } else {
+        X[d] = side ? 2 * n - 1 - X[d] : -1 - X[d];
+        flip[d] = true;
+        outside = true;
+      }
+    }
+    if (outside) {  // the image inside the domain, then the mirrored momenta
+      composite(L, X[0], X[1], X[2], out);
+      for (int d = 0; d < 3; ++d)
+        if (flip[d]) out[IM1 + d] = -out[IM1 + d];
+      return;
+    }
+    I = X[0];
+    J = X[1];
+    K = X[2];
     int64_t r0 = (I >> L) / cfg.nx[0], r1 = (J >> L) / cfg.nx[1], r2 = (K >> L) / cfg.nx[2];
     int s = root_slot(r0, r1, r2);
     if (root[s] >= 0) {  // the covering leaf is at level 0
@@ -435,6 +474,8 @@ struct Mesh {
         for (int side = 0; side < 2; ++side) {
           int64_t nl[3] = {id.lx[0], id.lx[1], id.lx[2]};
           nl[d] += side ? 1 : -1;
+          if ((nl[d] < 0 || nl[d] >= cfg.nb[d]) && cfg.bc[2 * d + side] != BC_PERIODIC)
+            continue;  // a physical boundary: no neighbour, nothing to correct
           nl[d] = wrap(nl[d], cfg.nb[d]);
           int s = root_slot(nl[0], nl[1], nl[2]);
           if (root[s] >= 0) continue;  // same-level neighbour

@@ -165,6 +165,24 @@ def sod_doubled(geo: Geometry, leaves, gamma: float = 1.4, x_if: float = 0.25, l
     return U
 
 
+def sod(geo: Geometry, leaves, gamma: float = 1.4, x_if: float = 0.0, left=(1.0, 0.0, 1.0),
+        right=(0.125, 0.0, 0.1)) -> np.ndarray:
+    """Sod shock tube along x1: the `left` state (rho, v1, p) for x1 < x_if,
+    the `right` state for x1 >= x_if (for domains with non-periodic x1
+    boundaries)."""
+    U = _alloc(geo, leaves)
+    for b, leaf in enumerate(leaves):
+        _, _, (x, _, _) = _block_cells(geo, leaf)
+        inside = x < x_if
+        rho = np.where(inside, left[0], right[0])
+        v1 = np.where(inside, left[1], right[1])
+        p = np.where(inside, left[2], right[2])
+        U[b, 0] = rho
+        U[b, 1] = rho * v1
+        U[b, 4] = p / (gamma - 1.0) + 0.5 * rho * v1 * v1
+    return U
+
+
 def _modes(kmax: int = 2):
     ks = []
     for a in range(-kmax, kmax + 1):
