@@ -64,6 +64,8 @@ extern "C" {
  *                  (static_lo, static_hi) are refined at creation and pinned
  *   precision      PH_FP64 or PH_FP32 (state and fluxes; dt and totals stay FP64)
  *   tile[3]        fused-stage tile (TX, TY, KC); 0,0,0 = pick a default
+ *   bc[6]          physical boundary of each face (PH_BC_*, below); all zero
+ *                  = periodic everywhere
  */
 typedef struct ph_config {
   int32_t nx[3];
@@ -84,7 +86,22 @@ typedef struct ph_config {
   double static_hi[3];
   int32_t precision;
   int32_t tile[3];
+  int32_t bc[6];
 } ph_config;
+
+/* Physical boundary conditions, per face in ph_config.bc (x1 inner, x1 outer,
+ * x2 inner, x2 outer, x3 inner, x3 outer).  A ghost location outside the
+ * domain takes the value of its image inside, at the same level:
+ *   PH_BC_PERIODIC  shifted by the domain length (both faces of an axis
+ *                   periodic or neither);
+ *   PH_BC_OUTFLOW   the nearest interior cell (zero-gradient copy);
+ *   PH_BC_REFLECT   mirrored about the face (ghost layer g takes interior
+ *                   layer g) with the momentum component normal to the face
+ *                   negated (the paper's reflective boundaries, Sec. 3.4).
+ * Batched meshes and the adjoint are periodic only. */
+#define PH_BC_PERIODIC 0
+#define PH_BC_OUTFLOW 1
+#define PH_BC_REFLECT 2
 
 typedef struct ph_mesh ph_mesh;
 
@@ -102,7 +119,7 @@ const char* ph_last_error(void);
 /* Create a mesh (Sec. 2.1): root grid, oct-tree, Z-order, static refinement
  * (Sec. 3.8).  `stream` is a cudaStream_t (NULL = legacy default stream).
  * The state is zero until ph_set_state.  *out receives the handle.
- * Errors: PH_ERR_INVALID (nx < 4, nb < 1, bad level/precision/tile),
+ * Errors: PH_ERR_INVALID (nx < 4, nb < 1, bad level/precision/tile/bc),
  * PH_ERR_OOM, PH_ERR_CUDA. */
 int ph_create(const ph_config* cfg, void* stream, ph_mesh** out);
 
@@ -205,7 +222,8 @@ int ph_step_dt(ph_mesh* mesh, int32_t ncycles, const double* dts);
  *   dLdU     dL/dU_final (interior layout); dLdU0 receives dL/dU0
  *   dLdgamma receives dL/dgamma (may be NULL)
  *   on_device: 1 if U0, dLdU and dLdU0 are device pointers
- * The mesh is left at the final state of the forward run. */
+ * The mesh is left at the final state of the forward run.  Periodic uniform
+ * meshes only (PH_ERR_INVALID otherwise). */
 int ph_adjoint(ph_mesh* mesh, const void* U0, int32_t ncycles, int32_t ckpt_every,
                const double* dts, const void* dLdU, void* dLdU0, double* dLdgamma,
                int32_t on_device);
@@ -225,7 +243,8 @@ int ph_adjoint(ph_mesh* mesh, const void* U0, int32_t ncycles, int32_t ckpt_ever
  * ------------------------------------------------------------------------- */
 typedef struct ph_batch ph_batch;
 
-/* Create from nsim configurations (uniform, same precision; tile ignored). */
+/* Create from nsim configurations (uniform, periodic, same precision; tile
+ * ignored); PH_ERR_INVALID otherwise. */
 int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch** out);
 int ph_batch_destroy(ph_batch* batch);
 int ph_batch_num_blocks(const ph_batch* batch, int32_t sim, int32_t* n);

@@ -44,7 +44,6 @@ class Config(ctypes.Structure):
         ("static_lo", ctypes.c_double * 3),
         ("static_hi", ctypes.c_double * 3),
         ("bc", ctypes.c_int32 * 6),
-        ("pad", ctypes.c_int32),
     ]
 
 

@@ -65,7 +65,6 @@ struct Config {
   int32_t bc[6];          // physical boundary per face (x1 inner, x1 outer, x2 ..., x3 ...):
                           // BC_PERIODIC, BC_OUTFLOW or BC_REFLECT; both faces of an axis
                           // periodic or neither
-  int32_t pad;
 };
 
 // Physical boundary conditions.  Reading (the paper's reflective boundaries

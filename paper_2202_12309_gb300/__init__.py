@@ -64,14 +64,21 @@ class Config(ctypes.Structure):
         ("static_hi", ctypes.c_double * 3),
         ("precision", ctypes.c_int32),
         ("tile", ctypes.c_int32 * 3),
+        ("bc", ctypes.c_int32 * 6),
     ]
+
+
+BC = {"periodic": 0, "outflow": 1, "reflect": 2}
 
 
 def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0 / 3.0, cfl=0.3,
                 max_level=0, adaptive=0, dfloor=None, pfloor=None, refine_tol=0.05,
                 derefine_tol=0.0125, derefine_count=10, static_region=0,
                 static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2), precision="fp64",
-                tile=(0, 0, 0)) -> Config:
+                tile=(0, 0, 0), bc=None) -> Config:
+    """bc: None (periodic everywhere) or 6 entries, names ("periodic",
+    "outflow", "reflect") or PH_BC_* codes, for the faces x1 inner, x1 outer,
+    x2 inner, x2 outer, x3 inner, x3 outer."""
     prec = PH_FP32 if precision in ("fp32", PH_FP32) else PH_FP64
     if dfloor is None:
         dfloor = 1e-7 if prec == PH_FP32 else 1e-12
@@ -96,6 +103,7 @@ def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0
     c.static_hi[:] = list(static_hi)
     c.precision = prec
     c.tile[:] = list(tile)
+    c.bc[:] = [BC[b] if isinstance(b, str) else int(b) for b in (bc or ["periodic"] * 6)]
     return c
 
 

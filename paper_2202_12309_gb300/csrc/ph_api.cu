@@ -288,7 +288,10 @@ int build_tables(ph_mesh* m) {
       for (int d = 0; d < 3; ++d)
         for (int side = 0; side < 2; ++side) {
           int64_t o[3] = {l.lx[0], l.lx[1], l.lx[2]};
-          o[d] = (o[d] + (side ? 1 : -1) + m->nb[d]) % m->nb[d];
+          o[d] += side ? 1 : -1;
+          if ((o[d] < 0 || o[d] >= m->nb[d]) && m->cfg.bc[2 * d + side] != PH_BC_PERIODIC)
+            continue;  // a physical boundary: no neighbour, nothing to correct
+          o[d] = (o[d] + m->nb[d]) % m->nb[d];
           const int s = root_slot(m, o[0], o[1], o[2]);
           if (m->root[s] >= 0) continue;
           if (!any) {
@@ -377,7 +380,15 @@ ph::TreeView tree_view(const ph_mesh* m) {
     tv.nx[d] = m->nx[d];
     tv.S[d] = m->S[d];
   }
+  for (int f = 0; f < 6; ++f) tv.bc[f] = m->cfg.bc[f];
   return tv;
+}
+
+// The six faces' boundary kinds packed 2 bits each (0: periodic everywhere).
+int bc_mask(const ph_mesh* m) {
+  int b = 0;
+  for (int f = 0; f < 6; ++f) b |= (m->cfg.bc[f] & 3) << (2 * f);
+  return b;
 }
 
 template <class T>
@@ -401,7 +412,8 @@ int fill_ghosts_t(ph_mesh* m, T* U) {
   if (m->two_level) {
     PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->nleaf(), m->stream));
   } else {
-    PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream));
+    PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream,
+                                        m->d_leaf_id, m->nb, bc_mask(m)));
   }
   return PH_OK;
 }
@@ -453,10 +465,12 @@ template <class T>
 int enqueue_uniform_cycle(ph_mesh* m, cudaStream_t s) {
   const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
   PH_CUDA(ph::launch_stage<T>(a1, m->tile[0], m->tile[1], s, tmap_for(m, 1)));
-  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s));
+  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s,
+                                      m->d_leaf_id, m->nb, bc_mask(m)));
   const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
   PH_CUDA(ph::launch_stage<T>(a2, m->tile[0], m->tile[1], s, tmap_for(m, 2)));
-  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s));
+  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s,
+                                      m->d_leaf_id, m->nb, bc_mask(m)));
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, s));
   return PH_OK;
 }
@@ -600,11 +614,11 @@ int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
     cudaError_t e = cudaEventRecord(ev[0], m->stream);
     if (!e) e = ph::launch_stage<T>(a1, m->tile[0], m->tile[1], m->stream, tmap_for(m, 1));
     if (!e) e = cudaEventRecord(ev[1], m->stream);
-    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream);
+    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m));
     if (!e) e = cudaEventRecord(ev[2], m->stream);
     if (!e) e = ph::launch_stage<T>(a2, m->tile[0], m->tile[1], m->stream, tmap_for(m, 2));
     if (!e) e = cudaEventRecord(ev[3], m->stream);
-    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream);
+    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m));
     if (!e) e = cudaEventRecord(ev[4], m->stream);
     if (!e) e = ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream);
     if (!e) e = cudaEventRecord(ev[5], m->stream);
@@ -727,6 +741,7 @@ namespace ph {
 
 int mesh_access(ph_mesh* m, MeshAccess* out) {
   if (m->two_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
+  if (bc_mask(m)) return fail(PH_ERR_INVALID, "adjoint: periodic meshes only");
   out->U0 = m->U0;
   out->U1 = m->U1;
   out->nbr = m->d_nbr;
@@ -806,6 +821,13 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     return fail(PH_ERR_INVALID, "ph_create: precision must be PH_FP64 or PH_FP32");
   if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0))
     return fail(PH_ERR_INVALID, "ph_create: need gamma > 1 and cfl > 0");
+  for (int d = 0; d < 3; ++d) {
+    const int lo = cfg->bc[2 * d], hi = cfg->bc[2 * d + 1];
+    if (lo < PH_BC_PERIODIC || lo > PH_BC_REFLECT || hi < PH_BC_PERIODIC || hi > PH_BC_REFLECT)
+      return fail(PH_ERR_INVALID, "ph_create: bc entries must be PH_BC_PERIODIC, _OUTFLOW or _REFLECT");
+    if ((lo == PH_BC_PERIODIC) != (hi == PH_BC_PERIODIC))
+      return fail(PH_ERR_INVALID, "ph_create: both faces of an axis periodic or neither");
+  }
   ph_mesh* m = new ph_mesh();
   m->cfg = *cfg;
   m->stream = (cudaStream_t)stream;

@@ -44,6 +44,7 @@ struct TreeView {
   int nb[3];
   int nx[3];
   int S[3];
+  int bc[6];  // physical boundary per face (PH_BC_*)
 };
 
 template <class T>
@@ -64,9 +65,13 @@ bool stage_tile_supported(int TX, int TY);
 cudaError_t configure_stage_kernels();
 
 // K1 (uniform mesh): every ghost cell of every leaf copied from the
-// same-level neighbour given by nbr[27 * leaf + region].
+// same-level neighbour given by nbr[27 * leaf + region], or, across a
+// physical boundary face (bcm: 2 bits per face, x1 inner first; leaf_id and
+// nb give the leaf's place in the root grid), from its image in the block.
 template <class T>
-cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s);
+cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
+                                 const int* leaf_id = nullptr, const int nb[3] = nullptr,
+                                 int bcm = 0);
 
 // K1 (two-level mesh): every ghost cell of every leaf takes the composite
 // field of the mesh (copy / restriction / prolongation), one launch.

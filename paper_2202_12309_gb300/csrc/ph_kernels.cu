@@ -14,11 +14,34 @@
 
 namespace ph {
 
+// Physical boundaries (PH_BC_*): a ghost index g outside the domain along
+// one axis maps to its image inside, in the same block: outflow takes the
+// first interior layer, reflecting mirrors about the face (and the caller
+// negates the normal momentum).  lo/hi: the block touches the inner / outer
+// face of the domain; bc_lo/bc_hi: the faces' boundary kinds.  Returns true
+// if the index was mapped (the offset along the axis becomes 0).
+__device__ __forceinline__ bool bc_image(int& g, int o, int n, bool lo, bool hi, int bc_lo,
+                                         int bc_hi, bool& reflect) {
+  if (o < 0 && lo && bc_lo != 0) {
+    g = bc_lo == 1 ? NG : 2 * NG - 1 - g;
+    reflect = bc_lo == 2;
+    return true;
+  }
+  if (o > 0 && hi && bc_hi != 0) {
+    g = bc_hi == 1 ? NG + n - 1 : 2 * (NG + n) - 1 - g;
+    reflect = bc_hi == 2;
+    return true;
+  }
+  return false;
+}
+
 // blockIdx.x = leaf, blockIdx.y = chunk of the leaf's ghost shell (each CTA
 // copies about 1024 ghost cells, so that small meshes of large blocks still
-// fill the GPU).
+// fill the GPU).  bcm packs the six faces' boundary kinds (2 bits each, x1
+// inner first); 0 = periodic everywhere, where leaf_id and nbl are unused.
 template <class T>
-__global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx) {
+__global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx,
+                                     const int* __restrict__ leaf_id, int3 nbl, int bcm) {
   const int nxa[3] = {nx.x, nx.y, nx.z};
   const Shell sh(nxa);
   const int b = blockIdx.x;
@@ -29,28 +52,50 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx)
   const int total = sh.count();
   const int per = (total + gridDim.y - 1) / gridDim.y;
   const int c0 = blockIdx.y * per, c1 = min(total, c0 + per);
+  int lx[3] = {0, 0, 0};
+  if (bcm) {
+    lx[0] = leaf_id[4 * b + 1];
+    lx[1] = leaf_id[4 * b + 2];
+    lx[2] = leaf_id[4 * b + 3];
+  }
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     int i, j, k;
     sh.cell(c, i, j, k);
-    const int ox = i < NG ? -1 : (i >= NG + nx.x ? 1 : 0);
-    const int oy = j < NG ? -1 : (j >= NG + nx.y ? 1 : 0);
-    const int oz = k < NG ? -1 : (k >= NG + nx.z ? 1 : 0);
+    int ox = i < NG ? -1 : (i >= NG + nx.x ? 1 : 0);
+    int oy = j < NG ? -1 : (j >= NG + nx.y ? 1 : 0);
+    int oz = k < NG ? -1 : (k >= NG + nx.z ? 1 : 0);
+    int si = i, sj = j, sk = k;
+    bool f1 = false, f2 = false, f3 = false;
+    if (bcm) {
+      if (bc_image(si, ox, nx.x, lx[0] == 0, lx[0] == nbl.x - 1, bcm & 3, (bcm >> 2) & 3, f1)) ox = 0;
+      if (bc_image(sj, oy, nx.y, lx[1] == 0, lx[1] == nbl.y - 1, (bcm >> 4) & 3, (bcm >> 6) & 3, f2)) oy = 0;
+      if (bc_image(sk, oz, nx.z, lx[2] == 0, lx[2] == nbl.z - 1, (bcm >> 8) & 3, (bcm >> 10) & 3, f3)) oz = 0;
+    }
     const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
     const T* srcb = U + (size_t)src * NV * vs;
-    const size_t so = ((size_t)(k - oz * nx.z) * S2 + (j - oy * nx.y)) * S1 + (i - ox * nx.x);
+    const size_t so = ((size_t)(sk - oz * nx.z) * S2 + (sj - oy * nx.y)) * S1 + (si - ox * nx.x);
     const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
+    T w[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dstb[v * vs + dofs] = srcb[v * vs + so];
+    for (int v = 0; v < NV; ++v) w[v] = srcb[v * vs + so];
+    if (f1) w[1] = -w[1];
+    if (f2) w[2] = -w[2];
+    if (f3) w[3] = -w[3];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dstb[v * vs + dofs] = w[v];
   }
 }
 
 template <class T>
-cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s) {
+cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
+                                 const int* leaf_id, const int nb[3], int bcm) {
   if (nleaf <= 0) return cudaSuccess;
   const long long S1 = nx[0] + 2 * NG, S2 = nx[1] + 2 * NG, S3 = nx[2] + 2 * NG;
   const long long shell = S1 * S2 * S3 - (long long)nx[0] * nx[1] * nx[2];
   const int chunks = (int)std::min<long long>(64, std::max<long long>(1, (shell + 1023) / 1024));
-  ghost_uniform_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(U, nbr, make_int3(nx[0], nx[1], nx[2]));
+  const int3 nbl = nb ? make_int3(nb[0], nb[1], nb[2]) : make_int3(1, 1, 1);
+  ghost_uniform_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(
+      U, nbr, make_int3(nx[0], nx[1], nx[2]), leaf_id, nbl, bcm);
   return cudaGetLastError();
 }
 
@@ -69,6 +114,31 @@ __device__ __forceinline__ long long wrapi(long long i, long long n) {
   return r < 0 ? r + n : r;
 }
 
+// Map a global cell index of a level whose axis has N cells into the domain
+// (PH_BC_*: periodic shift, outflow clamp, reflecting mirror); returns true
+// if the normal momentum must be negated.
+__device__ __forceinline__ bool domain_image(long long& X, long long N, int bc_lo, int bc_hi) {
+  if (X >= 0 && X < N) return false;
+  const int bc = X < 0 ? bc_lo : bc_hi;
+  if (bc == 0) {
+    X = wrapi(X, N);
+    return false;
+  }
+  if (bc == 1) {
+    X = X < 0 ? 0 : N - 1;
+    return false;
+  }
+  X = X < 0 ? -1 - X : 2 * N - 1 - X;
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ void negate_momenta(T out[NV], bool f1, bool f2, bool f3) {
+  if (f1) out[1] = -out[1];
+  if (f2) out[2] = -out[2];
+  if (f3) out[3] = -out[3];
+}
+
 template <class T>
 __device__ __forceinline__ void read_cell(const T* U, const TreeView& tv, int leaf, int li, int lj,
                                           int lk, T out[NV]) {
@@ -83,15 +153,16 @@ __device__ void coarse_value(const T* U, const TreeView& tv, long long I, long l
                              T out[NV]) {
   const long long N1 = (long long)tv.nb[0] * tv.nx[0], N2 = (long long)tv.nb[1] * tv.nx[1],
                   N3 = (long long)tv.nb[2] * tv.nx[2];
-  I = wrapi(I, N1);
-  J = wrapi(J, N2);
-  K = wrapi(K, N3);
+  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
+  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
+  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
   const int r1 = (int)(I / tv.nx[0]), r2 = (int)(J / tv.nx[1]), r3 = (int)(K / tv.nx[2]);
   const int s = (r3 * tv.nb[1] + r2) * tv.nb[0] + r1;
   const int lf = tv.root[s];
   if (lf >= 0) {
     read_cell(U, tv, lf, (int)(I - (long long)r1 * tv.nx[0]), (int)(J - (long long)r2 * tv.nx[1]),
               (int)(K - (long long)r3 * tv.nx[2]), out);
+    negate_momenta(out, f1, f2, f3);
     return;
   }
   T sum[NV];
@@ -111,6 +182,7 @@ __device__ void coarse_value(const T* U, const TreeView& tv, long long I, long l
       }
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = mul_rn(T(0.125), sum[v]);
+  negate_momenta(out, f1, f2, f3);
 }
 
 template <class T>
@@ -124,9 +196,9 @@ __device__ void fine_value(const T* U, const TreeView& tv, long long I, long lon
                            T out[NV]) {
   const long long N1 = 2LL * tv.nb[0] * tv.nx[0], N2 = 2LL * tv.nb[1] * tv.nx[1],
                   N3 = 2LL * tv.nb[2] * tv.nx[2];
-  I = wrapi(I, N1);
-  J = wrapi(J, N2);
-  K = wrapi(K, N3);
+  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
+  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
+  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
   const int r1 = (int)((I >> 1) / tv.nx[0]), r2 = (int)((J >> 1) / tv.nx[1]),
             r3 = (int)((K >> 1) / tv.nx[2]);
   const int s = (r3 * tv.nb[1] + r2) * tv.nb[0] + r1;
@@ -135,6 +207,7 @@ __device__ void fine_value(const T* U, const TreeView& tv, long long I, long lon
     const int kid = tv.kids[8 * s + (l1 & 1) + 2 * (l2 & 1) + 4 * (l3 & 1)];
     read_cell(U, tv, kid, (int)(I - (long long)l1 * tv.nx[0]), (int)(J - (long long)l2 * tv.nx[1]),
               (int)(K - (long long)l3 * tv.nx[2]), out);
+    negate_momenta(out, f1, f2, f3);
     return;
   }
   const long long C[3] = {I >> 1, J >> 1, K >> 1};
@@ -157,6 +230,7 @@ __device__ void fine_value(const T* U, const TreeView& tv, long long I, long lon
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) out[v] = acc[v];
+  negate_momenta(out, f1, f2, f3);
 }
 
 template <class T>
@@ -494,7 +568,8 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
 
 // explicit instantiations
 #define PH_INST(T)                                                                              \
-  template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t); \
+  template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t, \
+                                              const int*, const int*, int);                   \
   template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, int,          \
                                                  cudaStream_t);                                 \
   template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
