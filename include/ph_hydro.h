@@ -141,6 +141,18 @@ int ph_set_state(ph_mesh* mesh, const void* U, int64_t count, int32_t on_device)
 /* Copy the interior state out (same layout and count rule). */
 int ph_get_state(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
 
+/* Stream-ordered forms of ph_set_state / ph_get_state: the copies, ghost
+ * fill and first dt are queued on the mesh's stream and the call returns
+ * without waiting for them, so that transfers of one mesh overlap the cycles
+ * of another on another stream.  A host buffer must stay valid and unchanged
+ * (set) or unread (get) until the stream has passed the copy; page-locked
+ * host memory is needed for the copy to overlap anything (a pageable source
+ * or destination makes the driver copy synchronously).  Errors as the
+ * synchronous forms; ph_get_state_async also PH_ERR_STATE before a state was
+ * set. */
+int ph_set_state_async(ph_mesh* mesh, const void* U, int64_t count, int32_t on_device);
+int ph_get_state_async(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
+
 /* Copy whole blocks out, ghosts included: layout U[block][var][k][j][i] over
  * (nx+4)^3 cells (count = blocks*5*(nx1+4)*(nx2+4)*(nx3+4)). */
 int ph_get_full(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);

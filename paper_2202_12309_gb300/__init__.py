@@ -33,7 +33,7 @@ EXPORTS = [
     "ph_batch_get_state", "ph_batch_step", "ph_batch_get_dt", "ph_batch_get_time",
     "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
     "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint", "ph_debug_math",
-    "ph_save", "ph_load",
+    "ph_save", "ph_load", "ph_set_state_async", "ph_get_state_async",
 ]
 
 
@@ -163,6 +163,8 @@ def lib():
             "ph_adjoint": [P, P, i32, i32, dp, P, P, dp, i32],
             "ph_debug_math": [i32, i32, P, P, i64, P],
             "ph_save": [P, ctypes.c_char_p, i32],
+            "ph_set_state_async": [P, P, i64, i32],
+            "ph_get_state_async": [P, P, i64, i32],
             "ph_load": [ctypes.c_char_p, P, ctypes.POINTER(P)],
         }
         for name, args in sig.items():
@@ -326,18 +328,27 @@ class Mesh:
     def count(self) -> int:
         return int(np.prod(self.state_shape()))
 
-    def set_state(self, U):
+    def set_state(self, U, sync: bool = True):
+        """Copy a state in.  sync=False queues it on the mesh's stream
+        (ph_set_state_async): U must then stay alive and unchanged until the
+        stream has passed the copy (page-locked memory for overlap)."""
         if isinstance(U, np.ndarray):
+            if not sync and not (U.flags.c_contiguous and U.dtype == self.dtype):
+                raise ValueError("an asynchronous copy needs a contiguous array of the mesh's dtype")
             U = np.ascontiguousarray(U, dtype=self.dtype)
         p, dev = _ptr(U)
         # the element count of the buffer itself: the ABI rejects a mismatch
-        check(self.L.ph_set_state(self.h, ctypes.c_void_p(p), _count(U), dev))
+        fn = self.L.ph_set_state if sync else self.L.ph_set_state_async
+        check(fn(self.h, ctypes.c_void_p(p), _count(U), dev))
 
-    def get_state(self, out=None):
+    def get_state(self, out=None, sync: bool = True):
+        """Copy the state out.  sync=False queues the copy on the mesh's
+        stream (ph_get_state_async); read `out` after synchronising it."""
         if out is None:
             out = np.zeros(self.state_shape(), dtype=self.dtype)
         p, dev = _ptr(out)
-        check(self.L.ph_get_state(self.h, ctypes.c_void_p(p), _count(out), dev))
+        fn = self.L.ph_get_state if sync else self.L.ph_get_state_async
+        check(fn(self.h, ctypes.c_void_p(p), _count(out), dev))
         return out
 
     def get_full(self) -> np.ndarray:

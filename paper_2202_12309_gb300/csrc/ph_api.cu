@@ -636,7 +636,7 @@ int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
 }
 
 template <class T>
-int set_state_t(ph_mesh* m, const void* U, int on_device) {
+int set_state_t(ph_mesh* m, const void* U, int on_device, int async = 0) {
   int rc;
   const size_t count = (size_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
   T* packed;
@@ -649,22 +649,17 @@ int set_state_t(ph_mesh* m, const void* U, int on_device) {
   }
   PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 0, m->stream));
   if ((rc = fill_ghosts_t<T>(m, (T*)m->U0))) return rc;
-  ph::DevScalars zero;
-  std::memset(&zero, 0, sizeof(zero));
-  PH_CUDA(cudaMemcpyAsync(m->sc, &zero, sizeof(zero), cudaMemcpyHostToDevice, m->stream));
+  PH_CUDA(cudaMemsetAsync(m->sc, 0, sizeof(ph::DevScalars), m->stream));
   if ((rc = refresh_dt_t<T>(m))) return rc;
   // the first dt is reported as the "last" dt until a cycle runs
-  PH_CUDA(cudaStreamSynchronize(m->stream));
-  ph::DevScalars hs;
-  PH_CUDA(cudaMemcpy(&hs, m->sc, sizeof(hs), cudaMemcpyDeviceToHost));
-  hs.dt_last = hs.dt_next;
-  PH_CUDA(cudaMemcpy(m->sc, &hs, sizeof(hs), cudaMemcpyHostToDevice));
+  PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 4, m->stream));
+  if (!async) PH_CUDA(cudaStreamSynchronize(m->stream));
   m->state_set = true;
   return PH_OK;
 }
 
 template <class T>
-int get_state_t(ph_mesh* m, void* U, int on_device) {
+int get_state_t(ph_mesh* m, void* U, int on_device, int async = 0) {
   int rc;
   const size_t count = (size_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
   T* packed;
@@ -677,7 +672,7 @@ int get_state_t(ph_mesh* m, void* U, int on_device) {
   PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 1, m->stream));
   if (!on_device)
     PH_CUDA(cudaMemcpyAsync(U, packed, count * sizeof(T), cudaMemcpyDeviceToHost, m->stream));
-  PH_CUDA(cudaStreamSynchronize(m->stream));
+  if (!async) PH_CUDA(cudaStreamSynchronize(m->stream));
   return PH_OK;
 }
 
@@ -942,6 +937,19 @@ int ph_get_state(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
   if (!m || !U) return fail(PH_ERR_INVALID, "ph_get_state: null argument");
   if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_get_state: count mismatch");
   return DISPATCH(m, get_state_t, m, U, on_device);
+}
+
+int ph_set_state_async(ph_mesh* m, const void* U, int64_t count, int32_t on_device) {
+  if (!m || !U) return fail(PH_ERR_INVALID, "ph_set_state_async: null argument");
+  if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_set_state_async: count mismatch");
+  return DISPATCH(m, set_state_t, m, U, on_device, 1);
+}
+
+int ph_get_state_async(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
+  if (!m || !U) return fail(PH_ERR_INVALID, "ph_get_state_async: null argument");
+  if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_get_state_async: count mismatch");
+  if (!m->state_set) return fail(PH_ERR_STATE, "ph_get_state_async: set the state first");
+  return DISPATCH(m, get_state_t, m, U, on_device, 1);
 }
 
 int ph_get_full(ph_mesh* m, void* U, int64_t count, int32_t on_device) {

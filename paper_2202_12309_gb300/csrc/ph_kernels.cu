@@ -352,6 +352,7 @@ __global__ void advance_kernel(DevScalars* sc, double cfl, int mode) {
     if (!isfinite(dt) || !(dt > 0.0)) sc->nonfinite = 1;
     sc->wmax_bits = 0ull;
   }
+  if (mode & 4) sc->dt_last = sc->dt_next;  // a fresh state reports its first dt as the last
 }
 
 cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s) {
