@@ -32,6 +32,8 @@
 #include <complex>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <set>
 #include <vector>
 
 namespace ho {
@@ -55,7 +57,7 @@ struct Config {
   int32_t nx[3];          // interior cells per block along x1,x2,x3
   int32_t nb[3];          // root-grid blocks along x1,x2,x3
   double xmin[3], xmax[3];
-  int32_t max_level;      // 0 = uniform, 1 = two levels
+  int32_t max_level;      // 0 = uniform; finest level of the tree (at most 4)
   int32_t adaptive;       // tag + remesh after every cycle
   double gamma, cfl, dfloor, pfloor;
   double refine_tol, derefine_tol;
@@ -214,8 +216,8 @@ struct Mesh {
   std::vector<LeafId> leaf;
   std::vector<int32_t> age;            // cycles since the leaf was created
   std::vector<std::vector<R>> U;       // per leaf: NVAR x S3 x S2 x S1 (ghosts included)
-  std::vector<int32_t> root;           // root-grid slot -> leaf index, or -1 when refined
-  std::vector<std::vector<int32_t>> kids;  // root-grid slot -> 8 child leaf indices
+  std::vector<int32_t> root;           // root-grid slot -> level-0 leaf index, or -1 when refined
+  std::map<std::array<int64_t, 4>, int32_t> leaf_at;  // (level, lx1, lx2, lx3) -> leaf index
   double time = 0.0, dt = 0.0;
   int64_t cycle = 0;
   long floors = 0;
@@ -237,10 +239,12 @@ struct Mesh {
     age.assign(leaf.size(), 0);
     U.assign(leaf.size(), std::vector<R>(block_len(), R(0.0)));
     sort_and_index();
-    if (cfg.max_level >= 1 && cfg.static_region) {
+    // static refinement, one level at a time up to max_level (reading: the
+    // static region is refined to the finest level)
+    for (int l = 0; l < cfg.max_level && cfg.static_region; ++l) {
       std::vector<int8_t> flags(leaf.size(), 0);
       for (size_t b = 0; b < leaf.size(); ++b)
-        if (in_static_region(leaf[b])) flags[b] = 1;
+        if (leaf[b].level == l && in_static_region(leaf[b])) flags[b] = 1;
       remesh(flags);
     }
   }
@@ -288,17 +292,47 @@ struct Mesh {
     U.swap(u2);
     size_t nroot = (size_t)cfg.nb[0] * cfg.nb[1] * cfg.nb[2];
     root.assign(nroot, -1);
-    kids.assign(nroot, std::vector<int32_t>(8, -1));
+    leaf_at.clear();
     for (size_t b = 0; b < leaf.size(); ++b) {
       const LeafId& id = leaf[b];
-      if (id.level == 0) {
-        root[root_slot(id.lx[0], id.lx[1], id.lx[2])] = (int32_t)b;
-      } else {
-        int s = root_slot(id.lx[0] >> 1, id.lx[1] >> 1, id.lx[2] >> 1);
-        int c = (int)((id.lx[0] & 1) + 2 * (id.lx[1] & 1) + 4 * (id.lx[2] & 1));
-        kids[s][c] = (int32_t)b;
-      }
+      if (id.level == 0) root[root_slot(id.lx[0], id.lx[1], id.lx[2])] = (int32_t)b;
+      leaf_at[{id.level, id.lx[0], id.lx[1], id.lx[2]}] = (int32_t)b;
     }
+  }
+
+  // Number of blocks along d at level l.
+  int64_t nblk(int d, int l) const { return (int64_t)cfg.nb[d] << l; }
+
+  // The leaf covering block location blk of level L (Sec. 2.1: every
+  // location is covered by exactly one leaf): its index, with its level in
+  // *lev (<= L), or -1 when finer leaves cover it.
+  int cover(int L, const int64_t blk[3], int* lev) const {
+    for (int d = 0; d <= L; ++d) {
+      const int sh = L - d;
+      if (d == 0) {
+        const int b = root[root_slot(blk[0] >> sh, blk[1] >> sh, blk[2] >> sh)];
+        if (b >= 0) { *lev = 0; return b; }
+        continue;
+      }
+      auto it = leaf_at.find({d, blk[0] >> sh, blk[1] >> sh, blk[2] >> sh});
+      if (it != leaf_at.end()) { *lev = d; return it->second; }
+    }
+    return -1;
+  }
+
+  // Block location of level l adjacent to blk in direction o (each -1, 0, +1):
+  // false across a physical (non-periodic) boundary, else wrapped.
+  bool neighbour(int l, const int64_t blk[3], const int o[3], int64_t out[3]) const {
+    for (int d = 0; d < 3; ++d) {
+      int64_t x = blk[d] + o[d];
+      const int64_t n = nblk(d, l);
+      if (x < 0 || x >= n) {
+        if (cfg.bc[2 * d + (x < 0 ? 0 : 1)] != BC_PERIODIC) return false;
+        x = wrap(x, n);
+      }
+      out[d] = x;
+    }
+    return true;
   }
 
   static int64_t wrap(int64_t i, int64_t n) { return ((i % n) + n) % n; }
@@ -313,12 +347,14 @@ struct Mesh {
   }
 
   // The composite field: the value of cell (I,J,K) of level L built from the
-  // interior data of the leaves only (periodic wrap).  Same level: copy.
-  // Covered by finer leaves: restriction = mean of the 8 children (Sec. 3.7,
-  // "restricted first").  Covered by a coarser leaf: prolongation (Sec. 3.7,
-  // "interpolated (prolongated)"); reading: u_f = u_c + sum_d s_d minmod(
-  // u_c - u_{c-e_d}, u_{c+e_d} - u_c), s_d = +-1/4, evaluated d = 1,2,3 in
-  // order, with the coarse neighbours taken from the composite field.
+  // interior data of the leaves only, level by level.  Covered by a leaf of
+  // level L: copy.  Covered by finer leaves: restriction = mean of the 8 cells
+  // of level L+1 (Sec. 3.7, "restricted first").  Covered by a coarser leaf:
+  // prolongation from level L-1 (Sec. 3.7, "interpolated (prolongated)");
+  // reading: u_f = u_c + sum_d s_d minmod(u_c - u_{c-e_d}, u_{c+e_d} - u_c),
+  // s_d = +-1/4, evaluated d = 1,2,3 in order, with the coarse values taken
+  // from the composite field of level L-1 (itself prolonged or restricted
+  // where no level-(L-1) leaf covers them).
   void composite(int L, int64_t I, int64_t J, int64_t K, R out[NVAR]) const {
     int64_t X[3] = {I, J, K};
     bool flip[3] = {false, false, false};
@@ -348,15 +384,18 @@ struct Mesh {
     I = X[0];
     J = X[1];
     K = X[2];
-    int64_t r0 = (I >> L) / cfg.nx[0], r1 = (J >> L) / cfg.nx[1], r2 = (K >> L) / cfg.nx[2];
-    int s = root_slot(r0, r1, r2);
-    if (root[s] >= 0) {  // the covering leaf is at level 0
-      if (L == 0) { leaf_value(root[s], I, J, K, out); return; }
-      // prolongation from the coarse leaf (L == 1)
+    const int64_t blk[3] = {I / cfg.nx[0], J / cfg.nx[1], K / cfg.nx[2]};
+    int lev = 0;
+    const int b = cover(L, blk, &lev);
+    if (b >= 0 && lev == L) {  // a leaf of this level covers it
+      leaf_value(b, I, J, K, out);
+      return;
+    }
+    if (b >= 0) {  // a coarser leaf covers it: prolongation from level L-1
       int64_t C[3] = {I >> 1, J >> 1, K >> 1};
       int64_t F[3] = {I, J, K};
       R uc[NVAR];
-      composite(0, C[0], C[1], C[2], uc);
+      composite(L - 1, C[0], C[1], C[2], uc);
       R acc[NVAR];
       for (int v = 0; v < NVAR; ++v) acc[v] = uc[v];
       for (int d = 0; d < 3; ++d) {
@@ -364,8 +403,8 @@ struct Mesh {
         cm[d] -= 1;
         cp[d] += 1;
         R um[NVAR], up[NVAR];
-        composite(0, cm[0], cm[1], cm[2], um);
-        composite(0, cp[0], cp[1], cp[2], up);
+        composite(L - 1, cm[0], cm[1], cm[2], um);
+        composite(L - 1, cp[0], cp[1], cp[2], up);
         double sgn = (F[d] & 1) ? 0.25 : -0.25;
         for (int v = 0; v < NVAR; ++v)
           acc[v] = acc[v] + sgn * minmod(R(uc[v] - um[v]), R(up[v] - uc[v]));
@@ -373,20 +412,15 @@ struct Mesh {
       for (int v = 0; v < NVAR; ++v) out[v] = acc[v];
       return;
     }
-    // the location is refined: the covering leaves are at level 1
-    if (L == 1) {
-      int c = (int)(((I / cfg.nx[0]) & 1) + 2 * ((J / cfg.nx[1]) & 1) + 4 * ((K / cfg.nx[2]) & 1));
-      leaf_value(kids[s][c], I, J, K, out);
-      return;
-    }
-    // restriction (L == 0): mean of the 8 fine cells, summed c3 outer, c1 inner
+    // finer leaves cover it: restriction = mean of the 8 cells of level L+1,
+    // summed c3 outer, c1 inner
     R sum[NVAR];
     for (int v = 0; v < NVAR; ++v) sum[v] = R(0.0);
     for (int c3 = 0; c3 < 2; ++c3)
       for (int c2 = 0; c2 < 2; ++c2)
         for (int c1 = 0; c1 < 2; ++c1) {
           R f[NVAR];
-          composite(1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
+          composite(L + 1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
           for (int v = 0; v < NVAR; ++v) sum[v] = sum[v] + f[v];
         }
     for (int v = 0; v < NVAR; ++v) out[v] = 0.125 * sum[v];
@@ -460,24 +494,24 @@ struct Mesh {
     return F;
   }
 
-  // Flux correction (Sec. 3.7): at a face shared by a level-0 leaf and
-  // level-1 leaves, the coarse flux is replaced by the mean of the 4 fine
+  // Flux correction (Sec. 3.7): at a face shared by a leaf of level l and
+  // leaves of level l+1, the coarse flux is replaced by the mean of the 4 fine
   // fluxes over it (summed t1 inner, t2 outer).
   void flux_correct(std::vector<std::array<Fluxes, 3>>& F) {
     if (cfg.max_level < 1) return;
     for (size_t b = 0; b < leaf.size(); ++b) {
       const LeafId& id = leaf[b];
-      if (id.level != 0) continue;
+      const int l = id.level;
+      if (l >= cfg.max_level) continue;
       for (int d = 0; d < 3; ++d) {
         int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
         for (int side = 0; side < 2; ++side) {
-          int64_t nl[3] = {id.lx[0], id.lx[1], id.lx[2]};
-          nl[d] += side ? 1 : -1;
-          if ((nl[d] < 0 || nl[d] >= cfg.nb[d]) && cfg.bc[2 * d + side] != BC_PERIODIC)
-            continue;  // a physical boundary: no neighbour, nothing to correct
-          nl[d] = wrap(nl[d], cfg.nb[d]);
-          int s = root_slot(nl[0], nl[1], nl[2]);
-          if (root[s] >= 0) continue;  // same-level neighbour
+          int o[3] = {0, 0, 0};
+          o[d] = side ? 1 : -1;
+          int64_t nb_[3];
+          if (!neighbour(l, id.lx, o, nb_)) continue;  // physical boundary: nothing to correct
+          int lev = 0;
+          if (cover(l, nb_, &lev) >= 0) continue;      // same-level or coarser neighbour
           int cface = side ? cfg.nx[d] : 0;  // coarse face index along d
           int fface = side ? 0 : cfg.nx[d];  // fine face index along d in the fine block
           int childd = side ? 0 : 1;         // child offset along d adjacent to the face
@@ -489,23 +523,24 @@ struct Mesh {
                 for (int q1 = 0; q1 < 2; ++q1) {
                   int64_t g1 = 2 * (id.lx[t1] * cfg.nx[t1] + a1) + q1;  // fine global index
                   int64_t g2 = 2 * (id.lx[t2] * cfg.nx[t2] + a2) + q2;
-                  int c[3];
-                  c[d] = childd;
-                  c[t1] = (int)((g1 / cfg.nx[t1]) & 1);
-                  c[t2] = (int)((g2 / cfg.nx[t2]) & 1);
-                  int fb = kids[s][c[0] + 2 * c[1] + 4 * c[2]];
-                  int l[3];
-                  l[d] = fface;
-                  l[t1] = (int)(g1 % cfg.nx[t1]);
-                  l[t2] = (int)(g2 % cfg.nx[t2]);
+                  int64_t fblk[3];
+                  fblk[d] = 2 * nb_[d] + childd;
+                  fblk[t1] = g1 / cfg.nx[t1];
+                  fblk[t2] = g2 / cfg.nx[t2];
+                  auto it = leaf_at.find({l + 1, fblk[0], fblk[1], fblk[2]});
+                  const int fb = it->second;  // exists: neighbours differ by one level at most
+                  int lc[3];
+                  lc[d] = fface;
+                  lc[t1] = (int)(g1 % cfg.nx[t1]);
+                  lc[t2] = (int)(g2 % cfg.nx[t2]);
                   for (int v = 0; v < NVAR; ++v)
-                    sum[v] = sum[v] + F[fb][d].at(v, l[2], l[1], l[0]);
+                    sum[v] = sum[v] + F[fb][d].at(v, lc[2], lc[1], lc[0]);
                 }
-              int l[3];
-              l[d] = cface;
-              l[t1] = a1;
-              l[t2] = a2;
-              for (int v = 0; v < NVAR; ++v) F[b][d].at(v, l[2], l[1], l[0]) = 0.25 * sum[v];
+              int lc[3];
+              lc[d] = cface;
+              lc[t1] = a1;
+              lc[t2] = a2;
+              for (int v = 0; v < NVAR; ++v) F[b][d].at(v, lc[2], lc[1], lc[0]) = 0.25 * sum[v];
             }
         }
       }
@@ -616,42 +651,103 @@ struct Mesh {
 
   // Rebuild the tree (Sec. 2.1/3.8): refine every +1 leaf into 8 children;
   // merge 8 siblings that are all -1 and at least derefine_count cycles old
-  // ("derefinement only allowed periodically").  New data is the composite
-  // field of the old mesh at the new leaf's level, i.e. prolongation for new
-  // children and restriction for merged parents.  Returns true if changed.
+  // ("derefinement only allowed periodically").  Reading (the Athena++ rule
+  // the paper defers to): leaves that touch -- across a face, an edge or a
+  // corner -- differ by one level at most, so refining a leaf first refines
+  // every touching leaf that is coarser than it (repeated until nothing more
+  // changes), and 8 siblings do not merge if a leaf touching their parent
+  // would then be two levels finer.  New data is the composite field of the
+  // old mesh at the new leaf's level: prolongation for new children,
+  // restriction for merged parents.  Returns true if the tree changed.
   bool remesh(const std::vector<int8_t>& flags, bool check_age = true) {
-    std::vector<LeafId> nl;
-    std::vector<int32_t> na;
-    std::vector<bool> keep_old(leaf.size(), true);
-    bool changed = false;
-    for (size_t b = 0; b < leaf.size(); ++b) {
-      if (flags[b] == 1 && leaf[b].level == 0 && cfg.max_level >= 1) {
-        keep_old[b] = false;
-        changed = true;
-        for (int c = 0; c < 8; ++c) {
-          LeafId k{1, {2 * leaf[b].lx[0] + (c & 1), 2 * leaf[b].lx[1] + ((c >> 1) & 1),
-                       2 * leaf[b].lx[2] + ((c >> 2) & 1)}};
-          nl.push_back(k);
-          na.push_back(0);
+    static const int kDirs = 27;
+    auto dir = [](int q, int o[3]) {
+      o[0] = q % 3 - 1;
+      o[1] = (q / 3) % 3 - 1;
+      o[2] = q / 9 - 1;
+    };
+    // 1. refinement set, closed under the one-level rule
+    std::set<int> refine;
+    for (size_t b = 0; b < leaf.size(); ++b)
+      if (flags[b] == 1 && leaf[b].level < cfg.max_level) refine.insert((int)b);
+    std::vector<int> work(refine.begin(), refine.end());
+    while (!work.empty()) {
+      const int a = work.back();
+      work.pop_back();
+      const LeafId& A = leaf[a];
+      for (int q = 0; q < kDirs; ++q) {
+        int o[3];
+        dir(q, o);
+        if (o[0] == 0 && o[1] == 0 && o[2] == 0) continue;
+        int64_t nbk[3];
+        if (!neighbour(A.level, A.lx, o, nbk)) continue;
+        int lev = 0;
+        const int c = cover(A.level, nbk, &lev);
+        if (c >= 0 && lev < A.level && !refine.count(c)) {
+          refine.insert(c);
+          work.push_back(c);
         }
       }
     }
-    for (size_t s = 0; s < root.size(); ++s) {
-      if (root[s] >= 0) continue;
-      bool all = true;
+    // 2. merges: complete sibling sets, all -1, old enough, not static, none
+    //    refined now, and no leaf touching the parent left two levels finer
+    std::vector<LeafId> nl;
+    std::vector<int32_t> na;
+    std::vector<bool> keep_old(leaf.size(), true);
+    bool changed = !refine.empty();
+    for (int b : refine) {
+      keep_old[b] = false;
+      const LeafId& P = leaf[b];
       for (int c = 0; c < 8; ++c) {
-        int b = kids[s][c];
-        if (b < 0 || flags[b] != -1 || (check_age && age[b] < cfg.derefine_count) ||
-            in_static_region(leaf[b])) {
-          all = false;
-          break;
+        nl.push_back(LeafId{P.level + 1, {2 * P.lx[0] + (c & 1), 2 * P.lx[1] + ((c >> 1) & 1),
+                                          2 * P.lx[2] + ((c >> 2) & 1)}});
+        na.push_back(0);
+      }
+    }
+    std::set<std::array<int64_t, 4>> parents_done;
+    for (size_t b = 0; b < leaf.size(); ++b) {
+      const LeafId& K = leaf[b];
+      if (K.level == 0) continue;
+      const int pl = K.level - 1;
+      const int64_t P[3] = {K.lx[0] >> 1, K.lx[1] >> 1, K.lx[2] >> 1};
+      if (!parents_done.insert({pl, P[0], P[1], P[2]}).second) continue;
+      int sib[8];
+      bool ok = true;
+      for (int c = 0; c < 8 && ok; ++c) {
+        auto it = leaf_at.find({K.level, 2 * P[0] + (c & 1), 2 * P[1] + ((c >> 1) & 1),
+                                2 * P[2] + ((c >> 2) & 1)});
+        if (it == leaf_at.end()) { ok = false; break; }
+        const int sb = it->second;
+        sib[c] = sb;
+        if (flags[sb] != -1 || (check_age && age[sb] < cfg.derefine_count) ||
+            in_static_region(leaf[sb]) || refine.count(sb))
+          ok = false;
+      }
+      for (int q = 0; q < kDirs && ok; ++q) {
+        int o[3];
+        dir(q, o);
+        if (o[0] == 0 && o[1] == 0 && o[2] == 0) continue;
+        int64_t nbk[3];
+        if (!neighbour(pl, P, o, nbk)) continue;
+        int lev = 0;
+        const int c = cover(pl, nbk, &lev);
+        if (c >= 0) continue;  // covered at the parent's level or coarser
+        // finer: every child block of the neighbour that touches the parent
+        // must be a leaf of level pl+1 that is not being refined
+        for (int cc = 0; cc < 8 && ok; ++cc) {
+          const int cb[3] = {cc & 1, (cc >> 1) & 1, (cc >> 2) & 1};
+          bool touches = true;
+          for (int d = 0; d < 3; ++d)
+            if ((o[d] == 1 && cb[d] != 0) || (o[d] == -1 && cb[d] != 1)) touches = false;
+          if (!touches) continue;
+          auto it = leaf_at.find({pl + 1, 2 * nbk[0] + cb[0], 2 * nbk[1] + cb[1], 2 * nbk[2] + cb[2]});
+          if (it == leaf_at.end() || refine.count(it->second)) ok = false;
         }
       }
-      if (!all) continue;
+      if (!ok) continue;
       changed = true;
-      for (int c = 0; c < 8; ++c) keep_old[kids[s][c]] = false;
-      const LeafId& k0 = leaf[kids[s][0]];
-      nl.push_back(LeafId{0, {k0.lx[0] >> 1, k0.lx[1] >> 1, k0.lx[2] >> 1}});
+      for (int c = 0; c < 8; ++c) keep_old[sib[c]] = false;
+      nl.push_back(LeafId{pl, {P[0], P[1], P[2]}});
       na.push_back(0);
     }
     if (!changed) return false;

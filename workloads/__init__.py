@@ -183,6 +183,27 @@ def sod(geo: Geometry, leaves, gamma: float = 1.4, x_if: float = 0.0, left=(1.0,
     return U
 
 
+def kelvin_helmholtz(geo: Geometry, leaves, gamma: float = 1.4, seed: int = 0, amp: float = 0.01,
+                     rho_in: float = 2.0, rho_out: float = 1.0, shear: float = 0.5, p0: float = 2.5,
+                     half_width: float = 0.25) -> np.ndarray:
+    """Kelvin-Helmholtz shear layers (the paper's adaptive-refinement problem
+    generator, Sec. 4.1): rho = rho_in, v1 = +shear inside |x2| < half_width,
+    rho = rho_out, v1 = -shear outside; p = p0; seeded perturbations
+    amp (u - 1/2) on v1 and v2 in every cell (two independent draws)."""
+    U = _alloc(geo, leaves)
+    for b, leaf in enumerate(leaves):
+        lev, (I, J, K), (x, y, z) = _block_cells(geo, leaf)
+        inside = np.abs(y) < half_width
+        rho = np.where(inside, rho_in, rho_out)
+        v1 = np.where(inside, shear, -shear) + amp * (cell_uniform(seed, lev, I, J, K) - 0.5)
+        v2 = amp * (cell_uniform(seed + 1, lev, I, J, K) - 0.5)
+        U[b, 0] = rho
+        U[b, 1] = rho * v1
+        U[b, 2] = rho * v2
+        U[b, 4] = p0 / (gamma - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2)
+    return U
+
+
 def _modes(kmax: int = 2):
     ks = []
     for a in range(-kmax, kmax + 1):
