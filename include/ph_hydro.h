@@ -15,7 +15,7 @@
  *    crosses this ABI.
  *  - Work is enqueued on the stream given at creation; calls that return data
  *    to host memory synchronise that stream.  ph_step does not synchronise
- *    (except on two-level meshes, where it reads refinement flags each cycle).
+ *    (except on multi-level meshes, where it reads refinement flags each cycle).
  *  - Caller buffers are borrowed for the duration of the call only.
  *  - State arrays are in the mesh's precision (double for PH_FP64, float for
  *    PH_FP32), conserved variables (rho, m1, m2, m3, E), interior cells only,
@@ -51,14 +51,17 @@ extern "C" {
  * ph_create.
  *   nx[3]          interior cells per block along x1, x2, x3 (each >= 4)
  *   nb[3]          root-grid blocks along x1, x2, x3 (each >= 1)
- *   xmin/xmax      domain extent; boundaries are periodic
- *   max_level      0 (uniform) or 1 (two levels)
- *   adaptive       1: tag and remesh after every cycle (max_level 1 only)
+ *   xmin/xmax      domain extent; boundaries as in bc[] (periodic by default)
+ *   max_level      0 (uniform) .. 4: finest level of the block tree; blocks
+ *                  that touch (face, edge or corner) differ by one level at
+ *                  most (a refinement splits coarser touching blocks first;
+ *                  siblings do not merge next to blocks two levels finer)
+ *   adaptive       1: tag and remesh after every cycle (max_level >= 1)
  *   gamma          adiabatic index; cfl: Courant number
  *   dfloor/pfloor  density and pressure floors applied when converting to
  *                  primitive variables (every application is counted)
- *   refine_tol     refine a level-0 block whose indicator exceeds it
- *   derefine_tol   derefine 8 level-1 siblings whose indicators are all below it
+ *   refine_tol     refine a block below max_level whose indicator exceeds it
+ *   derefine_tol   merge 8 sibling blocks whose indicators are all below it
  *   derefine_count siblings must be at least this many cycles old to merge
  *   static_region  1: level-0 blocks overlapping the open box
  *                  (static_lo, static_hi) are refined at creation and pinned
@@ -158,7 +161,7 @@ int ph_get_state_async(ph_mesh* mesh, void* U, int64_t count, int32_t on_device)
 int ph_get_full(ph_mesh* mesh, void* U, int64_t count, int32_t on_device);
 
 /* Advance `ncycles` cycles (Sec. 3.11 MultiStageDriver): per cycle, two RK
- * stages each followed by the ghost exchange (Sec. 3.7) and, on two-level
+ * stages each followed by the ghost exchange (Sec. 3.7) and, on multi-level
  * meshes, flux correction; then dt for the next cycle (Sec. 3.10) and, when
  * adaptive, tagging and remesh (Sec. 3.8).  Uniform meshes replay a captured
  * CUDA graph of one cycle and return without synchronising. */

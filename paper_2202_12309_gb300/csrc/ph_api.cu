@@ -2,9 +2,9 @@
 // device tables, the per-cycle launch sequence and its CUDA-graph capture.
 //
 // Host tree (arXiv:2202.12309 Sec. 2.1): root grid of nb1 x nb2 x nb3 blocks,
-// each of which may split into 2^3 children (two levels); leaves are kept in
-// Z-order of their location scaled to the finest level (x1 in the lowest
-// bit).  Leaf b's data lives in slot b of the device pools, so a remesh
+// each of which may split into 2^3 children, recursively up to max_level;
+// leaves that touch differ by one level at most; leaves are kept in Z-order
+// of their location scaled to the finest level (x1 in the lowest bit).  Leaf b's data lives in slot b of the device pools, so a remesh
 // rebuilds the pool in the new order (Sec. 3.8: the tree is rebuilt first,
 // then populated).
 #include <algorithm>
@@ -74,10 +74,10 @@ struct ph_mesh {
   int nx[3], S[3], nb[3];
   size_t block_elems = 0;  // NV * S1 * S2 * S3
   size_t esize = 8;
-  bool two_level = false;
+  bool multi_level = false;
 
   std::vector<Leaf> leaf;
-  std::vector<int> root, kids;  // host copies of the lookup tables
+  std::vector<int> node;  // octree node table (ph_internal.h), host copy
 
   // device memory
   void* U0 = nullptr;
@@ -86,8 +86,7 @@ struct ph_mesh {
   ph::DevScalars* sc = nullptr;
   int* d_nbr = nullptr;
   int8_t* d_level = nullptr;
-  int* d_root = nullptr;
-  int* d_kids = nullptr;
+  int* d_node = nullptr;
   int* d_leaf_id = nullptr;
   double* d_partial = nullptr;
   double* d_totals = nullptr;
@@ -160,62 +159,165 @@ int root_slot(const ph_mesh* m, int64_t a, int64_t b, int64_t c) {
   return (int)((c * m->nb[1] + b) * m->nb[0] + a);
 }
 
-// Sort leaves in Z-order and rebuild the host lookup tables.
+// Octree node table of a leaf list (entries as in ph_internal.h): false if
+// the leaves overlap or leave a gap.
+bool build_nodes(const std::vector<Leaf>& leaves, const int nb[3], std::vector<int>& node) {
+  const size_t nroot = (size_t)nb[0] * nb[1] * nb[2];
+  node.assign(nroot, ph::NODE_UNSET);
+  for (size_t b = 0; b < leaves.size(); ++b) {
+    const Leaf& l = leaves[b];
+    const int L = l.level;
+    int n = (int)((((l.lx[2] >> L) * nb[1]) + (l.lx[1] >> L)) * nb[0] + (l.lx[0] >> L));
+    for (int d = 0; d < L; ++d) {
+      if (node[n] >= 0) return false;  // a coarser leaf already covers it
+      if (node[n] == ph::NODE_UNSET) {
+        const int base = (int)node.size();
+        node.resize(node.size() + 8, ph::NODE_UNSET);
+        node[n] = -2 - base;
+      }
+      const int s = L - d - 1;
+      n = ph::node_children(node[n]) +
+          (int)(((l.lx[0] >> s) & 1) + 2 * ((l.lx[1] >> s) & 1) + 4 * ((l.lx[2] >> s) & 1));
+    }
+    if (node[n] != ph::NODE_UNSET) return false;  // overlap
+    node[n] = (int)b;
+  }
+  for (int v : node)
+    if (v == ph::NODE_UNSET) return false;  // gap
+  return true;
+}
+
+// Sort leaves in Z-order and rebuild the node table.
 void index_tree(ph_mesh* m) {
   const int ml = m->cfg.max_level;
   std::stable_sort(m->leaf.begin(), m->leaf.end(), [ml](const Leaf& a, const Leaf& b) {
     const uint64_t ka = zkey(a, ml), kb = zkey(b, ml);
     return ka != kb ? ka < kb : a.level < b.level;
   });
-  const size_t nroot = (size_t)m->nb[0] * m->nb[1] * m->nb[2];
-  m->root.assign(nroot, -1);
-  m->kids.assign(nroot * 8, -1);
-  for (int b = 0; b < m->nleaf(); ++b) {
-    const Leaf& l = m->leaf[b];
-    if (l.level == 0) {
-      m->root[root_slot(m, l.lx[0], l.lx[1], l.lx[2])] = b;
-    } else {
-      const int s = root_slot(m, l.lx[0] >> 1, l.lx[1] >> 1, l.lx[2] >> 1);
-      m->kids[8 * s + (l.lx[0] & 1) + 2 * (l.lx[1] & 1) + 4 * (l.lx[2] & 1)] = b;
+  build_nodes(m->leaf, m->nb, m->node);
+}
+
+// Leaf covering block location blk of level L (inside the domain), with its
+// level in *lev; -1 when finer leaves cover it.
+int cover(const ph_mesh* m, int L, const int64_t blk[3], int* lev) {
+  int n = root_slot(m, blk[0] >> L, blk[1] >> L, blk[2] >> L);
+  for (int d = 0;; ++d) {
+    const int v = m->node[n];
+    if (v >= 0) {
+      *lev = d;
+      return v;
     }
+    if (d == L || v == ph::NODE_UNSET) return -1;
+    const int s = L - d - 1;
+    n = ph::node_children(v) + (int)(((blk[0] >> s) & 1) + 2 * ((blk[1] >> s) & 1) + 4 * ((blk[2] >> s) & 1));
   }
 }
 
-// New leaf list from flags: +1 splits a level-0 leaf; a complete set of 8
-// level-1 siblings all flagged -1 (old enough when check_age, none pinned by
-// the static region) merges.  Returns false if nothing changes.
+// Block location of level l next to blk in direction o: false across a
+// physical boundary face, otherwise wrapped periodically.
+bool neighbour(const ph_mesh* m, int l, const int64_t blk[3], const int o[3], int64_t out[3]) {
+  for (int d = 0; d < 3; ++d) {
+    int64_t x = blk[d] + o[d];
+    const int64_t n = (int64_t)m->nb[d] << l;
+    if (x < 0 || x >= n) {
+      if (m->cfg.bc[2 * d + (x < 0 ? 0 : 1)] != PH_BC_PERIODIC) return false;
+      x = (x + n) % n;
+    }
+    out[d] = x;
+  }
+  return true;
+}
+
+// New leaf list from flags (Sec. 2.1/3.8; the one-level rule of Athena++,
+// which the paper defers to): +1 splits a leaf below max_level, and every
+// leaf touching a splitting leaf (face, edge or corner) that is coarser than
+// it splits too, repeatedly; a complete set of 8 sibling leaves all flagged
+// -1 (old enough when check_age, none pinned by the static region, none
+// splitting) merges unless a leaf touching their parent would then be two
+// levels finer.  Returns false if nothing changes.
 bool next_tree(const ph_mesh* m, const std::vector<int8_t>& flags, bool check_age,
                std::vector<Leaf>& out) {
   out.clear();
-  std::vector<char> keep(m->leaf.size(), 1);
-  bool changed = false;
-  for (size_t b = 0; b < m->leaf.size(); ++b) {
-    const Leaf& l = m->leaf[b];
-    if (flags[b] == 1 && l.level == 0 && m->cfg.max_level >= 1) {
-      keep[b] = 0;
-      changed = true;
-      for (int c = 0; c < 8; ++c)
-        out.push_back(Leaf{1, {2 * l.lx[0] + (c & 1), 2 * l.lx[1] + ((c >> 1) & 1),
-                               2 * l.lx[2] + ((c >> 2) & 1)}, 0});
+  const int n = m->nleaf();
+  std::vector<char> split(n, 0), keep(n, 1);
+  std::vector<int> todo;
+  for (int b = 0; b < n; ++b)
+    if (flags[b] == 1 && m->leaf[b].level < m->cfg.max_level) {
+      split[b] = 1;
+      todo.push_back(b);
+    }
+  while (!todo.empty()) {
+    const Leaf& a = m->leaf[todo.back()];
+    todo.pop_back();
+    for (int q = 0; q < 27; ++q) {
+      const int o[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+      if (!o[0] && !o[1] && !o[2]) continue;
+      int64_t nbk[3];
+      if (!neighbour(m, a.level, a.lx, o, nbk)) continue;
+      int lev = 0;
+      const int c = cover(m, a.level, nbk, &lev);
+      if (c >= 0 && lev < a.level && !split[c]) {
+        split[c] = 1;
+        todo.push_back(c);
+      }
     }
   }
-  for (size_t s = 0; s < m->root.size(); ++s) {
-    if (m->root[s] >= 0) continue;
-    bool merge = true;
-    for (int c = 0; c < 8 && merge; ++c) {
-      const int b = m->kids[8 * s + c];
-      if (b < 0 || flags[b] != -1) merge = false;
-      else if (check_age && m->leaf[b].age < m->cfg.derefine_count) merge = false;
-      else if (overlaps_static(m, m->leaf[b])) merge = false;
-    }
-    if (!merge) continue;
+  bool changed = false;
+  for (int b = 0; b < n; ++b) {
+    if (!split[b]) continue;
     changed = true;
-    for (int c = 0; c < 8; ++c) keep[m->kids[8 * s + c]] = 0;
-    const Leaf& k0 = m->leaf[m->kids[8 * s]];
-    out.push_back(Leaf{0, {k0.lx[0] >> 1, k0.lx[1] >> 1, k0.lx[2] >> 1}, 0});
+    keep[b] = 0;
+    const Leaf& l = m->leaf[b];
+    for (int c = 0; c < 8; ++c)
+      out.push_back(Leaf{l.level + 1, {2 * l.lx[0] + (c & 1), 2 * l.lx[1] + ((c >> 1) & 1),
+                                       2 * l.lx[2] + ((c >> 2) & 1)}, 0});
+  }
+  // merges: visit each parent once, from its first child (child index 0)
+  for (int b = 0; b < n; ++b) {
+    const Leaf& k = m->leaf[b];
+    if (k.level == 0 || (k.lx[0] & 1) || (k.lx[1] & 1) || (k.lx[2] & 1)) continue;
+    const int pl = k.level - 1;
+    const int64_t P[3] = {k.lx[0] >> 1, k.lx[1] >> 1, k.lx[2] >> 1};
+    int sib[8];
+    bool ok = true;
+    for (int c = 0; c < 8 && ok; ++c) {
+      const int64_t cb[3] = {2 * P[0] + (c & 1), 2 * P[1] + ((c >> 1) & 1), 2 * P[2] + ((c >> 2) & 1)};
+      int lev = 0;
+      const int s = cover(m, k.level, cb, &lev);
+      if (s < 0 || lev != k.level) {
+        ok = false;
+        break;
+      }
+      sib[c] = s;
+      if (flags[s] != -1 || split[s] || (check_age && m->leaf[s].age < m->cfg.derefine_count) ||
+          overlaps_static(m, m->leaf[s]))
+        ok = false;
+    }
+    for (int q = 0; q < 27 && ok; ++q) {
+      const int o[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+      if (!o[0] && !o[1] && !o[2]) continue;
+      int64_t nbk[3];
+      if (!neighbour(m, pl, P, o, nbk)) continue;
+      int lev = 0;
+      if (cover(m, pl, nbk, &lev) >= 0) continue;  // the parent's level or coarser
+      for (int c = 0; c < 8 && ok; ++c) {          // finer: the blocks touching the parent
+        const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
+        bool touches = true;
+        for (int d = 0; d < 3; ++d)
+          if ((o[d] == 1 && cb[d] != 0) || (o[d] == -1 && cb[d] != 1)) touches = false;
+        if (!touches) continue;
+        const int64_t fb[3] = {2 * nbk[0] + cb[0], 2 * nbk[1] + cb[1], 2 * nbk[2] + cb[2]};
+        const int f = cover(m, pl + 1, fb, &lev);
+        if (f < 0 || split[f]) ok = false;
+      }
+    }
+    if (!ok) continue;
+    changed = true;
+    for (int c = 0; c < 8; ++c) keep[sib[c]] = 0;
+    out.push_back(Leaf{pl, {P[0], P[1], P[2]}, 0});
   }
   if (!changed) return false;
-  for (size_t b = 0; b < m->leaf.size(); ++b)
+  for (int b = 0; b < n; ++b)
     if (keep[b]) out.push_back(m->leaf[b]);
   return true;
 }
@@ -223,7 +325,7 @@ bool next_tree(const ph_mesh* m, const std::vector<int8_t>& flags, bool check_ag
 // ---------------------------------------------------------------- device tables
 
 void free_tables(ph_mesh* m) {
-  void** ptrs[] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_root, (void**)&m->d_kids,
+  void** ptrs[] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_node,
                    (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
                    (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
                    (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
@@ -255,14 +357,14 @@ int build_tables(ph_mesh* m) {
     level[b] = (int8_t)l.level;
     leaf_id[4 * b] = l.level;
     for (int d = 0; d < 3; ++d) leaf_id[4 * b + 1 + d] = (int)l.lx[d];
-    if (!m->two_level) {
+    if (!m->multi_level) {
       for (int oz = -1; oz <= 1; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
           for (int ox = -1; ox <= 1; ++ox) {
             const int64_t a = (l.lx[0] + ox + m->nb[0]) % m->nb[0];
             const int64_t bb = (l.lx[1] + oy + m->nb[1]) % m->nb[1];
             const int64_t c = (l.lx[2] + oz + m->nb[2]) % m->nb[2];
-            nbr[27 * b + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = m->root[root_slot(m, a, bb, c)];
+            nbr[27 * b + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = m->node[root_slot(m, a, bb, c)];
           }
     }
   }
@@ -270,30 +372,30 @@ int build_tables(ph_mesh* m) {
   if ((rc = upload(m, &m->d_level, level))) return rc;
   if ((rc = upload(m, &m->d_leaf_id, leaf_id))) return rc;
   if ((rc = upload(m, &m->d_nbr, nbr))) return rc;
-  if ((rc = upload(m, &m->d_root, m->root))) return rc;
-  if ((rc = upload(m, &m->d_kids, m->kids))) return rc;
+  if ((rc = upload(m, &m->d_node, m->node))) return rc;
   m->d_partial = (double*)m->dalloc(sizeof(double) * 5 * std::max(n, 1));
   m->d_mb = (double*)m->dalloc(sizeof(double) * std::max(n, 1));
   if (!m->d_partial || !m->d_mb) return fail(PH_ERR_OOM, "device allocation failed (tables)");
 
-  // flux-correction records: one per (level-0 leaf, face) whose neighbour is refined
+  // flux-correction records: one per (leaf, face) whose neighbour across the
+  // face is refined one level further; face_rec holds 2 rec on the coarse
+  // side and 2 rec + 1 on each of the 4 fine leaves across it
   m->nrec = 0;
   m->ncorr = 0;
-  if (m->two_level) {
+  if (m->multi_level) {
     std::vector<int> face_rec(6 * n, -1), fine_off(12 * n, 0), corr_leaf, rec_beg, rec_face;
     for (int b = 0; b < n; ++b) {
       const Leaf& l = m->leaf[b];
-      if (l.level != 0) continue;
+      if (l.level >= m->cfg.max_level) continue;
       bool any = false;
       for (int d = 0; d < 3; ++d)
         for (int side = 0; side < 2; ++side) {
-          int64_t o[3] = {l.lx[0], l.lx[1], l.lx[2]};
-          o[d] += side ? 1 : -1;
-          if ((o[d] < 0 || o[d] >= m->nb[d]) && m->cfg.bc[2 * d + side] != PH_BC_PERIODIC)
-            continue;  // a physical boundary: no neighbour, nothing to correct
-          o[d] = (o[d] + m->nb[d]) % m->nb[d];
-          const int s = root_slot(m, o[0], o[1], o[2]);
-          if (m->root[s] >= 0) continue;
+          int o[3] = {0, 0, 0};
+          o[d] = side ? 1 : -1;
+          int64_t nbk[3];
+          if (!neighbour(m, l.level, l.lx, o, nbk)) continue;  // physical boundary
+          int lev = 0;
+          if (cover(m, l.level, nbk, &lev) >= 0) continue;    // same level or coarser
           if (!any) {
             corr_leaf.push_back(b);
             rec_beg.push_back(m->nrec);
@@ -301,16 +403,20 @@ int build_tables(ph_mesh* m) {
           }
           const int rec = m->nrec++;
           const int face = 2 * d + side;
-          face_rec[6 * b + face] = rec;
+          face_rec[6 * b + face] = 2 * rec;
           rec_face.push_back(face);
-          // the 4 children of slot s adjacent to this face, on their opposite face
+          // the 4 finer leaves adjacent to this face, on their opposite face
           const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
           for (int c = 0; c < 8; ++c) {
             const int cb[3] = {c & 1, (c >> 1) & 1, (c >> 2) & 1};
             if (cb[d] != (side ? 0 : 1)) continue;
-            const int kid = m->kids[8 * s + c];
+            const int64_t fb[3] = {2 * nbk[0] + cb[0], 2 * nbk[1] + cb[1], 2 * nbk[2] + cb[2]};
+            int fl = 0;
+            const int kid = cover(m, l.level + 1, fb, &fl);
+            if (kid < 0 || fl != l.level + 1)
+              return fail(PH_ERR_STATE, "build_tables: leaves more than one level apart touch");
             const int kface = 2 * d + (1 - side);
-            face_rec[6 * kid + kface] = rec;
+            face_rec[6 * kid + kface] = 2 * rec + 1;
             fine_off[12 * kid + 2 * kface] = cb[t1];
             fine_off[12 * kid + 2 * kface + 1] = cb[t2];
           }
@@ -373,8 +479,8 @@ int ensure_staging(ph_mesh* m, size_t bytes) {
 
 ph::TreeView tree_view(const ph_mesh* m) {
   ph::TreeView tv;
-  tv.root = m->d_root;
-  tv.kids = m->d_kids;
+  tv.node = m->d_node;
+  tv.error = m->sc ? &m->sc->tree_error : nullptr;
   for (int d = 0; d < 3; ++d) {
     tv.nb[d] = m->nb[d];
     tv.nx[d] = m->nx[d];
@@ -402,14 +508,21 @@ ph::Phys<T> phys(const ph_mesh* m) {
   return P;
 }
 
-void inv_dx(const ph_mesh* m, double idx[2][3]) {
-  for (int l = 0; l < 2; ++l)
+void inv_dx(const ph_mesh* m, double idx[ph::MAXLEV + 1][3]) {
+  for (int l = 0; l <= ph::MAXLEV; ++l)
     for (int d = 0; d < 3; ++d) idx[l][d] = 1.0 / m->dx(d, l);
+}
+
+ph::LevelGeom level_geom(const ph_mesh* m) {
+  ph::LevelGeom g;
+  inv_dx(m, g.idx);
+  for (int l = 0; l <= ph::MAXLEV; ++l) g.vol[l] = m->dx(0, l) * m->dx(1, l) * m->dx(2, l);
+  return g;
 }
 
 template <class T>
 int fill_ghosts_t(ph_mesh* m, T* U) {
-  if (m->two_level) {
+  if (m->multi_level) {
     PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->nleaf(), m->stream));
   } else {
     PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream,
@@ -437,10 +550,10 @@ ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
   a.KC = m->tile[2];
   a.nleaf = m->nleaf();
   a.stage = stage;
-  a.want_rate = (stage == 2 && !m->two_level) ? 1 : 0;
+  a.want_rate = (stage == 2 && !m->multi_level) ? 1 : 0;
   a.P = phys<T>(m);
   a.sc = m->sc;
-  if (m->two_level && m->nrec > 0) {
+  if (m->multi_level && m->nrec > 0) {
     a.face_rec = m->d_face_rec;
     a.fc_coarse = (T*)m->d_fcc;
     a.fc_fine = (T*)m->d_fcf;
@@ -452,9 +565,7 @@ ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
 // New dt from the current state (K5 + bookkeeping), without committing a cycle.
 template <class T>
 int refresh_dt_t(ph_mesh* m) {
-  double idx[2][3];
-  inv_dx(m, idx);
-  PH_CUDA(ph::launch_rate<T>((const T*)m->U0, m->d_level, idx, m->nx, m->nleaf(), phys<T>(m), m->sc,
+  PH_CUDA(ph::launch_rate<T>((const T*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(), phys<T>(m), m->sc,
                              m->stream));
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 2, m->stream));
   return PH_OK;
@@ -506,19 +617,18 @@ int capture_graph(ph_mesh* m) {
 template <class T>
 int remesh_t(ph_mesh* m, std::vector<Leaf>& nl);
 
-// One two-level cycle (host-driven; flux correction after each stage).
+// One multi-level cycle (host-driven; flux correction after each stage).
 template <class T>
-int two_level_cycle(ph_mesh* m) {
+int multi_level_cycle(ph_mesh* m) {
   int rc;
   if ((rc = refresh_dt_t<T>(m))) return rc;
-  double idx[2][3];
-  inv_dx(m, idx);
+  const ph::LevelGeom geom = level_geom(m);
   for (int stage = 1; stage <= 2; ++stage) {
     const ph::StageArgs<T> a = stage_args<T>(m, stage);
     PH_CUDA(ph::launch_stage<T>(a, m->tile[0], m->tile[1], m->stream, tmap_for(m, stage)));
     T* out = (T*)(stage == 1 ? m->U1 : m->U0);
     PH_CUDA(ph::launch_flux_correct<T>(out, m->d_corr_leaf, m->d_rec_beg, m->ncorr, m->d_rec_face,
-                                       (const T*)m->d_fcc, (const T*)m->d_fcf, m->nx, idx[0],
+                                       (const T*)m->d_fcc, (const T*)m->d_fcf, m->nx, m->d_level, geom,
                                        stage == 1 ? 1.0 : 0.5, m->sc, m->stream));
     if ((rc = fill_ghosts_t<T>(m, out))) return rc;
   }
@@ -591,9 +701,9 @@ int remesh_t(ph_mesh* m, std::vector<Leaf>& nl) {
 template <class T>
 int step_t(ph_mesh* m, int n) {
   int rc;
-  if (m->two_level) {
+  if (m->multi_level) {
     for (int c = 0; c < n; ++c)
-      if ((rc = two_level_cycle<T>(m))) return rc;
+      if ((rc = multi_level_cycle<T>(m))) return rc;
     return PH_OK;
   }
   if (!m->gexec)
@@ -678,9 +788,7 @@ int get_state_t(ph_mesh* m, void* U, int on_device, int async = 0) {
 
 template <class T>
 int totals_t(ph_mesh* m, double out[5]) {
-  double vol[2];
-  for (int l = 0; l < 2; ++l) vol[l] = m->dx(0, l) * m->dx(1, l) * m->dx(2, l);
-  PH_CUDA(ph::launch_totals<T>((const T*)m->U0, m->d_level, vol, m->nx, m->nleaf(), m->d_partial,
+  PH_CUDA(ph::launch_totals<T>((const T*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(), m->d_partial,
                                m->d_totals, m->stream));
   PH_CUDA(cudaMemcpyAsync(out, m->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   PH_CUDA(cudaStreamSynchronize(m->stream));
@@ -735,7 +843,7 @@ namespace ph {
 
 
 int mesh_access(ph_mesh* m, MeshAccess* out) {
-  if (m->two_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
+  if (m->multi_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
   if (bc_mask(m)) return fail(PH_ERR_INVALID, "adjoint: periodic meshes only");
   out->U0 = m->U0;
   out->U1 = m->U1;
@@ -779,7 +887,7 @@ extern "C" {
 
 int ph_step_dt(ph_mesh* m, int32_t ncycles, const double* dts) {
   if (!m || (!dts && ncycles > 0) || ncycles < 0) return fail(PH_ERR_INVALID, "ph_step_dt: bad argument");
-  if (m->two_level) return fail(PH_ERR_INVALID, "ph_step_dt: uniform meshes only");
+  if (m->multi_level) return fail(PH_ERR_INVALID, "ph_step_dt: uniform meshes only");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_step_dt: set the state first");
   for (int c = 0; c < ncycles; ++c) {
     int rc = ph::mesh_cycle_fixed_dt(m, dts[c]);
@@ -808,10 +916,13 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     if (cfg->nb[d] < 1) return fail(PH_ERR_INVALID, "ph_create: nb must be >= 1");
     if (!(cfg->xmax[d] > cfg->xmin[d])) return fail(PH_ERR_INVALID, "ph_create: empty domain");
   }
-  if (cfg->max_level < 0 || cfg->max_level > 1)
-    return fail(PH_ERR_INVALID, "ph_create: max_level must be 0 or 1");
-  if (cfg->max_level == 1 && (cfg->nx[0] % 2 || cfg->nx[1] % 2 || cfg->nx[2] % 2))
-    return fail(PH_ERR_INVALID, "ph_create: two-level meshes need even nx");
+  if (cfg->max_level < 0 || cfg->max_level > ph::MAXLEV)
+    return fail(PH_ERR_INVALID, "ph_create: max_level must be 0 .. 4");
+  if (cfg->max_level >= 1 && (cfg->nx[0] % 2 || cfg->nx[1] % 2 || cfg->nx[2] % 2))
+    return fail(PH_ERR_INVALID, "ph_create: multi-level meshes need even nx");
+  for (int d = 0; d < 3; ++d)
+    if (((int64_t)cfg->nb[d] << cfg->max_level) > (1 << 20))
+      return fail(PH_ERR_INVALID, "ph_create: too many blocks along an axis at the finest level");
   if (cfg->precision != PH_FP64 && cfg->precision != PH_FP32)
     return fail(PH_ERR_INVALID, "ph_create: precision must be PH_FP64 or PH_FP32");
   if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0))
@@ -837,7 +948,7 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
   }
   m->esize = cfg->precision == PH_FP32 ? 4 : 8;
   m->block_elems = (size_t)5 * m->S[0] * m->S[1] * m->S[2];
-  m->two_level = cfg->max_level >= 1;
+  m->multi_level = cfg->max_level >= 1;
   int t[3] = {cfg->tile[0], cfg->tile[1], cfg->tile[2]};
   if (t[0] == 0 && t[1] == 0 && t[2] == 0) {
     t[0] = cfg->nx[0] >= 16 ? 16 : 8;
@@ -864,10 +975,11 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     for (int64_t j = 0; j < cfg->nb[1]; ++j)
       for (int64_t i = 0; i < cfg->nb[0]; ++i) m->leaf.push_back(Leaf{0, {i, j, k}, 0});
   index_tree(m);
-  if (m->two_level && cfg->static_region) {
+  // the static region is refined to the finest level, one level at a time
+  for (int l = 0; l < cfg->max_level && cfg->static_region; ++l) {
     std::vector<int8_t> flags(m->nleaf(), 0);
     for (int b = 0; b < m->nleaf(); ++b)
-      if (overlaps_static(m, m->leaf[b])) flags[b] = 1;
+      if (m->leaf[b].level == l && overlaps_static(m, m->leaf[b])) flags[b] = 1;
     std::vector<Leaf> nl;
     if (next_tree(m, flags, false, nl)) {
       m->leaf = nl;
@@ -1019,7 +1131,7 @@ int ph_refine_where(ph_mesh* m, const int8_t* flags, int32_t n, int32_t check_ag
                     int32_t* changed) {
   if (!m || !flags) return fail(PH_ERR_INVALID, "ph_refine_where: null argument");
   if (n != m->nleaf()) return fail(PH_ERR_INVALID, "ph_refine_where: flag count mismatch");
-  if (!m->two_level) return fail(PH_ERR_INVALID, "ph_refine_where: mesh has max_level 0");
+  if (!m->multi_level) return fail(PH_ERR_INVALID, "ph_refine_where: mesh has max_level 0");
   std::vector<int8_t> f(flags, flags + n);
   std::vector<Leaf> nl;
   const bool ch = next_tree(m, f, check_age != 0, nl);
@@ -1049,6 +1161,7 @@ int ph_status(ph_mesh* m, int64_t* floor_hits, int32_t* nonfinite) {
   if (floor_hits) *floor_hits = (int64_t)hs.floor_hits;
   if (nonfinite) *nonfinite = hs.nonfinite;
   if (hs.error) return fail(PH_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (hs.tree_error) return fail(PH_ERR_STATE, "a composite-field evaluation nested too deep");
   if (hs.floor_hits || hs.nonfinite)
     return fail(PH_ERR_NONPHYSICAL, "floors applied or non-finite dt");
   return PH_OK;
@@ -1065,14 +1178,14 @@ int ph_fill_ghosts(ph_mesh* m) {
 
 int ph_launches_per_cycle(const ph_mesh* m, int32_t* n) {
   if (!m || !n) return fail(PH_ERR_INVALID, "ph_launches_per_cycle: null argument");
-  *n = m->two_level ? 0 : 5;
+  *n = m->multi_level ? 0 : 5;
   return PH_OK;
 }
 
 int ph_profile_cycles(ph_mesh* m, int32_t ncycles, double* ms_out, int32_t nslots) {
   if (!m || !ms_out || nslots < 0 || nslots > 5 || ncycles < 0)
     return fail(PH_ERR_INVALID, "ph_profile_cycles: bad argument");
-  if (m->two_level) return fail(PH_ERR_INVALID, "ph_profile_cycles: uniform meshes only");
+  if (m->multi_level) return fail(PH_ERR_INVALID, "ph_profile_cycles: uniform meshes only");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_profile_cycles: set the state first");
   return DISPATCH(m, profile_t, m, ncycles, ms_out, nslots);
 }
@@ -1199,7 +1312,10 @@ int ph_load(const char* path, void* stream, ph_mesh** out) {
       return fail(PH_ERR_INVALID, "ph_load: bad block or grid size");
   const int64_t nroot = (int64_t)h.cfg.nb[0] * h.cfg.nb[1] * h.cfg.nb[2];
   const int64_t cells = (int64_t)h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
-  if (nroot > (1 << 24) || cells > (1 << 30) || h.nleaf < 1 || (int64_t)h.nleaf > 8 * nroot)
+  if (h.cfg.max_level < 0 || h.cfg.max_level > ph::MAXLEV)
+    return fail(PH_ERR_INVALID, "ph_load: bad max_level");
+  if (nroot > (1 << 24) || cells > (1 << 30) || h.nleaf < 1 ||
+      (int64_t)h.nleaf > (nroot << (3 * h.cfg.max_level)) || h.nleaf > (1 << 26))
     return fail(PH_ERR_INVALID, "ph_load: bad leaf count");
   {  // the file must hold exactly the tree and the state its header announces
     const int64_t want = (int64_t)sizeof(FileHead) + (int64_t)h.nleaf * sizeof(FileLeaf) +
@@ -1214,20 +1330,21 @@ int ph_load(const char* path, void* stream, ph_mesh** out) {
   std::vector<FileLeaf> lv(h.nleaf);
   if (fread(lv.data(), sizeof(FileLeaf), lv.size(), fc.f) != lv.size())
     return fail(PH_ERR_IO, "ph_load: truncated tree");
-  // the tree must tile the root grid with leaves of level 0 or 1
-  std::vector<int> cover(nroot, 0);
-  for (const FileLeaf& l : lv) {
-    if (l.level < 0 || l.level > h.cfg.max_level)
-      return fail(PH_ERR_INVALID, "ph_load: bad leaf level");
-    int64_t r[3];
-    for (int d = 0; d < 3; ++d) {
-      r[d] = l.lx[d] >> l.level;
-      if (l.lx[d] < 0 || r[d] >= h.cfg.nb[d]) return fail(PH_ERR_INVALID, "ph_load: leaf outside the domain");
+  // the tree must tile the root grid
+  {
+    std::vector<Leaf> tl;
+    for (const FileLeaf& l : lv) {
+      if (l.level < 0 || l.level > h.cfg.max_level)
+        return fail(PH_ERR_INVALID, "ph_load: bad leaf level");
+      for (int d = 0; d < 3; ++d)
+        if (l.lx[d] < 0 || l.lx[d] >= ((int64_t)h.cfg.nb[d] << l.level))
+          return fail(PH_ERR_INVALID, "ph_load: leaf outside the domain");
+      tl.push_back(Leaf{l.level, {l.lx[0], l.lx[1], l.lx[2]}, l.age});
     }
-    cover[(r[2] * h.cfg.nb[1] + r[1]) * h.cfg.nb[0] + r[0]] += l.level ? 1 : 8;
+    std::vector<int> nodes;
+    if (!build_nodes(tl, h.cfg.nb, nodes))
+      return fail(PH_ERR_INVALID, "ph_load: leaves do not tile the domain");
   }
-  for (int c : cover)
-    if (c != 8) return fail(PH_ERR_INVALID, "ph_load: leaves do not tile the domain");
   const int64_t count = (int64_t)h.nleaf * 5 * h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
   const size_t fbytes = (size_t)count * (h.data_precision == PH_FP32 ? 4 : 8);
   std::vector<unsigned char> data(fbytes);

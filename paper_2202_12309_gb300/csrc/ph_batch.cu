@@ -510,9 +510,10 @@ int set_state_member(ph_batch* b, int sim, const void* U, int on_device) {
   std::memset(&zero, 0, sizeof(zero));
   zero.error = sticky;
   PB_CUDA(cudaMemcpyAsync(b->d_sc + sim, &zero, sizeof(zero), cudaMemcpyHostToDevice, b->stream));
-  double idx[2][3];
-  for (int d = 0; d < 3; ++d) idx[0][d] = idx[1][d] = M.idx[d];
-  PB_CUDA(ph::launch_rate<T>(base, nullptr, idx, M.nx, M.nleaf, phys_of<T>(M), b->d_sc + sim,
+  ph::LevelGeom g;
+  std::memset(&g, 0, sizeof(g));
+  for (int d = 0; d < 3; ++d) g.idx[0][d] = M.idx[d];
+  PB_CUDA(ph::launch_rate<T>(base, nullptr, g, M.nx, M.nleaf, phys_of<T>(M), b->d_sc + sim,
                              b->stream));
   PB_CUDA(ph::launch_advance(b->d_sc + sim, M.cfl, 2, b->stream));
   DevScalars hs;

@@ -13,6 +13,7 @@ namespace ph {
 
 constexpr int NV = 5;   // conserved variables: rho, m1, m2, m3, E
 constexpr int NG = 2;   // ghost width: PLM needs two cells on each side
+constexpr int MAXLEV = 4;  // finest level a mesh tree may have
 
 // Device-resident scalars of one mesh.  The cycle's dt never leaves the GPU.
 struct DevScalars {
@@ -24,6 +25,8 @@ struct DevScalars {
   unsigned long long floor_hits;
   int nonfinite;                // a non-finite dt was produced
   int error;                    // bounded device wait gave up
+  int tree_error;               // composite evaluation needed more nesting than supported
+  int pad;
 };
 
 template <class T>

@@ -34,17 +34,29 @@ int mesh_cycle_read_dt(ph_mesh* m, double* dt);   // one CFL cycle, returns its 
 // Record the message that ph_last_error() returns on this thread.
 void set_error_message(const char* msg);
 
-// Device view of a mesh's block tree, used by the ghost exchange and remesh
-// kernels to find the leaf covering any cell (Sec. 2.1: one leaf covers each
-// location).  root[s] is the level-0 leaf at root slot s, or -1 when that
-// slot is refined, in which case kids[8 s + c] are its children.
+// Cell geometry per level: 1/dx per direction and the cell volume.
+struct LevelGeom {
+  double idx[MAXLEV + 1][3];
+  double vol[MAXLEV + 1];
+};
+
+// Octree node table of a mesh (Sec. 2.1: an oct-tree of blocks in which one
+// leaf covers each location).  Entries 0 .. nroot-1 are the root-grid slots
+// (x1 fastest); an entry >= 0 is the index of the leaf at that node, and an
+// entry v <= -2 marks a refined node whose 8 children are the entries
+// (-2 - v) + c, c = c1 + 2 c2 + 4 c3.
+constexpr int NODE_UNSET = -1;
+__host__ __device__ inline int node_children(int v) { return -2 - v; }
+
+// Device view of the tree, used by the ghost exchange and remesh kernels to
+// evaluate the composite field anywhere.
 struct TreeView {
-  const int* root;
-  const int* kids;
+  const int* node;
   int nb[3];
   int nx[3];
   int S[3];
-  int bc[6];  // physical boundary per face (PH_BC_*)
+  int bc[6];        // physical boundary per face (PH_BC_*)
+  int* error;       // set if an evaluation needs more nesting than supported
 };
 
 template <class T>
@@ -73,7 +85,7 @@ cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nlea
                                  const int* leaf_id = nullptr, const int nb[3] = nullptr,
                                  int bcm = 0);
 
-// K1 (two-level mesh): every ghost cell of every leaf takes the composite
+// K1 (multi-level mesh): every ghost cell of every leaf takes the composite
 // field of the mesh (copy / restriction / prolongation), one launch.
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
@@ -86,11 +98,12 @@ cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uo
 
 // K5: max over interior cells of (|v_d|+c)/dx_d into sc->wmax_bits.
 template <class T>
-cudaError_t launch_rate(const T* U, const int8_t* level, const double idx[2][3], const int nx[3],
+cudaError_t launch_rate(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
                         int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s);
 
 // dt bookkeeping: mode bit 1 commits the cycle (time += dt, cycle++),
-// bit 2 computes the next dt = cfl / wmax and clears wmax.
+// bit 2 computes the next dt = cfl / wmax and clears wmax, bit 4 copies the
+// next dt into the last (a fresh state).
 cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s);
 
 // Interior <-> padded copies.  dir 0: packed -> padded, 1: padded -> packed.
@@ -100,7 +113,7 @@ cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int di
 // Conserved totals: per-leaf FP64 sums into partial[nleaf*5], then one
 // ordered compensated sum into out[5].
 template <class T>
-cudaError_t launch_totals(const T* U, const int8_t* level, const double vol[2], const int nx[3],
+cudaError_t launch_totals(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
                           int nleaf, double* partial, double* out, cudaStream_t s);
 
 // K6: refinement indicator per leaf (FP64).
@@ -112,7 +125,7 @@ cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb,
 template <class T>
 cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
-                                const int nx[3], const double idx0[3], double beta,
-                                const DevScalars* sc, cudaStream_t s);
+                                const int nx[3], const int8_t* level, const LevelGeom& g,
+                                double beta, const DevScalars* sc, cudaStream_t s);
 
 }  // namespace ph

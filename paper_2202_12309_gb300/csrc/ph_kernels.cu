@@ -100,15 +100,29 @@ cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nlea
 }
 
 // --------------------------------------------------------------------------
-// Composite field of a two-level mesh (Sec. 2.1 + Sec. 3.7).
-//   level-0 cell: the level-0 leaf's value, or the mean of its 8 children
-//                 (restriction; summed c3 outer, c1 inner, then x 1/8);
-//   level-1 cell: the level-1 leaf's value, or the coarse value plus
-//                 +-1/4 of the minmod-limited coarse differences in x1, x2,
-//                 x3 in that order (prolongation).
+// Composite field of a multi-level mesh (Sec. 2.1 + Sec. 3.7).  The value of
+// cell (I,J,K) of level L, built from leaf interiors only:
+//   covered by a leaf of level L:  that leaf's value;
+//   covered by finer leaves:       mean of the 8 cells of level L+1
+//                                  (restriction; summed c3 outer, c1 inner,
+//                                  then x 1/8);
+//   covered by a coarser leaf:     the level-(L-1) value plus +-1/4 of the
+//                                  minmod-limited level-(L-1) differences in
+//                                  x1, x2, x3 in that order (prolongation).
+// Locations outside the domain first map to their image inside (PH_BC_*).
 // Every add/multiply is an unfused round-to-nearest operation so that the
 // result is reproducible operation by operation.
+//
+// The evaluation nests (a prolongation needs values of the next coarser
+// level, which may themselves be prolonged or restricted); it is written as
+// a chain of D non-inlined functions rather than a recursion, so that its
+// stack is sized statically.  In a tree whose touching leaves differ by one
+// level and whose blocks have at least 4 cells per axis, ghost cells need 2
+// nested evaluations and new leaves at a remesh 3; the chain allows 4 and
+// records an error instead of going deeper.
 // --------------------------------------------------------------------------
+constexpr int COMPOSITE_DEPTH = 4;
+
 __device__ __forceinline__ long long wrapi(long long i, long long n) {
   long long r = i % n;
   return r < 0 ? r + n : r;
@@ -139,6 +153,23 @@ __device__ __forceinline__ void negate_momenta(T out[NV], bool f1, bool f2, bool
   if (f3) out[3] = -out[3];
 }
 
+// Leaf covering block (b1,b2,b3) of level L (coordinates inside the domain):
+// its index with its level in *lev, or -1 when finer leaves cover it.
+__device__ __forceinline__ int tree_cover(const TreeView& tv, int L, long long b1, long long b2,
+                                          long long b3, int* lev) {
+  int node = (int)(((b3 >> L) * tv.nb[1] + (b2 >> L)) * tv.nb[0] + (b1 >> L));
+  for (int d = 0;; ++d) {
+    const int v = tv.node[node];
+    if (v >= 0) {
+      *lev = d;
+      return v;
+    }
+    if (d == L || v == NODE_UNSET) return -1;
+    const int s = L - d - 1;
+    node = node_children(v) + (int)(((b1 >> s) & 1) + 2 * ((b2 >> s) & 1) + 4 * ((b3 >> s) & 1));
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void read_cell(const T* U, const TreeView& tv, int leaf, int li, int lj,
                                           int lk, T out[NV]) {
@@ -149,88 +180,72 @@ __device__ __forceinline__ void read_cell(const T* U, const TreeView& tv, int le
 }
 
 template <class T>
-__device__ void coarse_value(const T* U, const TreeView& tv, long long I, long long J, long long K,
-                             T out[NV]) {
-  const long long N1 = (long long)tv.nb[0] * tv.nx[0], N2 = (long long)tv.nb[1] * tv.nx[1],
-                  N3 = (long long)tv.nb[2] * tv.nx[2];
-  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
-  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
-  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
-  const int r1 = (int)(I / tv.nx[0]), r2 = (int)(J / tv.nx[1]), r3 = (int)(K / tv.nx[2]);
-  const int s = (r3 * tv.nb[1] + r2) * tv.nb[0] + r1;
-  const int lf = tv.root[s];
-  if (lf >= 0) {
-    read_cell(U, tv, lf, (int)(I - (long long)r1 * tv.nx[0]), (int)(J - (long long)r2 * tv.nx[1]),
-              (int)(K - (long long)r3 * tv.nx[2]), out);
-    negate_momenta(out, f1, f2, f3);
-    return;
-  }
-  T sum[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) sum[v] = T(0);
-  for (int c3 = 0; c3 < 2; ++c3)
-    for (int c2 = 0; c2 < 2; ++c2)
-      for (int c1 = 0; c1 < 2; ++c1) {
-        const long long fi = 2 * I + c1, fj = 2 * J + c2, fk = 2 * K + c3;
-        const int l1 = (int)(fi / tv.nx[0]), l2 = (int)(fj / tv.nx[1]), l3 = (int)(fk / tv.nx[2]);
-        const int kid = tv.kids[8 * s + (l1 & 1) + 2 * (l2 & 1) + 4 * (l3 & 1)];
-        T f[NV];
-        read_cell(U, tv, kid, (int)(fi - (long long)l1 * tv.nx[0]), (int)(fj - (long long)l2 * tv.nx[1]),
-                  (int)(fk - (long long)l3 * tv.nx[2]), f);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sum[v] = add_rn(sum[v], f[v]);
-      }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = mul_rn(T(0.125), sum[v]);
-  negate_momenta(out, f1, f2, f3);
-}
-
-template <class T>
 __device__ __forceinline__ T minmod_dev(T a, T b) {
   if (mul_rn(a, b) > T(0)) return fabs(a) < fabs(b) ? a : b;
   return T(0);
 }
 
-template <class T>
-__device__ void fine_value(const T* U, const TreeView& tv, long long I, long long J, long long K,
-                           T out[NV]) {
-  const long long N1 = 2LL * tv.nb[0] * tv.nx[0], N2 = 2LL * tv.nb[1] * tv.nx[1],
-                  N3 = 2LL * tv.nb[2] * tv.nx[2];
+template <class T, int D>
+__device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int L, long long I,
+                                             long long J, long long K, T* out) {
+  const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
+                  N3 = (long long)tv.nb[2] * tv.nx[2] << L;
   const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
   const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
   const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
-  const int r1 = (int)((I >> 1) / tv.nx[0]), r2 = (int)((J >> 1) / tv.nx[1]),
-            r3 = (int)((K >> 1) / tv.nx[2]);
-  const int s = (r3 * tv.nb[1] + r2) * tv.nb[0] + r1;
-  if (tv.root[s] < 0) {
-    const int l1 = (int)(I / tv.nx[0]), l2 = (int)(J / tv.nx[1]), l3 = (int)(K / tv.nx[2]);
-    const int kid = tv.kids[8 * s + (l1 & 1) + 2 * (l2 & 1) + 4 * (l3 & 1)];
-    read_cell(U, tv, kid, (int)(I - (long long)l1 * tv.nx[0]), (int)(J - (long long)l2 * tv.nx[1]),
-              (int)(K - (long long)l3 * tv.nx[2]), out);
+  const long long b1 = I / tv.nx[0], b2 = J / tv.nx[1], b3 = K / tv.nx[2];
+  int lev = 0;
+  const int lf = tree_cover(tv, L, b1, b2, b3, &lev);
+  if (lf >= 0 && lev == L) {
+    read_cell(U, tv, lf, (int)(I - b1 * tv.nx[0]), (int)(J - b2 * tv.nx[1]), (int)(K - b3 * tv.nx[2]),
+              out);
     negate_momenta(out, f1, f2, f3);
     return;
   }
-  const long long C[3] = {I >> 1, J >> 1, K >> 1};
-  const long long F[3] = {I, J, K};
-  T uc[NV], acc[NV];
-  coarse_value(U, tv, C[0], C[1], C[2], uc);
+  if constexpr (D == 0) {
+    atomicExch(tv.error, 1);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = uc[v];
-  for (int d = 0; d < 3; ++d) {
-    long long cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
-    cm[d] -= 1;
-    cp[d] += 1;
-    T um[NV], up[NV];
-    coarse_value(U, tv, cm[0], cm[1], cm[2], um);
-    coarse_value(U, tv, cp[0], cp[1], cp[2], up);
-    const T sg = (F[d] & 1) ? T(0.25) : T(-0.25);
+    for (int v = 0; v < NV; ++v) out[v] = T(0);
+    return;
+  } else {
+    if (lf >= 0) {  // coarser leaf: prolongation from level L-1
+      const long long C[3] = {I >> 1, J >> 1, K >> 1};
+      const long long F[3] = {I, J, K};
+      T uc[NV], acc[NV];
+      composite_value<T, D - 1>(U, tv, L - 1, C[0], C[1], C[2], uc);
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      acc[v] = add_rn(acc[v], mul_rn(sg, minmod_dev(sub_rn(uc[v], um[v]), sub_rn(up[v], uc[v]))));
+      for (int v = 0; v < NV; ++v) acc[v] = uc[v];
+      for (int d = 0; d < 3; ++d) {
+        long long cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
+        cm[d] -= 1;
+        cp[d] += 1;
+        T um[NV], up[NV];
+        composite_value<T, D - 1>(U, tv, L - 1, cm[0], cm[1], cm[2], um);
+        composite_value<T, D - 1>(U, tv, L - 1, cp[0], cp[1], cp[2], up);
+        const T sg = (F[d] & 1) ? T(0.25) : T(-0.25);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          acc[v] = add_rn(acc[v], mul_rn(sg, minmod_dev(sub_rn(uc[v], um[v]), sub_rn(up[v], uc[v]))));
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) out[v] = acc[v];
+    } else {  // finer leaves: restriction from level L+1
+      T sum[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sum[v] = T(0);
+      for (int c3 = 0; c3 < 2; ++c3)
+        for (int c2 = 0; c2 < 2; ++c2)
+          for (int c1 = 0; c1 < 2; ++c1) {
+            T f[NV];
+            composite_value<T, D - 1>(U, tv, L + 1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sum[v] = add_rn(sum[v], f[v]);
+          }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) out[v] = mul_rn(T(0.125), sum[v]);
+    }
+    negate_momenta(out, f1, f2, f3);
   }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = acc[v];
-  negate_momenta(out, f1, f2, f3);
 }
 
 template <class T>
@@ -248,10 +263,7 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
     int i, j, k;
     sh.cell(c, i, j, k);
     T val[NV];
-    if (lev == 0)
-      coarse_value(U, tv, o1 + i, o2 + j, o3 + k, val);
-    else
-      fine_value(U, tv, o1 + i, o2 + j, o3 + k, val);
+    composite_value<T, COMPOSITE_DEPTH>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
     const size_t d = ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
 #pragma unroll
     for (int v = 0; v < NV; ++v) dst[v * vs + d] = val[v];
@@ -281,10 +293,7 @@ __global__ void remesh_kernel(T* Unew, const int* __restrict__ leaf_id, const T*
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     const int k = c / (n1 * n2), r = c - k * n1 * n2, j = r / n1, i = r - j * n1;
     T val[NV];
-    if (lev == 0)
-      coarse_value(Uold, tv, o1 + i, o2 + j, o3 + k, val);
-    else
-      fine_value(Uold, tv, o1 + i, o2 + j, o3 + k, val);
+    composite_value<T, COMPOSITE_DEPTH>(Uold, tv, lev, o1 + i, o2 + j, o3 + k, val);
     const size_t d = ((size_t)(k + NG) * tv.S[1] + (j + NG)) * tv.S[0] + (i + NG);
 #pragma unroll
     for (int v = 0; v < NV; ++v) dst[v * vs + d] = val[v];
@@ -303,15 +312,15 @@ cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uo
 // K5: signal-speed max for the CFL dt (Sec. 3.10), from interior cells.
 // --------------------------------------------------------------------------
 template <class T>
-__global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level, double4 ia,
-                            double4 ib, int3 nx, Phys<T> P, DevScalars* sc) {
+__global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
+                            const LevelGeom g, int3 nx, Phys<T> P, DevScalars* sc) {
   __shared__ double red[32];
   const int b = blockIdx.x;
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
   const size_t vs = (size_t)S1 * S2 * S3;
   const T* Ub = U + (size_t)b * NV * vs;
   const int lev = level ? (int)level[b] : 0;
-  const T i1 = (T)(lev ? ib.x : ia.x), i2 = (T)(lev ? ib.y : ia.y), i3 = (T)(lev ? ib.z : ia.z);
+  const T i1 = (T)g.idx[lev][0], i2 = (T)g.idx[lev][1], i3 = (T)g.idx[lev][2];
   unsigned floors = 0;
   double m = 0.0;
   const int total = nx.x * nx.y * nx.z;
@@ -330,12 +339,10 @@ __global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ 
 }
 
 template <class T>
-cudaError_t launch_rate(const T* U, const int8_t* level, const double idx[2][3], const int nx[3],
+cudaError_t launch_rate(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
                         int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s) {
   if (nleaf <= 0) return cudaSuccess;
-  rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, make_double4(idx[0][0], idx[0][1], idx[0][2], 0),
-                                        make_double4(idx[1][0], idx[1][1], idx[1][2], 0),
-                                        make_int3(nx[0], nx[1], nx[2]), P, sc);
+  rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]), P, sc);
   return cudaGetLastError();
 }
 
@@ -399,7 +406,7 @@ cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int di
 // --------------------------------------------------------------------------
 template <class T>
 __global__ void totals_block_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
-                                    double2 vol, int3 nx, double* partial) {
+                                    const LevelGeom g, int3 nx, double* partial) {
   __shared__ double red[NV][256];
   const int b = blockIdx.x;
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
@@ -423,7 +430,7 @@ __global__ void totals_block_kernel(const T* __restrict__ U, const int8_t* __res
     __syncthreads();
   }
   if (threadIdx.x < NV) {
-    const double dv = (level && level[b]) ? vol.y : vol.x;
+    const double dv = g.vol[level ? (int)level[b] : 0];
     partial[(size_t)b * NV + threadIdx.x] = red[threadIdx.x][0] * dv;
   }
 }
@@ -445,11 +452,11 @@ __global__ void totals_final_kernel(const double* __restrict__ partial, int nlea
 }
 
 template <class T>
-cudaError_t launch_totals(const T* U, const int8_t* level, const double vol[2], const int nx[3],
+cudaError_t launch_totals(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
                           int nleaf, double* partial, double* out, cudaStream_t s) {
   if (nleaf > 0)
-    totals_block_kernel<T><<<nleaf, 256, 0, s>>>(U, level, make_double2(vol[0], vol[1]),
-                                                  make_int3(nx[0], nx[1], nx[2]), partial);
+    totals_block_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]),
+                                                  partial);
   totals_final_kernel<<<1, 32, 0, s>>>(partial, nleaf, out);
   return cudaGetLastError();
 }
@@ -518,9 +525,11 @@ template <class T>
 __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
                                     const int* __restrict__ rec_beg,
                                     const int* __restrict__ rec_face, const T* __restrict__ fcc,
-                                    const T* __restrict__ fcf, int3 nx, double3 idx0, double beta,
-                                    const DevScalars* sc) {
+                                    const T* __restrict__ fcf, int3 nx,
+                                    const int8_t* __restrict__ level, const LevelGeom g,
+                                    double beta, const DevScalars* sc) {
   const int leaf = corr_leaf[blockIdx.x];
+  const int lev = level[leaf];
   const int n[3] = {nx.x, nx.y, nx.z};
   const int S[3] = {nx.x + 2 * NG, nx.y + 2 * NG, nx.z + 2 * NG};
   const size_t vs = (size_t)S[0] * S[1] * S[2];
@@ -530,7 +539,7 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
     const int d = face >> 1, side = face & 1;
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const int m1 = n[t1], m2 = n[t2];
-    const double id = d == 0 ? idx0.x : (d == 1 ? idx0.y : idx0.z);
+    const double id = g.idx[lev][d];
     const T coef = (T)(beta * sc->dt_next * id) * (side ? T(1) : T(-1));
     const T* Fc = fcc + (size_t)r * NV * m1 * m2;
     const T* Ff = fcf + (size_t)r * NV * 4 * m1 * m2;
@@ -558,12 +567,11 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
 template <class T>
 cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
-                                const int nx[3], const double idx0[3], double beta,
-                                const DevScalars* sc, cudaStream_t s) {
+                                const int nx[3], const int8_t* level, const LevelGeom& g,
+                                double beta, const DevScalars* sc, cudaStream_t s) {
   if (ncorr <= 0) return cudaSuccess;
   flux_correct_kernel<T><<<ncorr, 256, 0, s>>>(U, corr_leaf, rec_beg, rec_face, fc_coarse, fc_fine,
-                                                make_int3(nx[0], nx[1], nx[2]),
-                                                make_double3(idx0[0], idx0[1], idx0[2]), beta, sc);
+                                                make_int3(nx[0], nx[1], nx[2]), level, g, beta, sc);
   return cudaGetLastError();
 }
 
@@ -575,15 +583,17 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
                                                  cudaStream_t);                                 \
   template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
                                         cudaStream_t);                                          \
-  template cudaError_t launch_rate<T>(const T*, const int8_t*, const double[2][3], const int*, \
+  template cudaError_t launch_rate<T>(const T*, const int8_t*, const LevelGeom&, const int*,   \
                                       int, Phys<T>, DevScalars*, cudaStream_t);                 \
   template cudaError_t launch_pack<T>(T*, T*, const int*, int, int, cudaStream_t);              \
-  template cudaError_t launch_totals<T>(const T*, const int8_t*, const double*, const int*, int, \
+  template cudaError_t launch_totals<T>(const T*, const int8_t*, const LevelGeom&, const int*,  \
+                                        int,                                                    \
                                         double*, double*, cudaStream_t);                        \
   template cudaError_t launch_indicator<T>(const T*, const int*, int, double*, cudaStream_t);   \
   template cudaError_t launch_flux_correct<T>(T*, const int*, const int*, int, const int*,      \
-                                              const T*, const T*, const int*, const double*,    \
-                                              double, const DevScalars*, cudaStream_t);
+                                              const T*, const T*, const int*, const int8_t*,    \
+                                              const LevelGeom&, double, const DevScalars*,      \
+                                              cudaStream_t);
 PH_INST(double)
 PH_INST(float)
 #undef PH_INST

@@ -31,7 +31,7 @@ struct StageArgs {
   const T* U0;         // stage 2: state at the start of the cycle (pointwise)
   T* Uout;             // stage 1: U1; stage 2: U0 (in place)
   const int8_t* level; // per leaf (null: all level 0)
-  double idx[2][3];    // 1/dx per level and direction
+  double idx[MAXLEV + 1][3];  // 1/dx per level and direction
   int nx[3];           // interior cells per block
   int S[3];            // padded extents nx + 4
   int ntile[3];        // tiles per block along x1, x2 and k-chunks along x3
@@ -41,7 +41,8 @@ struct StageArgs {
   int want_rate;       // stage 2 on uniform meshes: fold the next dt's max
   Phys<T> P;
   DevScalars* sc;
-  // flux-correction capture (two-level meshes): per leaf 6 records (-1: none)
+  // flux-correction capture (multi-level meshes): per leaf and face,
+  // 2 rec + 1 on the fine side of record rec, 2 rec on the coarse side, -1 none
   const int* face_rec;
   T* fc_coarse;        // [rec][v][n_t2][n_t1] flux of the coarse block on the face
   T* fc_fine;          // [rec][v][2 n_t2][2 n_t1] fluxes of the fine blocks on the face
@@ -50,16 +51,17 @@ struct StageArgs {
 
 // Store one face flux of a leaf on a fine-coarse face (Sec. 3.7 flux
 // correction).  face = 2 d + side; (a1, a2) are the cell's indices along
-// t1 = d+1 and t2 = d+2 (mod 3).  A level-0 leaf writes the record's coarse
-// flux; a level-1 leaf writes its quadrant (q1, q2) of the record's fine
-// fluxes, which are 2 n_t1 x 2 n_t2 per variable.
+// t1 = d+1 and t2 = d+2 (mod 3).  The coarse leaf of the record writes its
+// coarse flux; each of the 4 fine leaves writes its quadrant (q1, q2) of the
+// record's fine fluxes, which are 2 n_t1 x 2 n_t2 per variable.
 template <class T>
 __device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int face, int a1, int a2,
                                         int v, T val) {
-  const int rec = a.face_rec[6 * leaf + face];
+  const int fr = a.face_rec[6 * leaf + face];
+  const int rec = fr >> 1;
   const int d = face >> 1;
   const int m1 = a.nx[(d + 1) % 3], m2 = a.nx[(d + 2) % 3];
-  if (a.level[leaf] == 0) {
+  if ((fr & 1) == 0) {
     a.fc_coarse[(((size_t)rec * NV + v) * m2 + a2) * m1 + a1] = val;
   } else {
     const int q1 = a.fine_off[12 * leaf + 2 * face], q2 = a.fine_off[12 * leaf + 2 * face + 1];
@@ -135,7 +137,7 @@ struct TileJob {
   T dt;
   int stage;
   int want_rate;
-  int leaf;        // leaf index for flux capture (two-level meshes)
+  int leaf;        // leaf index for flux capture (multi-level meshes)
 };
 
 // TMA = true: planes arrive by one tensor copy each (tmap over the stencil
@@ -400,7 +402,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         }
         J.Uoutb[cell + v * vstride] = unew[v];
       }
-      if (a.face_rec) {  // two-level mesh: keep fluxes on fine-coarse faces
+      if (a.face_rec) {  // multi-level mesh: keep fluxes on fine-coarse faces
         const int* fr = a.face_rec + 6 * leaf;
         if (i == 0 && fr[0] >= 0)
           for (int v = 0; v < NV; ++v) capture(a, leaf, 0, j, k, v, sfx[(v * TY + ty) * FP + tx]);

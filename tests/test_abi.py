@@ -52,8 +52,8 @@ def test_invalid_config_rejected_without_gpu_work():
 BAD_CONFIGS = [
     dict(nx=(16, 16, 16), nb=(0, 1, 1)),                       # no blocks
     dict(nx=(16, 16, 16), nb=(1, 1, 1), xmin=(0, 0, 0), xmax=(0, 1, 1)),  # empty domain
-    dict(nx=(16, 16, 16), nb=(1, 1, 1), max_level=2),          # more than two levels
-    dict(nx=(15, 16, 16), nb=(1, 1, 1), max_level=1),          # odd block on a two-level mesh
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), max_level=5),          # deeper than the supported tree
+    dict(nx=(15, 16, 16), nb=(1, 1, 1), max_level=1),          # odd block on a multi-level mesh
     dict(nx=(16, 16, 16), nb=(1, 1, 1), gamma=1.0),            # gamma must exceed 1
     dict(nx=(16, 16, 16), nb=(1, 1, 1), cfl=0.0),
     dict(nx=(16, 16, 16), nb=(1, 1, 1), tile=(24, 8, 16)),     # unsupported tile
