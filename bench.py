@@ -313,6 +313,39 @@ def two_level_variant(ph, torch, steps, warmup):
             "ms_per_cycle": dt / steps * 1e3, "status": rc, "floors": floors}
 
 
+def multilevel_variant(ph, torch, steps, warmup, max_level=2, precision="fp64"):
+    """Kelvin-Helmholtz shear layers on an adaptive tree of max_level+1
+    levels: root 128 x 128 x 32 zones in 16^3 blocks, refinement at a
+    density-gradient threshold of 0.05 (the layers refine to the finest
+    level, touching blocks within one level).  Each cycle reads the
+    refinement flags on the host, so the time is wall-clock around the
+    cycles; zones are counted per cycle over the leaves of that cycle."""
+    nx, nb = (16, 16, 16), (8, 8, 2)
+    cfg = ph.make_config(nx, nb, max_level=max_level, adaptive=1, gamma=1.4, precision=precision,
+                         xmin=(-0.5, -0.5, -0.125), xmax=(0.5, 0.5, 0.125))
+    m = ph.Mesh(cfg)
+    geo = W.Geometry(nx, nb, tuple(cfg.xmin), tuple(cfg.xmax))
+    dtype = np.float32 if precision == "fp32" else np.float64
+    m.set_state(W.kelvin_helmholtz(geo, m.tree(), seed=0).astype(dtype))
+    m.step(warmup)
+    torch.cuda.synchronize()
+    zones = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        zones += m.nblocks * 16 ** 3
+        m.step(1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rc, floors, nonfinite = m.status()
+    tree = m.tree()
+    m.close()
+    return {"workload": "adaptive Kelvin-Helmholtz, %d levels: root 128x128x32 in 16^3 blocks" % (max_level + 1),
+            "precision": precision, "leaves": int(len(tree)),
+            "leaves_per_level": [int((tree[:, 0] == l).sum()) for l in range(max_level + 1)],
+            "zone_cycles_per_s": zones / dt, "ms_per_cycle": dt / steps * 1e3,
+            "status": rc, "floors": floors}
+
+
 def adjoint_variant(ph, torch, precision, cycles=20, ckpt=5):
     """Gradient of the L2 density loss after 20 cycles on 64^3 zones (8 blocks
     of 32^3), checkpoint every 5: forward + recompute + reverse time."""
@@ -475,7 +508,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
     ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
     ap.add_argument("--batch-launch", help="TX,TY,KC,CTAS: skip the batch autotuner (profiling runs)")
-    ap.add_argument("--only", choices=["batch", "two_level", "adjoint", "restart"],
+    ap.add_argument("--only", choices=["batch", "two_level", "multilevel", "adjoint", "restart"],
                     help="run one variant workload only and print its record (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -509,6 +542,8 @@ def main():
             rec = two_level_variant(ph, torch, args.steps, args.warmup)
         elif args.only == "restart":
             rec = restart_variant(ph, torch)
+        elif args.only == "multilevel":
+            rec = multilevel_variant(ph, torch, args.steps, args.warmup)
         else:
             rec = adjoint_variant(ph, torch, args.precision)
         if rank == 0:
@@ -561,6 +596,11 @@ def main():
         v = two_level_variant(ph, torch, args.steps, args.warmup)
         variants.append(v)
         log("two-level: %.3e zone-cycles/s (%d leaves)" % (v["zone_cycles_per_s"], v["leaves"]))
+        for ml in (2, 3):
+            v = multilevel_variant(ph, torch, args.steps, args.warmup, max_level=ml)
+            variants.append(v)
+            log("KH %d levels: %.3e zone-cycles/s (leaves per level %s)"
+                % (ml + 1, v["zone_cycles_per_s"], v["leaves_per_level"]))
         for prec in ("fp64", "fp32"):
             v = adjoint_variant(ph, torch, prec)
             variants.append(v)
