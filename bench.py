@@ -142,8 +142,11 @@ def wave_state(geo, leaves, dtype, kvec=WAVE_K):
     return W.linear_wave(geo, leaves, gamma=GAMMA, seed=0, amp=1e-4, kvec=kvec).astype(dtype)
 
 
-def time_variant(ph, torch, block, precision, steps, warmup, kvec=WAVE_K, bc=None):
-    """Device-timed cycles of one variant; returns a dict."""
+def time_variant(ph, torch, block, precision, steps, warmup, kvec=WAVE_K, bc=None, barrier=None):
+    """Device-timed cycles of one variant; returns a dict.  barrier (if given)
+    is called right before and right after the timed cycles, with the device
+    synchronised on both sides (all ranks start and end the timed region
+    together)."""
     m, geo = build_mesh(ph, block, precision, bc=bc)
     dtype = np.float32 if precision == "fp32" else np.float64
     U = wave_state(geo, m.tree(), dtype, kvec)
@@ -152,12 +155,17 @@ def time_variant(ph, torch, block, precision, steps, warmup, kvec=WAVE_K, bc=Non
     stream = torch.cuda.current_stream()
     m.step(warmup)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     m.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     ms = e0.elapsed_time(e1)
     # per-launch device times over the same number of cycles (events between launches)
     prof = m.profile(steps)
@@ -462,6 +470,18 @@ def oracle_rate_all_cores(block, n_sample, cycles, warmup=0):
     return work / secs, res[0][1], secs, n
 
 
+def rank_reduce(x, op, world, device):
+    """max or min of x over the ranks of the default process group (x when
+    there is one rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.MIN)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -552,18 +572,12 @@ def main():
 
     # headline: timed with clocks sampled; barrier + max over ranks
     clocks = Clocks(local)
-    if world > 1:
-        torch.distributed.barrier()
+    barrier = torch.distributed.barrier if world > 1 else None
     torch.cuda.synchronize()
     clocks.start()
-    head = time_variant(ph, torch, args.block, args.precision, args.steps, args.warmup)
+    head = time_variant(ph, torch, args.block, args.precision, args.steps, args.warmup, barrier=barrier)
     ck = clocks.stop()
-    ms = head["ms_per_cycle"] * args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+    ms = rank_reduce(head["ms_per_cycle"] * args.steps, "max", world, "cuda")
     value = world * MESH ** 3 * args.steps / (ms / 1e3)
 
     variants = []
@@ -613,9 +627,7 @@ def main():
     if not args.quick:
         e2e = e2e_variant(ph, torch, args.block, args.precision, max(3, args.steps // 4), args.warmup)
     if world > 1 and e2e is not None:
-        t = torch.tensor([e2e["value"]], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
-        e2e["value"] = float(t.item()) * world
+        e2e["value"] = rank_reduce(e2e["value"], "min", world, "cuda") * world
 
     if rank != 0:
         if world > 1:
