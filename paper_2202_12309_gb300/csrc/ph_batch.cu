@@ -54,6 +54,9 @@ struct BatchArgs {
   DevScalars* sc;           // one per member
   GridBar* bar;
   unsigned long long spin_limit;
+  // TMA plane staging: per member, the tensor maps of the U0 and U1 pools
+  // (2 m and 2 m + 1), in device memory
+  const CUtensorMap* tmaps;
 };
 
 // Bounded grid barrier.  Returns false (in every thread of the CTA) if this
@@ -102,9 +105,10 @@ __device__ __forceinline__ Phys<T> member_phys(const Member& M) {
   return P;
 }
 
-template <class T, int TX, int TY>
-__device__ void batch_stage_phase(const BatchArgs<T>& a, int stage, const StageArgs<T>& nocap,
-                                  unsigned char* smem, double* red, unsigned& floors) {
+template <class T, int TX, int TY, bool TMA>
+__device__ bool batch_stage_phase(const BatchArgs<T>& a, int stage, const StageArgs<T>& nocap,
+                                  unsigned char* smem, double* red, unsigned& floors,
+                                  uint64_t* bars, int* failed, unsigned* parity) {
   for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
     const int2 item = a.items[it];
     const int g = item.x;
@@ -136,10 +140,14 @@ __device__ void batch_stage_phase(const BatchArgs<T>& a, int stage, const StageA
     J.stage = stage;
     J.want_rate = stage == 2;
     J.leaf = g;
-    const double rate = stage_tile<T, TX, TY, false>(J, member_phys<T>(M), nocap, smem, floors);
+    const CUtensorMap* tm = TMA ? a.tmaps + 2 * m + (stage == 1 ? 0 : 1) : nullptr;
+    const double rate = stage_tile<T, TX, TY, TMA>(J, member_phys<T>(M), nocap, smem, floors, tm,
+                                                   (g - M.leaf0) * NV, bars, failed, parity);
+    if (TMA && *(volatile int*)failed) return false;  // every thread saw it after a barrier
     if (stage == 2) block_max_to(&a.sc[m].wmax_bits, rate, red);
     __syncthreads();  // the next item's priming overwrites the ring
   }
+  return true;
 }
 
 template <class T>
@@ -169,12 +177,25 @@ __device__ void batch_ghost_phase(const BatchArgs<T>& a, T* U) {
   }
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, bool TMA>
 __global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, (sizeof(T) == 4 ? 3 : 0))
 batch_cycle_kernel(const BatchArgs<T> a) {
   using SM = StageSmem<T, TX, TY>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
   double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + SM::bar_off);
+  __shared__ int failed;
+  unsigned parity = 0;
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      failed = 0;
+      for (int s = 0; s < 4; ++s) mbar_init(bars + s, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+  }
   StageArgs<T> nocap = {};
   unsigned floors = 0;
   // a failed barrier leaves a sticky error in the first member's scalars
@@ -183,16 +204,29 @@ batch_cycle_kernel(const BatchArgs<T> a) {
     if (threadIdx.x == 0) atomicExch(&a.sc[0].error, 1);             \
     return;                                                          \
   }
-  batch_stage_phase<T, TX, TY>(a, 1, nocap, smem_raw, red, floors);
+  // a CTA whose plane wait gave up reports it and leaves; the others give
+  // up at the next grid barrier (bounded), so nothing hangs
+#define PH_STAGE_OR_RETURN(st)                                                                \
+  if (!batch_stage_phase<T, TX, TY, TMA>(a, st, nocap, smem_raw, red, floors, bars, &failed,   \
+                                         &parity)) {                                          \
+    if (threadIdx.x == 0) atomicExch(&a.sc[0].error, 1);                                      \
+    return;                                                                                   \
+  }
+  // stage 1's interior writes and the ghost writes to U1 are read by stage
+  // 2's TMA copies (async proxy) in other CTAs: proxy fence before the barrier
+  PH_STAGE_OR_RETURN(1)
+  if (TMA) fence_proxy_async_global();
   PH_BARRIER_OR_RETURN
   batch_ghost_phase<T>(a, a.U1);
+  if (TMA) fence_proxy_async_global();
   PH_BARRIER_OR_RETURN
-  batch_stage_phase<T, TX, TY>(a, 2, nocap, smem_raw, red, floors);
+  PH_STAGE_OR_RETURN(2)
   PH_BARRIER_OR_RETURN
   batch_ghost_phase<T>(a, a.U0);
   if (floors) atomicAdd(&a.sc[0].floor_hits, (unsigned long long)floors);
   PH_BARRIER_OR_RETURN
 #undef PH_BARRIER_OR_RETURN
+#undef PH_STAGE_OR_RETURN
   if (blockIdx.x == 0) {
     for (int m = threadIdx.x; m < a.nsim; m += blockDim.x) {
       DevScalars& s = a.sc[m];
@@ -281,6 +315,8 @@ struct ph_batch {
   int nitems = 0;
   DevScalars* d_sc = nullptr;
   GridBar* d_bar = nullptr;
+  CUtensorMap* d_tmaps = nullptr;  // 2 per member (U0, U1 pools), for TMA staging
+  bool tma = false;
   void* staging = nullptr;
   size_t staging_bytes = 0;
   // launch choice
@@ -300,33 +336,33 @@ struct ph_batch {
 
 namespace {
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, bool TMA>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(ph::batch_cycle_kernel<T, TX, TY>,
+  return cudaFuncSetAttribute(ph::batch_cycle_kernel<T, TX, TY, TMA>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)ph::batch_smem<T, TX, TY>());
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, bool TMA>
 int occupancy(int* per_sm) {
-  cudaError_t e = set_attr<T, TX, TY>();
+  cudaError_t e = set_attr<T, TX, TY, TMA>();
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ph::batch_cycle_kernel<T, TX, TY>,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ph::batch_cycle_kernel<T, TX, TY, TMA>,
                                                     ph::StageSmem<T, TX, TY>::NT, ph::batch_smem<T, TX, TY>());
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   return PH_OK;
 }
 
-template <class T>
+template <class T, bool TMA>
 int occupancy_t(int TX, int TY, int* per_sm) {
-  if (TX == 8 && TY == 8) return occupancy<T, 8, 8>(per_sm);
-  if (TX == 16 && TY == 8) return occupancy<T, 16, 8>(per_sm);
-  if (TX == 16 && TY == 16) return occupancy<T, 16, 16>(per_sm);
-  if (TX == 32 && TY == 8) return occupancy<T, 32, 8>(per_sm);
+  if (TX == 8 && TY == 8) return occupancy<T, 8, 8, TMA>(per_sm);
+  if (TX == 16 && TY == 8) return occupancy<T, 16, 8, TMA>(per_sm);
+  if (TX == 16 && TY == 16) return occupancy<T, 16, 16, TMA>(per_sm);
+  if (TX == 32 && TY == 8) return occupancy<T, 32, 8, TMA>(per_sm);
   return bfail(PH_ERR_INVALID, "unsupported tile");
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, bool TMA>
 cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   BatchArgs<T> a;
   a.U0 = (T*)b->U0;
@@ -341,6 +377,7 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   a.sc = b->d_sc;
   a.bar = b->d_bar;
   a.spin_limit = b->spin_limit;
+  a.tmaps = b->d_tmaps;
   cudaLaunchConfig_t lc;
   std::memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(b->grid);
@@ -352,16 +389,38 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  return cudaLaunchKernelEx(&lc, ph::batch_cycle_kernel<T, TX, TY>, a);
+  return cudaLaunchKernelEx(&lc, ph::batch_cycle_kernel<T, TX, TY, TMA>, a);
+}
+
+template <class T, bool TMA>
+cudaError_t launch_cycle_tt(ph_batch* b, cudaStream_t s) {
+  if (b->TX == 8 && b->TY == 8) return launch_cycle<T, 8, 8, TMA>(b, s);
+  if (b->TX == 16 && b->TY == 8) return launch_cycle<T, 16, 8, TMA>(b, s);
+  if (b->TX == 16 && b->TY == 16) return launch_cycle<T, 16, 16, TMA>(b, s);
+  if (b->TX == 32 && b->TY == 8) return launch_cycle<T, 32, 8, TMA>(b, s);
+  return cudaErrorInvalidValue;
 }
 
 template <class T>
 cudaError_t launch_cycle_t(ph_batch* b, cudaStream_t s) {
-  if (b->TX == 8 && b->TY == 8) return launch_cycle<T, 8, 8>(b, s);
-  if (b->TX == 16 && b->TY == 8) return launch_cycle<T, 16, 8>(b, s);
-  if (b->TX == 16 && b->TY == 16) return launch_cycle<T, 16, 16>(b, s);
-  if (b->TX == 32 && b->TY == 8) return launch_cycle<T, 32, 8>(b, s);
-  return cudaErrorInvalidValue;
+  return b->tma ? launch_cycle_tt<T, true>(b, s) : launch_cycle_tt<T, false>(b, s);
+}
+
+// Tensor maps of every member's blocks in both pools for the tile (TX, TY);
+// false if any member's geometry does not admit one (then plain loads).
+bool build_tmaps(ph_batch* b, int TX, int TY) {
+  if (!ph::stage_tma_wanted() || !b->d_tmaps) return false;
+  std::vector<CUtensorMap> maps(2 * (size_t)b->nsim);
+  for (int m = 0; m < b->nsim; ++m) {
+    const Member& M = b->mem[m];
+    const char* u0 = (const char*)b->U0 + (size_t)M.off * b->esize;
+    const char* u1 = (const char*)b->U1 + (size_t)M.off * b->esize;
+    if (!ph::make_stage_tmap(&maps[2 * m], u0, b->esize, M.S, M.nleaf, TX, TY) ||
+        !ph::make_stage_tmap(&maps[2 * m + 1], u1, b->esize, M.S, M.nleaf, TX, TY))
+      return false;
+  }
+  return cudaMemcpy(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                    cudaMemcpyHostToDevice) == cudaSuccess;
 }
 
 // One cycle: reset the barrier word, then the persistent kernel.
@@ -380,10 +439,13 @@ void drop_graph(ph_batch* b) {
 
 // Apply a launch choice: tiles per member, the cost-ordered work list, grid.
 int configure(ph_batch* b, int TX, int TY, int KC, int ctas) {
+  const bool tma = build_tmaps(b, TX, TY);
   int per_sm = 0;
-  int rc = b->precision == PH_FP32 ? occupancy_t<float>(TX, TY, &per_sm)
-                                   : occupancy_t<double>(TX, TY, &per_sm);
+  int rc = b->precision == PH_FP32
+               ? (tma ? occupancy_t<float, true>(TX, TY, &per_sm) : occupancy_t<float, false>(TX, TY, &per_sm))
+               : (tma ? occupancy_t<double, true>(TX, TY, &per_sm) : occupancy_t<double, false>(TX, TY, &per_sm));
   if (rc) return rc;
+  b->tma = tma;
   if (per_sm < 1) return bfail(PH_ERR_INVALID, "batch kernel does not fit on an SM");
   int dev = 0, nsm = 0;
   PB_CUDA(cudaGetDevice(&dev));
@@ -647,7 +709,9 @@ int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch*
     b->d_nbr = (int*)b->dalloc(sizeof(int) * nbr.size());
     b->d_sc = (DevScalars*)b->dalloc(sizeof(DevScalars) * nsim);
     b->d_bar = (GridBar*)b->dalloc(sizeof(GridBar));
-    if (!b->U0 || !b->U1 || !b->d_mem || !b->d_leaf_member || !b->d_nbr || !b->d_sc || !b->d_bar)
+    b->d_tmaps = (CUtensorMap*)b->dalloc(sizeof(CUtensorMap) * 2 * (size_t)nsim);  // 256-B aligned
+    if (!b->U0 || !b->U1 || !b->d_mem || !b->d_leaf_member || !b->d_nbr || !b->d_sc || !b->d_bar ||
+        !b->d_tmaps)
       rc = bfail(PH_ERR_OOM, "device allocation failed (batch)");
   }
   if (!rc) {
@@ -804,7 +868,9 @@ int ph_batch_autotune(ph_batch* b, int32_t trial_cycles, int32_t chosen[4]) {
     const int TX = kTiles[t][0], TY = kTiles[t][1];
     if (TX > 2 * minn || TY > minn) continue;
     int per_sm = 0;
-    rc = b->precision == PH_FP32 ? occupancy_t<float>(TX, TY, &per_sm) : occupancy_t<double>(TX, TY, &per_sm);
+    // an upper bound for the CTA count; configure() clamps to the variant it picks
+    rc = b->precision == PH_FP32 ? occupancy_t<float, false>(TX, TY, &per_sm)
+                                 : occupancy_t<double, false>(TX, TY, &per_sm);
     if (rc) break;
     const int kcs[3] = {8, 16, 32};
     for (int kci = 0; kci < 3 && !rc; ++kci) {

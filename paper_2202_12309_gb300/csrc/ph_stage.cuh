@@ -149,7 +149,8 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
                                              const StageArgs<T>& a, unsigned char* smem_raw,
                                              unsigned& floors, const CUtensorMap* tmap = nullptr,
                                              int vz0 = 0, uint64_t* bars = nullptr,
-                                             int* failed = nullptr) {
+                                             int* failed = nullptr,
+                                             unsigned* parity_io = nullptr) {
   using SM = StageSmem<T, TX, TY>;
   constexpr int NT = SM::NT;        // threads of the CTA
   constexpr int NC = TX * TY;       // threads that own a cell of the tile
@@ -198,7 +199,9 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   // place once its barrier completes (all threads).  Cells of a ragged tile
   // outside the padded block arrive as zeros and are left alone (no valid
   // cell's stencil reaches them).
-  unsigned parity = 0;  // bit s: parity of the next completion of slot s
+  // bit s: parity of the next completion of slot s (carried across calls by
+  // a CTA that runs several tiles on the same barriers)
+  unsigned parity = parity_io ? *parity_io : 0u;
   auto issue = [&](int p) {
     if (TMA && tid == 0) {
       const int sl = (p + 4) & 3;
@@ -425,6 +428,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       }
     }
   }
+  if (parity_io) *parity_io = parity;
   return rate;
 }
 

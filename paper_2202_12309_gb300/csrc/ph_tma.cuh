@@ -55,6 +55,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Order this thread's earlier generic-proxy writes to global memory before
+// later async-proxy (TMA) reads of it (by any thread, after a barrier).
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // 4-D tiled bulk tensor load global -> shared, completing on `bar`.
 // Coordinates are element indices (c0 innermost); c0 * element size must be a
 // multiple of 16 bytes.
