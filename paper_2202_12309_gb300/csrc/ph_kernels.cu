@@ -86,12 +86,67 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx,
   }
 }
 
+// Periodic meshes with an even nx1: the ghost shell's rows split into
+// aligned pairs of x1-adjacent cells (the x1-ghost layers are 2 wide and the
+// interior starts at an even index), and both cells of a pair come from the
+// same neighbour, contiguous and in order.  Each thread moves one pair of
+// every variable with one 2-element load and store (8 bytes in FP32, 16 in
+// FP64): half the threads and memory instructions of the per-cell copy.
+template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using V = float2;
+};
+template <>
+struct Pair<double> {
+  using V = double2;
+};
+
+template <class T>
+__global__ void ghost_uniform_pairs_kernel(T* U, const int* __restrict__ nbr, int3 nx) {
+  using V = typename Pair<T>::V;
+  const int nxa[3] = {nx.x, nx.y, nx.z};
+  const Shell sh(nxa);
+  const int b = blockIdx.x;
+  const int S1 = sh.S1, S2 = sh.S2, S3 = nx.z + 2 * NG;
+  const size_t vs = (size_t)S1 * S2 * S3;
+  T* dstb = U + (size_t)b * NV * vs;
+  const int* nb = nbr + 27 * b;
+  const int total = sh.count() / 2;
+  const int per = (total + gridDim.y - 1) / gridDim.y;
+  const int c0 = blockIdx.y * per, c1 = min(total, c0 + per);
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    int i, j, k;
+    sh.cell(2 * c, i, j, k);  // the pair's first cell; its partner is (i + 1, j, k)
+    const int ox = i < NG ? -1 : (i >= NG + nx.x ? 1 : 0);
+    const int oy = j < NG ? -1 : (j >= NG + nx.y ? 1 : 0);
+    const int oz = k < NG ? -1 : (k >= NG + nx.z ? 1 : 0);
+    const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    const T* srcb = U + (size_t)src * NV * vs;
+    const size_t so = ((size_t)(k - oz * nx.z) * S2 + (j - oy * nx.y)) * S1 + (i - ox * nx.x);
+    const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
+    V w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = *reinterpret_cast<const V*>(srcb + v * vs + so);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) *reinterpret_cast<V*>(dstb + v * vs + dofs) = w[v];
+  }
+}
+
 template <class T>
 cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
                                  const int* leaf_id, const int nb[3], int bcm) {
   if (nleaf <= 0) return cudaSuccess;
   const long long S1 = nx[0] + 2 * NG, S2 = nx[1] + 2 * NG, S3 = nx[2] + 2 * NG;
   const long long shell = S1 * S2 * S3 - (long long)nx[0] * nx[1] * nx[2];
+  if (bcm == 0 && nx[0] % 2 == 0) {
+    const long long pairs = shell / 2;
+    const int chunks = (int)std::min<long long>(64, std::max<long long>(1, (pairs + 1023) / 1024));
+    ghost_uniform_pairs_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(U, nbr,
+                                                                      make_int3(nx[0], nx[1], nx[2]));
+    return cudaGetLastError();
+  }
   const int chunks = (int)std::min<long long>(64, std::max<long long>(1, (shell + 1023) / 1024));
   const int3 nbl = nb ? make_int3(nb[0], nb[1], nb[2]) : make_int3(1, 1, 1);
   ghost_uniform_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(
