@@ -625,7 +625,7 @@ def main():
 
     e2e = None
     if not args.quick:
-        e2e = e2e_variant(ph, torch, args.block, args.precision, max(3, args.steps // 4), args.warmup)
+        e2e = e2e_variant(ph, torch, args.block, args.precision, args.steps, args.warmup)
     if world > 1 and e2e is not None:
         e2e["value"] = rank_reduce(e2e["value"], "min", world, "cuda") * world
 
