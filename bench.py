@@ -192,7 +192,7 @@ def measured_traffic(precision, block):
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
         h = hashlib.sha256()
-        for f in ("ph_stage.cuh", "ph_device.cuh", "ph_tma.cuh"):
+        for f in ("ph_stage.cuh", "ph_stage_pair.cuh", "ph_device.cuh", "ph_tma.cuh"):
             h.update(open(os.path.join(ROOT, "paper_2202_12309_gb300", "csrc", f), "rb").read())
         if h.hexdigest() != rec["kernel_source_sha256"] or rec[precision]["block"] != block:
             return None

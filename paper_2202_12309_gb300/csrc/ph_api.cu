@@ -443,6 +443,12 @@ void build_tmaps(ph_mesh* m) {
   m->tma = ph::stage_tma_wanted() &&
            ph::make_stage_tmap(&m->tm[0], m->U0, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1]) &&
            ph::make_stage_tmap(&m->tm[1], m->U1, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1]);
+  if (!m->tma && ph::stage_pair_tile(m->tile[0], m->tile[1])) {
+    // the paired kernel needs TMA staging: fall back to the 16 x 16 tile
+    m->tile[0] = 16;
+    m->tile[1] = 16;
+    build_tmaps(m);
+  }
 }
 
 const CUtensorMap* tmap_for(const ph_mesh* m, int stage) {
@@ -832,7 +838,11 @@ int cycle_fixed_dt_t(ph_mesh* m, double dt) {
   ((m)->cfg.precision == PH_FP32 ? fn<float>(__VA_ARGS__) : fn<double>(__VA_ARGS__))
 
 bool valid_tile(const ph_config* c, const int t[3]) {
-  return ph::stage_tile_supported(t[0], t[1]) && t[2] >= 1 && t[2] <= c->nx[2];
+  if (t[2] < 1 || t[2] > c->nx[2]) return false;
+  if (ph::stage_pair_tile(t[0], t[1]))
+    return c->precision == PH_FP32 && c->max_level == 0 && c->nx[0] % t[0] == 0 &&
+           c->nx[1] % t[1] == 0;
+  return ph::stage_tile_supported(t[0], t[1]);
 }
 
 }  // namespace
@@ -954,6 +964,15 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     t[0] = cfg->nx[0] >= 16 ? 16 : 8;
     t[1] = (cfg->nx[1] >= 16 && t[0] == 16) ? 16 : 8;
     t[2] = cfg->nx[2];
+    // FP32 uniform meshes: the paired kernel where the blocks tile into
+    // 32 x 16, marching 16 planes per CTA (measured: more, shorter tiles
+    // leave a smaller last wave than whole-block columns)
+    const int pt[3] = {32, 16, cfg->nx[2] >= 32 ? 16 : cfg->nx[2]};
+    if (ph::stage_tma_wanted() && valid_tile(cfg, pt)) {
+      t[0] = pt[0];
+      t[1] = pt[1];
+      t[2] = pt[2];
+    }
   }
   if (!valid_tile(cfg, t)) {
     delete m;

@@ -74,6 +74,9 @@ bool stage_tma_wanted();  // false when PH_STAGE_LOADS=plain
 template <class T>
 size_t stage_smem_bytes(int TX, int TY);
 bool stage_tile_supported(int TX, int TY);
+// 32 x 16: the paired FP32 kernel (FP32 uniform meshes with TMA staging,
+// nx1 a multiple of 32 and nx2 of 16)
+bool stage_pair_tile(int TX, int TY);
 cudaError_t configure_stage_kernels();
 
 // K1 (uniform mesh): every ghost cell of every leaf copied from the

@@ -8,6 +8,7 @@
 
 #include "ph_internal.h"
 #include "ph_stage.cuh"
+#include "ph_stage_pair.cuh"
 
 namespace ph {
 
@@ -16,8 +17,11 @@ bool stage_tile_supported(int TX, int TY) {
          (TX == 32 && TY == 8);
 }
 
+bool stage_pair_tile(int TX, int TY) { return TX == PairSmem::TX && TY == PairSmem::TY; }
+
 template <class T>
 size_t stage_smem_bytes(int TX, int TY) {
+  if (sizeof(T) == 4 && stage_pair_tile(TX, TY)) return PairSmem::bytes;
   if (TX == 8 && TY == 8) return StageSmem<T, 8, 8>::bytes;
   if (TX == 16 && TY == 8) return StageSmem<T, 16, 8>::bytes;
   if (TX == 16 && TY == 16) return StageSmem<T, 16, 16>::bytes;
@@ -46,7 +50,8 @@ cudaError_t configure_stage_kernels() {
   if ((e = configure_tile<float, 16, 8>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 16, 16>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 32, 8>()) != cudaSuccess) return e;
-  return cudaSuccess;
+  return cudaFuncSetAttribute(stage_kernel_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PairSmem::bytes);
 }
 
 template <class T, int TX, int TY>
@@ -61,8 +66,21 @@ static cudaError_t launch_tile(const StageArgs<T>& a, const CUtensorMap* tmap, c
   return cudaGetLastError();
 }
 
+// The paired FP32 kernel (32 x 16 tiles, TMA staging, uniform meshes).
+static cudaError_t launch_pair(const StageArgs<float>& a, const CUtensorMap* tmap, cudaStream_t s) {
+  if (!tmap || a.face_rec) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
+  if (grid == 0) return cudaSuccess;
+  stage_kernel_pair<<<grid, PairSmem::NT, PairSmem::bytes, s>>>(a, *tmap);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s, const CUtensorMap* tmap) {
+  if (stage_pair_tile(TX, TY)) {
+    if constexpr (sizeof(T) == 4) return launch_pair(a, tmap, s);
+    return cudaErrorInvalidValue;
+  }
   if (TX == 8 && TY == 8) return launch_tile<T, 8, 8>(a, tmap, s);
   if (TX == 16 && TY == 8) return launch_tile<T, 16, 8>(a, tmap, s);
   if (TX == 16 && TY == 16) return launch_tile<T, 16, 16>(a, tmap, s);

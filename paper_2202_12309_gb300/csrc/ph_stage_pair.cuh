@@ -1,0 +1,451 @@
+// ph_stage_pair.cuh -- the FP32 fused stage kernel with two x1-adjacent cells
+// per thread.
+//
+// The FP32 stage is bound by instruction issue, not by HBM.  Blackwell issues
+// FP32 add / multiply / fma on two lanes at once (PTX add/mul/fma .f32x2), and
+// shared memory serves 8-byte accesses as cheaply as 4-byte ones.  Here every
+// thread owns a pair of cells (i, i+1) of a 32 x 16 tile (256 threads), and
+// slopes, face states, HLLE fluxes and the update are computed on both cells
+// with one paired instruction where the method is the same on both lanes
+// (compares, selects and the special-function approximations stay per lane).
+// The method and the order of the tile march are those of ph_stage.cuh:
+// TMA-staged planes of primitives in a 4-slot ring, x3 slopes and fluxes in
+// registers, x1 / x2 slopes and fluxes in shared memory, SSPRK2 update and
+// the signal-speed max for dt in the epilogue.  Uniform meshes only (no
+// flux-correction capture).
+#pragma once
+#include "ph_stage.cuh"
+
+namespace ph {
+
+// Two FP32 lanes in one 64-bit register.
+struct __align__(8) F2 {
+  unsigned long long r;
+};
+
+__device__ __forceinline__ F2 f2(float a, float b) {
+  F2 o;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(o.r) : "f"(a), "f"(b));
+  return o;
+}
+__device__ __forceinline__ F2 f2(float a) { return f2(a, a); }
+__device__ __forceinline__ void split(F2 x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.r));
+}
+__device__ __forceinline__ float lane0(F2 x) {
+  float a, b;
+  split(x, a, b);
+  return a;
+}
+__device__ __forceinline__ float lane1(F2 x) {
+  float a, b;
+  split(x, a, b);
+  return b;
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+  F2 o;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+  return o;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  F2 o;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+  return o;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+  F2 o;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(o.r) : "l"(a.r), "l"(b.r));
+  return o;
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {
+  F2 o;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(o.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+  return o;
+}
+__device__ __forceinline__ F2 operator-(F2 a) {  // flip both sign bits
+  F2 o;
+  o.r = a.r ^ 0x8000000080000000ull;
+  return o;
+}
+// Per-lane helpers (the same operations as the scalar FP32 path).
+__device__ __forceinline__ F2 rcp2(F2 x) {
+  float a, b;
+  split(x, a, b);
+  float ya, yb;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(a));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(b));
+  const F2 y = f2(ya, yb);
+  return fma2(y, fma2(-x, y, f2(1.f)), y);
+}
+__device__ __forceinline__ F2 rsq2(F2 x) {
+  float a, b;
+  split(x, a, b);
+  return f2(rsqrtf(a), rsqrtf(b));
+}
+__device__ __forceinline__ F2 sq2(F2 x) {
+  float a, b;
+  split(x, a, b);
+  return f2(sq(a), sq(b));
+}
+__device__ __forceinline__ F2 max0_2(F2 x, F2 y) {
+  float a, b, c, d;
+  split(x, a, b);
+  split(y, c, d);
+  return f2(max0(a, c), max0(b, d));
+}
+__device__ __forceinline__ F2 min0_2(F2 x, F2 y) {
+  float a, b, c, d;
+  split(x, a, b);
+  split(y, c, d);
+  return f2(min0(a, c), min0(b, d));
+}
+__device__ __forceinline__ F2 ld2(const float* p) { return *reinterpret_cast<const F2*>(p); }
+__device__ __forceinline__ void st2(float* p, F2 v) { *reinterpret_cast<F2*>(p) = v; }
+
+// cons -> prim in place on both lanes, floors per lane (each counted).
+__device__ __forceinline__ void cons_to_prim2(F2 w[NV], const Phys<float>& P, unsigned& floors) {
+  float r0, r1;
+  split(w[0], r0, r1);
+  if (below_floor(r0, P.dfloor)) { r0 = P.dfloor; ++floors; }
+  if (below_floor(r1, P.dfloor)) { r1 = P.dfloor; ++floors; }
+  const F2 rho = f2(r0, r1);
+  const F2 ir = rcp2(rho);
+  const F2 v1 = w[1] * ir, v2 = w[2] * ir, v3 = w[3] * ir;
+  const F2 ke = fma2(w[1], v1, fma2(w[2], v2, w[3] * v3));
+  F2 p = f2(P.gm1) * fma2(f2(-0.5f), ke, w[4]);
+  float p0, p1;
+  split(p, p0, p1);
+  if (below_floor(p0, P.pfloor)) { p0 = P.pfloor; ++floors; }
+  if (below_floor(p1, P.pfloor)) { p1 = P.pfloor; ++floors; }
+  w[0] = rho;
+  w[1] = v1;
+  w[2] = v2;
+  w[3] = v3;
+  w[4] = f2(p0, p1);
+}
+
+// Half van Leer slopes of the five variables on both lanes.
+__device__ __forceinline__ void vanleer_half5_2(const F2 wm[NV], const F2 w0[NV], const F2 wp[NV],
+                                                F2 h[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const F2 dl = w0[v] - wm[v], dr = wp[v] - w0[v];
+    const F2 prod = dl * dr;
+    const F2 t = prod * rcp2(dl + dr);
+    float p0, p1, t0, t1;
+    split(prod, p0, p1);
+    split(t, t0, t1);
+    h[v] = f2(p0 > 0.f ? t0 : 0.f, p1 > 0.f ? t1 : 0.f);
+  }
+}
+
+// HLLE flux (Einfeldt bounds, Roe averages) on both lanes; the arithmetic of
+// hlle() in ph_device.cuh, two lanes per instruction.
+template <int DIR>
+__device__ __forceinline__ void hlle2(const F2 wl[NV], const F2 wr[NV], const Phys<float>& P, F2 f[NV]) {
+  constexpr int IN = 1 + DIR;
+  const F2 rl = wl[0], pl = wl[4], rr = wr[0], pr = wr[4];
+  const F2 vnl = wl[IN], vnr = wr[IN];
+  const F2 half = f2(0.5f);
+  const F2 kl = fma2(wl[1], wl[1], fma2(wl[2], wl[2], wl[3] * wl[3]));
+  const F2 kr = fma2(wr[1], wr[1], fma2(wr[2], wr[2], wr[3] * wr[3]));
+  const F2 el = fma2(pl, f2(P.igm1), (half * rl) * kl);
+  const F2 er = fma2(pr, f2(P.igm1), (half * rr) * kr);
+  const F2 ql = rsq2(rl), qr = rsq2(rr);
+  const F2 sl = rl * ql, sr = rr * qr;
+  const F2 gam = f2(P.gamma);
+  const F2 gl = sq2(gam * pl), gr = sq2(gam * pr);
+  const F2 hl = el + pl, hr = er + pr;
+  const F2 isum = rcp2(sl + sr);
+  const F2 wsl = sl * isum, wsr = sr * isum;
+  const F2 u1 = fma2(wsl, wl[1], wsr * wr[1]);
+  const F2 u2 = fma2(wsl, wl[2], wsr * wr[2]);
+  const F2 u3 = fma2(wsl, wl[3], wsr * wr[3]);
+  const F2 hroe = fma2(hl, ql, hr * qr) * isum;
+  const F2 a2 = f2(P.gm1) * fma2(f2(-0.5f), fma2(u1, u1, fma2(u2, u2, u3 * u3)), hroe);
+  float a20, a21;
+  split(a2, a20, a21);
+  const F2 croe = f2(a20 > 0.f ? sq(a20) : 0.f, a21 > 0.f ? sq(a21) : 0.f);
+  const F2 un = (IN == 1) ? u1 : ((IN == 2) ? u2 : u3);
+  const F2 bp = max0_2(fma2(gr, qr, vnr), un + croe);
+  const F2 bm = min0_2(fma2(-gl, ql, vnl), un - croe);
+  const F2 idb = rcp2(bp - bm);
+  const F2 cL = bp * idb, cR = (-bm) * idb, cD = (bp * bm) * idb;
+  const F2 aL = fma2(cL, rl * vnl, -(cD * rl));
+  const F2 aR = fma2(cR, rr * vnr, cD * rr);
+  f[0] = aL + aR;
+#pragma unroll
+  for (int a = 1; a <= 3; ++a) f[a] = fma2(aL, wl[a], aR * wr[a]);
+  f[IN] = f[IN] + fma2(cL, pl, cR * pr);
+  f[4] = fma2(cL * vnl, hl, fma2(cR * vnr, hr, cD * (er - el)));
+}
+
+// Shared-memory layout of the paired kernel (floats; every section starts
+// on an 8-byte boundary so that pairs load and store whole).
+struct PairSmem {
+  static constexpr int TX = 32, TY = 16, NT = 256;
+  static constexpr int WX = TX + 4, WY = TY + 4;
+  static constexpr int PLANE = NV * WX * WY;
+  static constexpr int SLOT = (PLANE * 4 + 127) / 128 * 128 / 4;
+  static constexpr unsigned PLANE_BYTES = PLANE * 4;
+  static constexpr int FPX = TX + 2;                 // x1 face pitch (faces 0..TX, one spare)
+  static constexpr int DXN = NV * TY * WX;           // x1 slopes, indexed by plane position
+  static constexpr int DYN = NV * (TY + 2) * TX;     // x2 slopes, rows -1..TY
+  static constexpr int FXN = NV * TY * FPX;          // x1 face fluxes
+  static constexpr int FYN = NV * (TY + 1) * TX;     // x2 face fluxes
+  static constexpr size_t body = 4 * (size_t)(4 * SLOT + DXN + DYN + FXN + FYN);
+  static constexpr size_t red_off = (body + 15) / 16 * 16;
+  static constexpr size_t bar_off = red_off + 32 * sizeof(double);
+  static constexpr size_t bytes = bar_off + 4 * sizeof(uint64_t) + 128;
+};
+
+// One 32 x 16 tile of one block for one stage (TMA staging); returns the
+// tile's max signal rate when J.want_rate.
+__device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const Phys<float>& P,
+                                                  unsigned char* smem_raw, unsigned& floors,
+                                                  const CUtensorMap* tmap, int vz0, uint64_t* bars,
+                                                  int* failed) {
+  using SM = PairSmem;
+  constexpr int TX = SM::TX, TY = SM::TY, NT = SM::NT, WX = SM::WX, WY = SM::WY, FPX = SM::FPX;
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  float* sdx = ring + 4 * SM::SLOT;
+  float* sdy = sdx + SM::DXN;
+  float* sfx = sdy + SM::DYN;
+  float* sfy = sfx + SM::FXN;
+  const int tid = threadIdx.x;
+  const int tx = 2 * (tid & 15), ty = tid >> 4;  // own cells (tx, tx+1) of row ty
+  const int S1 = J.S[0], S2 = J.S[1];
+  const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
+  const size_t vstride = (size_t)J.S[0] * J.S[1] * J.S[2];
+
+  unsigned parity = 0;
+  auto issue = [&](int p) {
+    if (tid == 0) {
+      const int sl = (p + 4) & 3;
+      mbar_expect_tx(bars + sl, SM::PLANE_BYTES);
+      tma_load_4d(ring + sl * SM::SLOT, tmap, bars + sl, i0, j0, p + NG, vz0);
+    }
+  };
+  auto convert = [&](int p) -> bool {
+    const int sl = (p + 4) & 3;
+    const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
+    parity ^= 1u << sl;
+    float* dst = ring + sl * SM::SLOT;
+    for (int c = tid; c < WY * (WX / 2); c += NT) {
+      const int r = c / (WX / 2), q = 2 * (c - r * (WX / 2));
+      F2 w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = ld2(dst + (v * WY + r) * WX + q);
+      cons_to_prim2(w, P, floors);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(dst + (v * WY + r) * WX + q, w[v]);
+    }
+    return ok;
+  };
+  auto check_failed = [&](bool ok) -> bool {
+    if (!ok) atomicExch(failed, 1);
+    __syncthreads();
+    return *(volatile int*)failed != 0;
+  };
+  auto col = [&](int p, F2 w[NV]) {
+    const float* s = ring + ((p + 4) & 3) * SM::SLOT;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = ld2(s + (v * WY + ty + 2) * WX + tx + 2);
+  };
+
+  // priming: planes k0-2 .. k0+1, the x3 slope at k0 and the flux below it
+  for (int p = k0 - 2; p <= k0 + 1; ++p) issue(p);
+  {
+    bool ok = true;
+    for (int p = k0 - 2; p <= k0 + 1; ++p) ok = convert(p) && ok;
+    fence_proxy_async_smem();
+    if (check_failed(ok)) return 0.0;
+  }
+  F2 dz[NV], fzm[NV];
+  {
+    F2 wa[NV], wb[NV], wc[NV], wd[NV], wl[NV], wr[NV], d0[NV];
+    col(k0 - 2, wa);
+    col(k0 - 1, wb);
+    col(k0, wc);
+    col(k0 + 1, wd);
+    vanleer_half5_2(wa, wb, wc, d0);
+    vanleer_half5_2(wb, wc, wd, dz);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      wl[v] = wb[v] + d0[v];
+      wr[v] = wc[v] - dz[v];
+    }
+    hlle2<2>(wl, wr, P, fzm);
+  }
+  __syncthreads();
+  issue(k0 + 2);
+  {
+    const bool ok = convert(k0 + 2);
+    fence_proxy_async_smem();
+    if (check_failed(ok)) return 0.0;
+  }
+  if (k0 + 3 <= k1 + 1) issue(k0 + 3);
+
+  const int i = i0 + tx, j = j0 + ty;
+  const F2 tdt = f2(J.dt);
+  double rate = 0.0;
+  const F2 idx1 = f2(J.idx1), idx2 = f2(J.idx2), idx3 = f2(J.idx3);
+
+  for (int k = k0; k < k1; ++k) {
+    F2 fzlo[NV];
+    {  // (C1) own x3 slope and flux
+      F2 wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], f[NV];
+      col(k, wa);
+      col(k + 1, wb);
+      col(k + 2, wc);
+      vanleer_half5_2(wa, wb, wc, d1);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        wl[v] = wa[v] + dz[v];
+        wr[v] = wb[v] - d1[v];
+        dz[v] = d1[v];
+      }
+      hlle2<2>(wl, wr, P, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        fzlo[v] = fzm[v];
+        fzm[v] = f[v];
+      }
+    }
+    const float* W = ring + ((k + 4) & 3) * SM::SLOT;
+    // (C2) x1 slopes of plane positions (2q, 2q+1), q = 0..WX/2-1 (cells -2..TX+1;
+    // the outermost lanes read clamped neighbours and are never used)
+    for (int c = tid; c < TY * (WX / 2); c += NT) {
+      const int jj = c / (WX / 2), q = 2 * (c - jj * (WX / 2));
+      F2 a[NV], b[NV], r[NV], h[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* row = W + (v * WY + jj + 2) * WX;
+        b[v] = ld2(row + q);
+        a[v] = f2(row[q > 0 ? q - 1 : 0], lane0(b[v]));
+        r[v] = f2(lane1(b[v]), row[q + 2 < WX ? q + 2 : WX - 1]);
+      }
+      vanleer_half5_2(a, b, r, h);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sdx + (v * TY + jj) * WX + q, h[v]);
+    }
+    // (C3) x2 slopes of rows -1..TY, column pairs
+    for (int c = tid; c < (TY + 2) * (TX / 2); c += NT) {
+      const int jj = c / (TX / 2), q = 2 * (c - jj * (TX / 2));
+      F2 a[NV], b[NV], r[NV], h[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* p = W + (v * WY + jj) * WX + q + 2;
+        a[v] = ld2(p);
+        b[v] = ld2(p + WX);
+        r[v] = ld2(p + 2 * WX);
+      }
+      vanleer_half5_2(a, b, r, h);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sdy + (v * (TY + 2) + jj) * TX + q, h[v]);
+    }
+    __syncthreads();
+    // (E1) x1 face pairs (f, f+1), f even; face f joins cells f-1 and f
+    for (int c = tid; c < TY * (FPX / 2); c += NT) {
+      const int jj = c / (FPX / 2), f = 2 * (c - jj * (FPX / 2));
+      F2 wl[NV], wr[NV], fl[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* row = W + (v * WY + jj + 2) * WX;
+        const float* srow = sdx + (v * TY + jj) * WX;
+        const F2 R = ld2(row + f + 2), SR = ld2(srow + f + 2);
+        const F2 L = f2(row[f + 1], lane0(R)), SL = f2(srow[f + 1], lane0(SR));
+        wl[v] = L + SL;
+        wr[v] = R - SR;
+      }
+      hlle2<0>(wl, wr, P, fl);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sfx + (v * TY + jj) * FPX + f, fl[v]);
+    }
+    // (E2) x2 faces between rows g-1 and g, column pairs
+    for (int c = tid; c < (TY + 1) * (TX / 2); c += NT) {
+      const int g = c / (TX / 2), q = 2 * (c - g * (TX / 2));
+      F2 wl[NV], wr[NV], fl[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* p = W + (v * WY + g + 1) * WX + q + 2;
+        const float* s = sdy + (v * (TY + 2) + g) * TX + q;
+        wl[v] = ld2(p) + ld2(s);
+        wr[v] = ld2(p + WX) - ld2(s + TX);
+      }
+      hlle2<1>(wl, wr, P, fl);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + g) * TX + q, fl[v]);
+    }
+    // (F) plane k+3 into the slot of plane k-1; then plane k+4 into the slot of plane k
+    {
+      const bool ok = k + 3 <= k1 + 1 ? convert(k + 3) : true;
+      fence_proxy_async_smem();
+      if (check_failed(ok)) return 0.0;
+      if (k + 4 <= k1 + 1) issue(k + 4);
+    }
+    // (G) flux divergence + SSPRK2 on the own pair
+    {
+      const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
+      F2 unew[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* fr = sfx + (v * TY + ty) * FPX + tx;
+        const F2 fa = ld2(fr);
+        const F2 fb = f2(lane1(fa), fr[2]);
+        const F2 dfx = fb - fa;
+        const F2 dfy = ld2(sfy + (v * (TY + 1) + ty + 1) * TX + tx) - ld2(sfy + (v * (TY + 1) + ty) * TX + tx);
+        const F2 L = -fma2(dfx, idx1, fma2(dfy, idx2, (fzm[v] - fzlo[v]) * idx3));
+        const F2 ucur = ld2(J.Ub + cell + v * vstride);
+        if (J.stage == 1) {
+          unew[v] = fma2(tdt, L, ucur);
+        } else {
+          const F2 u0 = ld2(J.U0b + cell + v * vstride);
+          unew[v] = fma2(f2(0.5f), u0, f2(0.5f) * fma2(tdt, L, ucur));
+        }
+        st2(J.Uoutb + cell + v * vstride, unew[v]);
+      }
+      if (J.want_rate) {
+        float a[NV], b[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) split(unew[v], a[v], b[v]);
+        cons_to_prim(a, P, floors);
+        cons_to_prim(b, P, floors);
+        const double ra = (double)wave_rate(a, P, J.idx1, J.idx2, J.idx3);
+        const double rb = (double)wave_rate(b, P, J.idx1, J.idx2, J.idx3);
+        if (!(ra <= rate)) rate = ra;
+        if (!(rb <= rate)) rate = rb;
+      }
+    }
+  }
+  return rate;
+}
+
+__global__ void __launch_bounds__(PairSmem::NT, 2)
+stage_kernel_pair(const __grid_constant__ StageArgs<float> a, const __grid_constant__ CUtensorMap tmap) {
+  using SM = PairSmem;
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
+  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + SM::bar_off);
+  __shared__ int failed;
+  TileJob<float> J;
+  if (!make_job<float, SM::TX, SM::TY>(a, J)) return;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int s = 0; s < 4; ++s) mbar_init(bars + s, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  unsigned floors = 0;
+  const double rate = stage_tile_pair(J, a.P, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
+  if (failed) {
+    if (threadIdx.x == 0) atomicExch(&a.sc->error, 1);
+    return;
+  }
+  if (a.want_rate) block_max_to(&a.sc->wmax_bits, rate, red);
+  if (floors) atomicAdd(&a.sc->floor_hits, (unsigned long long)floors);
+}
+
+}  // namespace ph
