@@ -56,6 +56,9 @@ def test_batch_matches_single_meshes_bit_exact(precision):
     t, cyc = B.time()
     assert np.all(cyc == 4)
     for s, (cfg, U) in enumerate(zip(cfgs, states)):
+        # the batch runs the one-cell stage kernel; FP32 single meshes default
+        # to the paired one, which rounds differently, so pin the tile
+        cfg.tile[:] = [16, 16, cfg.nx[2]]
         m = ph.Mesh(cfg)
         m.set_state(U.astype(dtype))
         m.step(4)
