@@ -44,6 +44,8 @@ class Config(ctypes.Structure):
         ("static_lo", ctypes.c_double * 3),
         ("static_hi", ctypes.c_double * 3),
         ("bc", ctypes.c_int32 * 6),
+        ("nscalars", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -53,7 +55,8 @@ BC = {"periodic": 0, "outflow": 1, "reflect": 2}
 def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0 / 3.0, cfl=0.3,
                 max_level=0, adaptive=0, dfloor=1e-12, pfloor=1e-12, refine_tol=0.05,
                 derefine_tol=0.0125, derefine_count=10, static_region=0,
-                static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2), bc=None) -> Config:
+                static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2), bc=None,
+                nscalars=0) -> Config:
     """bc: None (all periodic) or 6 entries, names or codes, for the faces
     x1 inner, x1 outer, x2 inner, x2 outer, x3 inner, x3 outer."""
     c = Config()
@@ -74,6 +77,7 @@ def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0
     c.static_lo[:] = list(static_lo)
     c.static_hi[:] = list(static_hi)
     c.bc[:] = [BC[b] if isinstance(b, str) else int(b) for b in (bc or ["periodic"] * 6)]
+    c.nscalars = int(nscalars)
     return c
 
 
@@ -146,13 +150,16 @@ def _dp(a: np.ndarray):
 
 
 class OracleMesh:
-    """One oracle mesh (uniform or two-level) with its state."""
+    """One oracle mesh (uniform or multi-level) with its state."""
 
     def __init__(self, cfg: Config):
+        if not 0 <= cfg.nscalars <= 2:
+            raise ValueError("0 .. 2 passive scalars")
         self.cfg = cfg
         self.L = lib()
         self.h = self.L.or_create(ctypes.byref(cfg))
         self.nx = tuple(cfg.nx)
+        self.nv = NVAR + int(cfg.nscalars)   # conserved variables per cell
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -170,7 +177,7 @@ class OracleMesh:
         return out
 
     def state_shape(self):
-        return (self.nblocks, NVAR, self.nx[2], self.nx[1], self.nx[0])
+        return (self.nblocks, self.nv, self.nx[2], self.nx[1], self.nx[0])
 
     def set_state(self, U: np.ndarray):
         U = np.ascontiguousarray(U, dtype=np.float64)
@@ -184,7 +191,7 @@ class OracleMesh:
 
     def get_full(self) -> np.ndarray:
         S = [n + 2 * NG for n in self.nx]
-        U = np.zeros((self.nblocks, NVAR, S[2], S[1], S[0]), dtype=np.float64)
+        U = np.zeros((self.nblocks, self.nv, S[2], S[1], S[0]), dtype=np.float64)
         self.L.or_get_full(self.h, _dp(U))
         return U
 
@@ -215,9 +222,9 @@ class OracleMesh:
         return float(t[0]), float(dt[0]), int(cyc[0])
 
     def totals(self) -> np.ndarray:
-        out = np.zeros(NVAR)
+        out = np.zeros(NVAR + 2)
         self.L.or_totals(self.h, _dp(out))
-        return out
+        return out[:self.nv]
 
     def floor_hits(self) -> int:
         return int(self.L.or_floor_hits(self.h))
@@ -235,9 +242,9 @@ class OracleMesh:
                                      1 if check_age else 0))
 
     def composite(self, level, I, J, K) -> np.ndarray:
-        out = np.zeros(NVAR)
+        out = np.zeros(NVAR + 2)
         self.L.or_composite(self.h, level, I, J, K, _dp(out))
-        return out
+        return out[:self.nv]
 
 
 def cons_to_prim(u, gamma, dfloor=1e-12, pfloor=1e-12):

@@ -18,9 +18,9 @@ namespace {
 template <class R>
 void copy_interior_in(Mesh<R>& m, const double* U, const double* V, double h) {
   size_t n1 = m.cfg.nx[0], n2 = m.cfg.nx[1], n3 = m.cfg.nx[2];
-  size_t per = NVAR * n1 * n2 * n3;
+  size_t per = (size_t)m.nv() * n1 * n2 * n3;
   for (size_t b = 0; b < m.leaf.size(); ++b)
-    for (int v = 0; v < NVAR; ++v)
+    for (int v = 0; v < m.nv(); ++v)
       for (size_t k = 0; k < n3; ++k)
         for (size_t j = 0; j < n2; ++j)
           for (size_t i = 0; i < n1; ++i) {
@@ -59,9 +59,9 @@ void or_set_state(void* h, const double* U) {
 void or_get_state(void* h, double* U) {
   auto* m = static_cast<Mesh<double>*>(h);
   size_t n1 = m->cfg.nx[0], n2 = m->cfg.nx[1], n3 = m->cfg.nx[2];
-  size_t per = NVAR * n1 * n2 * n3;
+  size_t per = (size_t)m->nv() * n1 * n2 * n3;
   for (size_t b = 0; b < m->leaf.size(); ++b)
-    for (int v = 0; v < NVAR; ++v)
+    for (int v = 0; v < m->nv(); ++v)
       for (size_t k = 0; k < n3; ++k)
         for (size_t j = 0; j < n2; ++j)
           for (size_t i = 0; i < n1; ++i)
@@ -187,9 +187,9 @@ void or_jvp_state(const Config* cfg, const double* U0, const double* V, double d
   copy_interior_in(m, U0, V, h);
   for (int c = 0; c < ncycles; ++c) m.cycle_with_dt(dts[c]);
   size_t n1 = cfg->nx[0], n2 = cfg->nx[1], n3 = cfg->nx[2];
-  size_t per = NVAR * n1 * n2 * n3;
+  size_t per = (size_t)m.nv() * n1 * n2 * n3;
   for (size_t b = 0; b < m.leaf.size(); ++b)
-    for (int v = 0; v < NVAR; ++v)
+    for (int v = 0; v < m.nv(); ++v)
       for (size_t k = 0; k < n3; ++k)
         for (size_t j = 0; j < n2; ++j)
           for (size_t i = 0; i < n1; ++i) {

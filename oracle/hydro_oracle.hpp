@@ -49,6 +49,11 @@ template <class R> inline R rmax(const R& a, const R& b) { return re(a) >= re(b)
 template <class R> inline R rmin(const R& a, const R& b) { return re(a) <= re(b) ? a : b; }
 
 enum { IDN = 0, IM1 = 1, IM2 = 2, IM3 = 3, IEN = 4, NVAR = 5 };
+// Passive scalars (Sec. 3.4: the hydro package advects every variable flagged
+// as advected): up to MAXS extra conserved variables rho r_s after the energy,
+// advected with the flow.  Arrays are sized for the maximum.
+constexpr int MAXS = 2;
+constexpr int NMAX = NVAR + MAXS;
 constexpr int NG = 2;  // ghost width (PLM needs two cells on each side)
 
 // Mesh / physics configuration.  Plain POD, mirrored field by field by the
@@ -67,6 +72,8 @@ struct Config {
   int32_t bc[6];          // physical boundary per face (x1 inner, x1 outer, x2 ..., x3 ...):
                           // BC_PERIODIC, BC_OUTFLOW or BC_REFLECT; both faces of an axis
                           // periodic or neither
+  int32_t nscalars;       // passive scalars, 0 .. MAXS
+  int32_t pad;
 };
 
 // Physical boundary conditions.  Reading (the paper's reflective boundaries
@@ -86,9 +93,10 @@ constexpr int BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_REFLECT = 2;
 // Conserved U = (rho, m1, m2, m3, E) -> primitive W = (rho, v1, v2, v3, p).
 // Reading: E = p/(gamma-1) + rho |v|^2 / 2; density and pressure floors are
 // applied here and only here, and every hit is counted.
+// Passive scalars: the concentration r = (rho r) / rho (after the floor).
 template <class R>
-inline void cons_to_prim(const R u[NVAR], R w[NVAR], const R& gamma, double dfloor,
-                         double pfloor, long* floors) {
+inline void cons_to_prim(const R u[NMAX], R w[NMAX], const R& gamma, double dfloor,
+                         double pfloor, long* floors, int ns = 0) {
   R rho = u[IDN];
   if (re(rho) < dfloor) { rho = R(dfloor); ++*floors; }
   w[IDN] = rho;
@@ -99,6 +107,7 @@ inline void cons_to_prim(const R u[NVAR], R w[NVAR], const R& gamma, double dflo
   R p = (gamma - 1.0) * (u[IEN] - ke);
   if (re(p) < pfloor) { p = R(pfloor); ++*floors; }
   w[IEN] = p;
+  for (int s = 0; s < ns; ++s) w[NVAR + s] = u[NVAR + s] / rho;
 }
 
 // Piecewise-linear reconstruction slope (Sec. 4.1 "piecewise linear
@@ -120,13 +129,15 @@ inline R vanleer(const R& wm, const R& w0, const R& wp) {
 // wave-speed bounds with Roe-averaged velocity and enthalpy:
 //   b+ = max(0, vR + cR, v~ + c~),  b- = min(0, vL - cL, v~ - c~),
 //   F  = (b+ FL - b- FR + b+ b- (UR - UL)) / (b+ - b-).
+// A passive scalar is one more conserved variable U = rho r with physical flux
+// rho v_n r, through the same formula with the same bounds.
 template <class R>
-inline void hlle_flux(const R wl[NVAR], const R wr[NVAR], int dir, const R& gamma,
-                      R flux[NVAR]) {
+inline void hlle_flux(const R wl[NMAX], const R wr[NMAX], int dir, const R& gamma,
+                      R flux[NMAX], int ns = 0) {
   const int ivn = IM1 + dir;
   const R gm1 = gamma - 1.0;
   // left and right conserved states and physical fluxes
-  R ul[NVAR], ur[NVAR], fl[NVAR], fr[NVAR];
+  R ul[NMAX], ur[NMAX], fl[NMAX], fr[NMAX];
   R v2l = wl[IM1] * wl[IM1] + wl[IM2] * wl[IM2] + wl[IM3] * wl[IM3];
   R v2r = wr[IM1] * wr[IM1] + wr[IM2] * wr[IM2] + wr[IM3] * wr[IM3];
   R el = wl[IEN] / gm1 + 0.5 * wl[IDN] * v2l;
@@ -150,6 +161,12 @@ inline void hlle_flux(const R wl[NVAR], const R wr[NVAR], int dir, const R& gamm
   fr[ivn] = fr[ivn] + wr[IEN];
   fl[IEN] = (el + wl[IEN]) * vnl;
   fr[IEN] = (er + wr[IEN]) * vnr;
+  for (int s = NVAR; s < NVAR + ns; ++s) {
+    ul[s] = wl[IDN] * wl[s];
+    ur[s] = wr[IDN] * wr[s];
+    fl[s] = wl[IDN] * vnl * wl[s];
+    fr[s] = wr[IDN] * vnr * wr[s];
+  }
 
   // sound speeds and Roe averages
   R cl = sqrt(gamma * wl[IEN] / wl[IDN]);
@@ -167,7 +184,7 @@ inline void hlle_flux(const R wl[NVAR], const R wr[NVAR], int dir, const R& gamm
 
   R bp = rmax(R(0.0), rmax(R(vnr + cr), R(vroe[dir] + croe)));
   R bm = rmin(R(0.0), rmin(R(vnl - cl), R(vroe[dir] - croe)));
-  for (int v = 0; v < NVAR; ++v)
+  for (int v = 0; v < NVAR + ns; ++v)
     flux[v] = (bp * fl[v] - bm * fr[v] + bp * bm * (ur[v] - ul[v])) / (bp - bm);
 }
 
@@ -215,7 +232,7 @@ struct Mesh {
   R gamma;
   std::vector<LeafId> leaf;
   std::vector<int32_t> age;            // cycles since the leaf was created
-  std::vector<std::vector<R>> U;       // per leaf: NVAR x S3 x S2 x S1 (ghosts included)
+  std::vector<std::vector<R>> U;       // per leaf: nv() x S3 x S2 x S1 (ghosts included)
   std::vector<int32_t> root;           // root-grid slot -> level-0 leaf index, or -1 when refined
   std::map<std::array<int64_t, 4>, int32_t> leaf_at;  // (level, lx1, lx2, lx3) -> leaf index
   double time = 0.0, dt = 0.0;
@@ -223,7 +240,8 @@ struct Mesh {
   long floors = 0;
 
   int S(int d) const { return cfg.nx[d] + 2 * NG; }
-  size_t block_len() const { return (size_t)NVAR * S(0) * S(1) * S(2); }
+  int nv() const { return NVAR + cfg.nscalars; }  // conserved variables per cell
+  size_t block_len() const { return (size_t)nv() * S(0) * S(1) * S(2); }
   size_t idx(int v, int k, int j, int i) const {
     return (((size_t)v * S(2) + k) * S(1) + j) * S(0) + i;
   }
@@ -338,12 +356,12 @@ struct Mesh {
   static int64_t wrap(int64_t i, int64_t n) { return ((i % n) + n) % n; }
 
   // Interior value of leaf b at global cell (I,J,K) of the leaf's own level.
-  void leaf_value(int b, int64_t I, int64_t J, int64_t K, R out[NVAR]) const {
+  void leaf_value(int b, int64_t I, int64_t J, int64_t K, R out[NMAX]) const {
     const LeafId& id = leaf[b];
     int i = (int)(I - id.lx[0] * cfg.nx[0]) + NG;
     int j = (int)(J - id.lx[1] * cfg.nx[1]) + NG;
     int k = (int)(K - id.lx[2] * cfg.nx[2]) + NG;
-    for (int v = 0; v < NVAR; ++v) out[v] = U[b][idx(v, k, j, i)];
+    for (int v = 0; v < nv(); ++v) out[v] = U[b][idx(v, k, j, i)];
   }
 
   // The composite field: the value of cell (I,J,K) of level L built from the
@@ -355,7 +373,7 @@ struct Mesh {
   // s_d = +-1/4, evaluated d = 1,2,3 in order, with the coarse values taken
   // from the composite field of level L-1 (itself prolonged or restricted
   // where no level-(L-1) leaf covers them).
-  void composite(int L, int64_t I, int64_t J, int64_t K, R out[NVAR]) const {
+  void composite(int L, int64_t I, int64_t J, int64_t K, R out[NMAX]) const {
     int64_t X[3] = {I, J, K};
     bool flip[3] = {false, false, false};
     bool outside = false;
@@ -394,36 +412,36 @@ struct Mesh {
     if (b >= 0) {  // a coarser leaf covers it: prolongation from level L-1
       int64_t C[3] = {I >> 1, J >> 1, K >> 1};
       int64_t F[3] = {I, J, K};
-      R uc[NVAR];
+      R uc[NMAX];
       composite(L - 1, C[0], C[1], C[2], uc);
-      R acc[NVAR];
-      for (int v = 0; v < NVAR; ++v) acc[v] = uc[v];
+      R acc[NMAX];
+      for (int v = 0; v < nv(); ++v) acc[v] = uc[v];
       for (int d = 0; d < 3; ++d) {
         int64_t cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
         cm[d] -= 1;
         cp[d] += 1;
-        R um[NVAR], up[NVAR];
+        R um[NMAX], up[NMAX];
         composite(L - 1, cm[0], cm[1], cm[2], um);
         composite(L - 1, cp[0], cp[1], cp[2], up);
         double sgn = (F[d] & 1) ? 0.25 : -0.25;
-        for (int v = 0; v < NVAR; ++v)
+        for (int v = 0; v < nv(); ++v)
           acc[v] = acc[v] + sgn * minmod(R(uc[v] - um[v]), R(up[v] - uc[v]));
       }
-      for (int v = 0; v < NVAR; ++v) out[v] = acc[v];
+      for (int v = 0; v < nv(); ++v) out[v] = acc[v];
       return;
     }
     // finer leaves cover it: restriction = mean of the 8 cells of level L+1,
     // summed c3 outer, c1 inner
-    R sum[NVAR];
-    for (int v = 0; v < NVAR; ++v) sum[v] = R(0.0);
+    R sum[NMAX];
+    for (int v = 0; v < nv(); ++v) sum[v] = R(0.0);
     for (int c3 = 0; c3 < 2; ++c3)
       for (int c2 = 0; c2 < 2; ++c2)
         for (int c1 = 0; c1 < 2; ++c1) {
-          R f[NVAR];
+          R f[NMAX];
           composite(L + 1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
-          for (int v = 0; v < NVAR; ++v) sum[v] = sum[v] + f[v];
+          for (int v = 0; v < nv(); ++v) sum[v] = sum[v] + f[v];
         }
-    for (int v = 0; v < NVAR; ++v) out[v] = 0.125 * sum[v];
+    for (int v = 0; v < nv(); ++v) out[v] = 0.125 * sum[v];
   }
 
   bool is_interior(int i, int j, int k) const {
@@ -440,18 +458,18 @@ struct Mesh {
         for (int j = 0; j < S(1); ++j)
           for (int i = 0; i < S(0); ++i) {
             if (is_interior(i, j, k)) continue;
-            R val[NVAR];
+            R val[NMAX];
             composite(id.level, id.lx[0] * cfg.nx[0] + i - NG, id.lx[1] * cfg.nx[1] + j - NG,
                       id.lx[2] * cfg.nx[2] + k - NG, val);
-            for (int v = 0; v < NVAR; ++v) U[b][idx(v, k, j, i)] = val[v];
+            for (int v = 0; v < nv(); ++v) U[b][idx(v, k, j, i)] = val[v];
           }
     }
   }
 
-  void prim_at(const std::vector<R>& u, int k, int j, int i, R w[NVAR]) {
-    R c[NVAR];
-    for (int v = 0; v < NVAR; ++v) c[v] = u[idx(v, k, j, i)];
-    cons_to_prim(c, w, gamma, cfg.dfloor, cfg.pfloor, &floors);
+  void prim_at(const std::vector<R>& u, int k, int j, int i, R w[NMAX]) {
+    R c[NMAX];
+    for (int v = 0; v < nv(); ++v) c[v] = u[idx(v, k, j, i)];
+    cons_to_prim(c, w, gamma, cfg.dfloor, cfg.pfloor, &floors, cfg.nscalars);
   }
 
   // Face fluxes of one leaf along direction d.  Face f lies between interior
@@ -469,7 +487,7 @@ struct Mesh {
   Fluxes face_fluxes(int b, int dir) {
     Fluxes F;
     for (int d = 0; d < 3; ++d) F.n[d] = cfg.nx[d] + (d == dir ? 1 : 0);
-    F.f.assign((size_t)NVAR * F.n[0] * F.n[1] * F.n[2], R(0.0));
+    F.f.assign((size_t)nv() * F.n[0] * F.n[1] * F.n[2], R(0.0));
     const std::vector<R>& u = U[b];
     int e[3] = {dir == 0, dir == 1, dir == 2};
     for (int k = 0; k < F.n[2]; ++k)
@@ -477,19 +495,19 @@ struct Mesh {
         for (int i = 0; i < F.n[0]; ++i) {
           // array indices of cell f (right of the face)
           int ci = i + NG, cj = j + NG, ck = k + NG;
-          R w[4][NVAR];  // cells f-2, f-1, f, f+1 along dir
+          R w[4][NMAX];  // cells f-2, f-1, f, f+1 along dir
           for (int s = 0; s < 4; ++s)
             prim_at(u, ck + (s - 2) * e[2], cj + (s - 2) * e[1], ci + (s - 2) * e[0], w[s]);
-          R wl[NVAR], wr[NVAR];
-          for (int v = 0; v < NVAR; ++v) {
+          R wl[NMAX], wr[NMAX];
+          for (int v = 0; v < nv(); ++v) {
             R dl = vanleer(w[0][v], w[1][v], w[2][v]);
             R dr = vanleer(w[1][v], w[2][v], w[3][v]);
             wl[v] = w[1][v] + 0.5 * dl;
             wr[v] = w[2][v] - 0.5 * dr;
           }
-          R fl[NVAR];
-          hlle_flux(wl, wr, dir, gamma, fl);
-          for (int v = 0; v < NVAR; ++v) F.at(v, k, j, i) = fl[v];
+          R fl[NMAX];
+          hlle_flux(wl, wr, dir, gamma, fl, cfg.nscalars);
+          for (int v = 0; v < nv(); ++v) F.at(v, k, j, i) = fl[v];
         }
     return F;
   }
@@ -517,8 +535,8 @@ struct Mesh {
           int childd = side ? 0 : 1;         // child offset along d adjacent to the face
           for (int a2 = 0; a2 < cfg.nx[t2]; ++a2)
             for (int a1 = 0; a1 < cfg.nx[t1]; ++a1) {
-              R sum[NVAR];
-              for (int v = 0; v < NVAR; ++v) sum[v] = R(0.0);
+              R sum[NMAX];
+              for (int v = 0; v < nv(); ++v) sum[v] = R(0.0);
               for (int q2 = 0; q2 < 2; ++q2)
                 for (int q1 = 0; q1 < 2; ++q1) {
                   int64_t g1 = 2 * (id.lx[t1] * cfg.nx[t1] + a1) + q1;  // fine global index
@@ -533,14 +551,14 @@ struct Mesh {
                   lc[d] = fface;
                   lc[t1] = (int)(g1 % cfg.nx[t1]);
                   lc[t2] = (int)(g2 % cfg.nx[t2]);
-                  for (int v = 0; v < NVAR; ++v)
+                  for (int v = 0; v < nv(); ++v)
                     sum[v] = sum[v] + F[fb][d].at(v, lc[2], lc[1], lc[0]);
                 }
               int lc[3];
               lc[d] = cface;
               lc[t1] = a1;
               lc[t2] = a2;
-              for (int v = 0; v < NVAR; ++v) F[b][d].at(v, lc[2], lc[1], lc[0]) = 0.25 * sum[v];
+              for (int v = 0; v < nv(); ++v) F[b][d].at(v, lc[2], lc[1], lc[0]) = 0.25 * sum[v];
             }
         }
       }
@@ -564,7 +582,7 @@ struct Mesh {
       for (int k = 0; k < cfg.nx[2]; ++k)
         for (int j = 0; j < cfg.nx[1]; ++j)
           for (int i = 0; i < cfg.nx[0]; ++i)
-            for (int v = 0; v < NVAR; ++v) {
+            for (int v = 0; v < nv(); ++v) {
               R L = -((F[b][0].at(v, k, j, i + 1) - F[b][0].at(v, k, j, i)) / h1 +
                       (F[b][1].at(v, k, j + 1, i) - F[b][1].at(v, k, j, i)) / h2 +
                       (F[b][2].at(v, k + 1, j, i) - F[b][2].at(v, k, j, i)) / h3);
@@ -587,8 +605,8 @@ struct Mesh {
       for (int k = NG; k < NG + cfg.nx[2]; ++k)
         for (int j = NG; j < NG + cfg.nx[1]; ++j)
           for (int i = NG; i < NG + cfg.nx[0]; ++i) {
-            double u[NVAR], w[NVAR];
-            for (int v = 0; v < NVAR; ++v) u[v] = re(U[b][idx(v, k, j, i)]);
+            double u[NMAX], w[NMAX];
+            for (int v = 0; v < nv(); ++v) u[v] = re(U[b][idx(v, k, j, i)]);
             long dummy = 0;
             cons_to_prim(u, w, re(gamma), cfg.dfloor, cfg.pfloor, &dummy);
             double cs = std::sqrt(re(gamma) * w[IEN] / w[IDN]);
@@ -760,10 +778,10 @@ struct Mesh {
       for (int k = NG; k < NG + cfg.nx[2]; ++k)
         for (int j = NG; j < NG + cfg.nx[1]; ++j)
           for (int i = NG; i < NG + cfg.nx[0]; ++i) {
-            R val[NVAR];
+            R val[NMAX];
             composite(id.level, id.lx[0] * cfg.nx[0] + i - NG, id.lx[1] * cfg.nx[1] + j - NG,
                       id.lx[2] * cfg.nx[2] + k - NG, val);
-            for (int v = 0; v < NVAR; ++v) nu[b][idx(v, k, j, i)] = val[v];
+            for (int v = 0; v < nv(); ++v) nu[b][idx(v, k, j, i)] = val[v];
           }
     }
     leaf.swap(nl);
@@ -789,8 +807,8 @@ struct Mesh {
   // Conserved totals: sum over interior cells of all leaves of U_v dV, with
   // Neumaier's compensated summation so that the sum itself adds no
   // round-off that a conservation check could mistake for a flux error.
-  void totals(double out[NVAR]) const {
-    for (int v = 0; v < NVAR; ++v) {
+  void totals(double out[NMAX]) const {
+    for (int v = 0; v < nv(); ++v) {
       double s = 0.0, comp = 0.0;
       for (size_t b = 0; b < leaf.size(); ++b) {
         int lev = leaf[b].level;
