@@ -18,7 +18,8 @@
  *    (except on multi-level meshes, where it reads refinement flags each cycle).
  *  - Caller buffers are borrowed for the duration of the call only.
  *  - State arrays are in the mesh's precision (double for PH_FP64, float for
- *    PH_FP32), conserved variables (rho, m1, m2, m3, E), interior cells only,
+ *    PH_FP32), conserved variables (rho, m1, m2, m3, E, then any passive
+ *    scalars rho r_s), interior cells only,
  *    layout U[block][var][k][j][i] with i fastest, blocks in the order of
  *    ph_tree (Z-order).
  *  - Device memory of a mesh is owned by the library and comes from the
@@ -69,6 +70,14 @@ extern "C" {
  *   tile[3]        fused-stage tile (TX, TY, KC); 0,0,0 = pick a default
  *   bc[6]          physical boundary of each face (PH_BC_*, below); all zero
  *                  = periodic everywhere
+ *   nscalars       passive scalars, 0 .. 2 (Sec. 3.4: the hydro package
+ *                  advects every variable flagged as advected): conserved
+ *                  rho r_s stored after the energy (state arrays then hold
+ *                  5 + nscalars variables per cell); the concentration r_s
+ *                  is reconstructed like the primitives and its flux is the
+ *                  HLLE formula with the hydro wave speeds.  Tiles 16x16 or
+ *                  8x8; not with ph_batch_* or ph_adjoint.
+ *   pad            unused
  */
 typedef struct ph_config {
   int32_t nx[3];
@@ -90,6 +99,8 @@ typedef struct ph_config {
   int32_t precision;
   int32_t tile[3];
   int32_t bc[6];
+  int32_t nscalars;
+  int32_t pad;
 } ph_config;
 
 /* Physical boundary conditions, per face in ph_config.bc (x1 inner, x1 outer,
@@ -175,8 +186,9 @@ int ph_get_next_dt(ph_mesh* mesh, double* dt);
 /* Simulation time and cycle count; synchronises. */
 int ph_get_time(ph_mesh* mesh, double* time, int64_t* cycle);
 
-/* Conserved totals: sum over interior cells of all leaves of U_v dV, in FP64. */
-int ph_totals(ph_mesh* mesh, double out[5]);
+/* Conserved totals: sum over interior cells of all leaves of U_v dV, in FP64;
+ * out receives 5 + nscalars values. */
+int ph_totals(ph_mesh* mesh, double* out);
 
 /* Refinement indicator of every leaf (reading of the unspecified criterion:
  * max over interior cells and directions of |rho_{+1} - rho_{-1}| / (2 rho))

@@ -65,6 +65,8 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int32),
         ("tile", ctypes.c_int32 * 3),
         ("bc", ctypes.c_int32 * 6),
+        ("nscalars", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -75,7 +77,7 @@ def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0
                 max_level=0, adaptive=0, dfloor=None, pfloor=None, refine_tol=0.05,
                 derefine_tol=0.0125, derefine_count=10, static_region=0,
                 static_lo=(-0.2, -0.2, -0.2), static_hi=(0.2, 0.2, 0.2), precision="fp64",
-                tile=(0, 0, 0), bc=None) -> Config:
+                tile=(0, 0, 0), bc=None, nscalars=0) -> Config:
     """bc: None (periodic everywhere) or 6 entries, names ("periodic",
     "outflow", "reflect") or PH_BC_* codes, for the faces x1 inner, x1 outer,
     x2 inner, x2 outer, x3 inner, x3 outer."""
@@ -104,6 +106,7 @@ def make_config(nx, nb, xmin=(-0.5, -0.5, -0.5), xmax=(0.5, 0.5, 0.5), gamma=5.0
     c.precision = prec
     c.tile[:] = list(tile)
     c.bc[:] = [BC[b] if isinstance(b, str) else int(b) for b in (bc or ["periodic"] * 6)]
+    c.nscalars = int(nscalars)
     return c
 
 
@@ -263,6 +266,7 @@ class Mesh:
         self.h = ctypes.c_void_p()
         check(self.L.ph_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(self.h)))
         self.nx = tuple(cfg.nx)
+        self.nvar = 5 + int(cfg.nscalars)
         self.dtype = np.float32 if cfg.precision == PH_FP32 else np.float64
 
     @classmethod
@@ -287,6 +291,7 @@ class Mesh:
             f.readinto(cfg)
         self.cfg = cfg
         self.nx = tuple(cfg.nx)
+        self.nvar = 5 + int(cfg.nscalars)
         self.dtype = np.float32 if cfg.precision == PH_FP32 else np.float64
         return self
 
@@ -323,7 +328,7 @@ class Mesh:
         return out
 
     def state_shape(self):
-        return (self.nblocks, 5, self.nx[2], self.nx[1], self.nx[0])
+        return (self.nblocks, self.nvar, self.nx[2], self.nx[1], self.nx[0])
 
     def count(self) -> int:
         return int(np.prod(self.state_shape()))
@@ -353,7 +358,7 @@ class Mesh:
 
     def get_full(self) -> np.ndarray:
         S = [n + 4 for n in self.nx]
-        out = np.zeros((self.nblocks, 5, S[2], S[1], S[0]), dtype=self.dtype)
+        out = np.zeros((self.nblocks, self.nvar, S[2], S[1], S[0]), dtype=self.dtype)
         check(self.L.ph_get_full(self.h, ctypes.c_void_p(out.ctypes.data), out.size, 0))
         return out
 
@@ -377,7 +382,7 @@ class Mesh:
         return t.value, c.value
 
     def totals(self) -> np.ndarray:
-        out = np.zeros(5)
+        out = np.zeros(self.nvar)
         check(self.L.ph_totals(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out
 

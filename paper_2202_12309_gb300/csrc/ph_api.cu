@@ -72,7 +72,8 @@ struct ph_mesh {
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   Allocator alloc;
   int nx[3], S[3], nb[3];
-  size_t block_elems = 0;  // NV * S1 * S2 * S3
+  int nvar = ph::NV;        // conserved variables per cell: NV + passive scalars
+  size_t block_elems = 0;  // nvar * S1 * S2 * S3
   size_t esize = 8;
   bool multi_level = false;
 
@@ -373,7 +374,7 @@ int build_tables(ph_mesh* m) {
   if ((rc = upload(m, &m->d_leaf_id, leaf_id))) return rc;
   if ((rc = upload(m, &m->d_nbr, nbr))) return rc;
   if ((rc = upload(m, &m->d_node, m->node))) return rc;
-  m->d_partial = (double*)m->dalloc(sizeof(double) * 5 * std::max(n, 1));
+  m->d_partial = (double*)m->dalloc(sizeof(double) * m->nvar * std::max(n, 1));
   m->d_mb = (double*)m->dalloc(sizeof(double) * std::max(n, 1));
   if (!m->d_partial || !m->d_mb) return fail(PH_ERR_OOM, "device allocation failed (tables)");
 
@@ -430,7 +431,7 @@ int build_tables(ph_mesh* m) {
     if ((rc = upload(m, &m->d_rec_beg, rec_beg))) return rc;
     if ((rc = upload(m, &m->d_rec_face, rec_face))) return rc;
     const int nmax = std::max(m->nx[0], std::max(m->nx[1], m->nx[2]));
-    const size_t face_elems = (size_t)5 * nmax * nmax;
+    const size_t face_elems = (size_t)m->nvar * nmax * nmax;
     m->d_fcc = m->dalloc(m->esize * face_elems * std::max(m->nrec, 1));
     m->d_fcf = m->dalloc(m->esize * face_elems * 4 * std::max(m->nrec, 1));
     if (!m->d_fcc || !m->d_fcf) return fail(PH_ERR_OOM, "device allocation failed (flux records)");
@@ -441,8 +442,10 @@ int build_tables(ph_mesh* m) {
 // (Re)build the tensor maps after the pools change.
 void build_tmaps(ph_mesh* m) {
   m->tma = ph::stage_tma_wanted() &&
-           ph::make_stage_tmap(&m->tm[0], m->U0, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1]) &&
-           ph::make_stage_tmap(&m->tm[1], m->U1, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1]);
+           ph::make_stage_tmap(&m->tm[0], m->U0, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1],
+                               m->nvar) &&
+           ph::make_stage_tmap(&m->tm[1], m->U1, m->esize, m->S, (int)m->pool_cap, m->tile[0], m->tile[1],
+                               m->nvar);
   if (!m->tma && ph::stage_pair_tile(m->tile[0], m->tile[1])) {
     // the paired kernel needs TMA staging: fall back to the 16 x 16 tile
     m->tile[0] = 16;
@@ -529,10 +532,11 @@ ph::LevelGeom level_geom(const ph_mesh* m) {
 template <class T>
 int fill_ghosts_t(ph_mesh* m, T* U) {
   if (m->multi_level) {
-    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->nleaf(), m->stream));
+    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->nleaf(), m->stream,
+                                          m->nvar));
   } else {
     PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream,
-                                        m->d_leaf_id, m->nb, bc_mask(m)));
+                                        m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
   }
   return PH_OK;
 }
@@ -559,6 +563,7 @@ ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
   a.want_rate = (stage == 2 && !m->multi_level) ? 1 : 0;
   a.P = phys<T>(m);
   a.sc = m->sc;
+  a.nvar = m->nvar;
   if (m->multi_level && m->nrec > 0) {
     a.face_rec = m->d_face_rec;
     a.fc_coarse = (T*)m->d_fcc;
@@ -572,7 +577,7 @@ ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
 template <class T>
 int refresh_dt_t(ph_mesh* m) {
   PH_CUDA(ph::launch_rate<T>((const T*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(), phys<T>(m), m->sc,
-                             m->stream));
+                             m->stream, m->nvar));
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 2, m->stream));
   return PH_OK;
 }
@@ -583,11 +588,11 @@ int enqueue_uniform_cycle(ph_mesh* m, cudaStream_t s) {
   const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
   PH_CUDA(ph::launch_stage<T>(a1, m->tile[0], m->tile[1], s, tmap_for(m, 1)));
   PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s,
-                                      m->d_leaf_id, m->nb, bc_mask(m)));
+                                      m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
   const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
   PH_CUDA(ph::launch_stage<T>(a2, m->tile[0], m->tile[1], s, tmap_for(m, 2)));
   PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s,
-                                      m->d_leaf_id, m->nb, bc_mask(m)));
+                                      m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, s));
   return PH_OK;
 }
@@ -635,7 +640,7 @@ int multi_level_cycle(ph_mesh* m) {
     T* out = (T*)(stage == 1 ? m->U1 : m->U0);
     PH_CUDA(ph::launch_flux_correct<T>(out, m->d_corr_leaf, m->d_rec_beg, m->ncorr, m->d_rec_face,
                                        (const T*)m->d_fcc, (const T*)m->d_fcf, m->nx, m->d_level, geom,
-                                       stage == 1 ? 1.0 : 0.5, m->sc, m->stream));
+                                       stage == 1 ? 1.0 : 0.5, m->sc, m->stream, m->nvar));
     if ((rc = fill_ghosts_t<T>(m, out))) return rc;
   }
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 1, m->stream));
@@ -643,7 +648,7 @@ int multi_level_cycle(ph_mesh* m) {
   if (m->cfg.adaptive) {
     std::vector<int8_t> flags;
     std::vector<double> mb;
-    PH_CUDA(ph::launch_indicator<T>((const T*)m->U0, m->nx, m->nleaf(), m->d_mb, m->stream));
+    PH_CUDA(ph::launch_indicator<T>((const T*)m->U0, m->nx, m->nleaf(), m->d_mb, m->stream, m->nvar));
     mb.resize(m->nleaf());
     PH_CUDA(cudaMemcpyAsync(mb.data(), m->d_mb, sizeof(double) * mb.size(), cudaMemcpyDeviceToHost,
                             m->stream));
@@ -688,7 +693,7 @@ int remesh_t(ph_mesh* m, std::vector<Leaf>& nl) {
   if (!U0n || !U1n) return fail(PH_ERR_OOM, "device allocation failed (remesh)");
   PH_CUDA(cudaMemsetAsync(U0n, 0, bytes, m->stream));
   PH_CUDA(cudaMemsetAsync(U1n, 0, bytes, m->stream));
-  PH_CUDA(ph::launch_remesh<T>((T*)U0n, d_new_id, nnew, (const T*)m->U0, old_tv, m->stream));
+  PH_CUDA(ph::launch_remesh<T>((T*)U0n, d_new_id, nnew, (const T*)m->U0, old_tv, m->stream, m->nvar));
   PH_CUDA(cudaStreamSynchronize(m->stream));
   m->dfree(d_new_id);
   m->dfree(m->U0);
@@ -730,11 +735,11 @@ int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
     cudaError_t e = cudaEventRecord(ev[0], m->stream);
     if (!e) e = ph::launch_stage<T>(a1, m->tile[0], m->tile[1], m->stream, tmap_for(m, 1));
     if (!e) e = cudaEventRecord(ev[1], m->stream);
-    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m));
+    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m), m->nvar);
     if (!e) e = cudaEventRecord(ev[2], m->stream);
     if (!e) e = ph::launch_stage<T>(a2, m->tile[0], m->tile[1], m->stream, tmap_for(m, 2));
     if (!e) e = cudaEventRecord(ev[3], m->stream);
-    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m));
+    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m), m->nvar);
     if (!e) e = cudaEventRecord(ev[4], m->stream);
     if (!e) e = ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream);
     if (!e) e = cudaEventRecord(ev[5], m->stream);
@@ -754,7 +759,7 @@ int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
 template <class T>
 int set_state_t(ph_mesh* m, const void* U, int on_device, int async = 0) {
   int rc;
-  const size_t count = (size_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
+  const size_t count = (size_t)m->nleaf() * m->nvar * m->nx[0] * m->nx[1] * m->nx[2];
   T* packed;
   if (on_device) {
     packed = (T*)U;
@@ -763,7 +768,7 @@ int set_state_t(ph_mesh* m, const void* U, int on_device, int async = 0) {
     packed = (T*)m->staging;
     PH_CUDA(cudaMemcpyAsync(packed, U, count * sizeof(T), cudaMemcpyHostToDevice, m->stream));
   }
-  PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 0, m->stream));
+  PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 0, m->stream, m->nvar));
   if ((rc = fill_ghosts_t<T>(m, (T*)m->U0))) return rc;
   PH_CUDA(cudaMemsetAsync(m->sc, 0, sizeof(ph::DevScalars), m->stream));
   if ((rc = refresh_dt_t<T>(m))) return rc;
@@ -777,7 +782,7 @@ int set_state_t(ph_mesh* m, const void* U, int on_device, int async = 0) {
 template <class T>
 int get_state_t(ph_mesh* m, void* U, int on_device, int async = 0) {
   int rc;
-  const size_t count = (size_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
+  const size_t count = (size_t)m->nleaf() * m->nvar * m->nx[0] * m->nx[1] * m->nx[2];
   T* packed;
   if (on_device) {
     packed = (T*)U;
@@ -785,7 +790,7 @@ int get_state_t(ph_mesh* m, void* U, int on_device, int async = 0) {
     if ((rc = ensure_staging(m, count * sizeof(T)))) return rc;
     packed = (T*)m->staging;
   }
-  PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 1, m->stream));
+  PH_CUDA(ph::launch_pack<T>((T*)m->U0, packed, m->nx, m->nleaf(), 1, m->stream, m->nvar));
   if (!on_device)
     PH_CUDA(cudaMemcpyAsync(U, packed, count * sizeof(T), cudaMemcpyDeviceToHost, m->stream));
   if (!async) PH_CUDA(cudaStreamSynchronize(m->stream));
@@ -793,17 +798,17 @@ int get_state_t(ph_mesh* m, void* U, int on_device, int async = 0) {
 }
 
 template <class T>
-int totals_t(ph_mesh* m, double out[5]) {
+int totals_t(ph_mesh* m, double* out) {
   PH_CUDA(ph::launch_totals<T>((const T*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(), m->d_partial,
-                               m->d_totals, m->stream));
-  PH_CUDA(cudaMemcpyAsync(out, m->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+                               m->d_totals, m->stream, m->nvar));
+  PH_CUDA(cudaMemcpyAsync(out, m->d_totals, m->nvar * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   PH_CUDA(cudaStreamSynchronize(m->stream));
   return PH_OK;
 }
 
 template <class T>
 int tag_t(ph_mesh* m, int8_t* flags, double* mb) {
-  PH_CUDA(ph::launch_indicator<T>((const T*)m->U0, m->nx, m->nleaf(), m->d_mb, m->stream));
+  PH_CUDA(ph::launch_indicator<T>((const T*)m->U0, m->nx, m->nleaf(), m->d_mb, m->stream, m->nvar));
   std::vector<double> h(m->nleaf());
   PH_CUDA(cudaMemcpyAsync(h.data(), m->d_mb, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                           m->stream));
@@ -839,6 +844,7 @@ int cycle_fixed_dt_t(ph_mesh* m, double dt) {
 
 bool valid_tile(const ph_config* c, const int t[3]) {
   if (t[2] < 1 || t[2] > c->nx[2]) return false;
+  if (c->nscalars > 0) return ph::stage_scalar_tile(t[0], t[1]);
   if (ph::stage_pair_tile(t[0], t[1]))
     return c->precision == PH_FP32 && c->max_level == 0 && c->nx[0] % t[0] == 0 &&
            c->nx[1] % t[1] == 0;
@@ -855,6 +861,7 @@ namespace ph {
 int mesh_access(ph_mesh* m, MeshAccess* out) {
   if (m->multi_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
   if (bc_mask(m)) return fail(PH_ERR_INVALID, "adjoint: periodic meshes only");
+  if (m->nvar != ph::NV) return fail(PH_ERR_INVALID, "adjoint: meshes without passive scalars only");
   out->U0 = m->U0;
   out->U1 = m->U1;
   out->nbr = m->d_nbr;
@@ -937,6 +944,8 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     return fail(PH_ERR_INVALID, "ph_create: precision must be PH_FP64 or PH_FP32");
   if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0))
     return fail(PH_ERR_INVALID, "ph_create: need gamma > 1 and cfl > 0");
+  if (cfg->nscalars < 0 || cfg->nscalars > ph::MAXS)
+    return fail(PH_ERR_INVALID, "ph_create: nscalars must be 0 .. 2");
   for (int d = 0; d < 3; ++d) {
     const int lo = cfg->bc[2 * d], hi = cfg->bc[2 * d + 1];
     if (lo < PH_BC_PERIODIC || lo > PH_BC_REFLECT || hi < PH_BC_PERIODIC || hi > PH_BC_REFLECT)
@@ -957,7 +966,8 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     m->S[d] = cfg->nx[d] + 2 * ph::NG;
   }
   m->esize = cfg->precision == PH_FP32 ? 4 : 8;
-  m->block_elems = (size_t)5 * m->S[0] * m->S[1] * m->S[2];
+  m->nvar = ph::NV + cfg->nscalars;
+  m->block_elems = (size_t)m->nvar * m->S[0] * m->S[1] * m->S[2];
   m->multi_level = cfg->max_level >= 1;
   int t[3] = {cfg->tile[0], cfg->tile[1], cfg->tile[2]};
   if (t[0] == 0 && t[1] == 0 && t[2] == 0) {
@@ -966,6 +976,7 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     t[0] = cfg->nx[0] >= 16 ? 16 : 8;
     t[1] = (cfg->nx[1] >= 16 && t[0] == 16) ? 16 : 8;
     t[2] = cfg->nx[2] >= 32 ? 16 : cfg->nx[2];
+    if (cfg->nscalars > 0 && !(t[0] == 16 && t[1] == 16)) t[0] = t[1] = 8;
     // FP32 uniform meshes: the paired kernel where the blocks tile into 32 x 16
     const int pt[3] = {32, 16, t[2]};
     if (ph::stage_tma_wanted() && valid_tile(cfg, pt)) {
@@ -1054,7 +1065,7 @@ int ph_tree(const ph_mesh* m, int64_t* out, int32_t n) {
 }
 
 static int64_t interior_count(const ph_mesh* m) {
-  return (int64_t)m->nleaf() * 5 * m->nx[0] * m->nx[1] * m->nx[2];
+  return (int64_t)m->nleaf() * m->nvar * m->nx[0] * m->nx[1] * m->nx[2];
 }
 
 int ph_set_state(ph_mesh* m, const void* U, int64_t count, int32_t on_device) {
@@ -1134,7 +1145,7 @@ int ph_get_time(ph_mesh* m, double* time, int64_t* cycle) {
   return PH_OK;
 }
 
-int ph_totals(ph_mesh* m, double out[5]) {
+int ph_totals(ph_mesh* m, double* out) {
   if (!m || !out) return fail(PH_ERR_INVALID, "ph_totals: null argument");
   return DISPATCH(m, totals_t, m, out);
 }
@@ -1328,6 +1339,8 @@ int ph_load(const char* path, void* stream, ph_mesh** out) {
   for (int d = 0; d < 3; ++d)
     if (h.cfg.nx[d] < 1 || h.cfg.nx[d] > (1 << 16) || h.cfg.nb[d] < 1 || h.cfg.nb[d] > (1 << 16))
       return fail(PH_ERR_INVALID, "ph_load: bad block or grid size");
+  if (h.cfg.nscalars < 0 || h.cfg.nscalars > ph::MAXS)
+    return fail(PH_ERR_INVALID, "ph_load: bad scalar count");
   const int64_t nroot = (int64_t)h.cfg.nb[0] * h.cfg.nb[1] * h.cfg.nb[2];
   const int64_t cells = (int64_t)h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
   if (h.cfg.max_level < 0 || h.cfg.max_level > ph::MAXLEV)
@@ -1337,7 +1350,8 @@ int ph_load(const char* path, void* stream, ph_mesh** out) {
     return fail(PH_ERR_INVALID, "ph_load: bad leaf count");
   {  // the file must hold exactly the tree and the state its header announces
     const int64_t want = (int64_t)sizeof(FileHead) + (int64_t)h.nleaf * sizeof(FileLeaf) +
-                         (int64_t)h.nleaf * 5 * cells * (h.data_precision == PH_FP32 ? 4 : 8);
+                         (int64_t)h.nleaf * (ph::NV + h.cfg.nscalars) * cells *
+                             (h.data_precision == PH_FP32 ? 4 : 8);
     if (fseek(fc.f, 0, SEEK_END) != 0) return fail(PH_ERR_IO, "ph_load: cannot seek");
     const long have = ftell(fc.f);
     if (have < 0 || (int64_t)have != want)
@@ -1363,7 +1377,7 @@ int ph_load(const char* path, void* stream, ph_mesh** out) {
     if (!build_nodes(tl, h.cfg.nb, nodes))
       return fail(PH_ERR_INVALID, "ph_load: leaves do not tile the domain");
   }
-  const int64_t count = (int64_t)h.nleaf * 5 * h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
+  const int64_t count = (int64_t)h.nleaf * (ph::NV + h.cfg.nscalars) * h.cfg.nx[0] * h.cfg.nx[1] * h.cfg.nx[2];
   const size_t fbytes = (size_t)count * (h.data_precision == PH_FP32 ? 4 : 8);
   std::vector<unsigned char> data(fbytes);
   if (fbytes && fread(data.data(), 1, fbytes, fc.f) != fbytes)

@@ -630,6 +630,7 @@ int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch*
     if (c.max_level != 0) return bfail(PH_ERR_INVALID, "ph_batch_create: members must be uniform");
     for (int f = 0; f < 6; ++f)
       if (c.bc[f] != PH_BC_PERIODIC) return bfail(PH_ERR_INVALID, "ph_batch_create: members must be periodic");
+    if (c.nscalars != 0) return bfail(PH_ERR_INVALID, "ph_batch_create: members without passive scalars only");
     for (int d = 0; d < 3; ++d) {
       if (c.nx[d] < 4 || c.nb[d] < 1 || !(c.xmax[d] > c.xmin[d]))
         return bfail(PH_ERR_INVALID, "ph_batch_create: bad member geometry");

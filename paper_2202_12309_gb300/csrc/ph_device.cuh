@@ -12,6 +12,7 @@
 namespace ph {
 
 constexpr int NV = 5;   // conserved variables: rho, m1, m2, m3, E
+constexpr int MAXS = 2; // passive scalars rho r_s stored after E (variables NV .. NV+MAXS-1)
 constexpr int NG = 2;   // ghost width: PLM needs two cells on each side
 constexpr int MAXLEV = 4;  // finest level a mesh tree may have
 
@@ -156,8 +157,9 @@ __device__ __forceinline__ bool mid_range(float x) {
 
 // Conserved -> primitive in place: (rho, m1, m2, m3, E) -> (rho, v1, v2, v3, p),
 // with density and pressure floors (each application counted).
-template <class T>
-__device__ __forceinline__ void cons_to_prim(T w[NV], const Phys<T>& P, unsigned& floors) {
+// Passive scalars (variables NV .. NVT-1) become concentrations r = (rho r) / rho.
+template <class T, int NVT = NV>
+__device__ __forceinline__ void cons_to_prim(T w[NVT], const Phys<T>& P, unsigned& floors) {
   T rho = w[0];
   if (below_floor(rho, P.dfloor)) { rho = P.dfloor; ++floors; }
   const T ir = rcp(rho);
@@ -169,6 +171,15 @@ __device__ __forceinline__ void cons_to_prim(T w[NV], const Phys<T>& P, unsigned
   w[2] = v2;
   w[3] = v3;
   w[4] = p;
+#pragma unroll
+  for (int v = NV; v < NVT; ++v) w[v] = w[v] * ir;
+}
+
+// Half van Leer slope of one passive-scalar concentration (one reciprocal).
+template <class T>
+__device__ __forceinline__ T vanleer_half_rcp(T wm, T w0, T wp) {
+  const T dl = w0 - wm, dr = wp - w0, prod = dl * dr;
+  return same_sign_nonzero(dl, dr) ? prod * rcp(dl + dr) : T(0);
 }
 
 // Half of the van Leer (harmonic) limited slope of a cell from its two
@@ -247,8 +258,8 @@ __device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], co
 // is aL + aR and the momentum flux aL v_L + aR v_R plus the pressure term on
 // the normal component: two FP64 operations per momentum component instead
 // of eight.  Roe averages use sqrt(rho) v and h sqrt(rho) = (E + p)/sqrt(rho).
-template <class T, int DIR>
-__device__ __forceinline__ void hlle(const T wl[NV], const T wr[NV], const Phys<T>& P, T f[NV]) {
+template <class T, int DIR, int NVT = NV>
+__device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phys<T>& P, T f[NVT]) {
   // Every multiply-add is an explicit fma, so that the rounding is the same
   // in every kernel this is inlined into (the single-mesh and the batched
   // kernels agree bit for bit).
@@ -283,6 +294,9 @@ __device__ __forceinline__ void hlle(const T wl[NV], const T wr[NV], const Phys<
   for (int a = 1; a <= 3; ++a) f[a] = fma(aL, wl[a], aR * wr[a]);
   f[IN] += fma(cL, pl, cR * pr);
   f[4] = fma(cL * vnl, hl, fma(cR * vnr, hr, cD * (er - el)));
+  // passive scalars: mass flux split like a transverse velocity component
+#pragma unroll
+  for (int v = NV; v < NVT; ++v) f[v] = fma(aL, wl[v], aR * wr[v]);
 }
 
 // Largest signal speed over cell width of one primitive state:

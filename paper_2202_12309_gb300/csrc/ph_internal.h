@@ -69,7 +69,7 @@ template <class T>
 cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s,
                          const CUtensorMap* tmap = nullptr);
 bool make_stage_tmap(CUtensorMap* out, const void* base, size_t esize, const int S[3], int nleaf, int TX,
-                     int TY);
+                     int TY, int nvar = NV);
 bool stage_tma_wanted();  // false when PH_STAGE_LOADS=plain
 template <class T>
 size_t stage_smem_bytes(int TX, int TY);
@@ -77,6 +77,8 @@ bool stage_tile_supported(int TX, int TY);
 // 32 x 16: the paired FP32 kernel (FP32 uniform meshes with TMA staging,
 // nx1 a multiple of 32 and nx2 of 16)
 bool stage_pair_tile(int TX, int TY);
+// tiles that meshes with passive scalars can use
+bool stage_scalar_tile(int TX, int TY);
 cudaError_t configure_stage_kernels();
 
 // K1 (uniform mesh): every ghost cell of every leaf copied from the
@@ -86,23 +88,23 @@ cudaError_t configure_stage_kernels();
 template <class T>
 cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
                                  const int* leaf_id = nullptr, const int nb[3] = nullptr,
-                                 int bcm = 0);
+                                 int bcm = 0, int nvar = NV);
 
 // K1 (multi-level mesh): every ghost cell of every leaf takes the composite
 // field of the mesh (copy / restriction / prolongation), one launch.
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
-                                   cudaStream_t s);
+                                   cudaStream_t s, int nvar = NV);
 
 // K7: interior of every new leaf from the old mesh's composite field.
 template <class T>
 cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uold,
-                          const TreeView& old_tv, cudaStream_t s);
+                          const TreeView& old_tv, cudaStream_t s, int nvar = NV);
 
 // K5: max over interior cells of (|v_d|+c)/dx_d into sc->wmax_bits.
 template <class T>
 cudaError_t launch_rate(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
-                        int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s);
+                        int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s, int nvar = NV);
 
 // dt bookkeeping: mode bit 1 commits the cycle (time += dt, cycle++),
 // bit 2 computes the next dt = cfl / wmax and clears wmax, bit 4 copies the
@@ -111,17 +113,19 @@ cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s)
 
 // Interior <-> padded copies.  dir 0: packed -> padded, 1: padded -> packed.
 template <class T>
-cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s);
+cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s,
+                        int nvar = NV);
 
 // Conserved totals: per-leaf FP64 sums into partial[nleaf*5], then one
 // ordered compensated sum into out[5].
 template <class T>
 cudaError_t launch_totals(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
-                          int nleaf, double* partial, double* out, cudaStream_t s);
+                          int nleaf, double* partial, double* out, cudaStream_t s, int nvar = NV);
 
 // K6: refinement indicator per leaf (FP64).
 template <class T>
-cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s);
+cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s,
+                             int nvar = NV);
 
 // K4: flux correction at fine-coarse faces, applied after the stage update.
 // One CTA per coarse leaf corr_leaf[c] with records rec_beg[c] .. rec_beg[c+1].
@@ -129,6 +133,6 @@ template <class T>
 cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
                                 const int nx[3], const int8_t* level, const LevelGeom& g,
-                                double beta, const DevScalars* sc, cudaStream_t s);
+                                double beta, const DevScalars* sc, cudaStream_t s, int nvar = NV);
 
 }  // namespace ph

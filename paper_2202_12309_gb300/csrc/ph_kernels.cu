@@ -39,7 +39,7 @@ __device__ __forceinline__ bool bc_image(int& g, int o, int n, bool lo, bool hi,
 // copies about 1024 ghost cells, so that small meshes of large blocks still
 // fill the GPU).  bcm packs the six faces' boundary kinds (2 bits each, x1
 // inner first); 0 = periodic everywhere, where leaf_id and nbl are unused.
-template <class T>
+template <class T, int NVT = NV>
 __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx,
                                      const int* __restrict__ leaf_id, int3 nbl, int bcm) {
   const int nxa[3] = {nx.x, nx.y, nx.z};
@@ -47,7 +47,7 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx,
   const int b = blockIdx.x;
   const int S1 = sh.S1, S2 = sh.S2, S3 = nx.z + 2 * NG;
   const size_t vs = (size_t)S1 * S2 * S3;
-  T* dstb = U + (size_t)b * NV * vs;
+  T* dstb = U + (size_t)b * NVT * vs;
   const int* nb = nbr + 27 * b;
   const int total = sh.count();
   const int per = (total + gridDim.y - 1) / gridDim.y;
@@ -72,17 +72,17 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx,
       if (bc_image(sk, oz, nx.z, lx[2] == 0, lx[2] == nbl.z - 1, (bcm >> 8) & 3, (bcm >> 10) & 3, f3)) oz = 0;
     }
     const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
-    const T* srcb = U + (size_t)src * NV * vs;
+    const T* srcb = U + (size_t)src * NVT * vs;
     const size_t so = ((size_t)(sk - oz * nx.z) * S2 + (sj - oy * nx.y)) * S1 + (si - ox * nx.x);
     const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
-    T w[NV];
+    T w[NVT];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = srcb[v * vs + so];
+    for (int v = 0; v < NVT; ++v) w[v] = srcb[v * vs + so];
     if (f1) w[1] = -w[1];
     if (f2) w[2] = -w[2];
     if (f3) w[3] = -w[3];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dstb[v * vs + dofs] = w[v];
+    for (int v = 0; v < NVT; ++v) dstb[v * vs + dofs] = w[v];
   }
 }
 
@@ -103,7 +103,7 @@ struct Pair<double> {
   using V = double2;
 };
 
-template <class T>
+template <class T, int NVT = NV>
 __global__ void ghost_uniform_pairs_kernel(T* U, const int* __restrict__ nbr, int3 nx) {
   using V = typename Pair<T>::V;
   const int nxa[3] = {nx.x, nx.y, nx.z};
@@ -111,7 +111,7 @@ __global__ void ghost_uniform_pairs_kernel(T* U, const int* __restrict__ nbr, in
   const int b = blockIdx.x;
   const int S1 = sh.S1, S2 = sh.S2, S3 = nx.z + 2 * NG;
   const size_t vs = (size_t)S1 * S2 * S3;
-  T* dstb = U + (size_t)b * NV * vs;
+  T* dstb = U + (size_t)b * NVT * vs;
   const int* nb = nbr + 27 * b;
   const int total = sh.count() / 2;
   const int per = (total + gridDim.y - 1) / gridDim.y;
@@ -123,35 +123,43 @@ __global__ void ghost_uniform_pairs_kernel(T* U, const int* __restrict__ nbr, in
     const int oy = j < NG ? -1 : (j >= NG + nx.y ? 1 : 0);
     const int oz = k < NG ? -1 : (k >= NG + nx.z ? 1 : 0);
     const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
-    const T* srcb = U + (size_t)src * NV * vs;
+    const T* srcb = U + (size_t)src * NVT * vs;
     const size_t so = ((size_t)(k - oz * nx.z) * S2 + (j - oy * nx.y)) * S1 + (i - ox * nx.x);
     const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
-    V w[NV];
+    V w[NVT];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = *reinterpret_cast<const V*>(srcb + v * vs + so);
+    for (int v = 0; v < NVT; ++v) w[v] = *reinterpret_cast<const V*>(srcb + v * vs + so);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) *reinterpret_cast<V*>(dstb + v * vs + dofs) = w[v];
+    for (int v = 0; v < NVT; ++v) *reinterpret_cast<V*>(dstb + v * vs + dofs) = w[v];
   }
 }
 
-template <class T>
-cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
-                                 const int* leaf_id, const int nb[3], int bcm) {
-  if (nleaf <= 0) return cudaSuccess;
+template <class T, int NVT>
+static cudaError_t launch_ghost_uniform_n(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
+                                          const int* leaf_id, const int nb[3], int bcm) {
   const long long S1 = nx[0] + 2 * NG, S2 = nx[1] + 2 * NG, S3 = nx[2] + 2 * NG;
   const long long shell = S1 * S2 * S3 - (long long)nx[0] * nx[1] * nx[2];
   if (bcm == 0 && nx[0] % 2 == 0) {
     const long long pairs = shell / 2;
     const int chunks = (int)std::min<long long>(64, std::max<long long>(1, (pairs + 1023) / 1024));
-    ghost_uniform_pairs_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(U, nbr,
-                                                                      make_int3(nx[0], nx[1], nx[2]));
+    ghost_uniform_pairs_kernel<T, NVT><<<dim3(nleaf, chunks), 256, 0, s>>>(
+        U, nbr, make_int3(nx[0], nx[1], nx[2]));
     return cudaGetLastError();
   }
   const int chunks = (int)std::min<long long>(64, std::max<long long>(1, (shell + 1023) / 1024));
   const int3 nbl = nb ? make_int3(nb[0], nb[1], nb[2]) : make_int3(1, 1, 1);
-  ghost_uniform_kernel<T><<<dim3(nleaf, chunks), 256, 0, s>>>(
+  ghost_uniform_kernel<T, NVT><<<dim3(nleaf, chunks), 256, 0, s>>>(
       U, nbr, make_int3(nx[0], nx[1], nx[2]), leaf_id, nbl, bcm);
   return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
+                                 const int* leaf_id, const int nb[3], int bcm, int nvar) {
+  if (nleaf <= 0) return cudaSuccess;
+  if (nvar == NV + 1) return launch_ghost_uniform_n<T, NV + 1>(U, nbr, nx, nleaf, s, leaf_id, nb, bcm);
+  if (nvar == NV + 2) return launch_ghost_uniform_n<T, NV + 2>(U, nbr, nx, nleaf, s, leaf_id, nb, bcm);
+  return launch_ghost_uniform_n<T, NV>(U, nbr, nx, nleaf, s, leaf_id, nb, bcm);
 }
 
 // --------------------------------------------------------------------------
@@ -202,7 +210,7 @@ __device__ __forceinline__ bool domain_image(long long& X, long long N, int bc_l
 }
 
 template <class T>
-__device__ __forceinline__ void negate_momenta(T out[NV], bool f1, bool f2, bool f3) {
+__device__ __forceinline__ void negate_momenta(T* out, bool f1, bool f2, bool f3) {
   if (f1) out[1] = -out[1];
   if (f2) out[2] = -out[2];
   if (f3) out[3] = -out[3];
@@ -225,13 +233,13 @@ __device__ __forceinline__ int tree_cover(const TreeView& tv, int L, long long b
   }
 }
 
-template <class T>
+template <class T, int NVT>
 __device__ __forceinline__ void read_cell(const T* U, const TreeView& tv, int leaf, int li, int lj,
-                                          int lk, T out[NV]) {
+                                          int lk, T out[NVT]) {
   const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
-  const T* p = U + (size_t)leaf * NV * vs + ((size_t)(lk + NG) * tv.S[1] + (lj + NG)) * tv.S[0] + (li + NG);
+  const T* p = U + (size_t)leaf * NVT * vs + ((size_t)(lk + NG) * tv.S[1] + (lj + NG)) * tv.S[0] + (li + NG);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[v] = p[v * vs];
+  for (int v = 0; v < NVT; ++v) out[v] = p[v * vs];
 }
 
 template <class T>
@@ -240,7 +248,7 @@ __device__ __forceinline__ T minmod_dev(T a, T b) {
   return T(0);
 }
 
-template <class T, int D>
+template <class T, int D, int NVT>
 __device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int L, long long I,
                                              long long J, long long K, T* out) {
   const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
@@ -252,7 +260,7 @@ __device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int
   int lev = 0;
   const int lf = tree_cover(tv, L, b1, b2, b3, &lev);
   if (lf >= 0 && lev == L) {
-    read_cell(U, tv, lf, (int)(I - b1 * tv.nx[0]), (int)(J - b2 * tv.nx[1]), (int)(K - b3 * tv.nx[2]),
+    read_cell<T, NVT>(U, tv, lf, (int)(I - b1 * tv.nx[0]), (int)(J - b2 * tv.nx[1]), (int)(K - b3 * tv.nx[2]),
               out);
     negate_momenta(out, f1, f2, f3);
     return;
@@ -260,50 +268,50 @@ __device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int
   if constexpr (D == 0) {
     atomicExch(tv.error, 1);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[v] = T(0);
+    for (int v = 0; v < NVT; ++v) out[v] = T(0);
     return;
   } else {
     if (lf >= 0) {  // coarser leaf: prolongation from level L-1
       const long long C[3] = {I >> 1, J >> 1, K >> 1};
       const long long F[3] = {I, J, K};
-      T uc[NV], acc[NV];
-      composite_value<T, D - 1>(U, tv, L - 1, C[0], C[1], C[2], uc);
+      T uc[NVT], acc[NVT];
+      composite_value<T, D - 1, NVT>(U, tv, L - 1, C[0], C[1], C[2], uc);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = uc[v];
+      for (int v = 0; v < NVT; ++v) acc[v] = uc[v];
       for (int d = 0; d < 3; ++d) {
         long long cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
         cm[d] -= 1;
         cp[d] += 1;
-        T um[NV], up[NV];
-        composite_value<T, D - 1>(U, tv, L - 1, cm[0], cm[1], cm[2], um);
-        composite_value<T, D - 1>(U, tv, L - 1, cp[0], cp[1], cp[2], up);
+        T um[NVT], up[NVT];
+        composite_value<T, D - 1, NVT>(U, tv, L - 1, cm[0], cm[1], cm[2], um);
+        composite_value<T, D - 1, NVT>(U, tv, L - 1, cp[0], cp[1], cp[2], up);
         const T sg = (F[d] & 1) ? T(0.25) : T(-0.25);
 #pragma unroll
-        for (int v = 0; v < NV; ++v)
+        for (int v = 0; v < NVT; ++v)
           acc[v] = add_rn(acc[v], mul_rn(sg, minmod_dev(sub_rn(uc[v], um[v]), sub_rn(up[v], uc[v]))));
       }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[v] = acc[v];
+      for (int v = 0; v < NVT; ++v) out[v] = acc[v];
     } else {  // finer leaves: restriction from level L+1
-      T sum[NV];
+      T sum[NVT];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sum[v] = T(0);
+      for (int v = 0; v < NVT; ++v) sum[v] = T(0);
       for (int c3 = 0; c3 < 2; ++c3)
         for (int c2 = 0; c2 < 2; ++c2)
           for (int c1 = 0; c1 < 2; ++c1) {
-            T f[NV];
-            composite_value<T, D - 1>(U, tv, L + 1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
+            T f[NVT];
+            composite_value<T, D - 1, NVT>(U, tv, L + 1, 2 * I + c1, 2 * J + c2, 2 * K + c3, f);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sum[v] = add_rn(sum[v], f[v]);
+            for (int v = 0; v < NVT; ++v) sum[v] = add_rn(sum[v], f[v]);
           }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[v] = mul_rn(T(0.125), sum[v]);
+      for (int v = 0; v < NVT; ++v) out[v] = mul_rn(T(0.125), sum[v]);
     }
     negate_momenta(out, f1, f2, f3);
   }
 }
 
-template <class T>
+template <class T, int NVT>
 __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id) {
   const Shell sh(tv.nx);
   const int b = blockIdx.x;
@@ -312,28 +320,33 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
   const long long o2 = (long long)leaf_id[4 * b + 2] * tv.nx[1] - NG;
   const long long o3 = (long long)leaf_id[4 * b + 3] * tv.nx[2] - NG;
   const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
-  T* dst = U + (size_t)b * NV * vs;
+  T* dst = U + (size_t)b * NVT * vs;
   const int total = sh.count();
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     int i, j, k;
     sh.cell(c, i, j, k);
-    T val[NV];
-    composite_value<T, COMPOSITE_DEPTH>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
+    T val[NVT];
+    composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
     const size_t d = ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * vs + d] = val[v];
+    for (int v = 0; v < NVT; ++v) dst[v * vs + d] = val[v];
   }
 }
 
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int nvar) {
   if (nleaf <= 0) return cudaSuccess;
-  ghost_composite_kernel<T><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+  if (nvar == NV + 1)
+    ghost_composite_kernel<T, NV + 1><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+  else if (nvar == NV + 2)
+    ghost_composite_kernel<T, NV + 2><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+  else
+    ghost_composite_kernel<T, NV><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
   return cudaGetLastError();
 }
 
-template <class T>
+template <class T, int NVT>
 __global__ void remesh_kernel(T* Unew, const int* __restrict__ leaf_id, const T* Uold,
                               const TreeView tv) {
   const int b = blockIdx.x;
@@ -343,23 +356,28 @@ __global__ void remesh_kernel(T* Unew, const int* __restrict__ leaf_id, const T*
   const long long o2 = (long long)leaf_id[4 * b + 2] * n2;
   const long long o3 = (long long)leaf_id[4 * b + 3] * n3;
   const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
-  T* dst = Unew + (size_t)b * NV * vs;
+  T* dst = Unew + (size_t)b * NVT * vs;
   const int total = n1 * n2 * n3;
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     const int k = c / (n1 * n2), r = c - k * n1 * n2, j = r / n1, i = r - j * n1;
-    T val[NV];
-    composite_value<T, COMPOSITE_DEPTH>(Uold, tv, lev, o1 + i, o2 + j, o3 + k, val);
+    T val[NVT];
+    composite_value<T, COMPOSITE_DEPTH, NVT>(Uold, tv, lev, o1 + i, o2 + j, o3 + k, val);
     const size_t d = ((size_t)(k + NG) * tv.S[1] + (j + NG)) * tv.S[0] + (i + NG);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * vs + d] = val[v];
+    for (int v = 0; v < NVT; ++v) dst[v * vs + d] = val[v];
   }
 }
 
 template <class T>
 cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uold,
-                          const TreeView& old_tv, cudaStream_t s) {
+                          const TreeView& old_tv, cudaStream_t s, int nvar) {
   if (nnew <= 0) return cudaSuccess;
-  remesh_kernel<T><<<nnew, 256, 0, s>>>(Unew, new_leaf_id, Uold, old_tv);
+  if (nvar == NV + 1)
+    remesh_kernel<T, NV + 1><<<nnew, 256, 0, s>>>(Unew, new_leaf_id, Uold, old_tv);
+  else if (nvar == NV + 2)
+    remesh_kernel<T, NV + 2><<<nnew, 256, 0, s>>>(Unew, new_leaf_id, Uold, old_tv);
+  else
+    remesh_kernel<T, NV><<<nnew, 256, 0, s>>>(Unew, new_leaf_id, Uold, old_tv);
   return cudaGetLastError();
 }
 
@@ -368,12 +386,12 @@ cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uo
 // --------------------------------------------------------------------------
 template <class T>
 __global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
-                            const LevelGeom g, int3 nx, Phys<T> P, DevScalars* sc) {
+                            const LevelGeom g, int3 nx, Phys<T> P, DevScalars* sc, int nvar) {
   __shared__ double red[32];
   const int b = blockIdx.x;
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
   const size_t vs = (size_t)S1 * S2 * S3;
-  const T* Ub = U + (size_t)b * NV * vs;
+  const T* Ub = U + (size_t)b * nvar * vs;
   const int lev = level ? (int)level[b] : 0;
   const T i1 = (T)g.idx[lev][0], i2 = (T)g.idx[lev][1], i3 = (T)g.idx[lev][2];
   unsigned floors = 0;
@@ -395,9 +413,9 @@ __global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ 
 
 template <class T>
 cudaError_t launch_rate(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
-                        int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s) {
+                        int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s, int nvar) {
   if (nleaf <= 0) return cudaSuccess;
-  rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]), P, sc);
+  rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]), P, sc, nvar);
   return cudaGetLastError();
 }
 
@@ -426,10 +444,10 @@ cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s)
 // Interior <-> padded copies
 // --------------------------------------------------------------------------
 template <class T>
-__global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir) {
+__global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir, int nvar) {
   const int b = blockIdx.y;
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
-  const size_t per = (size_t)NV * nx.x * nx.y * nx.z;
+  const size_t per = (size_t)nvar * nx.x * nx.y * nx.z;
   const size_t vs = (size_t)S1 * S2 * S3;
   const int cells = nx.x * nx.y * nx.z;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per;
@@ -437,7 +455,7 @@ __global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir) {
     const int v = (int)(e / cells);
     const int c = (int)(e - (size_t)v * cells);
     const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
-    T* pp = padded + (size_t)b * NV * vs + v * vs + ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
+    T* pp = padded + (size_t)b * nvar * vs + v * vs + ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
     T* qq = packed + (size_t)b * per + e;
     if (dir == 0)
       *pp = *qq;
@@ -447,55 +465,60 @@ __global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir) {
 }
 
 template <class T>
-cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s) {
+cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s,
+                        int nvar) {
   if (nleaf <= 0) return cudaSuccess;
-  const size_t per = (size_t)NV * nx[0] * nx[1] * nx[2];
+  const size_t per = (size_t)nvar * nx[0] * nx[1] * nx[2];
   int gx = (int)((per + 255) / 256);
   if (gx > 64) gx = 64;
-  pack_kernel<T><<<dim3(gx, nleaf), 256, 0, s>>>(padded, packed, make_int3(nx[0], nx[1], nx[2]), dir);
+  pack_kernel<T><<<dim3(gx, nleaf), 256, 0, s>>>(padded, packed, make_int3(nx[0], nx[1], nx[2]), dir,
+                                                  nvar);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------
 // Conserved totals in FP64
 // --------------------------------------------------------------------------
-template <class T>
+template <class T, int NVT>
 __global__ void totals_block_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
                                     const LevelGeom g, int3 nx, double* partial) {
-  __shared__ double red[NV][256];
+  __shared__ double red[NVT][256];
   const int b = blockIdx.x;
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
   const size_t vs = (size_t)S1 * S2 * S3;
-  const T* Ub = U + (size_t)b * NV * vs;
-  double acc[NV] = {0, 0, 0, 0, 0};
+  const T* Ub = U + (size_t)b * NVT * vs;
+  double acc[NVT];
+#pragma unroll
+  for (int v = 0; v < NVT; ++v) acc[v] = 0.0;
   const int total = nx.x * nx.y * nx.z;
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
     const size_t o = ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] += (double)Ub[v * vs + o];
+    for (int v = 0; v < NVT; ++v) acc[v] += (double)Ub[v * vs + o];
   }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) red[v][threadIdx.x] = acc[v];
+  for (int v = 0; v < NVT; ++v) red[v][threadIdx.x] = acc[v];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + w];
+      for (int v = 0; v < NVT; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < NV) {
+  if (threadIdx.x < NVT) {
     const double dv = g.vol[level ? (int)level[b] : 0];
-    partial[(size_t)b * NV + threadIdx.x] = red[threadIdx.x][0] * dv;
+    partial[(size_t)b * NVT + threadIdx.x] = red[threadIdx.x][0] * dv;
   }
 }
 
-__global__ void totals_final_kernel(const double* __restrict__ partial, int nleaf, double* out) {
+__global__ void totals_final_kernel(const double* __restrict__ partial, int nleaf, double* out,
+                                    int nvar) {
   const int v = threadIdx.x;
-  if (v >= NV) return;
+  if (v >= nvar) return;
   double s = 0.0, comp = 0.0;  // Neumaier compensated sum over leaves in order
   for (int b = 0; b < nleaf; ++b) {
-    const double x = partial[(size_t)b * NV + v];
+    const double x = partial[(size_t)b * nvar + v];
     const double t = s + x;
     if (fabs(s) >= fabs(x))
       comp += (s - t) + x;
@@ -508,11 +531,17 @@ __global__ void totals_final_kernel(const double* __restrict__ partial, int nlea
 
 template <class T>
 cudaError_t launch_totals(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
-                          int nleaf, double* partial, double* out, cudaStream_t s) {
-  if (nleaf > 0)
-    totals_block_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]),
-                                                  partial);
-  totals_final_kernel<<<1, 32, 0, s>>>(partial, nleaf, out);
+                          int nleaf, double* partial, double* out, cudaStream_t s, int nvar) {
+  const int3 n = make_int3(nx[0], nx[1], nx[2]);
+  if (nleaf > 0) {
+    if (nvar == NV + 1)
+      totals_block_kernel<T, NV + 1><<<nleaf, 256, 0, s>>>(U, level, g, n, partial);
+    else if (nvar == NV + 2)
+      totals_block_kernel<T, NV + 2><<<nleaf, 256, 0, s>>>(U, level, g, n, partial);
+    else
+      totals_block_kernel<T, NV><<<nleaf, 256, 0, s>>>(U, level, g, n, partial);
+  }
+  totals_final_kernel<<<1, 32, 0, s>>>(partial, nleaf, out, nvar);
   return cudaGetLastError();
 }
 
@@ -521,11 +550,11 @@ cudaError_t launch_totals(const T* U, const int8_t* level, const LevelGeom& g, c
 // |rho_{+e_d} - rho_{-e_d}| / (2 rho), in FP64 (IEEE division).
 // --------------------------------------------------------------------------
 template <class T>
-__global__ void indicator_kernel(const T* __restrict__ U, int3 nx, double* mb) {
+__global__ void indicator_kernel(const T* __restrict__ U, int3 nx, double* mb, int nvar) {
   __shared__ unsigned long long red[32];
   const int b = blockIdx.x;
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
-  const T* r = U + (size_t)b * NV * S1 * S2 * S3;  // density is variable 0
+  const T* r = U + (size_t)b * nvar * S1 * S2 * S3;  // density is variable 0
   double m = 0.0;
   const int total = nx.x * nx.y * nx.z;
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
@@ -557,9 +586,10 @@ __global__ void indicator_kernel(const T* __restrict__ U, int3 nx, double* mb) {
 }
 
 template <class T>
-cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s) {
+cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s,
+                             int nvar) {
   if (nleaf <= 0) return cudaSuccess;
-  indicator_kernel<T><<<nleaf, 256, 0, s>>>(U, make_int3(nx[0], nx[1], nx[2]), mb);
+  indicator_kernel<T><<<nleaf, 256, 0, s>>>(U, make_int3(nx[0], nx[1], nx[2]), mb, nvar);
   return cudaGetLastError();
 }
 
@@ -582,13 +612,13 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
                                     const int* __restrict__ rec_face, const T* __restrict__ fcc,
                                     const T* __restrict__ fcf, int3 nx,
                                     const int8_t* __restrict__ level, const LevelGeom g,
-                                    double beta, const DevScalars* sc) {
+                                    double beta, const DevScalars* sc, int nvar) {
   const int leaf = corr_leaf[blockIdx.x];
   const int lev = level[leaf];
   const int n[3] = {nx.x, nx.y, nx.z};
   const int S[3] = {nx.x + 2 * NG, nx.y + 2 * NG, nx.z + 2 * NG};
   const size_t vs = (size_t)S[0] * S[1] * S[2];
-  T* Ub = U + (size_t)leaf * NV * vs;
+  T* Ub = U + (size_t)leaf * nvar * vs;
   for (int r = rec_beg[blockIdx.x]; r < rec_beg[blockIdx.x + 1]; ++r) {
     const int face = rec_face[r];
     const int d = face >> 1, side = face & 1;
@@ -596,8 +626,8 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
     const int m1 = n[t1], m2 = n[t2];
     const double id = g.idx[lev][d];
     const T coef = (T)(beta * sc->dt_next * id) * (side ? T(1) : T(-1));
-    const T* Fc = fcc + (size_t)r * NV * m1 * m2;
-    const T* Ff = fcf + (size_t)r * NV * 4 * m1 * m2;
+    const T* Fc = fcc + (size_t)r * nvar * m1 * m2;
+    const T* Ff = fcf + (size_t)r * nvar * 4 * m1 * m2;
     for (int c = threadIdx.x; c < m1 * m2; c += blockDim.x) {
       const int a2 = c / m1, a1 = c - a2 * m1;
       int l[3];
@@ -606,8 +636,7 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
       l[t2] = a2;
       const size_t o = ((size_t)(l[2] + NG) * S[1] + (l[1] + NG)) * S[0] + (l[0] + NG);
       const int w = 2 * m1;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
+      for (int v = 0; v < nvar; ++v) {
         const T* f = Ff + (size_t)v * 4 * m1 * m2;
         const T fmean = T(0.25) * (f[(2 * a2) * w + 2 * a1] + f[(2 * a2) * w + 2 * a1 + 1] +
                                    f[(2 * a2 + 1) * w + 2 * a1] + f[(2 * a2 + 1) * w + 2 * a1 + 1]);
@@ -623,32 +652,33 @@ template <class T>
 cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
                                 const int nx[3], const int8_t* level, const LevelGeom& g,
-                                double beta, const DevScalars* sc, cudaStream_t s) {
+                                double beta, const DevScalars* sc, cudaStream_t s, int nvar) {
   if (ncorr <= 0) return cudaSuccess;
   flux_correct_kernel<T><<<ncorr, 256, 0, s>>>(U, corr_leaf, rec_beg, rec_face, fc_coarse, fc_fine,
-                                                make_int3(nx[0], nx[1], nx[2]), level, g, beta, sc);
+                                                make_int3(nx[0], nx[1], nx[2]), level, g, beta, sc,
+                                                nvar);
   return cudaGetLastError();
 }
 
 // explicit instantiations
 #define PH_INST(T)                                                                              \
   template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t, \
-                                              const int*, const int*, int);                   \
+                                              const int*, const int*, int, int);              \
   template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, int,          \
-                                                 cudaStream_t);                                 \
+                                                 cudaStream_t, int);                            \
   template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
-                                        cudaStream_t);                                          \
+                                        cudaStream_t, int);                                     \
   template cudaError_t launch_rate<T>(const T*, const int8_t*, const LevelGeom&, const int*,   \
-                                      int, Phys<T>, DevScalars*, cudaStream_t);                 \
-  template cudaError_t launch_pack<T>(T*, T*, const int*, int, int, cudaStream_t);              \
+                                      int, Phys<T>, DevScalars*, cudaStream_t, int);            \
+  template cudaError_t launch_pack<T>(T*, T*, const int*, int, int, cudaStream_t, int);         \
   template cudaError_t launch_totals<T>(const T*, const int8_t*, const LevelGeom&, const int*,  \
-                                        int,                                                    \
-                                        double*, double*, cudaStream_t);                        \
-  template cudaError_t launch_indicator<T>(const T*, const int*, int, double*, cudaStream_t);   \
+                                        int, double*, double*, cudaStream_t, int);              \
+  template cudaError_t launch_indicator<T>(const T*, const int*, int, double*, cudaStream_t,    \
+                                           int);                                                \
   template cudaError_t launch_flux_correct<T>(T*, const int*, const int*, int, const int*,      \
                                               const T*, const T*, const int*, const int8_t*,    \
                                               const LevelGeom&, double, const DevScalars*,      \
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 PH_INST(double)
 PH_INST(float)
 #undef PH_INST

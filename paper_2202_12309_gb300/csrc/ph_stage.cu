@@ -29,14 +29,17 @@ size_t stage_smem_bytes(int TX, int TY) {
   return 0;
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, int NVT = NV>
 static cudaError_t configure_tile() {
-  cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)StageSmem<T, TX, TY>::bytes);
+  cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)StageSmem<T, TX, TY, NVT>::bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel_tma<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)StageSmem<T, TX, TY>::bytes);
+  return cudaFuncSetAttribute(stage_kernel_tma<T, TX, TY, NVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)StageSmem<T, TX, TY, NVT>::bytes);
 }
+
+// Meshes with passive scalars: tiles 16 x 16 and 8 x 8, one or two scalars.
+bool stage_scalar_tile(int TX, int TY) { return (TX == 16 && TY == 16) || (TX == 8 && TY == 8); }
 
 // Opt every instantiation into its dynamic shared memory once per device,
 // outside any stream capture.
@@ -50,20 +53,36 @@ cudaError_t configure_stage_kernels() {
   if ((e = configure_tile<float, 16, 8>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 16, 16>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 32, 8>()) != cudaSuccess) return e;
+  if ((e = configure_tile<double, 16, 16, NV + 1>()) != cudaSuccess) return e;
+  if ((e = configure_tile<double, 16, 16, NV + 2>()) != cudaSuccess) return e;
+  if ((e = configure_tile<double, 8, 8, NV + 1>()) != cudaSuccess) return e;
+  if ((e = configure_tile<double, 8, 8, NV + 2>()) != cudaSuccess) return e;
+  if ((e = configure_tile<float, 16, 16, NV + 1>()) != cudaSuccess) return e;
+  if ((e = configure_tile<float, 16, 16, NV + 2>()) != cudaSuccess) return e;
+  if ((e = configure_tile<float, 8, 8, NV + 1>()) != cudaSuccess) return e;
+  if ((e = configure_tile<float, 8, 8, NV + 2>()) != cudaSuccess) return e;
   return cudaFuncSetAttribute(stage_kernel_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PairSmem::bytes);
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, int NVT = NV>
 static cudaError_t launch_tile(const StageArgs<T>& a, const CUtensorMap* tmap, cudaStream_t s) {
-  const size_t smem = StageSmem<T, TX, TY>::bytes;
+  using SM = StageSmem<T, TX, TY, NVT>;
   const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
   if (grid == 0) return cudaSuccess;
   if (tmap)
-    stage_kernel_tma<T, TX, TY><<<grid, StageSmem<T, TX, TY>::NT, smem, s>>>(a, *tmap);
+    stage_kernel_tma<T, TX, TY, NVT><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
   else
-    stage_kernel<T, TX, TY><<<grid, StageSmem<T, TX, TY>::NT, smem, s>>>(a);
+    stage_kernel<T, TX, TY, NVT><<<grid, SM::NT, SM::bytes, s>>>(a);
   return cudaGetLastError();
+}
+
+template <class T, int NVT>
+static cudaError_t launch_scalar_tiles(const StageArgs<T>& a, int TX, int TY, cudaStream_t s,
+                                       const CUtensorMap* tmap) {
+  if (TX == 16 && TY == 16) return launch_tile<T, 16, 16, NVT>(a, tmap, s);
+  if (TX == 8 && TY == 8) return launch_tile<T, 8, 8, NVT>(a, tmap, s);
+  return cudaErrorInvalidValue;
 }
 
 // The paired FP32 kernel (32 x 16 tiles, TMA staging, uniform meshes).
@@ -77,6 +96,9 @@ static cudaError_t launch_pair(const StageArgs<float>& a, const CUtensorMap* tma
 
 template <class T>
 cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s, const CUtensorMap* tmap) {
+  if (a.nvar == NV + 1) return launch_scalar_tiles<T, NV + 1>(a, TX, TY, s, tmap);
+  if (a.nvar == NV + 2) return launch_scalar_tiles<T, NV + 2>(a, TX, TY, s, tmap);
+  if (a.nvar != NV) return cudaErrorInvalidValue;
   if (stage_pair_tile(TX, TY)) {
     if constexpr (sizeof(T) == 4) return launch_pair(a, tmap, s);
     return cudaErrorInvalidValue;
@@ -116,21 +138,21 @@ bool stage_tma_wanted() {
 }
 
 // Tensor map over a pool of padded blocks [leaf][v][k][j][i] seen as a 4-D
-// tensor (S1, S2, S3, 5 * nleaf) with box (TX+4, TY+4, 1, 5).  Returns false
+// tensor (S1, S2, S3, nvar * nleaf) with box (TX+4, TY+4, 1, nvar).  Returns false
 // (and the stage kernel keeps its plain loads) when the layout breaks a TMA
 // rule: rows of S1 elements must be a multiple of 16 bytes, as must the box
 // rows and the base address.
 bool make_stage_tmap(CUtensorMap* out, const void* base, size_t esize, const int S[3], int nleaf, int TX,
-                     int TY) {
+                     int TY, int nvar) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || !base || nleaf <= 0) return false;
   if (((size_t)S[0] * esize) % 16 || ((size_t)(TX + 4) * esize) % 16) return false;
   if (reinterpret_cast<uintptr_t>(base) % 16) return false;
   if (TY + 4 > 256 || TX + 4 > 256) return false;
-  cuuint64_t dims[4] = {(cuuint64_t)S[0], (cuuint64_t)S[1], (cuuint64_t)S[2], (cuuint64_t)NV * nleaf};
+  cuuint64_t dims[4] = {(cuuint64_t)S[0], (cuuint64_t)S[1], (cuuint64_t)S[2], (cuuint64_t)nvar * nleaf};
   cuuint64_t strides[3] = {(cuuint64_t)S[0] * esize, (cuuint64_t)S[0] * S[1] * esize,
                            (cuuint64_t)S[0] * S[1] * S[2] * esize};
-  cuuint32_t box[4] = {(cuuint32_t)(TX + 4), (cuuint32_t)(TY + 4), 1, (cuuint32_t)NV};
+  cuuint32_t box[4] = {(cuuint32_t)(TX + 4), (cuuint32_t)(TY + 4), 1, (cuuint32_t)nvar};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   std::memset(out, 0, sizeof(*out));
   CUresult r = fn(out, esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,

@@ -47,6 +47,7 @@ struct StageArgs {
   T* fc_coarse;        // [rec][v][n_t2][n_t1] flux of the coarse block on the face
   T* fc_fine;          // [rec][v][2 n_t2][2 n_t1] fluxes of the fine blocks on the face
   const int* fine_off; // per leaf 6 x 2: offset of the fine block's quadrant (t1, t2)
+  int nvar;            // conserved variables per cell: NV + passive scalars
 };
 
 // Store one face flux of a leaf on a fine-coarse face (Sec. 3.7 flux
@@ -62,14 +63,14 @@ __device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int fac
   const int d = face >> 1;
   const int m1 = a.nx[(d + 1) % 3], m2 = a.nx[(d + 2) % 3];
   if ((fr & 1) == 0) {
-    a.fc_coarse[(((size_t)rec * NV + v) * m2 + a2) * m1 + a1] = val;
+    a.fc_coarse[(((size_t)rec * a.nvar + v) * m2 + a2) * m1 + a1] = val;
   } else {
     const int q1 = a.fine_off[12 * leaf + 2 * face], q2 = a.fine_off[12 * leaf + 2 * face + 1];
-    a.fc_fine[(((size_t)rec * NV + v) * (2 * m2) + q2 * m2 + a2) * (2 * m1) + q1 * m1 + a1] = val;
+    a.fc_fine[(((size_t)rec * a.nvar + v) * (2 * m2) + q2 * m2 + a2) * (2 * m1) + q1 * m1 + a1] = val;
   }
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, int NVT = NV>
 struct StageSmem {
   static constexpr int WX = TX + 4, WY = TY + 4;
   // threads.  FP32 (issue-bound): enough for the largest per-plane work list
@@ -82,16 +83,16 @@ struct StageSmem {
   // resident CTAs per SM the registers are allocated for (FP32: 3; FP64: left
   // to the compiler, which keeps 2 CTAs of 256 threads without spills)
   static constexpr int MINB = sizeof(T) == 4 ? 3 : 0;
-  static constexpr int PLANE = NV * WX * WY;          // one plane of 5 variables with halo
+  static constexpr int PLANE = NVT * WX * WY;         // one plane of every variable with halo
   static constexpr int SLOT = (PLANE * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T);
   static constexpr unsigned PLANE_BYTES = PLANE * sizeof(T);  // one TMA box
   // row pitch of the face-flux arrays: TX+4 keeps the FP32 warps of own_cell
   // on distinct banks; FP64 keeps the dense TX+1
   static constexpr int FP = sizeof(T) == 4 ? TX + 4 : TX + 1;
-  static constexpr int DXN = NV * TY * (TX + 2);      // x1 slopes
-  static constexpr int DYN = NV * (TY + 2) * TX;      // x2 slopes
-  static constexpr int FXN = NV * TY * FP;            // x1 face fluxes (TX+1 used per row)
-  static constexpr int FYN = NV * (TY + 1) * FP;      // x2 face fluxes (TX used per row)
+  static constexpr int DXN = NVT * TY * (TX + 2);     // x1 slopes
+  static constexpr int DYN = NVT * (TY + 2) * TX;     // x2 slopes
+  static constexpr int FXN = NVT * TY * FP;           // x1 face fluxes (TX+1 used per row)
+  static constexpr int FYN = NVT * (TY + 1) * FP;     // x2 face fluxes (TX used per row)
   static constexpr size_t body = sizeof(T) * (size_t)(4 * SLOT + DXN + DYN + FXN + FYN);
   static constexpr size_t red_off = (body + 15) / 16 * 16;
   static constexpr size_t bar_off = red_off + 32 * sizeof(double);
@@ -144,14 +145,23 @@ struct TileJob {
 // input pool, box (TX+4, TY+4, 1, 5) at (i0, j0, plane, vz0)), issued one plane
 // ahead on the slot's mbarrier, and are converted to primitives in place.
 // Returns with *failed set (and every thread leaving) if a wait gave up.
-template <class T, int TX, int TY, bool TMA>
+// Half slopes of every variable: the five hydro ones batched, the passive
+// scalars one by one.
+template <class T, int NVT>
+__device__ __forceinline__ void vanleer_all(const T wm[NVT], const T w0[NVT], const T wp[NVT], T h[NVT]) {
+  vanleer_half5(wm, w0, wp, h);
+#pragma unroll
+  for (int v = NV; v < NVT; ++v) h[v] = vanleer_half_rcp(wm[v], w0[v], wp[v]);
+}
+
+template <class T, int TX, int TY, bool TMA, int NVT = NV>
 __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>& P,
                                              const StageArgs<T>& a, unsigned char* smem_raw,
                                              unsigned& floors, const CUtensorMap* tmap = nullptr,
                                              int vz0 = 0, uint64_t* bars = nullptr,
                                              int* failed = nullptr,
                                              unsigned* parity_io = nullptr) {
-  using SM = StageSmem<T, TX, TY>;
+  using SM = StageSmem<T, TX, TY, NVT>;
   constexpr int NT = SM::NT;        // threads of the CTA
   constexpr int NC = TX * TY;       // threads that own a cell of the tile
   constexpr int FP = SM::FP;
@@ -187,12 +197,12 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       const int jj = c / WX, ii = c - jj * WX;
       const int jp = min(j0 + jj, S2 - 1), ip = min(i0 + ii, S1 - 1);
       const T* src = Ub + kofs + (size_t)jp * S1 + ip;
-      T w[NV];
+      T w[NVT];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = __ldg(src + v * vstride);
-      cons_to_prim(w, P, floors);
+      for (int v = 0; v < NVT; ++v) w[v] = __ldg(src + v * vstride);
+      cons_to_prim<T, NVT>(w, P, floors);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
+      for (int v = 0; v < NVT; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
     }
   };
   // TMA path: issue the copy of plane p (one thread), then convert it in
@@ -218,12 +228,12 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     for (int c = tid; c < WX * WY; c += NT) {
       const int jj = c / WX, ii = c - jj * WX;
       if (ii >= vi || jj >= vj) continue;
-      T w[NV];
+      T w[NVT];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) w[v] = dst[(v * WY + jj) * WX + ii];
-      cons_to_prim(w, P, floors);
+      for (int v = 0; v < NVT; ++v) w[v] = dst[(v * WY + jj) * WX + ii];
+      cons_to_prim<T, NVT>(w, P, floors);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
+      for (int v = 0; v < NVT; ++v) dst[(v * WY + jj) * WX + ii] = w[v];
     }
     return ok;
   };
@@ -233,10 +243,10 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     __syncthreads();
     return *(volatile int*)failed != 0;
   };
-  auto col = [&](int p, T w[NV]) {  // own column's primitive at plane p
+  auto col = [&](int p, T w[NVT]) {  // own column's primitive at plane p
     const T* s = ring + ((p + 4) & 3) * SM::SLOT;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = s[(v * WY + ty + 2) * WX + tx + 2];
+    for (int v = 0; v < NVT; ++v) w[v] = s[(v * WY + ty + 2) * WX + tx + 2];
   };
 
   // Priming: planes k0-2 .. k0+1 give the x3 slope at k0 and the flux at k0-1/2.
@@ -253,22 +263,22 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     load_plane(k0 + 1);
     __syncthreads();
   }
-  T dz[NV], fzm[NV];
+  T dz[NVT], fzm[NVT];
   if (has_cell) {  // x3 work is per owned column
-    T wa[NV], wb[NV], wc[NV], wd[NV], wl[NV], wr[NV];
+    T wa[NVT], wb[NVT], wc[NVT], wd[NVT], wl[NVT], wr[NVT];
     col(k0 - 2, wa);
     col(k0 - 1, wb);
     col(k0, wc);
     col(k0 + 1, wd);
-    T d0[NV];
-    vanleer_half5(wa, wb, wc, d0);
-    vanleer_half5(wb, wc, wd, dz);
+    T d0[NVT];
+    vanleer_all<T, NVT>(wa, wb, wc, d0);
+    vanleer_all<T, NVT>(wb, wc, wd, dz);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < NVT; ++v) {
       wl[v] = wb[v] + d0[v];
       wr[v] = wc[v] - dz[v];
     }
-    hlle<T, 2>(wl, wr, P, fzm);
+    hlle<T, 2, NVT>(wl, wr, P, fzm);
   }
   __syncthreads();
   // Plane k0+2 into the slot of plane k0-2 (read above); the loop's step k
@@ -291,23 +301,23 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 
   for (int k = k0; k < k1; ++k) {
     // (C) slopes; own x3 flux (planes k, k+1, k+2 are in the ring)
-    T fzlo[NV];  // x3 flux below the cell; fzm becomes the flux above it
+    T fzlo[NVT];  // x3 flux below the cell; fzm becomes the flux above it
     if (has_cell) {
-      T wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], f[NV];
+      T wa[NVT], wb[NVT], wc[NVT], wl[NVT], wr[NVT], f[NVT];
       col(k, wa);
       col(k + 1, wb);
       col(k + 2, wc);
-      T d1[NV];
-      vanleer_half5(wa, wb, wc, d1);
+      T d1[NVT];
+      vanleer_all<T, NVT>(wa, wb, wc, d1);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
+      for (int v = 0; v < NVT; ++v) {
         wl[v] = wa[v] + dz[v];
         wr[v] = wb[v] - d1[v];
         dz[v] = d1[v];
       }
-      hlle<T, 2>(wl, wr, P, f);
+      hlle<T, 2, NVT>(wl, wr, P, f);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
+      for (int v = 0; v < NVT; ++v) {
         fzlo[v] = fzm[v];
         fzm[v] = f[v];
       }
@@ -316,31 +326,31 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       const T* W = ring + ((k + 4) & 3) * SM::SLOT;
       for (int c = tid; c < (TX + 2) * TY; c += NT) {   // x1 slopes, cells -1..TX
         const int jj = c / (TX + 2), ii = c - jj * (TX + 2);
-        T a[NV], b[NV], q[NV], h[NV];
+        T a[NVT], b[NVT], q[NVT], h[NVT];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 0; v < NVT; ++v) {
           const T* r = W + (v * WY + jj + 2) * WX + ii;
           a[v] = r[0];
           b[v] = r[1];
           q[v] = r[2];
         }
-        vanleer_half5(a, b, q, h);
+        vanleer_all<T, NVT>(a, b, q, h);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sdx[(v * TY + jj) * (TX + 2) + ii] = h[v];
+        for (int v = 0; v < NVT; ++v) sdx[(v * TY + jj) * (TX + 2) + ii] = h[v];
       }
       for (int c = trot; c < TX * (TY + 2); c += NT) {  // x2 slopes, rows -1..TY
         const int jj = c / TX, ii = c - jj * TX;
-        T a[NV], b[NV], q[NV], h[NV];
+        T a[NVT], b[NVT], q[NVT], h[NVT];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 0; v < NVT; ++v) {
           const T* r = W + (v * WY + jj) * WX + ii + 2;
           a[v] = r[0];
           b[v] = r[WX];
           q[v] = r[2 * WX];
         }
-        vanleer_half5(a, b, q, h);
+        vanleer_all<T, NVT>(a, b, q, h);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sdy[(v * (TY + 2) + jj) * TX + ii] = h[v];
+        for (int v = 0; v < NVT; ++v) sdy[(v * (TY + 2) + jj) * TX + ii] = h[v];
       }
     }
     __syncthreads();
@@ -349,31 +359,31 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       const T* W = ring + ((k + 4) & 3) * SM::SLOT;
       for (int c = tid; c < (TX + 1) * TY; c += NT) {
         const int jj = c / (TX + 1), f = c - jj * (TX + 1);  // face between cells f-1, f
-        T wl[NV], wr[NV], fl[NV];
+        T wl[NVT], wr[NVT], fl[NVT];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 0; v < NVT; ++v) {
           const T* r = W + (v * WY + jj + 2) * WX + f + 1;
           const T* s = sdx + (v * TY + jj) * (TX + 2) + f;
           wl[v] = r[0] + s[0];
           wr[v] = r[1] - s[1];
         }
-        hlle<T, 0>(wl, wr, P, fl);
+        hlle<T, 0, NVT>(wl, wr, P, fl);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sfx[(v * TY + jj) * FP + f] = fl[v];
+        for (int v = 0; v < NVT; ++v) sfx[(v * TY + jj) * FP + f] = fl[v];
       }
       for (int c = trot; c < TX * (TY + 1); c += NT) {
         const int g = c / TX, ii = c - g * TX;   // face between rows g-1, g
-        T wl[NV], wr[NV], fl[NV];
+        T wl[NVT], wr[NVT], fl[NVT];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 0; v < NVT; ++v) {
           const T* r = W + (v * WY + g + 1) * WX + ii + 2;
           const T* s = sdy + (v * (TY + 2) + g) * TX + ii;
           wl[v] = r[0] + s[0];
           wr[v] = r[WX] - s[TX];
         }
-        hlle<T, 1>(wl, wr, P, fl);
+        hlle<T, 1, NVT>(wl, wr, P, fl);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sfy[(v * (TY + 1) + g) * FP + ii] = fl[v];
+        for (int v = 0; v < NVT; ++v) sfy[(v * (TY + 1) + g) * FP + ii] = fl[v];
       }
     }
     // (F) plane k+3 into the slot of plane k-1, which step k does not read
@@ -390,9 +400,9 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     // (G) flux divergence + SSPRK2 combination
     if (own) {
       const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
-      T unew[NV];
+      T unew[NVT];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
+      for (int v = 0; v < NVT; ++v) {
         const T dfx = sfx[(v * TY + ty) * FP + tx + 1] - sfx[(v * TY + ty) * FP + tx];
         const T dfy = sfy[(v * (TY + 1) + ty + 1) * FP + tx] - sfy[(v * (TY + 1) + ty) * FP + tx];
         const T L = -(dfx * idx1 + dfy * idx2 + (fzm[v] - fzlo[v]) * idx3);
@@ -408,20 +418,20 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       if (a.face_rec) {  // multi-level mesh: keep fluxes on fine-coarse faces
         const int* fr = a.face_rec + 6 * leaf;
         if (i == 0 && fr[0] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 0, j, k, v, sfx[(v * TY + ty) * FP + tx]);
+          for (int v = 0; v < NVT; ++v) capture(a, leaf, 0, j, k, v, sfx[(v * TY + ty) * FP + tx]);
         if (i == n1 - 1 && fr[1] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 1, j, k, v, sfx[(v * TY + ty) * FP + tx + 1]);
+          for (int v = 0; v < NVT; ++v) capture(a, leaf, 1, j, k, v, sfx[(v * TY + ty) * FP + tx + 1]);
         if (j == 0 && fr[2] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 2, k, i, v, sfy[(v * (TY + 1) + ty) * FP + tx]);
+          for (int v = 0; v < NVT; ++v) capture(a, leaf, 2, k, i, v, sfy[(v * (TY + 1) + ty) * FP + tx]);
         if (j == n2 - 1 && fr[3] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 3, k, i, v, sfy[(v * (TY + 1) + ty + 1) * FP + tx]);
+          for (int v = 0; v < NVT; ++v) capture(a, leaf, 3, k, i, v, sfy[(v * (TY + 1) + ty + 1) * FP + tx]);
         if (k == 0 && fr[4] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 4, i, j, v, fzlo[v]);
+          for (int v = 0; v < NVT; ++v) capture(a, leaf, 4, i, j, v, fzlo[v]);
         if (k == n3 - 1 && fr[5] >= 0)
-          for (int v = 0; v < NV; ++v) capture(a, leaf, 5, i, j, v, fzm[v]);
+          for (int v = 0; v < NVT; ++v) capture(a, leaf, 5, i, j, v, fzm[v]);
       }
       if (J.want_rate) {
-        cons_to_prim(unew, P, floors);
+        cons_to_prim<T, NVT>(unew, P, floors);
         const T r = wave_rate(unew, P, idx1, idx2, idx3);
         const double rd = (double)r;
         if (!(rd <= rate)) rate = rd;
@@ -432,7 +442,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   return rate;
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, int NVT = NV>
 __device__ __forceinline__ bool make_job(const StageArgs<T>& a, TileJob<T>& J) {
   const int tiles_per_block = a.ntile[0] * a.ntile[1] * a.ntile[2];
   const int leaf = blockIdx.x / tiles_per_block;
@@ -442,7 +452,7 @@ __device__ __forceinline__ bool make_job(const StageArgs<T>& a, TileJob<T>& J) {
   t -= tk * a.ntile[0] * a.ntile[1];
   const int tj = t / a.ntile[0];
   const int ti = t - tj * a.ntile[0];
-  const size_t bsize = (size_t)NV * a.S[0] * a.S[1] * a.S[2];
+  const size_t bsize = (size_t)NVT * a.S[0] * a.S[1] * a.S[2];
   J.Ub = a.Uin + (size_t)leaf * bsize;
   J.U0b = a.U0 + (size_t)leaf * bsize;
   J.Uoutb = a.Uout + (size_t)leaf * bsize;
@@ -465,26 +475,26 @@ __device__ __forceinline__ bool make_job(const StageArgs<T>& a, TileJob<T>& J) {
   return true;
 }
 
-template <class T, int TX, int TY>
-__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, StageSmem<T, TX, TY>::MINB)
+template <class T, int TX, int TY, int NVT = NV>
+__global__ void __launch_bounds__(StageSmem<T, TX, TY, NVT>::NT, StageSmem<T, TX, TY, NVT>::MINB)
 stage_kernel(const StageArgs<T> a) {
-  using SM = StageSmem<T, TX, TY>;
+  using SM = StageSmem<T, TX, TY, NVT>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);
   TileJob<T> J;
-  if (!make_job<T, TX, TY>(a, J)) return;
+  if (!make_job<T, TX, TY, NVT>(a, J)) return;
   unsigned floors = 0;
-  const double rate = stage_tile<T, TX, TY, false>(J, a.P, a, smem_raw, floors);
+  const double rate = stage_tile<T, TX, TY, false, NVT>(J, a.P, a, smem_raw, floors);
   if (a.want_rate) block_max_to(&a.sc->wmax_bits, rate, red);
   if (floors) atomicAdd(&a.sc->floor_hits, (unsigned long long)floors);
 }
 
 // The same stage with planes staged by TMA from the tensor map of the stencil
 // input pool.
-template <class T, int TX, int TY>
-__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, StageSmem<T, TX, TY>::MINB)
+template <class T, int TX, int TY, int NVT = NV>
+__global__ void __launch_bounds__(StageSmem<T, TX, TY, NVT>::NT, StageSmem<T, TX, TY, NVT>::MINB)
 stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__ CUtensorMap tmap) {
-  using SM = StageSmem<T, TX, TY>;
+  using SM = StageSmem<T, TX, TY, NVT>;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
@@ -492,7 +502,7 @@ stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + SM::bar_off);
   __shared__ int failed;
   TileJob<T> J;
-  if (!make_job<T, TX, TY>(a, J)) return;
+  if (!make_job<T, TX, TY, NVT>(a, J)) return;
   if (threadIdx.x == 0) {
     failed = 0;
     for (int s = 0; s < 4; ++s) mbar_init(bars + s, 1);
@@ -501,7 +511,7 @@ stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__
   __syncthreads();
   unsigned floors = 0;
   const double rate =
-      stage_tile<T, TX, TY, true>(J, a.P, a, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
+      stage_tile<T, TX, TY, true, NVT>(J, a.P, a, smem_raw, floors, &tmap, J.leaf * NVT, bars, &failed);
   if (failed) {
     if (threadIdx.x == 0) atomicExch(&a.sc->error, 1);
     return;

@@ -33,9 +33,9 @@ def test_library_exports_all_declared_symbols():
 
 def test_config_struct_layout_matches_header():
     # the ctypes mirror must have the C struct's size:
-    # 3*4*2 + 6*8 + 2*4 + 6*8 + 2*4 + 6*8 + 4 + 12 + 6*4
+    # 3*4*2 + 6*8 + 2*4 + 6*8 + 2*4 + 6*8 + 4 + 12 + 6*4 + 4 + 4
     import paper_2202_12309_gb300 as ph
-    expected = 24 + 48 + 8 + 48 + 8 + 48 + 4 + 12 + 24
+    expected = 24 + 48 + 8 + 48 + 8 + 48 + 4 + 12 + 24 + 8
     assert ctypes.sizeof(ph.Config) == expected
 
 
@@ -60,6 +60,8 @@ BAD_CONFIGS = [
     dict(nx=(16, 16, 16), nb=(1, 1, 1), tile=(16, 16, 17)),    # chunk deeper than the block
     dict(nx=(16, 16, 16), nb=(1, 1, 1), bc=("periodic", "outflow") + ("periodic",) * 4),  # half periodic
     dict(nx=(16, 16, 16), nb=(1, 1, 1), bc=(0, 0, 3, 3, 0, 0)),  # unknown boundary kind
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), nscalars=3),           # more passive scalars than supported
+    dict(nx=(16, 16, 16), nb=(1, 1, 1), nscalars=1, tile=(32, 8, 16)),  # tile without a scalar kernel
 ]
 
 
