@@ -263,6 +263,34 @@ def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0, launch=N
             "autotune_s": tune_s, "status": rc, "floors": floors, "nonfinite": nonfinite}
 
 
+def scalar_variant(ph, torch, steps, warmup, precision="fp64", nscalars=2, block=32):
+    """The 256^3 wave with passive scalars carried along (two smooth
+    concentrations): the cost of advecting extra conserved variables."""
+    nb = MESH // block
+    cfg = ph.make_config((block,) * 3, (nb,) * 3, precision=precision, nscalars=nscalars)
+    m = ph.Mesh(cfg)
+    geo = W.Geometry((block,) * 3, (nb,) * 3)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    U = wave_state(geo, m.tree(), np.float64)
+    conc = [W.smooth_random_density(geo, m.tree(), seed=30 + s)[:, 0:1] - 0.5 for s in range(nscalars)]
+    m.set_state(np.concatenate([U] + [U[:, 0:1] * c for c in conc], axis=1).astype(dtype))
+    stream = torch.cuda.current_stream()
+    m.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tile = list(m.tile())
+    m.close()
+    return {"workload": "256^3 wave with %d passive scalars, %d blocks of %d^3" % (nscalars, nb ** 3, block),
+            "precision": precision, "tile": tile, "ms_per_cycle": ms / steps,
+            "zone_cycles_per_s": MESH ** 3 * steps / (ms / 1e3)}
+
+
 def restart_variant(ph, torch, block=32):
     """Write and read a restart file of the 256^3 FP64 benchmark mesh (state,
     tree, scalars) in the system's temporary directory: GB/s of file bytes,
@@ -528,7 +556,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
     ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
     ap.add_argument("--batch-launch", help="TX,TY,KC,CTAS: skip the batch autotuner (profiling runs)")
-    ap.add_argument("--only", choices=["batch", "two_level", "multilevel", "adjoint", "restart"],
+    ap.add_argument("--only", choices=["batch", "two_level", "multilevel", "adjoint", "restart", "scalars"],
                     help="run one variant workload only and print its record (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -564,6 +592,8 @@ def main():
             rec = restart_variant(ph, torch)
         elif args.only == "multilevel":
             rec = multilevel_variant(ph, torch, args.steps, args.warmup)
+        elif args.only == "scalars":
+            rec = scalar_variant(ph, torch, args.steps, args.warmup, precision=args.precision)
         else:
             rec = adjoint_variant(ph, torch, args.precision)
         if rank == 0:
@@ -619,6 +649,10 @@ def main():
             v = adjoint_variant(ph, torch, prec)
             variants.append(v)
             log("adjoint %s: %.3f s per gradient" % (prec, v["seconds_per_gradient"]))
+        for prec in ("fp64", "fp32"):
+            v = scalar_variant(ph, torch, args.steps, args.warmup, precision=prec)
+            variants.append(v)
+            log("%s with 2 passive scalars: %.3e zone-cycles/s" % (prec, v["zone_cycles_per_s"]))
         v = restart_variant(ph, torch)
         variants.append(v)
         log("restart: save %.2f GB/s, load %.2f GB/s (%.0f MB)" % (v["save_gbs"], v["load_gbs"], v["bytes"] / 1e6))
