@@ -217,7 +217,10 @@ int ph_status(ph_mesh* mesh, int64_t* floor_hits, int32_t* nonfinite);
 /* Ghost exchange alone on the current state (Sec. 3.7). */
 int ph_fill_ghosts(ph_mesh* mesh);
 
-/* Number of kernel launches one uniform-mesh cycle enqueues. */
+/* Number of kernel launches one uniform-mesh cycle enqueues: 3 on periodic
+ * meshes (the stages write the ghost zones of their output themselves), 5
+ * with physical boundaries or with the environment variable PH_GHOSTS=launch
+ * at ph_create (a separate exchange launch after each stage). */
 int ph_launches_per_cycle(const ph_mesh* mesh, int32_t* n);
 
 /* Fused-stage tile in use (TX, TY, KC). */
@@ -227,7 +230,8 @@ int ph_get_tile(const ph_mesh* mesh, int32_t tile[3]);
  * without the graph, recording a CUDA event on the mesh's stream between
  * launches; ms_out[s] (s < nslots, nslots <= 5) receives the summed device
  * time of launch slot s of the cycle: 0 stage 1, 1 ghost exchange, 2 stage 2,
- * 3 ghost exchange, 4 dt bookkeeping.  Synchronises.  Uniform meshes only
+ * 3 ghost exchange, 4 dt bookkeeping (slots 1 and 3 are empty, about zero,
+ * where the stages write the ghost zones themselves).  Synchronises.  Uniform meshes only
  * (PH_ERR_INVALID otherwise). */
 int ph_profile_cycles(ph_mesh* mesh, int32_t ncycles, double* ms_out, int32_t nslots);
 

@@ -76,6 +76,9 @@ struct ph_mesh {
   size_t block_elems = 0;  // nvar * S1 * S2 * S3
   size_t esize = 8;
   bool multi_level = false;
+  // uniform periodic mesh: the stage kernels write the ghost zones of their
+  // output themselves (push exchange), no separate exchange launch per stage
+  bool push = false;
 
   std::vector<Leaf> leaf;
   std::vector<int> node;  // octree node table (ph_internal.h), host copy
@@ -564,6 +567,7 @@ ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
   a.P = phys<T>(m);
   a.sc = m->sc;
   a.nvar = m->nvar;
+  a.nbr = m->push ? m->d_nbr : nullptr;
   if (m->multi_level && m->nrec > 0) {
     a.face_rec = m->d_face_rec;
     a.fc_coarse = (T*)m->d_fcc;
@@ -582,17 +586,20 @@ int refresh_dt_t(ph_mesh* m) {
   return PH_OK;
 }
 
-// Enqueue one uniform-mesh cycle: 5 launches.
+// Enqueue one uniform-mesh cycle: stage, exchange, stage, exchange, dt
+// (the exchanges are part of the stages on periodic meshes: 3 launches).
 template <class T>
 int enqueue_uniform_cycle(ph_mesh* m, cudaStream_t s) {
   const ph::StageArgs<T> a1 = stage_args<T>(m, 1);
   PH_CUDA(ph::launch_stage<T>(a1, m->tile[0], m->tile[1], s, tmap_for(m, 1)));
-  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s,
-                                      m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
+  if (!m->push)
+    PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), s,
+                                        m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
   const ph::StageArgs<T> a2 = stage_args<T>(m, 2);
   PH_CUDA(ph::launch_stage<T>(a2, m->tile[0], m->tile[1], s, tmap_for(m, 2)));
-  PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s,
-                                      m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
+  if (!m->push)
+    PH_CUDA(ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), s,
+                                        m->d_leaf_id, m->nb, bc_mask(m), m->nvar));
   PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, s));
   return PH_OK;
 }
@@ -735,11 +742,11 @@ int profile_t(ph_mesh* m, int n, double* ms, int nslots) {
     cudaError_t e = cudaEventRecord(ev[0], m->stream);
     if (!e) e = ph::launch_stage<T>(a1, m->tile[0], m->tile[1], m->stream, tmap_for(m, 1));
     if (!e) e = cudaEventRecord(ev[1], m->stream);
-    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m), m->nvar);
+    if (!e && !m->push) e = ph::launch_ghost_uniform<T>((T*)m->U1, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m), m->nvar);
     if (!e) e = cudaEventRecord(ev[2], m->stream);
     if (!e) e = ph::launch_stage<T>(a2, m->tile[0], m->tile[1], m->stream, tmap_for(m, 2));
     if (!e) e = cudaEventRecord(ev[3], m->stream);
-    if (!e) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m), m->nvar);
+    if (!e && !m->push) e = ph::launch_ghost_uniform<T>((T*)m->U0, m->d_nbr, m->nx, m->nleaf(), m->stream, m->d_leaf_id, m->nb, bc_mask(m), m->nvar);
     if (!e) e = cudaEventRecord(ev[4], m->stream);
     if (!e) e = ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream);
     if (!e) e = cudaEventRecord(ev[5], m->stream);
@@ -969,6 +976,12 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
   m->nvar = ph::NV + cfg->nscalars;
   m->block_elems = (size_t)m->nvar * m->S[0] * m->S[1] * m->S[2];
   m->multi_level = cfg->max_level >= 1;
+  {
+    const char* g = std::getenv("PH_GHOSTS");  // "launch": keep the separate exchange launch
+    bool periodic = true;
+    for (int f = 0; f < 6; ++f) periodic = periodic && cfg->bc[f] == PH_BC_PERIODIC;
+    m->push = !m->multi_level && periodic && !(g && std::strcmp(g, "launch") == 0);
+  }
   int t[3] = {cfg->tile[0], cfg->tile[1], cfg->tile[2]};
   if (t[0] == 0 && t[1] == 0 && t[2] == 0) {
     // tiles march 16 planes (measured on 256^3 meshes: more, shorter tiles
@@ -1207,7 +1220,7 @@ int ph_fill_ghosts(ph_mesh* m) {
 
 int ph_launches_per_cycle(const ph_mesh* m, int32_t* n) {
   if (!m || !n) return fail(PH_ERR_INVALID, "ph_launches_per_cycle: null argument");
-  *n = m->multi_level ? 0 : 5;
+  *n = m->multi_level ? 0 : (m->push ? 3 : 5);
   return PH_OK;
 }
 

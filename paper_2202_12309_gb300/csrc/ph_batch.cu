@@ -14,6 +14,7 @@
 // barrier can never hang the GPU (the host reads PH_ERR_TIMEOUT).
 #include <algorithm>
 #include <array>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -57,6 +58,9 @@ struct BatchArgs {
   // TMA plane staging: per member, the tensor maps of the U0 and U1 pools
   // (2 m and 2 m + 1), in device memory
   const CUtensorMap* tmaps;
+  // the stages write the ghost zones of their output (push exchange), so the
+  // cycle has no ghost phases
+  int push;
 };
 
 // Bounded grid barrier.  Returns false (in every thread of the CTA) if this
@@ -140,6 +144,9 @@ __device__ bool batch_stage_phase(const BatchArgs<T>& a, int stage, const StageA
     J.stage = stage;
     J.want_rate = stage == 2;
     J.leaf = g;
+    J.nbr27 = a.push ? a.nbr + 27 * g : nullptr;
+    J.pool = (stage == 1 ? a.U1 : a.U0) + M.off;
+    J.bsize = bsize;
     const CUtensorMap* tm = TMA ? a.tmaps + 2 * m + (stage == 1 ? 0 : 1) : nullptr;
     const double rate = stage_tile<T, TX, TY, TMA>(J, member_phys<T>(M), nocap, smem, floors, tm,
                                                    (g - M.leaf0) * NV, bars, failed, parity);
@@ -217,14 +224,18 @@ batch_cycle_kernel(const BatchArgs<T> a) {
   PH_STAGE_OR_RETURN(1)
   if (TMA) fence_proxy_async_global();
   PH_BARRIER_OR_RETURN
-  batch_ghost_phase<T>(a, a.U1);
-  if (TMA) fence_proxy_async_global();
-  PH_BARRIER_OR_RETURN
+  if (!a.push) {
+    batch_ghost_phase<T>(a, a.U1);
+    if (TMA) fence_proxy_async_global();
+    PH_BARRIER_OR_RETURN
+  }
   PH_STAGE_OR_RETURN(2)
   PH_BARRIER_OR_RETURN
-  batch_ghost_phase<T>(a, a.U0);
+  if (!a.push) {
+    batch_ghost_phase<T>(a, a.U0);
+    PH_BARRIER_OR_RETURN
+  }
   if (floors) atomicAdd(&a.sc[0].floor_hits, (unsigned long long)floors);
-  PH_BARRIER_OR_RETURN
 #undef PH_BARRIER_OR_RETURN
 #undef PH_STAGE_OR_RETURN
   if (blockIdx.x == 0) {
@@ -317,6 +328,7 @@ struct ph_batch {
   GridBar* d_bar = nullptr;
   CUtensorMap* d_tmaps = nullptr;  // 2 per member (U0, U1 pools), for TMA staging
   bool tma = false;
+  bool push = true;  // stages fill the ghost zones (PH_GHOSTS=launch: ghost phases)
   void* staging = nullptr;
   size_t staging_bytes = 0;
   // launch choice
@@ -378,6 +390,7 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   a.bar = b->d_bar;
   a.spin_limit = b->spin_limit;
   a.tmaps = b->d_tmaps;
+  a.push = b->push ? 1 : 0;
   cudaLaunchConfig_t lc;
   std::memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(b->grid);
@@ -643,6 +656,10 @@ int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch*
   b->precision = prec;
   b->esize = prec == PH_FP32 ? 4 : 8;
   b->stream = (cudaStream_t)stream;
+  {
+    const char* g = std::getenv("PH_GHOSTS");
+    b->push = !(g && std::strcmp(g, "launch") == 0);
+  }
   b->cfg.assign(cfgs, cfgs + nsim);
   std::vector<int> leaf_member, nbr;
   long long off = 0;

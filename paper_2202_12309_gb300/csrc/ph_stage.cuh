@@ -48,6 +48,11 @@ struct StageArgs {
   T* fc_fine;          // [rec][v][2 n_t2][2 n_t1] fluxes of the fine blocks on the face
   const int* fine_off; // per leaf 6 x 2: offset of the fine block's quadrant (t1, t2)
   int nvar;            // conserved variables per cell: NV + passive scalars
+  // Uniform periodic meshes: the 27 neighbours of every leaf (as the ghost
+  // exchange uses them).  When set, the stage also writes each new interior
+  // value into the ghost zones of Uout that it fills (push exchange), and the
+  // separate exchange launch is not needed.
+  const int* nbr;
 };
 
 // Store one face flux of a leaf on a fine-coarse face (Sec. 3.7 flux
@@ -139,7 +144,52 @@ struct TileJob {
   int stage;
   int want_rate;
   int leaf;        // leaf index for flux capture (multi-level meshes)
+  const int* nbr27;  // push exchange: the leaf's 27 neighbours (null: none)
+  T* pool;           // push exchange: the output pool (block b at b * bsize)
+  size_t bsize;
 };
+
+// Push form of the same-level ghost exchange (uniform periodic meshes): the
+// new value u of interior cell (i, j, k) of a block is also the ghost value
+// of every neighbour whose ghost region holds the cell's periodic image.  A
+// cell within NG cells of the low (high) face along x_d lies in the high
+// (low) ghost layer of the neighbour on that side, at index i_d + n_d
+// (i_d - n_d); a cell near faces along several axes also fills the edge and
+// corner regions of the neighbours across them (up to 7 writes).  Writes the
+// same values as the pull exchange (ph_kernels.cu), into ghost cells only, so
+// concurrent tiles never write a cell twice or a cell another tile reads.
+template <class T, int W, int NVT>
+__device__ __forceinline__ void push_ghosts(const TileJob<T>& J, int i, int j, int k, const T* u,
+                                            size_t vstride) {
+  // W = 1: one cell; W = 2: cells (i, i+1) as one 2-wide store, i even
+  const int n1 = J.nx[0], n2 = J.nx[1], n3 = J.nx[2];
+  const int s1 = i < NG ? -1 : (i + W > n1 - NG ? 1 : 0);
+  const int s2 = j < NG ? -1 : (j >= n2 - NG ? 1 : 0);
+  const int s3 = k < NG ? -1 : (k >= n3 - NG ? 1 : 0);
+  if ((s1 | s2 | s3) == 0) return;
+  const int S1 = J.S[0], S2 = J.S[1];
+#pragma unroll
+  for (int m = 1; m < 8; ++m) {
+    const int o1 = (m & 1) ? s1 : 0, o2 = (m & 2) ? s2 : 0, o3 = (m & 4) ? s3 : 0;
+    if (((m & 1) && !s1) || ((m & 2) && !s2) || ((m & 4) && !s3)) continue;
+    const int nb = J.nbr27[(o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1)];
+    T* dst = J.pool + (size_t)nb * J.bsize +
+             ((size_t)(k - o3 * n3 + NG) * S2 + (j - o2 * n2 + NG)) * S1 + (i - o1 * n1 + NG);
+    if constexpr (W == 1) {
+#pragma unroll
+      for (int v = 0; v < NVT; ++v) dst[v * vstride] = u[v];
+    } else {
+      static_assert(W == 1 || sizeof(T) == 4, "paired pushes are FP32");
+#pragma unroll
+      for (int v = 0; v < NVT; ++v) {
+        float2 p;
+        p.x = u[2 * v];
+        p.y = u[2 * v + 1];
+        *reinterpret_cast<float2*>(dst + v * vstride) = p;
+      }
+    }
+  }
+}
 
 // TMA = true: planes arrive by one tensor copy each (tmap over the stencil
 // input pool, box (TX+4, TY+4, 1, 5) at (i0, j0, plane, vz0)), issued one plane
@@ -219,13 +269,17 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       tma_load_4d(ring + sl * SM::SLOT, tmap, bars + sl, J.i0, J.j0, p + NG, vz0);
     }
   };
+  // The conversion list is walked from warp 2 on, so that its partial second
+  // round falls on other warps than the x1 / x2 face lists' (warps 0 and 1)
+  // in the same barrier interval.
+  const int crot = (tid + NT - (64 % NT)) % NT;
   auto convert = [&](int p) -> bool {
     const int sl = (p + 4) & 3;
     const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
     parity ^= 1u << sl;
     T* dst = ring + sl * SM::SLOT;
     const int vi = min(WX, S1 - i0), vj = min(WY, S2 - j0);
-    for (int c = tid; c < WX * WY; c += NT) {
+    for (int c = crot; c < WX * WY; c += NT) {
       const int jj = c / WX, ii = c - jj * WX;
       if (ii >= vi || jj >= vj) continue;
       T w[NVT];
@@ -415,6 +469,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         }
         J.Uoutb[cell + v * vstride] = unew[v];
       }
+      if (J.nbr27) push_ghosts<T, 1, NVT>(J, i, j, k, unew, vstride);
       if (a.face_rec) {  // multi-level mesh: keep fluxes on fine-coarse faces
         const int* fr = a.face_rec + 6 * leaf;
         if (i == 0 && fr[0] >= 0)
@@ -472,6 +527,9 @@ __device__ __forceinline__ bool make_job(const StageArgs<T>& a, TileJob<T>& J) {
   J.stage = a.stage;
   J.want_rate = a.want_rate;
   J.leaf = leaf;
+  J.nbr27 = a.nbr ? a.nbr + 27 * leaf : nullptr;
+  J.pool = a.Uout;
+  J.bsize = bsize;
   return true;
 }
 

@@ -214,6 +214,11 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   float* sfy = sfx + SM::FXN;
   const int tid = threadIdx.x;
   const int tx = 2 * (tid & 15), ty = tid >> 4;  // own cells (tx, tx+1) of row ty
+  // Work lists that leave a partial second round start on different warps,
+  // so that no warp takes two extra rounds in one barrier interval: the x1
+  // slope and face lists at warp 0, the x2 ones at warp 1, the conversion
+  // of a staged plane at warp 2.
+  const int trot = (tid + NT - 32) % NT, crot = (tid + NT - 64) % NT;
   const int S1 = J.S[0], S2 = J.S[1];
   const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
   const size_t vstride = (size_t)J.S[0] * J.S[1] * J.S[2];
@@ -231,7 +236,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
     parity ^= 1u << sl;
     float* dst = ring + sl * SM::SLOT;
-    for (int c = tid; c < WY * (WX / 2); c += NT) {
+    for (int c = crot; c < WY * (WX / 2); c += NT) {
       const int r = c / (WX / 2), q = 2 * (c - r * (WX / 2));
       F2 w[NV];
 #pragma unroll
@@ -330,7 +335,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       for (int v = 0; v < NV; ++v) st2(sdx + (v * TY + jj) * WX + q, h[v]);
     }
     // (C3) x2 slopes of rows -1..TY, column pairs
-    for (int c = tid; c < (TY + 2) * (TX / 2); c += NT) {
+    for (int c = trot; c < (TY + 2) * (TX / 2); c += NT) {
       const int jj = c / (TX / 2), q = 2 * (c - jj * (TX / 2));
       F2 a[NV], b[NV], r[NV], h[NV];
 #pragma unroll
@@ -363,7 +368,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       for (int v = 0; v < NV; ++v) st2(sfx + (v * TY + jj) * FPX + f, fl[v]);
     }
     // (E2) x2 faces between rows g-1 and g, column pairs
-    for (int c = tid; c < (TY + 1) * (TX / 2); c += NT) {
+    for (int c = trot; c < (TY + 1) * (TX / 2); c += NT) {
       const int g = c / (TX / 2), q = 2 * (c - g * (TX / 2));
       F2 wl[NV], wr[NV], fl[NV];
 #pragma unroll
@@ -404,6 +409,12 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
           unew[v] = fma2(f2(0.5f), u0, f2(0.5f) * fma2(tdt, L, ucur));
         }
         st2(J.Uoutb + cell + v * vstride, unew[v]);
+      }
+      if (J.nbr27) {
+        float u[2 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) split(unew[v], u[2 * v], u[2 * v + 1]);
+        push_ghosts<float, 2, NV>(J, i, j, k, u, vstride);
       }
       if (J.want_rate) {
         float a[NV], b[NV];

@@ -61,7 +61,7 @@ def test_blast_32cube_8blocks_10cycles_fp64():
     errs, dterr, gm, om = run_pair((16, 16, 16), (2, 2, 2), blast, 10)
     assert errs.max() <= TOL64, describe(errs.max(axis=0))
     assert dterr.max() <= TOL64
-    assert gm.launches_per_cycle() == 5
+    assert gm.launches_per_cycle() == 3   # periodic: the stages fill the ghost zones
 
 
 @pytest.mark.parametrize("nx,nb,tile", [
