@@ -297,6 +297,13 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   const F2 idx1 = f2(J.idx1), idx2 = f2(J.idx2), idx3 = f2(J.idx3);
 
   for (int k = k0; k < k1; ++k) {
+    // stage 2 reads U0 at plane k+1 in the next step's (G): bring its rows
+    // into L2 now (the last 80 threads, one 16-row x 36-cell row each)
+    if (J.stage == 2 && k + 1 < k1 && tid >= NT - NV * TY) {
+      const int r = tid - (NT - NV * TY), v = r / TY, row = r - v * TY;
+      prefetch_l2(J.U0b + v * vstride + ((size_t)(k + 1 + NG) * S2 + (j0 + row + NG)) * S1 + i0,
+                  (TX + 4) * 4);
+    }
     F2 fzlo[NV];
     {  // (C1) own x3 slope and flux
       F2 wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], f[NV];

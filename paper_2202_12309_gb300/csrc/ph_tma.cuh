@@ -61,6 +61,12 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Prefetch `bytes` (a multiple of 16) of global memory at p (16-byte
+// aligned) into L2, without waiting for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // 4-D tiled bulk tensor load global -> shared, completing on `bar`.
 // Coordinates are element indices (c0 innermost); c0 * element size must be a
 // multiple of 16 bytes.
