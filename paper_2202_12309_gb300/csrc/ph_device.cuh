@@ -54,10 +54,11 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 // (Householder) step in FP64:
 //   reciprocal:  e = 1 - x y,   y' = y (1 + e + e^2)        error e^3
 //   rsqrt:       e = 1 - x y^2, y' = y (1 + e/2 + 3e^2/8)   error 5e^3/16
+//   sqrt:        s = x y, e = 1 - s y, s' = s (1 + e/2 + 3e^2/8)
 // (the truncated binomial series of (1-e)^-1 and (1-e)^-1/2).  With the
 // approximation good to ~2^-20 the truncation error is below 2^-56, so the
-// reciprocal and rsqrt are within one ulp of the exact values and
-// sqrt = x rsqrt(x) within two (tested against them).  Arguments outside [2^-1000, 2^1000] in magnitude (zero,
+// reciprocal and rsqrt are within one ulp of the exact values and the
+// square root within two (tested against them).  Arguments outside [2^-1000, 2^1000] in magnitude (zero,
 // subnormals, infinities, NaN; negative ones for the roots) take the
 // correctly rounded path instead.  FP32: the approximation plus one Newton
 // step for the reciprocal, the approximate rsqrt as is.
@@ -104,8 +105,9 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sq(double x) {
   if (!nr_range_pos(x)) return sqrt(x);
   const double y = rsqrt_approx(x);
-  const double e = fma(-(x * y), y, 1.0);
-  return x * fma(y * e, fma(0.375, e, 0.5), y);
+  const double s = x * y;
+  const double e = fma(-s, y, 1.0);
+  return fma(s * e, fma(0.375, e, 0.5), s);
 }
 __device__ __forceinline__ float sq(float x) { return x > 1e-30f ? x * rsqrtf(x) : sqrt_exact(x); }
 
@@ -175,11 +177,16 @@ __device__ __forceinline__ void cons_to_prim(T w[NVT], const Phys<T>& P, unsigne
   for (int v = NV; v < NVT; ++v) w[v] = w[v] * ir;
 }
 
-// Half van Leer slope of one passive-scalar concentration (one reciprocal).
+// Half van Leer slope of one passive-scalar concentration (one reciprocal)
+// from its left and right differences.
+template <class T>
+__device__ __forceinline__ T vanleer_half_rcp_d(T dl, T dr) {
+  const T prod = dl * dr;
+  return same_sign_nonzero(dl, dr) ? prod * rcp(dl + dr) : T(0);
+}
 template <class T>
 __device__ __forceinline__ T vanleer_half_rcp(T wm, T w0, T wp) {
-  const T dl = w0 - wm, dr = wp - w0, prod = dl * dr;
-  return same_sign_nonzero(dl, dr) ? prod * rcp(dl + dr) : T(0);
+  return vanleer_half_rcp_d(w0 - wm, wp - w0);
 }
 
 // Half of the van Leer (harmonic) limited slope of a cell from its two
@@ -199,26 +206,24 @@ __device__ __forceinline__ T vanleer_half(T wm, T w0, T wp) {
 // [2^-150, 2^150] the product could leave the normal range, and the slopes
 // are divided one by one instead.  The reciprocals carry a few ulp of
 // rounding more than separate divisions.
+// (vanleer_half5_d takes the differences dL = w0 - wm, dR = wp - w0.)
 template <class T>
-__device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], const T wp[NV],
-                                              T h[NV]) {
+__device__ __forceinline__ void vanleer_half5_d(const T dl[NV], const T dr[NV], T h[NV]) {
   if constexpr (sizeof(T) == 4) {
     // FP32: a reciprocal is one special-function op and two FMAs, cheaper
     // than the range checks of the batched form; one per variable.
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const T dl = w0[v] - wm[v], dr = wp[v] - w0[v], prod = dl * dr;
-      h[v] = prod > T(0) ? prod * rcp(dl + dr) : T(0);
+      const T prod = dl[v] * dr[v];
+      h[v] = prod > T(0) ? prod * rcp(dl[v] + dr[v]) : T(0);
     }
     return;
   }
-  T dl[NV], dr[NV], s[NV];
+  T s[NV];
   bool on[NV];
   bool ok = true, any = false;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    dl[v] = w0[v] - wm[v];
-    dr[v] = wp[v] - w0[v];
     on[v] = same_sign_nonzero(dl[v], dr[v]);
     any = any || on[v];
     s[v] = on[v] ? dl[v] + dr[v] : T(1);
@@ -247,17 +252,29 @@ __device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], co
     for (int v = 0; v < NV; ++v) h[v] = on[v] ? (dl[v] * dr[v]) / s[v] : T(0);
   }
 }
+template <class T>
+__device__ __forceinline__ void vanleer_half5(const T wm[NV], const T w0[NV], const T wp[NV],
+                                              T h[NV]) {
+  T dl[NV], dr[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    dl[v] = w0[v] - wm[v];
+    dr[v] = wp[v] - w0[v];
+  }
+  vanleer_half5_d(dl, dr, h);
+}
 
 // HLLE flux with Einfeldt's wave-speed bounds (Roe averages) through a face
 // whose normal is x_{DIR+1}; wl/wr are primitive states.
 //   F = (b+ F_L - b- F_R + b+ b- (U_R - U_L)) / (b+ - b-)
 // is evaluated as F = cL F_L + cR F_R + cD (U_R - U_L) with cL = b+/(b+ - b-),
-// cR = -b-/(b+ - b-), cD = b+ b-/(b+ - b-).  Every conserved component except
-// the energy is a density times a velocity component, so with
-// aL = cL rho_L v_nL - cD rho_L and aR = cR rho_R v_nR + cD rho_R the mass flux
-// is aL + aR and the momentum flux aL v_L + aR v_R plus the pressure term on
-// the normal component: two FP64 operations per momentum component instead
-// of eight.  Roe averages use sqrt(rho) v and h sqrt(rho) = (E + p)/sqrt(rho).
+// cR = -b-/(b+ - b-), cD = b+ b-/(b+ - b-).  With alL = cL v_nL - cD and
+// alR = cR v_nR + cD, every conserved density q carried with the flow has
+// the flux alL q_L + alR q_R: the mass flux is aL + aR (aL = alL rho_L,
+// aR = alR rho_R), the momentum flux aL v_L + aR v_R plus the pressure term
+// on the normal component, and since E = rho h - p the energy flux is
+// alL (rho h)_L + alR (rho h)_R - cD (p_R - p_L).  Roe averages use
+// sqrt(rho) v and h sqrt(rho) = (rho h)/sqrt(rho).
 template <class T, int DIR, int NVT = NV>
 __device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phys<T>& P, T f[NVT]) {
   // Every multiply-add is an explicit fma, so that the rounding is the same
@@ -268,12 +285,12 @@ __device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phy
   const T vnl = wl[IN], vnr = wr[IN];
   const T kl = fma(wl[1], wl[1], fma(wl[2], wl[2], wl[3] * wl[3]));
   const T kr = fma(wr[1], wr[1], fma(wr[2], wr[2], wr[3] * wr[3]));
-  const T el = fma(pl, P.igm1, (T(0.5) * rl) * kl);
-  const T er = fma(pr, P.igm1, (T(0.5) * rr) * kr);
+  // rho h = E + p = p / (gamma - 1) + rho |v|^2 / 2 + p
+  const T hl = fma(pl, P.igm1, fma(T(0.5) * rl, kl, pl));
+  const T hr = fma(pr, P.igm1, fma(T(0.5) * rr, kr, pr));
   const T ql = rsq(rl), qr = rsq(rr);            // 1/sqrt(rho)
   const T sl = rl * ql, sr = rr * qr;            // sqrt(rho)
   const T gl = sq(P.gamma * pl), gr = sq(P.gamma * pr);  // c = g / sqrt(rho)
-  const T hl = el + pl, hr = er + pr;            // rho h
   const T isum = rcp(add_rn(sl, sr));
   const T wsl = sl * isum, wsr = sr * isum;      // Roe weights
   const T u1 = fma(wsl, wl[1], wsr * wr[1]);
@@ -287,13 +304,13 @@ __device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phy
   const T bm = min0(fma(-gl, ql, vnl), sub_rn(un, croe));
   const T idb = rcp(bp - bm);
   const T cL = bp * idb, cR = -bm * idb, cD = (bp * bm) * idb;
-  const T aL = fma(cL, rl * vnl, -(cD * rl));
-  const T aR = fma(cR, rr * vnr, cD * rr);
+  const T alL = fma(cL, vnl, -cD), alR = fma(cR, vnr, cD);
+  const T aL = alL * rl, aR = alR * rr;
   f[0] = aL + aR;
 #pragma unroll
   for (int a = 1; a <= 3; ++a) f[a] = fma(aL, wl[a], aR * wr[a]);
   f[IN] += fma(cL, pl, cR * pr);
-  f[4] = fma(cL * vnl, hl, fma(cR * vnr, hr, cD * (er - el)));
+  f[4] = fma(alL, hl, fma(alR, hr, -cD * (pr - pl)));
   // passive scalars: mass flux split like a transverse velocity component
 #pragma unroll
   for (int v = NV; v < NVT; ++v) f[v] = fma(aL, wl[v], aR * wr[v]);

@@ -204,6 +204,7 @@ __device__ __forceinline__ void vanleer_all(const T wm[NVT], const T w0[NVT], co
   for (int v = NV; v < NVT; ++v) h[v] = vanleer_half_rcp(wm[v], w0[v], wp[v]);
 }
 
+
 template <class T, int TX, int TY, bool TMA, int NVT = NV>
 __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>& P,
                                              const StageArgs<T>& a, unsigned char* smem_raw,
@@ -317,6 +318,8 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     load_plane(k0 + 1);
     __syncthreads();
   }
+  // (the x3 differences are recomputed per plane rather than carried: a
+  // carried difference costs more registers than the subtraction it saves)
   T dz[NVT], fzm[NVT];
   if (has_cell) {  // x3 work is per owned column
     T wa[NVT], wb[NVT], wc[NVT], wd[NVT], wl[NVT], wr[NVT];

@@ -124,19 +124,28 @@ __device__ __forceinline__ void cons_to_prim2(F2 w[NV], const Phys<float>& P, un
   w[4] = f2(p0, p1);
 }
 
-// Half van Leer slopes of the five variables on both lanes.
-__device__ __forceinline__ void vanleer_half5_2(const F2 wm[NV], const F2 w0[NV], const F2 wp[NV],
-                                                F2 h[NV]) {
+// Half van Leer slopes of the five variables on both lanes, from the
+// differences dL = w0 - wm and dR = wp - w0 or from the three values.
+__device__ __forceinline__ void vanleer_half5_2d(const F2 dl[NV], const F2 dr[NV], F2 h[NV]) {
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const F2 dl = w0[v] - wm[v], dr = wp[v] - w0[v];
-    const F2 prod = dl * dr;
-    const F2 t = prod * rcp2(dl + dr);
+    const F2 prod = dl[v] * dr[v];
+    const F2 t = prod * rcp2(dl[v] + dr[v]);
     float p0, p1, t0, t1;
     split(prod, p0, p1);
     split(t, t0, t1);
     h[v] = f2(p0 > 0.f ? t0 : 0.f, p1 > 0.f ? t1 : 0.f);
   }
+}
+__device__ __forceinline__ void vanleer_half5_2(const F2 wm[NV], const F2 w0[NV], const F2 wp[NV],
+                                                F2 h[NV]) {
+  F2 dl[NV], dr[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    dl[v] = w0[v] - wm[v];
+    dr[v] = wp[v] - w0[v];
+  }
+  vanleer_half5_2d(dl, dr, h);
 }
 
 // HLLE flux (Einfeldt bounds, Roe averages) on both lanes; the arithmetic of
@@ -149,13 +158,12 @@ __device__ __forceinline__ void hlle2(const F2 wl[NV], const F2 wr[NV], const Ph
   const F2 half = f2(0.5f);
   const F2 kl = fma2(wl[1], wl[1], fma2(wl[2], wl[2], wl[3] * wl[3]));
   const F2 kr = fma2(wr[1], wr[1], fma2(wr[2], wr[2], wr[3] * wr[3]));
-  const F2 el = fma2(pl, f2(P.igm1), (half * rl) * kl);
-  const F2 er = fma2(pr, f2(P.igm1), (half * rr) * kr);
+  const F2 hl = fma2(pl, f2(P.igm1), fma2(half * rl, kl, pl));  // rho h
+  const F2 hr = fma2(pr, f2(P.igm1), fma2(half * rr, kr, pr));
   const F2 ql = rsq2(rl), qr = rsq2(rr);
   const F2 sl = rl * ql, sr = rr * qr;
   const F2 gam = f2(P.gamma);
   const F2 gl = sq2(gam * pl), gr = sq2(gam * pr);
-  const F2 hl = el + pl, hr = er + pr;
   const F2 isum = rcp2(sl + sr);
   const F2 wsl = sl * isum, wsr = sr * isum;
   const F2 u1 = fma2(wsl, wl[1], wsr * wr[1]);
@@ -171,13 +179,13 @@ __device__ __forceinline__ void hlle2(const F2 wl[NV], const F2 wr[NV], const Ph
   const F2 bm = min0_2(fma2(-gl, ql, vnl), un - croe);
   const F2 idb = rcp2(bp - bm);
   const F2 cL = bp * idb, cR = (-bm) * idb, cD = (bp * bm) * idb;
-  const F2 aL = fma2(cL, rl * vnl, -(cD * rl));
-  const F2 aR = fma2(cR, rr * vnr, cD * rr);
+  const F2 alL = fma2(cL, vnl, -cD), alR = fma2(cR, vnr, cD);
+  const F2 aL = alL * rl, aR = alR * rr;
   f[0] = aL + aR;
 #pragma unroll
   for (int a = 1; a <= 3; ++a) f[a] = fma2(aL, wl[a], aR * wr[a]);
   f[IN] = f[IN] + fma2(cL, pl, cR * pr);
-  f[4] = fma2(cL * vnl, hl, fma2(cR * vnr, hr, cD * (er - el)));
+  f[4] = fma2(alL, hl, fma2(alR, hr, -(cD * (pr - pl))));
 }
 
 // Shared-memory layout of the paired kernel (floats; every section starts
@@ -266,7 +274,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     fence_proxy_async_smem();
     if (check_failed(ok)) return 0.0;
   }
-  F2 dz[NV], fzm[NV];
+  F2 dz[NV], dzr[NV], fzm[NV];  // dzr: the difference to the plane above (next left difference)
   {
     F2 wa[NV], wb[NV], wc[NV], wd[NV], wl[NV], wr[NV], d0[NV];
     col(k0 - 2, wa);
@@ -279,6 +287,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     for (int v = 0; v < NV; ++v) {
       wl[v] = wb[v] + d0[v];
       wr[v] = wc[v] - dz[v];
+      dzr[v] = wd[v] - wc[v];
     }
     hlle2<2>(wl, wr, P, fzm);
   }
@@ -306,16 +315,19 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     }
     F2 fzlo[NV];
     {  // (C1) own x3 slope and flux
-      F2 wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], f[NV];
+      F2 wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], dr[NV], f[NV];
       col(k, wa);
       col(k + 1, wb);
       col(k + 2, wc);
-      vanleer_half5_2(wa, wb, wc, d1);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dr[v] = wc[v] - wb[v];
+      vanleer_half5_2d(dzr, dr, d1);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         wl[v] = wa[v] + dz[v];
         wr[v] = wb[v] - d1[v];
         dz[v] = d1[v];
+        dzr[v] = dr[v];
       }
       hlle2<2>(wl, wr, P, f);
 #pragma unroll
