@@ -353,7 +353,9 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 
   const int i = i0 + tx, j = j0 + ty;
   const bool own = has_cell && (i < n1) && (j < n2);
-  const T tdt = J.dt;
+  // dt / dx_d (stage 2: half of it, the SSPRK2 weight of dt L)
+  const T hs = J.stage == 1 ? T(1) : T(0.5);
+  const T c1 = hs * J.dt * idx1, c2 = hs * J.dt * idx2, c3 = hs * J.dt * idx3;
   double rate = 0.0;
 
   for (int k = k0; k < k1; ++k) {
@@ -460,16 +462,14 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       T unew[NVT];
 #pragma unroll
       for (int v = 0; v < NVT; ++v) {
+        // stage 1: U + dt L; stage 2: (U0 + U1)/2 + (dt/2) L, with
+        // dt L = -sum_d (F_d+ - F_d-) dt/dx_d
         const T dfx = sfx[(v * TY + ty) * FP + tx + 1] - sfx[(v * TY + ty) * FP + tx];
         const T dfy = sfy[(v * (TY + 1) + ty + 1) * FP + tx] - sfy[(v * (TY + 1) + ty) * FP + tx];
-        const T L = -(dfx * idx1 + dfy * idx2 + (fzm[v] - fzlo[v]) * idx3);
+        const T dfz = fzm[v] - fzlo[v];
         const T ucur = Ub[cell + v * vstride];
-        if (J.stage == 1) {
-          unew[v] = ucur + tdt * L;
-        } else {
-          const T u0 = J.U0b[cell + v * vstride];
-          unew[v] = T(0.5) * u0 + T(0.5) * (ucur + tdt * L);
-        }
+        const T base = J.stage == 1 ? ucur : T(0.5) * (J.U0b[cell + v * vstride] + ucur);
+        unew[v] = fma(-dfx, c1, fma(-dfy, c2, fma(-dfz, c3, base)));
         J.Uoutb[cell + v * vstride] = unew[v];
       }
       if (J.nbr27) push_ghosts<T, 1, NVT>(J, i, j, k, unew, vstride);
