@@ -210,24 +210,31 @@ def measured_traffic(precision, block):
 
 
 def roofline_for(v, pk, peak_kind):
+    """Roofline of the stage kernel: the binding roof (FP32: HBM; FP64: the
+    FP64 pipe), with the other roof's fraction beside it."""
     zones = MESH ** 3
     traffic = measured_traffic(v["precision"], v["block"])
+    word = 4 if v["precision"] == "fp32" else 8
+    words = WORDS_PER_ZONE_LAUNCH
+    if v.get("launches_per_cycle") == 3:  # the stage also writes the ghost shell
+        words += ghost_words_per_zone(v["block"])
+    secs = v["stage_ms_avg"] / 1e3
+    gbs = words * word * zones / secs / 1e9
+    hbm_peak = pk.get("hbm_gbs", 6800.0)
+    tflops = FLOPS_PER_ZONE_CYCLE * 0.5 * zones / secs / 1e12
     if v["precision"] == "fp32":
-        word = 4
-        words = WORDS_PER_ZONE_LAUNCH
-        if v.get("launches_per_cycle") == 3:  # the stage also writes the ghost shell
-            words += ghost_words_per_zone(v["block"])
-        achieved = words * word * zones / (v["stage_ms_avg"] / 1e3) / 1e9
-        peak = pk.get("hbm_gbs", 6800.0)
-        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
-                "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
+                "peak_source": peak_kind + " hbm_gbs (copy bandwidth)",
+                "algorithmic_bytes_per_zone_launch": words * word}
     # FP64: bound by the FP64 pipe
-    achieved = FLOPS_PER_ZONE_CYCLE * 0.5 * zones / (v["stage_ms_avg"] / 1e3) / 1e12
     peak = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
-            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)"}
+    return {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+            "frac": tflops / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
+            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
+            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "algorithmic_bytes_per_zone_launch": words * word,
+                    "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}}
 
 
 def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0, launch=None):
