@@ -61,7 +61,10 @@ cudaError_t configure_stage_kernels() {
   if ((e = configure_tile<float, 16, 16, NV + 2>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 8, 8, NV + 1>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 8, 8, NV + 2>()) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(stage_kernel_pair<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PairSmem::bytes)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(stage_kernel_pair<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PairSmem::bytes);
 }
 
@@ -90,7 +93,10 @@ static cudaError_t launch_pair(const StageArgs<float>& a, const CUtensorMap* tma
   if (!tmap || a.face_rec) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
   if (grid == 0) return cudaSuccess;
-  stage_kernel_pair<<<grid, PairSmem::NT, PairSmem::bytes, s>>>(a, *tmap);
+  if (a.stage == 1)
+    stage_kernel_pair<1><<<grid, PairSmem::NT, PairSmem::bytes, s>>>(a, *tmap);
+  else
+    stage_kernel_pair<2><<<grid, PairSmem::NT, PairSmem::bytes, s>>>(a, *tmap);
   return cudaGetLastError();
 }
 

@@ -209,6 +209,10 @@ struct PairSmem {
 
 // One 32 x 16 tile of one block for one stage (TMA staging); returns the
 // tile's max signal rate when J.want_rate.
+// STAGE (1 or 2) is a template argument: the two stages keep different
+// values live across the plane (stage 2 also U0), and each gets its own
+// register allocation.
+template <int STAGE>
 __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const Phys<float>& P,
                                                   unsigned char* smem_raw, unsigned& floors,
                                                   const CUtensorMap* tmap, int vz0, uint64_t* bars,
@@ -308,10 +312,20 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   for (int k = k0; k < k1; ++k) {
     // stage 2 reads U0 at plane k+1 in the next step's (G): bring its rows
     // into L2 now (the last 80 threads, one 16-row x 36-cell row each)
-    if (J.stage == 2 && k + 1 < k1 && tid >= NT - NV * TY) {
+    if (STAGE == 2 && k + 1 < k1 && tid >= NT - NV * TY) {
       const int r = tid - (NT - NV * TY), v = r / TY, row = r - v * TY;
       prefetch_l2(J.U0b + v * vstride + ((size_t)(k + 1 + NG) * S2 + (j0 + row + NG)) * S1 + i0,
                   (TX + 4) * 4);
+    }
+    // the own pair's current state (stage 2 also U0), loaded now so that the
+    // loads complete while the plane's slopes and fluxes are computed
+    const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
+    F2 ucur[NV], u0[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) ucur[v] = ld2(J.Ub + cell + v * vstride);
+    if (STAGE == 2) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) u0[v] = ld2(J.U0b + cell + v * vstride);
     }
     F2 fzlo[NV];
     {  // (C1) own x3 slope and flux
@@ -410,7 +424,6 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     }
     // (G) flux divergence + SSPRK2 on the own pair
     {
-      const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
       F2 unew[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -420,12 +433,10 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         const F2 dfx = fb - fa;
         const F2 dfy = ld2(sfy + (v * (TY + 1) + ty + 1) * TX + tx) - ld2(sfy + (v * (TY + 1) + ty) * TX + tx);
         const F2 L = -fma2(dfx, idx1, fma2(dfy, idx2, (fzm[v] - fzlo[v]) * idx3));
-        const F2 ucur = ld2(J.Ub + cell + v * vstride);
-        if (J.stage == 1) {
-          unew[v] = fma2(tdt, L, ucur);
+        if (STAGE == 1) {
+          unew[v] = fma2(tdt, L, ucur[v]);
         } else {
-          const F2 u0 = ld2(J.U0b + cell + v * vstride);
-          unew[v] = fma2(f2(0.5f), u0, f2(0.5f) * fma2(tdt, L, ucur));
+          unew[v] = fma2(f2(0.5f), u0[v], f2(0.5f) * fma2(tdt, L, ucur[v]));
         }
         st2(J.Uoutb + cell + v * vstride, unew[v]);
       }
@@ -451,6 +462,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   return rate;
 }
 
+template <int STAGE>
 __global__ void __launch_bounds__(PairSmem::NT, 2)
 stage_kernel_pair(const __grid_constant__ StageArgs<float> a, const __grid_constant__ CUtensorMap tmap) {
   using SM = PairSmem;
@@ -469,7 +481,7 @@ stage_kernel_pair(const __grid_constant__ StageArgs<float> a, const __grid_const
   }
   __syncthreads();
   unsigned floors = 0;
-  const double rate = stage_tile_pair(J, a.P, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
+  const double rate = stage_tile_pair<STAGE>(J, a.P, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
   if (failed) {
     if (threadIdx.x == 0) atomicExch(&a.sc->error, 1);
     return;
