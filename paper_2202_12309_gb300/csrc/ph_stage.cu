@@ -34,8 +34,14 @@ static cudaError_t configure_tile() {
   cudaError_t e = cudaFuncSetAttribute(stage_kernel<T, TX, TY, NVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)StageSmem<T, TX, TY, NVT>::bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(stage_kernel_tma<T, TX, TY, NVT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)StageSmem<T, TX, TY, NVT>::bytes);
+  for (int st = 0; st < 3; ++st) {
+    if (NVT != NV && st > 0) break;  // per-stage instances: hydro variables only
+    auto* k = st == 0 ? stage_kernel_tma<T, TX, TY, NVT, 0>
+                      : (st == 1 ? stage_kernel_tma<T, TX, TY, NVT, 1> : stage_kernel_tma<T, TX, TY, NVT, 2>);
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StageSmem<T, TX, TY, NVT>::bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Meshes with passive scalars: tiles 16 x 16 and 8 x 8, one or two scalars.
@@ -74,7 +80,12 @@ static cudaError_t launch_tile(const StageArgs<T>& a, const CUtensorMap* tmap, c
   const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
   if (grid == 0) return cudaSuccess;
   if (tmap)
-    stage_kernel_tma<T, TX, TY, NVT><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
+    if (NVT != NV)
+      stage_kernel_tma<T, TX, TY, NVT, 0><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
+    else if (a.stage == 1)
+      stage_kernel_tma<T, TX, TY, NVT, 1><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
+    else
+      stage_kernel_tma<T, TX, TY, NVT, 2><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
   else
     stage_kernel<T, TX, TY, NVT><<<grid, SM::NT, SM::bytes, s>>>(a);
   return cudaGetLastError();

@@ -205,7 +205,9 @@ __device__ __forceinline__ void vanleer_all(const T wm[NVT], const T w0[NVT], co
 }
 
 
-template <class T, int TX, int TY, bool TMA, int NVT = NV>
+// STAGE: 1 or 2 fixes the stage at compile time (its own register
+// allocation); 0 takes it from J.stage.
+template <class T, int TX, int TY, bool TMA, int NVT = NV, int STAGE = 0>
 __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>& P,
                                              const StageArgs<T>& a, unsigned char* smem_raw,
                                              unsigned& floors, const CUtensorMap* tmap = nullptr,
@@ -354,7 +356,8 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   const int i = i0 + tx, j = j0 + ty;
   const bool own = has_cell && (i < n1) && (j < n2);
   // dt / dx_d (stage 2: half of it, the SSPRK2 weight of dt L)
-  const T hs = J.stage == 1 ? T(1) : T(0.5);
+  const int stg = STAGE ? STAGE : J.stage;
+  const T hs = stg == 1 ? T(1) : T(0.5);
   const T c1 = hs * J.dt * idx1, c2 = hs * J.dt * idx2, c3 = hs * J.dt * idx3;
   double rate = 0.0;
 
@@ -468,7 +471,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         const T dfy = sfy[(v * (TY + 1) + ty + 1) * FP + tx] - sfy[(v * (TY + 1) + ty) * FP + tx];
         const T dfz = fzm[v] - fzlo[v];
         const T ucur = Ub[cell + v * vstride];
-        const T base = J.stage == 1 ? ucur : T(0.5) * (J.U0b[cell + v * vstride] + ucur);
+        const T base = stg == 1 ? ucur : T(0.5) * (J.U0b[cell + v * vstride] + ucur);
         unew[v] = fma(-dfx, c1, fma(-dfy, c2, fma(-dfz, c3, base)));
         J.Uoutb[cell + v * vstride] = unew[v];
       }
@@ -552,7 +555,7 @@ stage_kernel(const StageArgs<T> a) {
 
 // The same stage with planes staged by TMA from the tensor map of the stencil
 // input pool.
-template <class T, int TX, int TY, int NVT = NV>
+template <class T, int TX, int TY, int NVT = NV, int STAGE = 0>
 __global__ void __launch_bounds__(StageSmem<T, TX, TY, NVT>::NT, StageSmem<T, TX, TY, NVT>::MINB)
 stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__ CUtensorMap tmap) {
   using SM = StageSmem<T, TX, TY, NVT>;
@@ -572,7 +575,8 @@ stage_kernel_tma(const __grid_constant__ StageArgs<T> a, const __grid_constant__
   __syncthreads();
   unsigned floors = 0;
   const double rate =
-      stage_tile<T, TX, TY, true, NVT>(J, a.P, a, smem_raw, floors, &tmap, J.leaf * NVT, bars, &failed);
+      stage_tile<T, TX, TY, true, NVT, STAGE>(J, a.P, a, smem_raw, floors, &tmap, J.leaf * NVT, bars,
+                                              &failed);
   if (failed) {
     if (threadIdx.x == 0) atomicExch(&a.sc->error, 1);
     return;
