@@ -124,6 +124,33 @@ __device__ __forceinline__ void cons_to_prim2(F2 w[NV], const Phys<float>& P, un
   w[4] = f2(p0, p1);
 }
 
+// Signal rate max_d (|v_d| + c)/dx_d of a primitive state on both lanes
+// (the arithmetic of wave_rate() in ph_device.cuh); the NaN-propagating max
+// over directions per lane.
+__device__ __forceinline__ F2 abs2(F2 x) {
+  F2 o;
+  o.r = x.r & 0x7fffffff7fffffffull;
+  return o;
+}
+__device__ __forceinline__ void wave_rate2(const F2 w[NV], const Phys<float>& P, float idx1, float idx2,
+                                           float idx3, float& ra, float& rb) {
+  const F2 g = f2(P.gamma) * w[4];
+  const F2 c = g * rsq2(g * w[0]);
+  const F2 a = (abs2(w[1]) + c) * f2(idx1);
+  const F2 b = (abs2(w[2]) + c) * f2(idx2);
+  const F2 d = (abs2(w[3]) + c) * f2(idx3);
+  float a0, a1, b0, b1, d0, d1;
+  split(a, a0, a1);
+  split(b, b0, b1);
+  split(d, d0, d1);
+  ra = a0;
+  if (!(b0 <= ra)) ra = b0;
+  if (!(d0 <= ra)) ra = d0;
+  rb = a1;
+  if (!(b1 <= rb)) rb = b1;
+  if (!(d1 <= rb)) rb = d1;
+}
+
 // Half van Leer slopes of the five variables on both lanes, from the
 // differences dL = w0 - wm and dR = wp - w0 or from the three values.
 __device__ __forceinline__ void vanleer_half5_2d(const F2 dl[NV], const F2 dr[NV], F2 h[NV]) {
@@ -447,15 +474,14 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         push_ghosts<float, 2, NV>(J, i, j, k, u, vstride);
       }
       if (J.want_rate) {
-        float a[NV], b[NV];
+        F2 w[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) split(unew[v], a[v], b[v]);
-        cons_to_prim(a, P, floors);
-        cons_to_prim(b, P, floors);
-        const double ra = (double)wave_rate(a, P, J.idx1, J.idx2, J.idx3);
-        const double rb = (double)wave_rate(b, P, J.idx1, J.idx2, J.idx3);
-        if (!(ra <= rate)) rate = ra;
-        if (!(rb <= rate)) rate = rb;
+        for (int v = 0; v < NV; ++v) w[v] = unew[v];
+        cons_to_prim2(w, P, floors);
+        float ra, rb;
+        wave_rate2(w, P, J.idx1, J.idx2, J.idx3, ra, rb);
+        if (!((double)ra <= rate)) rate = (double)ra;
+        if (!((double)rb <= rate)) rate = (double)rb;
       }
     }
   }
