@@ -279,12 +279,16 @@ template <class T, int DIR, int NVT = NV>
 __device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phys<T>& P, T f[NVT]) {
   // Every multiply-add is an explicit fma, so that the rounding is the same
   // in every kernel this is inlined into (the single-mesh and the batched
-  // kernels agree bit for bit).
+  // kernels agree bit for bit).  Sums over the velocity components run in
+  // the cyclic order (normal, next, next but one), so that the flux of a
+  // state whose components were rotated to put the normal first is the same
+  // to the last bit.
   constexpr int IN = 1 + DIR;
+  constexpr int IB = 1 + (DIR + 1) % 3, IC = 1 + (DIR + 2) % 3;
   const T rl = wl[0], pl = wl[4], rr = wr[0], pr = wr[4];
   const T vnl = wl[IN], vnr = wr[IN];
-  const T kl = fma(wl[1], wl[1], fma(wl[2], wl[2], wl[3] * wl[3]));
-  const T kr = fma(wr[1], wr[1], fma(wr[2], wr[2], wr[3] * wr[3]));
+  const T kl = fma(wl[IN], wl[IN], fma(wl[IB], wl[IB], wl[IC] * wl[IC]));
+  const T kr = fma(wr[IN], wr[IN], fma(wr[IB], wr[IB], wr[IC] * wr[IC]));
   // rho h = E + p = p / (gamma - 1) + rho |v|^2 / 2 + p
   const T hl = fma(pl, P.igm1, fma(T(0.5) * rl, kl, pl));
   const T hr = fma(pr, P.igm1, fma(T(0.5) * rr, kr, pr));
@@ -293,13 +297,12 @@ __device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phy
   const T gl = sq(P.gamma * pl), gr = sq(P.gamma * pr);  // c = g / sqrt(rho)
   const T isum = rcp(add_rn(sl, sr));
   const T wsl = sl * isum, wsr = sr * isum;      // Roe weights
-  const T u1 = fma(wsl, wl[1], wsr * wr[1]);
-  const T u2 = fma(wsl, wl[2], wsr * wr[2]);
-  const T u3 = fma(wsl, wl[3], wsr * wr[3]);
+  const T un = fma(wsl, wl[IN], wsr * wr[IN]);  // Roe velocity, normal first
+  const T ub = fma(wsl, wl[IB], wsr * wr[IB]);
+  const T uc = fma(wsl, wl[IC], wsr * wr[IC]);
   const T hroe = fma(hl, ql, hr * qr) * isum;
-  const T a2 = P.gm1 * fma(T(-0.5), fma(u1, u1, fma(u2, u2, u3 * u3)), hroe);
+  const T a2 = P.gm1 * fma(T(-0.5), fma(un, un, fma(ub, ub, uc * uc)), hroe);
   const T croe = positive(a2) ? sq(a2) : T(0);
-  const T un = (IN == 1) ? u1 : ((IN == 2) ? u2 : u3);
   const T bp = max0(fma(gr, qr, vnr), add_rn(un, croe));
   const T bm = min0(fma(-gl, ql, vnl), sub_rn(un, croe));
   const T idb = rcp(bp - bm);

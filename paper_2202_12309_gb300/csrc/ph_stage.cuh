@@ -416,10 +416,18 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       }
     }
     __syncthreads();
-    // (E) x1 and x2 face fluxes of the plane
+    // (E) x1 and x2 face fluxes of the plane.  FP64: when both lists leave a
+    // partial second round that together fit one warp, the last warp takes
+    // both remainders at once, x2 faces with their velocity components
+    // rotated so that the normal one comes first (the flux is then the same
+    // to the last bit), instead of two half-empty warps each issuing the whole
+    // flux on the FP64 pipe.
     {
+      constexpr int NF1 = (TX + 1) * TY, NF2 = TX * (TY + 1);
+      constexpr int E1 = NF1 - NT, E2 = NF2 - NT;
+      constexpr bool MERGE = sizeof(T) == 8 && E1 > 0 && E2 > 0 && E1 + E2 <= 32;
       const T* W = ring + ((k + 4) & 3) * SM::SLOT;
-      for (int c = tid; c < (TX + 1) * TY; c += NT) {
+      for (int c = tid; c < (MERGE ? NT : NF1); c += NT) {
         const int jj = c / (TX + 1), f = c - jj * (TX + 1);  // face between cells f-1, f
         T wl[NVT], wr[NVT], fl[NVT];
 #pragma unroll
@@ -433,7 +441,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 #pragma unroll
         for (int v = 0; v < NVT; ++v) sfx[(v * TY + jj) * FP + f] = fl[v];
       }
-      for (int c = trot; c < TX * (TY + 1); c += NT) {
+      for (int c = MERGE ? tid : trot; c < (MERGE ? NT : NF2); c += NT) {
         const int g = c / TX, ii = c - g * TX;   // face between rows g-1, g
         T wl[NVT], wr[NVT], fl[NVT];
 #pragma unroll
@@ -446,6 +454,40 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         hlle<T, 1, NVT>(wl, wr, P, fl);
 #pragma unroll
         for (int v = 0; v < NVT; ++v) sfy[(v * (TY + 1) + g) * FP + ii] = fl[v];
+      }
+      if (MERGE && tid >= NT - 32 && tid < NT - 32 + E1 + E2) {
+        const int l = tid - (NT - 32);
+        const bool y = l >= E1;              // lanes E1.. take x2 faces
+        const int c = NT + (y ? l - E1 : l);
+        const int jj = c / (TX + 1), f = c - jj * (TX + 1);
+        const int g = c / TX, ii = c - g * TX;
+        const T* r = y ? W + (g + 1) * WX + ii + 2 : W + (jj + 2) * WX + f + 1;
+        const T* sp = y ? sdy + g * TX + ii : sdx + jj * (TX + 2) + f;
+        const int rs = y ? WX : 1, ss = y ? TX : 1;
+        const int svs = y ? (TY + 2) * TX : TY * (TX + 2);
+        T* o = y ? sfy + g * FP + ii : sfx + jj * FP + f;
+        const int ovs = y ? (TY + 1) * FP : TY * FP;
+        T wl[NVT], wr[NVT], fl[NVT];
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) {
+          wl[v] = r[v * WY * WX] + sp[v * svs];
+          wr[v] = r[v * WY * WX + rs] - sp[v * svs + ss];
+        }
+        // x2 faces: (v1, v2, v3) -> (v2, v3, v1)
+        const T l1 = wl[1], r1 = wr[1];
+        wl[1] = y ? wl[2] : wl[1];
+        wl[2] = y ? wl[3] : wl[2];
+        wl[3] = y ? l1 : wl[3];
+        wr[1] = y ? wr[2] : wr[1];
+        wr[2] = y ? wr[3] : wr[2];
+        wr[3] = y ? r1 : wr[3];
+        hlle<T, 0, NVT>(wl, wr, P, fl);
+        const T f3 = fl[3];
+        fl[3] = y ? fl[2] : fl[3];
+        fl[2] = y ? fl[1] : fl[2];
+        fl[1] = y ? f3 : fl[1];
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) o[v * ovs] = fl[v];
       }
     }
     // (F) plane k+3 into the slot of plane k-1, which step k does not read
