@@ -275,15 +275,33 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   // The conversion list is walked from warp 2 on, so that its partial second
   // round falls on other warps than the x1 / x2 face lists' (warps 0 and 1)
   // in the same barrier interval.
+  // The four 2 x 2 corners of a staged plane are read by no stencil and are
+  // not converted: the list is rows 0-1 (columns 2..TX+1), rows 2..TY+1
+  // (every column), rows TY+2..TY+3 (columns 2..TX+1).
   const int crot = (tid + NT - (64 % NT)) % NT;
+  constexpr int NCV = WX * WY - 16;
   auto convert = [&](int p) -> bool {
     const int sl = (p + 4) & 3;
     const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
     parity ^= 1u << sl;
     T* dst = ring + sl * SM::SLOT;
     const int vi = min(WX, S1 - i0), vj = min(WY, S2 - j0);
-    for (int c = crot; c < WX * WY; c += NT) {
-      const int jj = c / WX, ii = c - jj * WX;
+    for (int c = crot; c < NCV; c += NT) {
+      int jj, ii;
+      if (c < 2 * TX) {
+        jj = c / TX;
+        ii = 2 + c - jj * TX;
+      } else if (c < 2 * TX + TY * WX) {
+        const int q = c - 2 * TX;
+        jj = q / WX;
+        ii = q - jj * WX;
+        jj += 2;
+      } else {
+        const int q = c - 2 * TX - TY * WX;
+        jj = q / TX;
+        ii = 2 + q - jj * TX;
+        jj += TY + 2;
+      }
       if (ii >= vi || jj >= vj) continue;
       T w[NVT];
 #pragma unroll
