@@ -275,11 +275,13 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   // The conversion list is walked from warp 2 on, so that its partial second
   // round falls on other warps than the x1 / x2 face lists' (warps 0 and 1)
   // in the same barrier interval.
-  // The four 2 x 2 corners of a staged plane are read by no stencil and are
-  // not converted: the list is rows 0-1 (columns 2..TX+1), rows 2..TY+1
-  // (every column), rows TY+2..TY+3 (columns 2..TX+1).
+  // The four 2 x 2 corners of a staged plane are read by no stencil.  FP64
+  // does not convert them: the list is rows 0-1 (columns 2..TX+1), rows
+  // 2..TY+1 (every column), rows TY+2..TY+3 (columns 2..TX+1).  FP32, bound
+  // by instruction issue, converts the whole plane (the mapping costs more
+  // than the 16 conversions it saves).
   const int crot = (tid + NT - (64 % NT)) % NT;
-  constexpr int NCV = WX * WY - 16;
+  constexpr int NCV = sizeof(T) == 4 ? WX * WY : WX * WY - 16;
   auto convert = [&](int p) -> bool {
     const int sl = (p + 4) & 3;
     const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
@@ -288,7 +290,10 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
     const int vi = min(WX, S1 - i0), vj = min(WY, S2 - j0);
     for (int c = crot; c < NCV; c += NT) {
       int jj, ii;
-      if (c < 2 * TX) {
+      if (sizeof(T) == 4) {
+        jj = c / WX;
+        ii = c - jj * WX;
+      } else if (c < 2 * TX) {
         jj = c / TX;
         ii = 2 + c - jj * TX;
       } else if (c < 2 * TX + TY * WX) {
