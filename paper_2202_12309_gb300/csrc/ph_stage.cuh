@@ -407,9 +407,14 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         fzm[v] = f[v];
       }
     }
+    // FP64: the warps that take the lists' partial rounds move by two every
+    // other plane, to the other two SM sub-partitions (warp w runs on
+    // sub-partition w % 4), so that the two CTAs on an SM less often load
+    // the same sub-partition's FP64 unit with their extra rounds.
+    const int sh = (sizeof(T) == 8 && NT >= 128) ? 64 * (k & 1) : 0;
     {
       const T* W = ring + ((k + 4) & 3) * SM::SLOT;
-      for (int c = tid; c < (TX + 2) * TY; c += NT) {   // x1 slopes, cells -1..TX
+      for (int c = (tid + NT - sh) % NT; c < (TX + 2) * TY; c += NT) {   // x1 slopes, cells -1..TX
         const int jj = c / (TX + 2), ii = c - jj * (TX + 2);
         T a[NVT], b[NVT], q[NVT], h[NVT];
 #pragma unroll
@@ -423,7 +428,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 #pragma unroll
         for (int v = 0; v < NVT; ++v) sdx[(v * TY + jj) * (TX + 2) + ii] = h[v];
       }
-      for (int c = trot; c < TX * (TY + 2); c += NT) {  // x2 slopes, rows -1..TY
+      for (int c = (trot + NT - sh) % NT; c < TX * (TY + 2); c += NT) {  // x2 slopes, rows -1..TY
         const int jj = c / TX, ii = c - jj * TX;
         T a[NVT], b[NVT], q[NVT], h[NVT];
 #pragma unroll
@@ -478,8 +483,8 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
 #pragma unroll
         for (int v = 0; v < NVT; ++v) sfy[(v * (TY + 1) + g) * FP + ii] = fl[v];
       }
-      if (MERGE && tid >= NT - 32 && tid < NT - 32 + E1 + E2) {
-        const int l = tid - (NT - 32);
+      if (MERGE && tid >= NT - 32 - sh && tid < NT - 32 - sh + E1 + E2) {
+        const int l = tid - (NT - 32 - sh);
         const bool y = l >= E1;              // lanes E1.. take x2 faces
         const int c = NT + (y ? l - E1 : l);
         const int jj = c / (TX + 1), f = c - jj * (TX + 1);
