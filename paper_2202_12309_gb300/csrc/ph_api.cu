@@ -370,6 +370,19 @@ int build_tables(ph_mesh* m) {
             const int64_t c = (l.lx[2] + oz + m->nb[2]) % m->nb[2];
             nbr[27 * b + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = m->node[root_slot(m, a, bb, c)];
           }
+    } else {
+      // the same-level leaf across each neighbour region, where there is one
+      // (the composite ghost exchange copies those regions directly)
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int o[3] = {ox, oy, oz};
+            int64_t nbk[3];
+            int lev = -1;
+            if (!neighbour(m, l.level, l.lx, o, nbk)) continue;  // physical boundary
+            const int v = cover(m, l.level, nbk, &lev);
+            if (v >= 0 && lev == l.level) nbr[27 * b + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] = v;
+          }
     }
   }
   int rc;
@@ -535,7 +548,7 @@ ph::LevelGeom level_geom(const ph_mesh* m) {
 template <class T>
 int fill_ghosts_t(ph_mesh* m, T* U) {
   if (m->multi_level) {
-    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->nleaf(), m->stream,
+    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->d_nbr, m->nleaf(), m->stream,
                                           m->nvar));
   } else {
     PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream,

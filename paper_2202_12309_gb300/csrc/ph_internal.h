@@ -92,9 +92,11 @@ cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nlea
 
 // K1 (multi-level mesh): every ghost cell of every leaf takes the composite
 // field of the mesh (copy / restriction / prolongation), one launch.
+// nbr[27 * leaf + region]: the same-level leaf covering that neighbour
+// region (its ghost cells are copied directly), or -1.
 template <class T>
-cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
-                                   cudaStream_t s, int nvar = NV);
+cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
+                                   int nleaf, cudaStream_t s, int nvar = NV);
 
 // K7: interior of every new leaf from the old mesh's composite field.
 template <class T>

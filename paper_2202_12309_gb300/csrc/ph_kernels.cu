@@ -311,8 +311,14 @@ __device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int
   }
 }
 
+// nbr[27 b + region]: the leaf of the same level that covers the block
+// location next to leaf b in that neighbour region, or -1 (finer or coarser
+// leaves, or a physical boundary).  Ghost cells of such a region are plain
+// copies of that leaf's interior, the value the composite evaluation gives
+// there, read directly instead of through the tree.
 template <class T, int NVT>
-__global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id) {
+__global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id,
+                                       const int* __restrict__ nbr) {
   const Shell sh(tv.nx);
   const int b = blockIdx.x;
   const int lev = leaf_id[4 * b];
@@ -321,12 +327,24 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
   const long long o3 = (long long)leaf_id[4 * b + 3] * tv.nx[2] - NG;
   const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
   T* dst = U + (size_t)b * NVT * vs;
+  const int* nb = nbr + 27 * b;
   const int total = sh.count();
   for (int c = threadIdx.x; c < total; c += blockDim.x) {
     int i, j, k;
     sh.cell(c, i, j, k);
+    const int ox = i < NG ? -1 : (i >= NG + tv.nx[0] ? 1 : 0);
+    const int oy = j < NG ? -1 : (j >= NG + tv.nx[1] ? 1 : 0);
+    const int oz = k < NG ? -1 : (k >= NG + tv.nx[2] ? 1 : 0);
+    const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
     T val[NVT];
-    composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
+    if (src >= 0) {
+      const T* s = U + (size_t)src * NVT * vs +
+                   ((size_t)(k - oz * tv.nx[2]) * tv.S[1] + (j - oy * tv.nx[1])) * tv.S[0] + (i - ox * tv.nx[0]);
+#pragma unroll
+      for (int v = 0; v < NVT; ++v) val[v] = s[v * vs];
+    } else {
+      composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
+    }
     const size_t d = ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
 #pragma unroll
     for (int v = 0; v < NVT; ++v) dst[v * vs + d] = val[v];
@@ -334,15 +352,15 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
 }
 
 template <class T>
-cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, int nleaf,
-                                   cudaStream_t s, int nvar) {
+cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
+                                   int nleaf, cudaStream_t s, int nvar) {
   if (nleaf <= 0) return cudaSuccess;
   if (nvar == NV + 1)
-    ghost_composite_kernel<T, NV + 1><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+    ghost_composite_kernel<T, NV + 1><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
   else if (nvar == NV + 2)
-    ghost_composite_kernel<T, NV + 2><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+    ghost_composite_kernel<T, NV + 2><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
   else
-    ghost_composite_kernel<T, NV><<<nleaf, 256, 0, s>>>(U, tv, leaf_id);
+    ghost_composite_kernel<T, NV><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
   return cudaGetLastError();
 }
 
@@ -664,8 +682,8 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
 #define PH_INST(T)                                                                              \
   template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t, \
                                               const int*, const int*, int, int);              \
-  template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, int,          \
-                                                 cudaStream_t, int);                            \
+  template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, const int*,  \
+                                                 int, cudaStream_t, int);                       \
   template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
                                         cudaStream_t, int);                                     \
   template cudaError_t launch_rate<T>(const T*, const int8_t*, const LevelGeom&, const int*,   \
