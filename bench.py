@@ -191,18 +191,32 @@ def time_variant(ph, torch, block, precision, steps, warmup, kvec=WAVE_K, bc=Non
     return res
 
 
+STAGE_SOURCES = ("ph_stage.cuh", "ph_stage_pair.cuh", "ph_device.cuh", "ph_tma.cuh")
+
+
+def kernel_source_hash():
+    """SHA-256 of the stage kernels' source with comments and whitespace
+    removed: a change of the code, not of its comments, retires a traffic
+    capture."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in STAGE_SOURCES:
+        text = open(os.path.join(ROOT, "paper_2202_12309_gb300", "csrc", f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def measured_traffic(precision, block):
     """DRAM bytes of one stage launch at this mesh size, from the committed ncu
     capture (profiles/stage_kernel_traffic.json: mean of the stage-1 and stage-2
     launches, per zone, scaled by zones), or None when the kernel source changed
     since the capture or the block size differs from the captured one."""
-    import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")))
-        h = hashlib.sha256()
-        for f in ("ph_stage.cuh", "ph_stage_pair.cuh", "ph_device.cuh", "ph_tma.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_2202_12309_gb300", "csrc", f), "rb").read())
-        if h.hexdigest() != rec["kernel_source_sha256"] or rec[precision]["block"] != block:
+        if kernel_source_hash() != rec["kernel_source_sha256"] or rec[precision]["block"] != block:
             return None
         return rec[precision]["bytes_per_zone"] * MESH ** 3
     except Exception:

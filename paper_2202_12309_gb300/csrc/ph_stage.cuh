@@ -15,7 +15,10 @@
 //       plane k;
 //   (G) forms the flux divergence and the SSPRK2 combination and writes the
 //       new conserved state (stage 2 also folds the cell's signal speed into
-//       the block-wide max that becomes the next dt, Sec. 3.10).
+//       the block-wide max that becomes the next dt, Sec. 3.10); on periodic
+//       uniform meshes it also writes each new value within two cells of a
+//       block face into the ghost zones of the neighbours it fills, which is
+//       the whole ghost exchange of the stage (Sec. 3.7).
 // Every face flux is computed once per tile (twice only on tile borders),
 // every slope once per tile (plus one halo column/row), every primitive
 // once per tile plus halo.
