@@ -223,32 +223,67 @@ def measured_traffic(precision, block):
         return None
 
 
-def roofline_for(v, pk, peak_kind):
+def fma_peak(ph, torch, kind="fp64", reps=5):
+    """Measured peak of one arithmetic pipe: the best of `reps` CUDA-event
+    timings of ph_debug_fma_rate (8 independent multiply-add chains per
+    thread, 8 CTAs of 256 threads per SM) on the current stream, in TFLOP/s."""
+    ctas = SMS * 8
+    iters = 4096 if kind == "fp64" else 4096 * 64
+    out = torch.empty(ctas * 256, dtype=torch.float64 if kind == "fp64" else torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flops = ph.debug_fma_rate(kind, ctas, iters, out)  # warm-up
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ph.debug_fma_rate(kind, ctas, iters, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return flops / best / 1e12
+
+
+def roofline_for(v, pk, peak_kind, fp64_measured=None):
     """Roofline of the stage kernel: the binding roof (FP32: HBM; FP64: the
-    FP64 pipe), with the other roof's fraction beside it."""
+    FP64 pipe), with the other roof's fraction beside it.  Algorithmic bytes
+    are the streaming model's 12.5 words per zone and launch (100 B per
+    zone-cycle FP32, 200 B FP64); the ghost shell a periodic stage also
+    writes is overhead, reported separately."""
     zones = MESH ** 3
     traffic = measured_traffic(v["precision"], v["block"])
     word = 4 if v["precision"] == "fp32" else 8
     words = WORDS_PER_ZONE_LAUNCH
-    if v.get("launches_per_cycle") == 3:  # the stage also writes the ghost shell
-        words += ghost_words_per_zone(v["block"])
+    ghost = ghost_words_per_zone(v["block"]) * word if v.get("launches_per_cycle") == 3 else 0.0
     secs = v["stage_ms_avg"] / 1e3
     gbs = words * word * zones / secs / 1e9
     hbm_peak = pk.get("hbm_gbs", 6800.0)
     tflops = FLOPS_PER_ZONE_CYCLE * 0.5 * zones / secs / 1e12
+    hbm = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "algorithmic_bytes_per_zone_launch": words * word,
+           "ghost_bytes_per_zone_launch": ghost,
+           "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}
     if v["precision"] == "fp32":
-        return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": gbs / hbm_peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
-                "peak_source": peak_kind + " hbm_gbs (copy bandwidth)",
-                "algorithmic_bytes_per_zone_launch": words * word}
+        out = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+               "frac": gbs / hbm_peak, "traffic": traffic,
+               "traffic_launch": "mean of stage 1 and 2 (ncu)",
+               "peak_source": peak_kind + " hbm_gbs (copy bandwidth)",
+               "algorithmic_bytes_per_zone_launch": words * word,
+               "ghost_bytes_per_zone_launch": ghost}
+        return out
     # FP64: bound by the FP64 pipe
     peak = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    return {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-            "frac": tflops / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
-            "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
-            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                    "algorithmic_bytes_per_zone_launch": words * word,
-                    "peak_source": peak_kind + " hbm_gbs (copy bandwidth)"}}
+    out = {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+           "frac": tflops / peak, "traffic": traffic, "traffic_launch": "mean of stage 1 and 2 (ncu)",
+           "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
+           "flops_per_zone_launch": FLOPS_PER_ZONE_CYCLE * 0.5,
+           "hbm": hbm}
+    if fp64_measured:
+        out["peak_measured"] = fp64_measured
+        out["frac_of_measured"] = tflops / fp64_measured
+        out["peak_measured_source"] = ("measured in this run: ph_debug_fma_rate, FP64 DFMA chains, "
+                                       "%d CTAs x 256 threads, best of 5" % (SMS * 8))
+    return out
 
 
 def batch_variant(ph, torch, precision, steps, warmup, nsim=64, seed=0, launch=None):
@@ -556,25 +591,40 @@ def dist_setup(args):
     return world, rank, local
 
 
+def headline_config(block, precision, nb, world=1):
+    """The `config` of the benchmark line: the workload both arms report on."""
+    cfg = {"workload": "uniform 256^3-zone periodic linear sound wave (A=1e-4, k=2pi(1,1,1)), "
+                       "%d blocks of %d^3, 2 ghost zones, %s, 1 cycle per step"
+                       % (nb, block, precision.upper()),
+           "zones": MESH ** 3, "block": block, "nblocks": nb,
+           "l2": "state %.0f MB > 129 MB L2: no flush needed"
+                 % (MESH ** 3 * 5 * (8 if precision == "fp64" else 4) / 1e6 * (1 + 4.0 / block) ** 3),
+           "parallelism": "replicas" if world > 1 else "single GPU"}
+    return cfg
+
+
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (written from the paper; there is
+    no reference program) on the host cores, on the headline's config and
+    metric.  Each step is one oracle cycle of a bounded sample of that
+    workload (a 64^3-zone piece, 8 blocks of 32^3, in one process per core);
+    value = zone-cycles/s over all cores."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
-    # each step: one oracle cycle on a 64^3-zone sample (8 blocks of 32^3) in
-    # every host core's process
     block, n_sample = 32, 64
     value, n, secs, cores = oracle_rate_all_cores(block, n_sample, args.steps, args.warmup)
+    nb = (MESH // args.block) ** 3
+    sample = ("%d processes, each a 64^3-zone sample of the workload (8 blocks of 32^3), "
+              "%d cycles after %d warm-up, %.1f s" % (cores, args.steps, args.warmup, secs))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "zone-cycles/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "FP64 CPU oracle, linear sound wave, 64^3-zone sample of the "
-                               "256^3 workload (8 blocks of 32^3) per host core, 1 cycle per step",
-                   "zones_per_step": cores * n_sample ** 3},
+        "config": headline_config(args.block, args.precision, nb, world=1),
         "cpu_baseline": {"value": value, "unit": "zone-cycles/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d processes, each 64^3 zones (8 blocks of 32^3), %d cycles"
-                                   % (cores, args.steps)},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "zone-cycles/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -621,6 +671,7 @@ def main():
         torch.distributed.barrier()
     ph.use_torch_allocator()
     pk, peak_kind = peaks()
+    fp64_peak = fma_peak(ph, torch, "fp64") if not args.only else None
     if args.only:
         if args.only == "batch":
             launch = [int(x) for x in args.batch_launch.split(",")] if args.batch_launch else None
@@ -658,19 +709,19 @@ def main():
                 if prec == args.precision and block == args.block:
                     continue
                 v = time_variant(ph, torch, block, prec, args.steps, args.warmup)
-                v["roofline"] = roofline_for(v, pk, peak_kind)
+                v["roofline"] = roofline_for(v, pk, peak_kind, fp64_peak)
                 variants.append(v)
                 log("variant %s block %d: %.3e zone-cycles/s" % (prec, block, v["zone_cycles_per_s"]))
         for prec in ("fp64", "fp32"):
             v = time_variant(ph, torch, args.block, prec, args.steps, args.warmup, kvec=(1, 0, 0))
-            v["roofline"] = roofline_for(v, pk, peak_kind)
+            v["roofline"] = roofline_for(v, pk, peak_kind, fp64_peak)
             v["workload"] = "wave along x1 only (v2, v3 and all x2/x3 differences exactly 0)"
             variants.append(v)
             log("variant %s x1-wave: %.3e zone-cycles/s" % (prec, v["zone_cycles_per_s"]))
         for prec in ("fp64", "fp32"):
             v = time_variant(ph, torch, args.block, prec, args.steps, args.warmup,
                              bc=("reflect",) * 6)
-            v["roofline"] = roofline_for(v, pk, peak_kind)
+            v["roofline"] = roofline_for(v, pk, peak_kind, fp64_peak)
             v["workload"] = "closed box: reflecting walls on all six faces"
             variants.append(v)
             log("variant %s reflecting box: %.3e zone-cycles/s" % (prec, v["zone_cycles_per_s"]))
@@ -720,27 +771,20 @@ def main():
                          "%d cycles, %.1f s; %.3g zone-cycles/s per core"
                          % (cores, n, min(args.block, n), ncyc, secs, rate / cores)}
 
-    roof = roofline_for(head, pk, peak_kind)
+    roof = roofline_for(head, pk, peak_kind, fp64_peak)
     nb = (MESH // args.block) ** 3
     line = {
         "metric": METRIC, "value": value, "unit": "zone-cycles/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_cycle"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-        "config": {"workload": "uniform 256^3-zone periodic linear sound wave (A=1e-4, k=2pi(1,1,1)), "
-                               "%d blocks of %d^3, 2 ghost zones, %s, 1 cycle per step"
-                               % (nb, args.block, args.precision.upper()),
-                   "zones": MESH ** 3, "block": args.block, "nblocks": nb, "tile": head["tile"],
-                   "l2": "state %.0f MB > 129 MB L2: no flush needed"
-                         % (MESH ** 3 * 5 * (8 if args.precision == "fp64" else 4) / 1e6 *
-                            (1 + 4.0 / args.block) ** 3),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": headline_config(args.block, args.precision, nb, world=world),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": head["launches_per_cycle"] * args.steps,
         "clocks": ck,
-        "kernel_ms": {"stage_avg": head["stage_ms_avg"], "ghost_avg": head["ghost_ms_avg"],
+        "kernel_ms": {"tile": head["tile"], "stage_avg": head["stage_ms_avg"], "ghost_avg": head["ghost_ms_avg"],
                       "per_launch": head["launch_ms"]},
         "variants": variants,
     }

@@ -351,6 +351,23 @@ int ph_load(const char* path, void* stream, ph_mesh** out);
 #define PH_MATH_RSQRT_APPROX 4
 int ph_debug_math(int32_t fn, int32_t precision, const void* x, void* y, int64_t n, void* stream);
 
+/* Multiply-add throughput probe (the paper has no counterpart): measures the
+ * peak rate of the arithmetic pipe that bounds the FP64 stage kernel, so that
+ * its roofline fraction is taken against a measured rather than a nominal
+ * peak.  Launches `ctas` CTAs of 256 threads on `stream` (a cudaStream_t,
+ * asynchronous); every thread runs `iters` rounds of 8 independent
+ * multiply-add chains with no memory traffic and writes one value to
+ * out[cta * 256 + thread] (a device array of ctas * 256 doubles for kind
+ * PH_FMA_FP64, floats otherwise).  The caller times the launch on the stream;
+ * it performs ctas * 256 * iters * 16 flops (twice that for
+ * PH_FMA_FP32X2, whose instructions work on two lanes).
+ * Errors: PH_ERR_INVALID (kind, ctas outside 1 .. 2^20, iters outside
+ * 1 .. 2^32, null out), PH_ERR_CUDA (launch). */
+#define PH_FMA_FP64 0
+#define PH_FMA_FP32 1
+#define PH_FMA_FP32X2 2
+int ph_debug_fma_rate(int32_t kind, int32_t ctas, int64_t iters, void* out, void* stream);
+
 /* Conserved totals of a caller-owned state without any device allocation.
  * The paper has no counterpart: this exists for callers that may not call
  * cudaMalloc at all (a plugin whose host application owns every byte of
@@ -362,14 +379,18 @@ int ph_debug_math(int32_t fn, int32_t precision, const void* x, void* y, int64_t
  *           (U[block][var][k][j][i] over nx cells), double for PH_FP64 or
  *           float for PH_FP32
  *   nx[3]   host array, interior cells per block
+ *   nvar    variables per cell: 5 + the mesh's passive scalars (5, 6 or 7);
+ *           it sets the block stride and the number of totals
  *   nblocks 0 .. PH_TOTALS_NOALLOC_MAX_BLOCKS; more is rejected with
  *           PH_ERR_INVALID
- *   level   device pointer to nblocks levels (0 or 1), or NULL for all 0
- *   vol0/1  cell volume at level 0 / level 1
- *   out     device pointer to 5 doubles, written asynchronously on `stream`
+ *   level   device pointer to nblocks levels, or NULL for all level 0
+ *   vol     host array of nlevels cell volumes, vol[l] for level l
+ *           (1 <= nlevels <= 5, nlevels = 1 when level is NULL); a block whose
+ *           level is outside [0, nlevels) makes every total NaN
+ *   out     device pointer to nvar doubles, written asynchronously on `stream`
  *           (a cudaStream_t; NULL = legacy default stream)
  * Its scratch (per-block partial sums) is a fixed device array of
- * PH_TOTALS_NOALLOC_MAX_BLOCKS x 5 doubles (640 KiB) that every GPU which
+ * PH_TOTALS_NOALLOC_MAX_BLOCKS x 7 doubles (896 KiB) that every GPU which
  * loads the library holds until the process exits.  The first call on a
  * device, made with that device current, looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
@@ -377,8 +398,9 @@ int ph_debug_math(int32_t fn, int32_t precision, const void* x, void* y, int64_t
  * streams, other host threads) race and must be serialised by the caller.
  * Each call overwrites the entries it reads, so nothing needs clearing. */
 #define PH_TOTALS_NOALLOC_MAX_BLOCKS 16384
-int ph_totals_noalloc(const void* U, int32_t precision, const int32_t nx[3], int32_t nblocks,
-                      const int8_t* level, double vol0, double vol1, double* out, void* stream);
+int ph_totals_noalloc(const void* U, int32_t precision, const int32_t nx[3], int32_t nvar,
+                      int32_t nblocks, const int8_t* level, const double* vol, int32_t nlevels,
+                      double* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -32,7 +32,7 @@ EXPORTS = [
     "ph_batch_create", "ph_batch_destroy", "ph_batch_num_blocks", "ph_batch_set_state",
     "ph_batch_get_state", "ph_batch_step", "ph_batch_get_dt", "ph_batch_get_time",
     "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
-    "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint", "ph_debug_math",
+    "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint", "ph_debug_math", "ph_debug_fma_rate",
     "ph_save", "ph_load", "ph_set_state_async", "ph_get_state_async",
 ]
 
@@ -147,8 +147,7 @@ def lib():
             "ph_launches_per_cycle": [P, ctypes.POINTER(i32)],
             "ph_get_tile": [P, ctypes.POINTER(i32)],
             "ph_profile_cycles": [P, i32, dp, i32],
-            "ph_totals_noalloc": [P, i32, ctypes.POINTER(i32), i32, P, ctypes.c_double,
-                                  ctypes.c_double, P, P],
+            "ph_totals_noalloc": [P, i32, ctypes.POINTER(i32), i32, i32, P, dp, i32, P, P],
             "ph_batch_create": [ctypes.POINTER(Config), i32, P, ctypes.POINTER(P)],
             "ph_batch_destroy": [P],
             "ph_batch_num_blocks": [P, i32, ctypes.POINTER(i32)],
@@ -165,6 +164,7 @@ def lib():
             "ph_step_dt": [P, i32, dp],
             "ph_adjoint": [P, P, i32, i32, dp, P, P, dp, i32],
             "ph_debug_math": [i32, i32, P, P, i64, P],
+            "ph_debug_fma_rate": [i32, i32, i64, P, P],
             "ph_save": [P, ctypes.c_char_p, i32],
             "ph_set_state_async": [P, P, i64, i32],
             "ph_get_state_async": [P, P, i64, i32],
@@ -205,24 +205,29 @@ def use_torch_allocator():
     _alloc_refs = (a, f)
 
 
-def totals_noalloc(U, nx, nblocks, out, precision="fp64", level=None, vol=(1.0, 0.125),
+def totals_noalloc(U, nx, nblocks, out, precision="fp64", nvar=5, level=None, vol=(1.0,),
                    stream: Optional[int] = None):
     """ph_totals_noalloc on caller-owned device tensors (U packed interior
-    state, out 5 doubles); the library allocates nothing for this call."""
+    state of nvar variables per cell, out nvar doubles, level int8 per block
+    or None); vol[l] is the cell volume of level l.  The library allocates
+    nothing for this call."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     n3 = (ctypes.c_int32 * 3)(*nx)
     prec = PH_FP32 if precision in ("fp32", PH_FP32) else PH_FP64
-    if 0 <= int(nblocks) <= 16384:  # larger counts are rejected by the library itself
-        _check_buffer(U, int(nblocks) * 5 * nx[0] * nx[1] * nx[2], 4 if prec == PH_FP32 else 8, "U")
-        _check_buffer(out, 5, 8, "out")
-    if not (U.is_cuda and out.is_cuda):
-        raise ValueError("U and out must be device tensors")
+    vols = np.ascontiguousarray(vol, dtype=np.float64)
+    if 0 <= int(nblocks) <= 16384 and 5 <= int(nvar) <= 7:  # else rejected by the library itself
+        _check_buffer(U, int(nblocks) * int(nvar) * nx[0] * nx[1] * nx[2], 4 if prec == PH_FP32 else 8, "U")
+        _check_buffer(out, int(nvar), 8, "out")
+        if level is not None:
+            _check_buffer(level, int(nblocks), 1, "level")
+    if not (U.is_cuda and out.is_cuda) or (level is not None and not level.is_cuda):
+        raise ValueError("U, out and level must be device tensors")
     lvl = ctypes.c_void_p(level.data_ptr()) if level is not None else None
-    check(lib().ph_totals_noalloc(ctypes.c_void_p(U.data_ptr()), prec, n3, int(nblocks), lvl,
-                                  float(vol[0]), float(vol[1]), ctypes.c_void_p(out.data_ptr()),
-                                  ctypes.c_void_p(stream)))
+    check(lib().ph_totals_noalloc(ctypes.c_void_p(U.data_ptr()), prec, n3, int(nvar), int(nblocks), lvl,
+                                  vols.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(vols),
+                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream)))
 
 
 def _ptr(x):
@@ -580,6 +585,25 @@ def debug_math(fn: str, x):
                               ctypes.c_void_p(y.data_ptr()), x.numel(),
                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return y
+
+
+FMA_KIND = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+
+
+def debug_fma_rate(kind: str, ctas: int, iters: int, out, stream: Optional[int] = None):
+    """Queue the multiply-add throughput probe (ph_debug_fma_rate) on the
+    stream: `out` is a CUDA tensor of ctas * 256 elements (float64 for
+    "fp64", float32 otherwise).  Returns the flops the launch performs."""
+    import torch
+    k = FMA_KIND[kind]
+    want = torch.float64 if k == 0 else torch.float32
+    if not (out.is_cuda and out.is_contiguous() and out.dtype == want and out.numel() == ctas * 256):
+        raise ValueError("out must be a contiguous %s CUDA tensor of %d elements" % (want, ctas * 256))
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib().ph_debug_fma_rate(k, int(ctas), int(iters), ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(stream)))
+    return ctas * 256 * iters * 16 * (2 if k == 2 else 1)
 
 
 def _hydro_run_function():

@@ -9,11 +9,12 @@
 // variant takes the state from the caller and keeps its scratch in a fixed
 // file-scope __device__ array instead.
 //
-// The array holds PH_TOTALS_NOALLOC_MAX_BLOCKS x 5 doubles (640 KiB) on
-// every GPU that loads the library, for the life of the process.  In host
-// code the array's name is only a host-side stand-in, so its device address
-// is looked up once per device with cudaGetSymbolAddress (on the first call
-// made while that device is current) and passed to the kernels.
+// The array holds PH_TOTALS_NOALLOC_MAX_BLOCKS x 7 doubles (896 KiB: up to
+// 5 conserved variables plus 2 passive scalars per block) on every GPU that
+// loads the library, for the life of the process.  In host code the array's
+// name is only a host-side stand-in, so its device address is looked up once
+// per device with cudaGetSymbolAddress (on the first call made while that
+// device is current) and passed to the kernels.
 #include <mutex>
 
 #include "../../include/ph_hydro.h"
@@ -22,48 +23,62 @@
 namespace {
 
 constexpr int kMaxBlocks = PH_TOTALS_NOALLOC_MAX_BLOCKS;
+constexpr int kMaxVar = ph::NV + ph::MAXS;
+constexpr int kMaxLevels = ph::MAXLEV + 1;
 constexpr int kMaxDevices = 64;
 
-// Per-block partial sums: every call overwrites entries [0, nblocks) and
-// reads only those, so nothing has to start at zero.  Shared by all calls.
-static __device__ __align__(256) double g_partial[kMaxBlocks * ph::NV];
+// Per-block partial sums, kMaxVar entries per block: every call overwrites
+// entries [0, nblocks * nvar) and reads only those, so nothing has to start
+// at zero.  Shared by all calls.
+static __device__ __align__(256) double g_partial[kMaxBlocks * kMaxVar];
 
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
 
+struct Vols {
+  double v[kMaxLevels];
+  int nlevels;
+};
+
+// One CTA per block: FP64 sums of every variable over the block's interior
+// cells, times the cell volume of the block's level.  A level outside
+// [0, nlevels) has no volume: its sums become NaN, and so do the totals.
 template <class T>
-__global__ void noalloc_block_sums(const T* __restrict__ U, int3 nx,
-                                   const int8_t* __restrict__ level, double2 vol,
-                                   double* partial) {
-  __shared__ double red[ph::NV][256];
+__global__ void noalloc_block_sums(const T* __restrict__ U, int3 nx, int nvar,
+                                   const int8_t* __restrict__ level, Vols vol, double* partial) {
+  __shared__ double red[kMaxVar][256];
   const int b = blockIdx.x;
   const int cells = nx.x * nx.y * nx.z;
-  const T* Ub = U + (size_t)b * ph::NV * cells;
-  double acc[ph::NV] = {0, 0, 0, 0, 0};
+  const T* Ub = U + (size_t)b * nvar * cells;
+  double acc[kMaxVar];
+#pragma unroll
+  for (int v = 0; v < kMaxVar; ++v) acc[v] = 0.0;
   for (int c = threadIdx.x; c < cells; c += blockDim.x)
 #pragma unroll
-    for (int v = 0; v < ph::NV; ++v) acc[v] += (double)Ub[(size_t)v * cells + c];
+    for (int v = 0; v < kMaxVar; ++v)
+      if (v < nvar) acc[v] += (double)Ub[(size_t)v * cells + c];
 #pragma unroll
-  for (int v = 0; v < ph::NV; ++v) red[v][threadIdx.x] = acc[v];
+  for (int v = 0; v < kMaxVar; ++v) red[v][threadIdx.x] = acc[v];
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w)
 #pragma unroll
-      for (int v = 0; v < ph::NV; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + w];
+      for (int v = 0; v < kMaxVar; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < ph::NV) {
-    const double dv = (level && level[b]) ? vol.y : vol.x;
-    partial[(size_t)b * ph::NV + threadIdx.x] = red[threadIdx.x][0] * dv;
+  if ((int)threadIdx.x < nvar) {
+    const int l = level ? (int)level[b] : 0;
+    const double dv = (l >= 0 && l < vol.nlevels) ? vol.v[l] : __longlong_as_double(0x7ff8000000000000ll);
+    partial[(size_t)b * nvar + threadIdx.x] = red[threadIdx.x][0] * dv;
   }
 }
 
-__global__ void noalloc_final(const double* __restrict__ partial, int nblocks, double* out) {
+__global__ void noalloc_final(const double* __restrict__ partial, int nblocks, int nvar, double* out) {
   const int v = threadIdx.x;
-  if (v >= ph::NV) return;
+  if (v >= nvar) return;
   double s = 0.0, comp = 0.0;  // Neumaier compensated sum over blocks in order
   for (int b = 0; b < nblocks; ++b) {
-    const double x = partial[(size_t)b * ph::NV + v];
+    const double x = partial[(size_t)b * nvar + v];
     const double t = s + x;
     if (fabs(s) >= fabs(x))
       comp += (s - t) + x;
@@ -81,17 +96,26 @@ int reject(int code, const char* msg) {
 
 }  // namespace
 
-extern "C" int ph_totals_noalloc(const void* U, int32_t precision, const int32_t nx[3],
-                                 int32_t nblocks, const int8_t* level, double vol0, double vol1,
-                                 double* out, void* stream) {
-  if (!U || !nx || !out) return reject(PH_ERR_INVALID, "ph_totals_noalloc: null argument");
+extern "C" int ph_totals_noalloc(const void* U, int32_t precision, const int32_t nx[3], int32_t nvar,
+                                 int32_t nblocks, const int8_t* level, const double* vol,
+                                 int32_t nlevels, double* out, void* stream) {
+  if (!U || !nx || !out || !vol) return reject(PH_ERR_INVALID, "ph_totals_noalloc: null argument");
   if (precision != PH_FP64 && precision != PH_FP32)
     return reject(PH_ERR_INVALID, "ph_totals_noalloc: precision must be PH_FP64 or PH_FP32");
   if (nx[0] < 1 || nx[1] < 1 || nx[2] < 1)
     return reject(PH_ERR_INVALID, "ph_totals_noalloc: nx must be positive");
+  if (nvar < ph::NV || nvar > kMaxVar)
+    return reject(PH_ERR_INVALID, "ph_totals_noalloc: nvar must be 5, 6 or 7 (5 + passive scalars)");
+  if (nlevels < 1 || nlevels > kMaxLevels)
+    return reject(PH_ERR_INVALID, "ph_totals_noalloc: nlevels must be 1 .. 5");
+  if (!level && nlevels != 1)
+    return reject(PH_ERR_INVALID, "ph_totals_noalloc: level is NULL but nlevels > 1");
   if (nblocks < 0 || nblocks > kMaxBlocks)
     return reject(PH_ERR_INVALID,
                   "ph_totals_noalloc: nblocks exceeds PH_TOTALS_NOALLOC_MAX_BLOCKS (16384)");
+  Vols vols{};
+  vols.nlevels = nlevels;
+  for (int l = 0; l < nlevels; ++l) vols.v[l] = vol[l];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return reject(PH_ERR_CUDA, cudaGetErrorString(e));
@@ -110,14 +134,13 @@ extern "C" int ph_totals_noalloc(const void* U, int32_t precision, const int32_t
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int3 n3 = make_int3(nx[0], nx[1], nx[2]);
-  const double2 vol = make_double2(vol0, vol1);
   if (nblocks > 0) {
     if (precision == PH_FP64)
-      noalloc_block_sums<double><<<nblocks, 256, 0, s>>>((const double*)U, n3, level, vol, scratch);
+      noalloc_block_sums<double><<<nblocks, 256, 0, s>>>((const double*)U, n3, nvar, level, vols, scratch);
     else
-      noalloc_block_sums<float><<<nblocks, 256, 0, s>>>((const float*)U, n3, level, vol, scratch);
+      noalloc_block_sums<float><<<nblocks, 256, 0, s>>>((const float*)U, n3, nvar, level, vols, scratch);
   }
-  noalloc_final<<<1, 32, 0, s>>>(scratch, nblocks, out);
+  noalloc_final<<<1, 32, 0, s>>>(scratch, nblocks, nvar, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return reject(PH_ERR_CUDA, cudaGetErrorString(e));
   return PH_OK;

@@ -108,9 +108,13 @@ def test_null_handles_rejected():
     # no-allocation totals: checks happen before any device work
     out = ctypes.c_void_p(8)
     n3 = (ctypes.c_int32 * 3)(4, 4, 4)
-    assert L.ph_totals_noalloc(None, 0, n3, 1, None, 1.0, 1.0, out, None) == -1
-    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 3, n3, 1, None, 1.0, 1.0, out, None) == -1
-    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 1 << 20, None, 1.0, 1.0, out, None) == -1
+    vol = (ctypes.c_double * 2)(1.0, 0.125)
+    assert L.ph_totals_noalloc(None, 0, n3, 5, 1, None, vol, 1, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 3, n3, 5, 1, None, vol, 1, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 5, 1 << 20, None, vol, 1, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 8, 1, None, vol, 1, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 5, 1, None, vol, 2, out, None) == -1
+    assert L.ph_totals_noalloc(ctypes.c_void_p(8), 0, n3, 5, 1, None, None, 1, out, None) == -1
 
 
 def test_load_validates_the_file_before_any_device_work(tmp_path):

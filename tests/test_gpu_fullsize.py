@@ -4,8 +4,13 @@ benchmark times.
 * uniform 256^3 zones in 512 blocks of 32^3 (the benchmark mesh, default
   tile): one full cycle against the FP64 oracle, FP64 and FP32;
 * two-level blast, root 128^3 zones in 16^3 blocks with the static cube and
-  adaptive refinement (960 leaves): two cycles against the oracle, then 50
-  cycles of invariants (conservation, no floors, leaves tile the domain);
+  adaptive refinement (960 leaves): all 50 cycles against the oracle (tree,
+  refinement indicator and flags bit for bit, state within 1e-12 per field
+  every cycle), then conservation and tiling.  The blast stays inside the
+  pinned static cube, so the tree does not change in these 50 cycles;
+* derefinement on the same 960-leaf mesh: 64 refined parents carrying a
+  smooth state merge as soon as their children reach the derefinement age,
+  against the oracle every cycle;
 * the 64-member batch as the benchmark autotunes it: a member of every size
   matches its own single-mesh run bit for bit (single meshes are pinned to
   the oracle above and in test_gpu_uniform)."""
@@ -54,6 +59,17 @@ def test_uniform_256cube_one_cycle(oracle_256, precision):
     assert m.status()[0] == 0
 
 
+def _cycle_against_oracle(m, om, c):
+    assert np.array_equal(m.tree(), om.tree()), "cycle %d: tree" % c
+    gf, gmb = m.tag()
+    of, omb = om.tag()
+    assert np.array_equal(gmb, omb), "cycle %d: indicator" % c
+    assert np.array_equal(gf, of), "cycle %d: flags" % c
+    err, plain = field_errors(m.get_state(), om.get_state(), with_plain=True)
+    assert err.max() <= 1e-12, "cycle %d: %s" % (c, describe(err, plain))
+
+
+@pytest.mark.slow
 def test_two_level_blast_full_size():
     ph = _ph()
     nx, nb = (16, 16, 16), (8, 8, 8)
@@ -67,14 +83,12 @@ def test_two_level_blast_full_size():
     U0 = W.blast(geo, tree, seed=0)
     om.set_state(U0)
     m.set_state(U0)
-    for c in range(2):
-        om.step(1)
-        m.step(1)
-        assert np.array_equal(m.tree(), om.tree())
-        err = field_errors(m.get_state(), om.get_state())
-        assert err.max() <= 1e-12, "cycle %d: %s" % (c, describe(err))
     t0 = m.totals()
-    m.step(48)
+    for c in range(50):
+        odt = om.step(1)[0]
+        m.step(1)
+        assert abs(m.dt() - odt) <= 1e-12 * odt, "cycle %d: dt" % c
+        _cycle_against_oracle(m, om, c)
     t1 = m.totals()
     assert np.all(np.abs(t1 - t0) <= 1e-12 * np.abs(t0).max()), t1 - t0
     rc, floors, nonfinite = m.status()
@@ -88,6 +102,39 @@ def test_two_level_blast_full_size():
         a, b, c = (int(v) * s for v in (a, b, c))
         cover[c:c + s, b:b + s, a:a + s] += 1
     assert np.all(cover == 1)
+
+
+@pytest.mark.slow
+def test_derefinement_full_size():
+    """The 960-leaf mesh of the two-level blast built by explicit refinement
+    of the central 4^3 root blocks (no static region), carrying the 1e-4
+    sound wave: every indicator is below the derefinement tolerance, so all
+    64 parents merge at the cycle their children reach derefine_count (10)
+    cycles of age."""
+    ph = _ph()
+    nx, nb = (16, 16, 16), (8, 8, 8)
+    kw = dict(max_level=1, adaptive=1, derefine_count=10)
+    om = O.OracleMesh(O.make_config(nx, nb, **kw))
+    m = ph.Mesh(ph.make_config(nx, nb, **kw))
+    flags = np.zeros(512, dtype=np.int8)
+    for b, (l, a, j, k) in enumerate(om.tree()):
+        if 2 <= a < 6 and 2 <= j < 6 and 2 <= k < 6:
+            flags[b] = 1
+    assert om.remesh(flags, check_age=False)
+    assert m.refine_where(flags, check_age=False)
+    assert np.array_equal(m.tree(), om.tree()) and m.nblocks == 960
+    geo = W.Geometry(nx, nb)
+    U0 = W.linear_wave(geo, om.tree(), seed=1, amp=1e-4, kvec=(1, 1, 1))
+    om.set_state(U0)
+    m.set_state(U0)
+    merged_at = None
+    for c in range(12):
+        om.step(1)
+        m.step(1)
+        _cycle_against_oracle(m, om, c)
+        if merged_at is None and m.nblocks == 512:
+            merged_at = c
+    assert merged_at is not None and 8 <= merged_at <= 10, merged_at
 
 
 def test_batch_full_members_match_single_meshes():

@@ -1,6 +1,6 @@
-"""Pins of the oracle's trees deeper than two levels (SURVEY's next row: more
-levels with the one-level rule between touching leaves, and the
-Kelvin-Helmholtz problem): the tree tiles the domain and touching leaves
+"""Pins of the oracle's trees deeper than two levels (more levels with the
+one-level rule between touching leaves, and the Kelvin-Helmholtz problem of
+Sec. 4.1): the tree tiles the domain and touching leaves
 differ by one level at most (brute force), refinement cascades and blocked
 merges follow that rule, a uniform state is preserved bit for bit, mass,
 momentum and energy are conserved to round-off across every level jump,
