@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/ph_hydro.h"
+#include "ph_nvtx.h"
 #include "ph_internal.h"
 
 namespace ph {
@@ -746,6 +747,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
 extern "C" int ph_adjoint(ph_mesh* m, const void* U0, int32_t ncycles, int32_t ckpt_every,
                           const double* dts, const void* dLdU, void* dLdU0, double* dLdgamma,
                           int32_t on_device) {
+  PH_RANGE("ph_adjoint");
   if (!m || !U0 || !dLdU || !dLdU0 || ncycles < 1 || ckpt_every < 1)
     return afail(PH_ERR_INVALID, "ph_adjoint: bad argument");
   ph::MeshAccess A;

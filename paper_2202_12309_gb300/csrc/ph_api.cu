@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/ph_hydro.h"
+#include "ph_nvtx.h"
 #include "ph_internal.h"
 #include "ph_stage.cuh"
 
@@ -328,13 +329,20 @@ bool next_tree(const ph_mesh* m, const std::vector<int8_t>& flags, bool check_ag
 
 // ---------------------------------------------------------------- device tables
 
+// The device tables of a mesh (rebuilt whenever the tree changes).
+void table_slots(ph_mesh* m, void** (&slot)[13]) {
+  void** ptrs[13] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_node,
+                     (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
+                     (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
+                     (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
+                     (void**)&m->d_fcf};
+  for (int i = 0; i < 13; ++i) slot[i] = ptrs[i];
+}
+
 void free_tables(ph_mesh* m) {
-  void** ptrs[] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_node,
-                   (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
-                   (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
-                   (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
-                   (void**)&m->d_fcf};
-  for (void** p : ptrs) {
+  void** slot[13];
+  table_slots(m, slot);
+  for (void** p : slot) {
     m->dfree(*p);
     *p = nullptr;
   }
@@ -350,9 +358,33 @@ int upload(ph_mesh* m, V** dst, const std::vector<V>& src) {
   return PH_OK;
 }
 
-// Build and upload every per-leaf table for the current tree.
+int build_tables_fresh(ph_mesh* m);
+
+// Build and upload every per-leaf table for the current tree.  The new
+// tables are made beside the old ones, which are released only when every
+// new one exists: on a failure (PH_ERR_OOM) the mesh keeps its old tables.
 int build_tables(ph_mesh* m) {
-  free_tables(m);
+  void** slot[13];
+  table_slots(m, slot);
+  void* keep[13];
+  for (int i = 0; i < 13; ++i) {
+    keep[i] = *slot[i];
+    *slot[i] = nullptr;
+  }
+  const int nrec = m->nrec, ncorr = m->ncorr;
+  const int rc = build_tables_fresh(m);
+  if (rc) {
+    free_tables(m);
+    for (int i = 0; i < 13; ++i) *slot[i] = keep[i];
+    m->nrec = nrec;
+    m->ncorr = ncorr;
+    return rc;
+  }
+  for (int i = 0; i < 13; ++i) m->dfree(keep[i]);
+  return PH_OK;
+}
+
+int build_tables_fresh(ph_mesh* m) {
   const int n = m->nleaf();
   std::vector<int8_t> level(n);
   std::vector<int> leaf_id(4 * n), nbr(27 * n, -1);
@@ -693,6 +725,7 @@ int multi_level_cycle(ph_mesh* m) {
 // merged parents, copy otherwise), then ghosts are refilled.
 template <class T>
 int remesh_t(ph_mesh* m, std::vector<Leaf>& nl) {
+  PH_RANGE("ph remesh (tree and data)");
   int rc;
   std::vector<Leaf> old = m->leaf;
   m->leaf = nl;
@@ -706,24 +739,41 @@ int remesh_t(ph_mesh* m, std::vector<Leaf>& nl) {
   // the old device tables and pool stay valid until the copy is enqueued
   ph::TreeView old_tv = tree_view(m);
   int* d_new_id = nullptr;
-  if ((rc = upload(m, &d_new_id, leaf_id))) return rc;
   const size_t bytes = m->esize * m->block_elems * (size_t)std::max(nnew, 1);
-  void* U0n = m->dalloc(bytes);
-  void* U1n = m->dalloc(bytes);
-  if (!U0n || !U1n) return fail(PH_ERR_OOM, "device allocation failed (remesh)");
+  void* U0n = nullptr;
+  void* U1n = nullptr;
+  rc = upload(m, &d_new_id, leaf_id);
+  if (!rc) {
+    U0n = m->dalloc(bytes);
+    U1n = U0n ? m->dalloc(bytes) : nullptr;
+    if (!U1n) rc = fail(PH_ERR_OOM, "device allocation failed (remesh)");
+  }
+  if (rc) {  // nothing has moved yet: give back what was taken, keep the old tree
+    m->dfree(U0n);
+    m->dfree(U1n);
+    m->dfree(d_new_id);
+    m->leaf = old;
+    index_tree(m);
+    return rc;
+  }
   PH_CUDA(cudaMemsetAsync(U0n, 0, bytes, m->stream));
   PH_CUDA(cudaMemsetAsync(U1n, 0, bytes, m->stream));
   PH_CUDA(ph::launch_remesh<T>((T*)U0n, d_new_id, nnew, (const T*)m->U0, old_tv, m->stream, m->nvar));
   PH_CUDA(cudaStreamSynchronize(m->stream));
   m->dfree(d_new_id);
+  if ((rc = build_tables(m))) {  // the old tables, pools and tree stay as they were
+    m->dfree(U0n);
+    m->dfree(U1n);
+    m->leaf = old;
+    index_tree(m);
+    return rc;
+  }
   m->dfree(m->U0);
   m->dfree(m->U1);
   m->U0 = U0n;
   m->U1 = U1n;
   m->pool_cap = (size_t)std::max(nnew, 1);
   build_tmaps(m);
-  (void)old;
-  if ((rc = build_tables(m))) return rc;
   if ((rc = fill_ghosts_t<T>(m, (T*)m->U0))) return rc;
   drop_graph(m);
   return PH_OK;
@@ -739,6 +789,7 @@ int step_t(ph_mesh* m, int n) {
   }
   if (!m->gexec)
     if ((rc = capture_graph<T>(m))) return rc;
+  PH_RANGE("ph cycle graph replays");
   for (int c = 0; c < n; ++c) PH_CUDA(cudaGraphLaunch(m->gexec, m->stream));
   return PH_OK;
 }
@@ -923,6 +974,7 @@ int mesh_cycle_read_dt(ph_mesh* m, double* dt) {
 extern "C" {
 
 int ph_step_dt(ph_mesh* m, int32_t ncycles, const double* dts) {
+  PH_RANGE("ph_step_dt");
   if (!m || (!dts && ncycles > 0) || ncycles < 0) return fail(PH_ERR_INVALID, "ph_step_dt: bad argument");
   if (m->multi_level) return fail(PH_ERR_INVALID, "ph_step_dt: uniform meshes only");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_step_dt: set the state first");
@@ -1095,24 +1147,28 @@ static int64_t interior_count(const ph_mesh* m) {
 }
 
 int ph_set_state(ph_mesh* m, const void* U, int64_t count, int32_t on_device) {
+  PH_RANGE("ph_set_state");
   if (!m || !U) return fail(PH_ERR_INVALID, "ph_set_state: null argument");
   if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_set_state: count mismatch");
   return DISPATCH(m, set_state_t, m, U, on_device);
 }
 
 int ph_get_state(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
+  PH_RANGE("ph_get_state");
   if (!m || !U) return fail(PH_ERR_INVALID, "ph_get_state: null argument");
   if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_get_state: count mismatch");
   return DISPATCH(m, get_state_t, m, U, on_device);
 }
 
 int ph_set_state_async(ph_mesh* m, const void* U, int64_t count, int32_t on_device) {
+  PH_RANGE("ph_set_state_async");
   if (!m || !U) return fail(PH_ERR_INVALID, "ph_set_state_async: null argument");
   if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_set_state_async: count mismatch");
   return DISPATCH(m, set_state_t, m, U, on_device, 1);
 }
 
 int ph_get_state_async(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
+  PH_RANGE("ph_get_state_async");
   if (!m || !U) return fail(PH_ERR_INVALID, "ph_get_state_async: null argument");
   if (count != interior_count(m)) return fail(PH_ERR_INVALID, "ph_get_state_async: count mismatch");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_get_state_async: set the state first");
@@ -1130,6 +1186,7 @@ int ph_get_full(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
 }
 
 int ph_step(ph_mesh* m, int32_t ncycles) {
+  PH_RANGE("ph_step");
   if (!m) return fail(PH_ERR_INVALID, "ph_step: null mesh");
   if (ncycles < 0) return fail(PH_ERR_INVALID, "ph_step: negative cycle count");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_step: set the state first");
@@ -1172,6 +1229,7 @@ int ph_get_time(ph_mesh* m, double* time, int64_t* cycle) {
 }
 
 int ph_totals(ph_mesh* m, double* out) {
+  PH_RANGE("ph_totals");
   if (!m || !out) return fail(PH_ERR_INVALID, "ph_totals: null argument");
   return DISPATCH(m, totals_t, m, out);
 }
@@ -1184,6 +1242,7 @@ int ph_tag(ph_mesh* m, int8_t* flags, double* indicator, int32_t n) {
 
 int ph_refine_where(ph_mesh* m, const int8_t* flags, int32_t n, int32_t check_age,
                     int32_t* changed) {
+  PH_RANGE("ph_refine_where");
   if (!m || !flags) return fail(PH_ERR_INVALID, "ph_refine_where: null argument");
   if (n != m->nleaf()) return fail(PH_ERR_INVALID, "ph_refine_where: flag count mismatch");
   if (!m->multi_level) return fail(PH_ERR_INVALID, "ph_refine_where: mesh has max_level 0");

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/ph_hydro.h"
+#include "ph_nvtx.h"
 #include "ph_internal.h"
 #include "ph_stage.cuh"
 
@@ -376,6 +377,7 @@ int occupancy_t(int TX, int TY, int* per_sm) {
 
 template <class T, int TX, int TY, bool TMA>
 cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
+  PH_RANGE("ph batch cycle");
   BatchArgs<T> a;
   a.U0 = (T*)b->U0;
   a.U1 = (T*)b->U1;
@@ -788,6 +790,7 @@ int ph_batch_get_state(ph_batch* b, int32_t sim, void* U, int64_t count, int32_t
 }
 
 int ph_batch_step(ph_batch* b, int32_t ncycles) {
+  PH_RANGE("ph_batch_step");
   if (!b || ncycles < 0) return bfail(PH_ERR_INVALID, "ph_batch_step: bad argument");
   if (ncycles == 0) return PH_OK;
   if (!b->gexec) {

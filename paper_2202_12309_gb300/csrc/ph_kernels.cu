@@ -10,6 +10,7 @@
 // writes ghost cells only, so one launch has no ordering hazard.
 #include <algorithm>
 
+#include "ph_nvtx.h"
 #include "ph_internal.h"
 
 namespace ph {
@@ -156,6 +157,7 @@ static cudaError_t launch_ghost_uniform_n(T* U, const int* nbr, const int nx[3],
 template <class T>
 cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nleaf, cudaStream_t s,
                                  const int* leaf_id, const int nb[3], int bcm, int nvar) {
+  PH_RANGE("ph ghost exchange (uniform)");
   if (nleaf <= 0) return cudaSuccess;
   if (nvar == NV + 1) return launch_ghost_uniform_n<T, NV + 1>(U, nbr, nx, nleaf, s, leaf_id, nb, bcm);
   if (nvar == NV + 2) return launch_ghost_uniform_n<T, NV + 2>(U, nbr, nx, nleaf, s, leaf_id, nb, bcm);
@@ -354,6 +356,7 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
                                    int nleaf, cudaStream_t s, int nvar) {
+  PH_RANGE("ph ghost exchange (composite)");
   if (nleaf <= 0) return cudaSuccess;
   if (nvar == NV + 1)
     ghost_composite_kernel<T, NV + 1><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
@@ -389,6 +392,7 @@ __global__ void remesh_kernel(T* Unew, const int* __restrict__ leaf_id, const T*
 template <class T>
 cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uold,
                           const TreeView& old_tv, cudaStream_t s, int nvar) {
+  PH_RANGE("ph remesh");
   if (nnew <= 0) return cudaSuccess;
   if (nvar == NV + 1)
     remesh_kernel<T, NV + 1><<<nnew, 256, 0, s>>>(Unew, new_leaf_id, Uold, old_tv);
@@ -432,6 +436,7 @@ __global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ 
 template <class T>
 cudaError_t launch_rate(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
                         int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s, int nvar) {
+  PH_RANGE("ph dt rate");
   if (nleaf <= 0) return cudaSuccess;
   rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]), P, sc, nvar);
   return cudaGetLastError();
@@ -454,6 +459,7 @@ __global__ void advance_kernel(DevScalars* sc, double cfl, int mode) {
 }
 
 cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s) {
+  PH_RANGE("ph dt advance");
   advance_kernel<<<1, 1, 0, s>>>(sc, cfl, mode);
   return cudaGetLastError();
 }
@@ -485,6 +491,7 @@ __global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir, int nvar) {
 template <class T>
 cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int dir, cudaStream_t s,
                         int nvar) {
+  PH_RANGE("ph pack");
   if (nleaf <= 0) return cudaSuccess;
   const size_t per = (size_t)nvar * nx[0] * nx[1] * nx[2];
   int gx = (int)((per + 255) / 256);
@@ -550,6 +557,7 @@ __global__ void totals_final_kernel(const double* __restrict__ partial, int nlea
 template <class T>
 cudaError_t launch_totals(const T* U, const int8_t* level, const LevelGeom& g, const int nx[3],
                           int nleaf, double* partial, double* out, cudaStream_t s, int nvar) {
+  PH_RANGE("ph totals");
   const int3 n = make_int3(nx[0], nx[1], nx[2]);
   if (nleaf > 0) {
     if (nvar == NV + 1)
@@ -606,6 +614,7 @@ __global__ void indicator_kernel(const T* __restrict__ U, int3 nx, double* mb, i
 template <class T>
 cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb, cudaStream_t s,
                              int nvar) {
+  PH_RANGE("ph refinement indicator");
   if (nleaf <= 0) return cudaSuccess;
   indicator_kernel<T><<<nleaf, 256, 0, s>>>(U, make_int3(nx[0], nx[1], nx[2]), mb, nvar);
   return cudaGetLastError();
@@ -671,6 +680,7 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
                                 const int nx[3], const int8_t* level, const LevelGeom& g,
                                 double beta, const DevScalars* sc, cudaStream_t s, int nvar) {
+  PH_RANGE("ph flux correction");
   if (ncorr <= 0) return cudaSuccess;
   flux_correct_kernel<T><<<ncorr, 256, 0, s>>>(U, corr_leaf, rec_beg, rec_face, fc_coarse, fc_fine,
                                                 make_int3(nx[0], nx[1], nx[2]), level, g, beta, sc,

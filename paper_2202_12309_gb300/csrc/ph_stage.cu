@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "ph_nvtx.h"
 #include "ph_internal.h"
 #include "ph_stage.cuh"
 #include "ph_stage_pair.cuh"
@@ -113,6 +114,7 @@ static cudaError_t launch_pair(const StageArgs<float>& a, const CUtensorMap* tma
 
 template <class T>
 cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s, const CUtensorMap* tmap) {
+  PH_RANGE("ph stage");
   if (a.nvar == NV + 1) return launch_scalar_tiles<T, NV + 1>(a, TX, TY, s, tmap);
   if (a.nvar == NV + 2) return launch_scalar_tiles<T, NV + 2>(a, TX, TY, s, tmap);
   if (a.nvar != NV) return cudaErrorInvalidValue;
