@@ -60,13 +60,26 @@ def test_uniform_256cube_one_cycle(oracle_256, precision):
 
 
 def _cycle_against_oracle(m, om, c):
+    """Tree and refinement flags bit for bit, state within 1e-12 per field.
+    The indicator is computed from each side's own state, which agree to
+    rounding, so it agrees to 1e-10 (a flag decided that close to a
+    tolerance would be a near-threshold event, reported as such)."""
     assert np.array_equal(m.tree(), om.tree()), "cycle %d: tree" % c
     gf, gmb = m.tag()
     of, omb = om.tag()
-    assert np.array_equal(gmb, omb), "cycle %d: indicator" % c
-    assert np.array_equal(gf, of), "cycle %d: flags" % c
+    near = np.min(np.abs(omb - 0.05)), np.min(np.abs(omb - 0.0125))
+    assert np.array_equal(gf, of), "cycle %d: flags (closest to a tolerance: %.3g, %.3g)" % ((c,) + near)
+    assert np.all(np.abs(gmb - omb) <= 1e-10 * np.abs(omb).max()), "cycle %d: indicator" % c
     err, plain = field_errors(m.get_state(), om.get_state(), with_plain=True)
     assert err.max() <= 1e-12, "cycle %d: %s" % (c, describe(err, plain))
+
+
+def _indicator_on_oracle_state(m, om):
+    """The GPU indicator of the oracle's own state is the oracle's, bit for bit."""
+    m.set_state(om.get_state())
+    gf, gmb = m.tag()
+    of, omb = om.tag()
+    assert np.array_equal(gmb, omb) and np.array_equal(gf, of)
 
 
 @pytest.mark.slow
@@ -95,6 +108,7 @@ def test_two_level_blast_full_size():
     assert rc == 0 and floors == 0 and nonfinite == 0
     t, cyc = m.time()
     assert cyc == 50
+    _indicator_on_oracle_state(m, om)
     tree = m.tree()
     cover = np.zeros((16, 16, 16), dtype=int)
     for l, a, b, c in tree:
@@ -135,6 +149,7 @@ def test_derefinement_full_size():
         if merged_at is None and m.nblocks == 512:
             merged_at = c
     assert merged_at is not None and 8 <= merged_at <= 10, merged_at
+    _indicator_on_oracle_state(m, om)
 
 
 def test_batch_full_members_match_single_meshes():
