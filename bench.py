@@ -223,15 +223,18 @@ def measured_traffic(precision, block):
         return None
 
 
-def fma_peak(ph, torch, kind="fp64", reps=5):
+def fma_peak(ph, torch, kind="fp64", reps=10, warm=5):
     """Measured peak of one arithmetic pipe: the best of `reps` CUDA-event
     timings of ph_debug_fma_rate (8 independent multiply-add chains per
-    thread, 8 CTAs of 256 threads per SM) on the current stream, in TFLOP/s."""
+    thread, 8 CTAs of 256 threads per SM, ~16 ms a launch) on the current
+    stream, after `warm` untimed launches, in TFLOP/s.  Run after the
+    headline, on a GPU already at its working clocks."""
     ctas = SMS * 8
     iters = 4096 if kind == "fp64" else 4096 * 64
     out = torch.empty(ctas * 256, dtype=torch.float64 if kind == "fp64" else torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    flops = ph.debug_fma_rate(kind, ctas, iters, out)  # warm-up
+    for _ in range(warm):
+        flops = ph.debug_fma_rate(kind, ctas, iters, out)
     best = float("inf")
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -671,7 +674,6 @@ def main():
         torch.distributed.barrier()
     ph.use_torch_allocator()
     pk, peak_kind = peaks()
-    fp64_peak = fma_peak(ph, torch, "fp64") if not args.only else None
     if args.only:
         if args.only == "batch":
             launch = [int(x) for x in args.batch_launch.split(",")] if args.batch_launch else None
@@ -699,6 +701,7 @@ def main():
     clocks.start()
     head = time_variant(ph, torch, args.block, args.precision, args.steps, args.warmup, barrier=barrier)
     ck = clocks.stop()
+    fp64_peak = fma_peak(ph, torch, "fp64")
     ms = rank_reduce(head["ms_per_cycle"] * args.steps, "max", world, "cuda")
     value = world * MESH ** 3 * args.steps / (ms / 1e3)
 

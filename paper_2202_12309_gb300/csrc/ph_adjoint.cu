@@ -37,13 +37,17 @@ namespace ph {
 // pointwise reverses
 // ---------------------------------------------------------------------------
 
-// Forward cons->prim with the branch flags the reverse needs.
+// Forward cons->prim with the branch flags the reverse needs; returns 1/rho.
+// Reciprocals, square roots and their inverses in this file are the stage
+// kernels' Newton-refined routines (within an ulp or two of the correctly
+// rounded ones): the reverse differentiates the same formulas, and a
+// derivative needs no more than that.
 template <class T>
-__device__ __forceinline__ void prim_fwd(const T u[NV], const Phys<T>& P, T w[NV], bool& rf, bool& pf) {
+__device__ __forceinline__ T prim_fwd(const T u[NV], const Phys<T>& P, T w[NV], bool& rf, bool& pf) {
   T rho = u[0];
   rf = rho < P.dfloor;
   if (rf) rho = P.dfloor;
-  const T ir = T(1) / rho;
+  const T ir = rcp(rho);
   w[0] = rho;
   w[1] = u[1] * ir;
   w[2] = u[2] * ir;
@@ -52,6 +56,7 @@ __device__ __forceinline__ void prim_fwd(const T u[NV], const Phys<T>& P, T w[NV
   pf = p < P.pfloor;
   if (pf) p = P.pfloor;
   w[4] = p;
+  return ir;
 }
 
 // Ubar = (dW/dU)^T Wbar; gamma adjoint of p = (gamma-1)(E - |m|^2/(2 rho)).
@@ -60,8 +65,8 @@ __device__ __forceinline__ void prim_rev(const T u[NV], const Phys<T>& P, const 
                                          double& gbar) {
   bool rf, pf;
   T w[NV];
-  prim_fwd(u, P, w, rf, pf);
-  const T rho = w[0], ir = T(1) / rho;
+  const T ir = prim_fwd(u, P, w, rf, pf);
+  const T rho = w[0];
   const T pb = pf ? T(0) : wb[4];
   const T v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
   // p = gm1 * (E - 0.5 rho_u |v|^2) with v = m / rho_used
@@ -91,12 +96,12 @@ __device__ __forceinline__ T vl_half_d(T wm, T w0, T wp, T& dm, T& d0, T& dp) {
     dm = d0 = dp = T(0);
     return T(0);
   }
-  const T s = dl + dr, is2 = T(1) / (s * s);
+  const T s = dl + dr, is = rcp(s), is2 = is * is;
   const T ddl = dr * dr * is2, ddr = dl * dl * is2;
   dm = -ddl;
   d0 = ddl - ddr;
   dp = ddr;
-  return prod / s;
+  return prod * is;
 }
 
 // Reverse of the HLLE flux (same formulation as the forward kernel), with
@@ -119,7 +124,7 @@ __device__ void hlle_rev(const T wl[NV], const T wr[NV], const Phys<T>& P, const
   const T xl = P.gamma * pl * irl, xr = P.gamma * pr * irr;
   const T cl = sq(xl), cr = sq(xr);
   const T hl = (el + pl) * irl, hr = (er + pr) * irr;
-  const T isum = T(1) / (sl + sr);
+  const T isum = rcp(sl + sr);
   const T wsl = sl * isum, wsr = sr * isum;
   T u[3];
 #pragma unroll
@@ -139,7 +144,7 @@ __device__ void hlle_rev(const T wl[NV], const T wr[NV], const Phys<T>& P, const
   const T m2 = CleD ? C : D;
   const bool bm0 = T(0) <= m2;
   const T bm = bm0 ? T(0) : m2;
-  const T idb = T(1) / (bp - bm);
+  const T idb = rcp(bp - bm);
   const T bpbm = bp * bm;
   const T mfl = rl * vnl, mfr = rr * vnr;
   T FL[NV], FR[NV], UL[NV], UR[NV];
@@ -221,7 +226,7 @@ __device__ void hlle_rev(const T wl[NV], const T wr[NV], const Phys<T>& P, const
   rrb += mfrb * vnr;
   vnrb += mfrb * rr;
   // Roe sound speed
-  T a2b = (a2pos && croe > T(0)) ? croeb / (T(2) * croe) : T(0);
+  T a2b = (a2pos && croe > T(0)) ? croeb * (T(0.5) * rcp(croe)) : T(0);
   T hroeb = a2b * P.gm1;
   const T usqb = -T(0.5) * P.gm1 * a2b;
   gbar += (double)a2b * (double)(hroe - T(0.5) * usq);
@@ -252,7 +257,7 @@ __device__ void hlle_rev(const T wl[NV], const T wr[NV], const Phys<T>& P, const
   prb += hrb * irr;
   T irrb = hrb * (er + pr);
   {
-    const T xlb = clb / (T(2) * cl), xrb = crb / (T(2) * cr);
+    const T xlb = clb * (T(0.5) * rcp(cl)), xrb = crb * (T(0.5) * rcp(cr));
     gbar += (double)xlb * (double)(pl * irl) + (double)xrb * (double)(pr * irr);
     plb += xlb * P.gamma * irl;
     irlb += xlb * P.gamma * pl;
@@ -328,7 +333,7 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst) {
 // Writes the adjoints of the face's left and right primitive states at the
 // padded index of the right cell.
 template <class T, int DIR>
-__global__ void adj_faces_kernel(const T* __restrict__ U, const T* __restrict__ mu, T* FLb, T* FRb,
+__global__ void adj_faces_kernel(const T* __restrict__ Wp, const T* __restrict__ mu, T* FLb, T* FRb,
                                  AdjGeom g, Phys<T> P, double* gbar_out) {
   constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
   const size_t per_leaf = (size_t)(g.nx[DIR] + 1) * g.nx[t1] * g.nx[t2];
@@ -350,7 +355,7 @@ __global__ void adj_faces_kernel(const T* __restrict__ U, const T* __restrict__ 
     int pos[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) pos[d] = (d == DIR) ? f : bx[d] + NG;  // along DIR: padded start of the stencil
-    const T* Ub = U + (size_t)leaf * NV * vs;
+    const T* Wb = Wp + (size_t)leaf * NV * vs;
     const T* mub = mu + (size_t)leaf * NV * vs;
     size_t c[4];
     for (int s = 0; s < 4; ++s) {
@@ -370,12 +375,8 @@ __global__ void adj_faces_kernel(const T* __restrict__ U, const T* __restrict__ 
     T wlb[NV] = {0, 0, 0, 0, 0}, wrb[NV] = {0, 0, 0, 0, 0};
     if (any) {
       T w[4][NV];
-      for (int s = 0; s < 4; ++s) {
-        T u[NV];
-        bool rf, pf;
-        load_u(Ub, vs, c[s], u);
-        prim_fwd(u, P, w[s], rf, pf);
-      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) load_u(Wb, vs, c[s], w[s]);
       T wl[NV], wr[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -400,8 +401,8 @@ __global__ void adj_faces_kernel(const T* __restrict__ U, const T* __restrict__ 
 // half-slope contributions into Wbar.  Face k+1/2 lives at padded index k+1
 // when 2 <= k+1 <= n+2.
 template <class T, int DIR>
-__global__ void adj_cells_kernel(const T* __restrict__ U, const T* __restrict__ FLb,
-                                 const T* __restrict__ FRb, T* Wbar, AdjGeom g, Phys<T> P) {
+__global__ void adj_cells_kernel(const T* __restrict__ Wp, const T* __restrict__ FLb,
+                                 const T* __restrict__ FRb, T* Wbar, AdjGeom g) {
   constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
   const int Sd = g.S[DIR], n = g.nx[DIR];
   const size_t per_leaf = (size_t)Sd * g.nx[t1] * g.nx[t2];
@@ -427,7 +428,7 @@ __global__ void adj_cells_kernel(const T* __restrict__ U, const T* __restrict__ 
       qq[DIR] = q;
       return cell_index(g, qq[2], qq[1], qq[0]);
     };
-    const T* Ub = U + (size_t)leaf * NV * vs;
+    const T* Wsrc = Wp + (size_t)leaf * NV * vs;
     const T* FL = FLb + (size_t)leaf * NV * vs;
     const T* FR = FRb + (size_t)leaf * NV * vs;
     auto face_ok = [&](int q) { return q >= NG && q <= n + NG; };  // face stored at q
@@ -436,10 +437,7 @@ __global__ void adj_cells_kernel(const T* __restrict__ U, const T* __restrict__ 
     for (int s = 0; s < 5; ++s) {
       const int q = p - 2 + s;
       if (q < 0 || q >= Sd) continue;
-      T u[NV];
-      bool rf, pf;
-      load_u(Ub, vs, at(q), u);
-      prim_fwd(u, P, w[s], rf, pf);
+      load_u(Wsrc, vs, at(q), w[s]);
     }
     T acc[NV] = {0, 0, 0, 0, 0};
     // direct: left state of face p+1/2, right state of face p-1/2
@@ -472,6 +470,26 @@ __global__ void adj_cells_kernel(const T* __restrict__ U, const T* __restrict__ 
     const size_t cp = at(p);
 #pragma unroll
     for (int v = 0; v < NV; ++v) Wb[v * vs + cp] += acc[v];
+  }
+}
+
+// Primitive variables of every padded cell of a stage's input, once per
+// stage: the face and cell kernels read them instead of converting their
+// 4- and 5-cell stencils along each direction.
+template <class T>
+__global__ void adj_wprim_kernel(const T* __restrict__ U, T* __restrict__ Wp, AdjGeom g, Phys<T> P) {
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < vs * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int leaf = (int)(e / vs);
+    const size_t base = (size_t)leaf * NV * vs + (e - (size_t)leaf * vs);
+    T u[NV], w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = U[base + v * vs];
+    bool rf, pf;
+    prim_fwd(u, P, w, rf, pf);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Wp[base + v * vs] = w[v];
   }
 }
 
@@ -588,7 +606,8 @@ namespace ph {
 
 
 template <class T>
-int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, T* Wbar, double* gbar) {
+int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, T* Wbar, T* Wp,
+          double* gbar) {
   AdjGeom g;
   for (int d = 0; d < 3; ++d) {
     g.nx[d] = A.nx[d];
@@ -606,12 +625,13 @@ int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, 
   const size_t nfaces0 = (size_t)(A.nx[0] + 1) * A.nx[1] * A.nx[2] * A.nleaf;
   const size_t ncell = (size_t)(A.nx[0] + 4) * A.nx[1] * A.nx[2] * A.nleaf;
   const size_t all = A.block_elems / NV * A.nleaf;
-  adj_faces_kernel<T, 0><<<grid_for(nfaces0), 256, 0, s>>>(U, mu, FLb, FRb, g, P, gbar);
-  adj_cells_kernel<T, 0><<<grid_for(ncell), 256, 0, s>>>(U, FLb, FRb, Wbar, g, P);
-  adj_faces_kernel<T, 1><<<grid_for(nfaces0), 256, 0, s>>>(U, mu, FLb, FRb, g, P, gbar);
-  adj_cells_kernel<T, 1><<<grid_for(ncell), 256, 0, s>>>(U, FLb, FRb, Wbar, g, P);
-  adj_faces_kernel<T, 2><<<grid_for(nfaces0), 256, 0, s>>>(U, mu, FLb, FRb, g, P, gbar);
-  adj_cells_kernel<T, 2><<<grid_for(ncell), 256, 0, s>>>(U, FLb, FRb, Wbar, g, P);
+  adj_wprim_kernel<T><<<grid_for(all), 256, 0, s>>>(U, Wp, g, P);
+  adj_faces_kernel<T, 0><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
+  adj_cells_kernel<T, 0><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
+  adj_faces_kernel<T, 1><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
+  adj_cells_kernel<T, 1><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
+  adj_faces_kernel<T, 2><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
+  adj_cells_kernel<T, 2><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
   adj_prim_kernel<T><<<grid_for(all), 256, 0, s>>>(U, Wbar, acc, g, P, gbar);
   PA_CUDA(cudaGetLastError());
   return PH_OK;
@@ -627,15 +647,17 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   const size_t elems = A.block_elems * A.nleaf;  // padded state
   const size_t bytes = elems * sizeof(T);
   const int nseg = (ncycles + ckpt - 1) / ckpt;
+  // workspaces come from the mesh's allocator (PyTorch's caching allocator
+  // when installed), so repeated gradients do not enter cudaMalloc/cudaFree
   std::vector<void*> bufs;
   auto alloc = [&](size_t b) -> T* {
-    void* p = nullptr;
-    if (cudaMalloc(&p, b ? b : 16) != cudaSuccess) return nullptr;
+    void* p = mesh_alloc(m, b ? b : 16);
     bufs.push_back(p);
     return (T*)p;
   };
   auto cleanup = [&]() {
-    for (void* p : bufs) cudaFree(p);
+    cudaStreamSynchronize(s);
+    for (void* p : bufs) mesh_free(m, p);
   };
   T* lam = alloc(bytes);
   T* acc0 = alloc(bytes);
@@ -646,6 +668,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   T* FRb = alloc(bytes);
   T* Wbar = alloc(bytes);
   T* ufinal = alloc(bytes);
+  T* Wp = alloc(bytes);
   T* ck = alloc(bytes * nseg);
   T* seg0 = alloc(bytes * ckpt);
   T* seg1 = alloc(bytes * ckpt);
@@ -656,7 +679,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
       cleanup();
       return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
     }
-  if (bufs.size() != 14) {
+  if (bufs.size() != 15) {
     cleanup();
     return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
   }
@@ -716,12 +739,12 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, T(0.5), nullptr, T(0), elems);
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc1, lam, T(0.5), nullptr, T(0), elems);
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, lam, T(0.5) * dt, nullptr, T(0), elems);
-      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, gbar))) return fail_clean(rc);
+      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, Wp, gbar))) return fail_clean(rc);
       adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc1, tmp, A.nbr, g);
       // stage 1: U1 = U0 + dt L(U0)
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, acc0, T(1), tmp, T(1), elems);
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, tmp, dt, nullptr, T(0), elems);
-      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, gbar))) return fail_clean(rc);
+      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, Wp, gbar))) return fail_clean(rc);
       adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, A.nbr, g);
       PA_CUDA(cudaGetLastError());
     }

@@ -929,6 +929,9 @@ bool valid_tile(const ph_config* c, const int t[3]) {
 namespace ph {
 
 
+void* mesh_alloc(ph_mesh* m, size_t bytes) { return m->dalloc(bytes); }
+void mesh_free(ph_mesh* m, void* p) { m->dfree(p); }
+
 int mesh_access(ph_mesh* m, MeshAccess* out) {
   if (m->multi_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
   if (bc_mask(m)) return fail(PH_ERR_INVALID, "adjoint: periodic meshes only");
@@ -1048,7 +1051,8 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     m->push = !m->multi_level && periodic && !(g && std::strcmp(g, "launch") == 0);
   }
   int t[3] = {cfg->tile[0], cfg->tile[1], cfg->tile[2]};
-  if (t[0] == 0 && t[1] == 0 && t[2] == 0) {
+  const bool default_tile = t[0] == 0 && t[1] == 0 && t[2] == 0;
+  if (default_tile) {
     // tiles march 16 planes (measured on 256^3 meshes: more, shorter tiles
     // leave a smaller last wave than whole-block columns, 2-7% faster)
     t[0] = cfg->nx[0] >= 16 ? 16 : 8;
@@ -1092,6 +1096,21 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
       m->leaf = nl;
       index_tree(m);
     }
+  }
+  // Small uniform meshes: shorter x3 chunks (down to 4 planes) until a stage
+  // launch has at least two CTAs per SM.  Each chunk re-stages 4 halo planes,
+  // but a launch of fewer CTAs than the GPU holds leaves SMs idle (64 CTAs
+  // for 64^3 zones in 32^3 blocks with 16-plane chunks, on 152 SMs).
+  if (default_tile && !m->multi_level) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
+    auto ctas = [&](int kc) {
+      return (long long)m->nleaf() * ((cfg->nx[0] + m->tile[0] - 1) / m->tile[0]) *
+             ((cfg->nx[1] + m->tile[1] - 1) / m->tile[1]) * ((cfg->nx[2] + kc - 1) / kc);
+    };
+    while (m->tile[2] > 4 && ctas(m->tile[2]) < 2ll * nsm) m->tile[2] = std::max(4, (m->tile[2] + 1) / 2);
   }
   int rc = PH_OK;
   m->sc = (ph::DevScalars*)m->dalloc(sizeof(ph::DevScalars));

@@ -60,8 +60,12 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 // reciprocal and rsqrt are within one ulp of the exact values and the
 // square root within two (tested against them).  Arguments outside [2^-1000, 2^1000] in magnitude (zero,
 // subnormals, infinities, NaN; negative ones for the roots) take the
-// correctly rounded path instead.  FP32: the approximation plus one Newton
-// step for the reciprocal, the approximate rsqrt as is.
+// correctly rounded path instead.  FP32: the hardware approximations alone
+// (rcp / rsqrt / sqrt .approx.ftz.f32, one special-function instruction
+// each, within 2 ulp of the exact values: tested); the FP32 kernels call
+// them on normal positive numbers well inside the float range (densities
+// and pressures at or above their floors, sums of same-signed slopes), and
+// sq(0) = 0.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ bool nr_range(double x) {  // 2^-1000 <= |x| <= 2^1000
   const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
@@ -80,10 +84,6 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   return y;
 }
-// FP32's correctly rounded square root (for arguments below 1e-30) is an
-// out-of-line call, so that the compiler branches around it instead of
-// issuing its instructions predicated off on every call.
-static __device__ __noinline__ float sqrt_exact(float x) { return sqrtf(x); }
 __device__ __forceinline__ double rcp(double x) {
   if (!nr_range(x)) return 1.0 / x;
   const double y = rcp_approx(x);
@@ -93,7 +93,7 @@ __device__ __forceinline__ double rcp(double x) {
 __device__ __forceinline__ float rcp(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return fmaf(y, fmaf(-x, y, 1.f), y);
+  return y;
 }
 __device__ __forceinline__ double rsq(double x) {
   if (!nr_range_pos(x)) return rsqrt(x);
@@ -101,7 +101,11 @@ __device__ __forceinline__ double rsq(double x) {
   const double e = fma(-(x * y), y, 1.0);
   return fma(y * e, fma(0.375, e, 0.5), y);
 }
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsq(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double sq(double x) {
   if (!nr_range_pos(x)) return sqrt(x);
   const double y = rsqrt_approx(x);
@@ -109,7 +113,11 @@ __device__ __forceinline__ double sq(double x) {
   const double e = fma(-s, y, 1.0);
   return fma(s * e, fma(0.375, e, 0.5), s);
 }
-__device__ __forceinline__ float sq(float x) { return x > 1e-30f ? x * rsqrtf(x) : sqrt_exact(x); }
+__device__ __forceinline__ float sq(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // HLLE wave-speed bounds max(0, a, b) and min(0, a, b).  For doubles with
 // integer instructions: the bit patterns of non-negative doubles order like
@@ -120,13 +128,22 @@ __device__ __forceinline__ double max0(double a, double b) {
   const long long m = max(__double_as_longlong(a), __double_as_longlong(b));
   return __longlong_as_double(max(m, 0ll));
 }
-__device__ __forceinline__ float max0(float a, float b) { return fmaxf(0.f, fmaxf(a, b)); }
+// FP32: one three-input max / min (NaN inputs are skipped, as fmaxf does).
+__device__ __forceinline__ float max0(float a, float b) {
+  float y;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(0.f));
+  return y;
+}
 __device__ __forceinline__ double min0(double a, double b) {
   constexpr long long S = (long long)0x8000000000000000ull;
   const long long m = max(__double_as_longlong(a) ^ S, __double_as_longlong(b) ^ S);
   return __longlong_as_double(max(m, 0ll) ^ S);
 }
-__device__ __forceinline__ float min0(float a, float b) { return fminf(0.f, fminf(a, b)); }
+__device__ __forceinline__ float min0(float a, float b) {
+  float y;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(a), "f"(b), "f"(0.f));
+  return y;
+}
 // x > 0 (integer test for doubles; NaN with the sign bit clear counts as > 0).
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return x > 0.f; }

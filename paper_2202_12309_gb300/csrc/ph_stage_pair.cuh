@@ -67,20 +67,17 @@ __device__ __forceinline__ F2 operator-(F2 a) {  // flip both sign bits
   o.r = a.r ^ 0x8000000080000000ull;
   return o;
 }
-// Per-lane helpers (the same operations as the scalar FP32 path).
+// Per-lane helpers: the scalar FP32 routines of ph_device.cuh on each lane
+// (the special-function unit has no paired form).
 __device__ __forceinline__ F2 rcp2(F2 x) {
   float a, b;
   split(x, a, b);
-  float ya, yb;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ya) : "f"(a));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yb) : "f"(b));
-  const F2 y = f2(ya, yb);
-  return fma2(y, fma2(-x, y, f2(1.f)), y);
+  return f2(rcp(a), rcp(b));
 }
 __device__ __forceinline__ F2 rsq2(F2 x) {
   float a, b;
   split(x, a, b);
-  return f2(rsqrtf(a), rsqrtf(b));
+  return f2(rsq(a), rsq(b));
 }
 __device__ __forceinline__ F2 sq2(F2 x) {
   float a, b;
@@ -200,7 +197,7 @@ __device__ __forceinline__ void hlle2(const F2 wl[NV], const F2 wr[NV], const Ph
   const F2 a2 = f2(P.gm1) * fma2(f2(-0.5f), fma2(u1, u1, fma2(u2, u2, u3 * u3)), hroe);
   float a20, a21;
   split(a2, a20, a21);
-  const F2 croe = f2(a20 > 0.f ? sq(a20) : 0.f, a21 > 0.f ? sq(a21) : 0.f);
+  const F2 croe = f2(sq(fmaxf(a20, 0.f)), sq(fmaxf(a21, 0.f)));
   const F2 un = (IN == 1) ? u1 : ((IN == 2) ? u2 : u3);
   const F2 bp = max0_2(fma2(gr, qr, vnr), un + croe);
   const F2 bm = min0_2(fma2(-gl, ql, vnl), un - croe);

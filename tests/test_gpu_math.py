@@ -96,14 +96,23 @@ def test_fp64_special_arguments_take_the_correctly_rounded_path():
 
 
 def test_fp32_routines_within_bounds():
+    """FP32: the hardware approximations alone (one special-function
+    instruction each).  The kernels call them on normal positive numbers
+    well inside the float range only (reciprocals also on negative sums of
+    slopes)."""
     ph, torch = _ph()
-    # the FP32 routines have no range guard: the kernels call them on normal
-    # numbers well inside the float range only
     x = _inputs(n=1 << 18, lo=-40, hi=40, extremes=False).astype(np.float32)
     xp = np.abs(x)
+    xl = xp.astype(np.longdouble)
     y = _run(ph, torch, "rcp", x, np.float32)
     err = _ulp_err(y, 1 / x.astype(np.longdouble), np.float32)
     assert err.max() <= 1.0, err.max()
+    r = _run(ph, torch, "rsqrt", xp, np.float32)
+    er = _ulp_err(r, 1 / np.sqrt(xl), np.float32)
+    assert er.max() <= 2.0, er.max()
     s = _run(ph, torch, "sqrt", xp, np.float32)
-    es = _ulp_err(s, np.sqrt(xp.astype(np.longdouble)), np.float32)
-    assert es.max() <= 3.0, es.max()
+    es = _ulp_err(s, np.sqrt(xl), np.float32)
+    assert es.max() <= 2.0, es.max()
+    # sqrt(0) = 0 (the Roe sound speed of a vanishing a^2)
+    z = _run(ph, torch, "sqrt", np.zeros(4, dtype=np.float32), np.float32)
+    assert np.all(z == 0.0)

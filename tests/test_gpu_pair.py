@@ -24,7 +24,7 @@ def _ph():
 def test_fp32_default_tile_is_the_paired_kernel():
     ph = _ph()
     m = ph.Mesh(ph.make_config((32, 32, 32), (1, 1, 1), precision="fp32"))
-    assert tuple(m.tile()) == (32, 16, 16)
+    assert tuple(m.tile())[:2] == (32, 16)
     m16 = ph.Mesh(ph.make_config((16, 16, 16), (1, 1, 1), precision="fp32"))
     assert tuple(m16.tile())[:2] == (16, 16)
     m64 = ph.Mesh(ph.make_config((32, 32, 32), (1, 1, 1)))

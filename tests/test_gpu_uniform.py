@@ -164,3 +164,23 @@ def test_tma_and_plain_loads_bit_identical(precision, nx, nb, tile, monkeypatch)
         m.close()
     assert np.array_equal(out["tma"][0], out["plain"][0])
     assert out["tma"][1] == out["plain"][1]
+
+
+def test_default_chunks_fill_the_gpu_on_small_meshes():
+    """Default tiles march 16 planes; a uniform mesh too small to give two
+    CTAs per SM gets shorter chunks (down to 4 planes), and the result does
+    not depend on the chunk length."""
+    ph = _ph()
+    big = ph.Mesh(ph.make_config((32, 32, 32), (4, 4, 4)))
+    assert big.tile() == (16, 16, 16)
+    small = ph.Mesh(ph.make_config((32, 32, 32), (2, 2, 2)))
+    assert small.tile() == (16, 16, 4)
+    nx, nb = (32, 32, 32), (2, 2, 2)
+    geo = W.Geometry(nx, nb)
+    U = W.blast(geo, small.tree(), seed=8, radius=0.2)
+    fixed = ph.Mesh(ph.make_config(nx, nb, tile=(16, 16, 16)))
+    small.set_state(U)
+    fixed.set_state(U)
+    small.step(2)
+    fixed.step(2)
+    assert np.array_equal(small.get_state(), fixed.get_state())
