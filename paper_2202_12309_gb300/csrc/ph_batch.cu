@@ -23,6 +23,7 @@
 #include "ph_nvtx.h"
 #include "ph_internal.h"
 #include "ph_stage.cuh"
+#include "ph_stage_pair.cuh"
 
 namespace ph {
 
@@ -37,6 +38,8 @@ struct Member {
   long long off;  // element offset of the member's first block in each pool
   int nx[3], S[3], nb[3];
   int ntile[3];
+  int tile[2];    // the member's tile (TX, TY)
+  int pair;       // 1: the member runs the paired FP32 tile (32 x 16)
   int KC;
   int nleaf, leaf0;
   double idx[3];
@@ -110,49 +113,93 @@ __device__ __forceinline__ Phys<T> member_phys(const Member& M) {
   return P;
 }
 
-template <class T, int TX, int TY, bool TMA>
-__device__ bool batch_stage_phase(const BatchArgs<T>& a, int stage, const StageArgs<T>& nocap,
-                                  unsigned char* smem, double* red, unsigned& floors,
-                                  uint64_t* bars, int* failed, unsigned* parity) {
+// Pair mode (FP32, launch choice 32 x 16): members whose blocks tile into
+// 32 x 16 run the paired tile of ph_stage_pair.cuh, the others the one-cell
+// 16 x 16 tile with the same 256 threads.  Both share the ring at the start
+// of shared memory and the mbarriers and reduction scratch placed after the
+// larger of the two layouts.
+using OneCell16x256 = StageSmem<float, 16, 16, NV, PairSmem::NT>;
+struct PairBatchSmem {
+  static constexpr size_t body = PairSmem::body > OneCell16x256::body ? PairSmem::body : OneCell16x256::body;
+  static constexpr size_t red_off = (body + 15) / 16 * 16;
+  static constexpr size_t bar_off = red_off + 32 * sizeof(double);
+  static constexpr size_t bytes = bar_off + 4 * sizeof(uint64_t) + 128;
+};
+
+// Threads, shared memory and CTAs per SM (register budget) of the batch
+// kernel for a launch choice.
+template <class T, int TX, int TY>
+struct BatchTile {
+  static constexpr bool PAIR = sizeof(T) == 4 && TX == 32 && TY == 16;
+  using One = StageSmem<T, (PAIR ? 16 : TX), (PAIR ? 16 : TY)>;
+  static constexpr int NT = PAIR ? PairSmem::NT : One::NT;
+  static constexpr size_t bytes = PAIR ? PairBatchSmem::bytes : One::bytes;
+  static constexpr size_t red_off = PAIR ? PairBatchSmem::red_off : One::red_off;
+  static constexpr size_t bar_off = PAIR ? PairBatchSmem::bar_off : One::bar_off;
+  static constexpr int MINB = PAIR ? 2 : (sizeof(T) == 4 ? 3 : 0);
+};
+
+// The tile job of work item `it` in the given stage; returns the member.
+template <class T>
+__device__ __forceinline__ int batch_job(const BatchArgs<T>& a, int it, int stage, TileJob<T>& J) {
+  const int2 item = a.items[it];
+  const int g = item.x;
+  const int m = a.leaf_member[g];
+  const Member& M = a.mem[m];
+  const size_t bsize = (size_t)NV * M.S[0] * M.S[1] * M.S[2];
+  const size_t boff = (size_t)M.off + (size_t)(g - M.leaf0) * bsize;
+  int t = item.y;
+  const int tk = t / (M.ntile[0] * M.ntile[1]);
+  t -= tk * M.ntile[0] * M.ntile[1];
+  const int tj = t / M.ntile[0];
+  const int ti = t - tj * M.ntile[0];
+  J.Ub = (stage == 1 ? a.U0 : a.U1) + boff;
+  J.U0b = a.U0 + boff;
+  J.Uoutb = (stage == 1 ? a.U1 : a.U0) + boff;
+  for (int d = 0; d < 3; ++d) {
+    J.nx[d] = M.nx[d];
+    J.S[d] = M.S[d];
+  }
+  J.i0 = ti * M.tile[0];
+  J.j0 = tj * M.tile[1];
+  J.k0 = tk * M.KC;
+  J.k1 = min(J.k0 + M.KC, M.nx[2]);
+  J.idx1 = (T)M.idx[0];
+  J.idx2 = (T)M.idx[1];
+  J.idx3 = (T)M.idx[2];
+  J.dt = (T)a.sc[m].dt_next;
+  J.stage = stage;
+  J.want_rate = stage == 2;
+  J.leaf = g;
+  J.nbr27 = a.push ? a.nbr + 27 * g : nullptr;
+  J.pool = (stage == 1 ? a.U1 : a.U0) + M.off;
+  J.bsize = bsize;
+  return m;
+}
+
+template <class T, int TX, int TY, bool TMA, int STAGE>
+__device__ bool batch_stage_phase(const BatchArgs<T>& a, const StageArgs<T>& nocap, unsigned char* smem,
+                                  double* red, unsigned& floors, uint64_t* bars, int* failed,
+                                  unsigned* parity) {
   for (int it = blockIdx.x; it < a.nitems; it += gridDim.x) {
-    const int2 item = a.items[it];
-    const int g = item.x;
-    const int m = a.leaf_member[g];
-    const Member& M = a.mem[m];
-    const size_t bsize = (size_t)NV * M.S[0] * M.S[1] * M.S[2];
-    const size_t boff = (size_t)M.off + (size_t)(g - M.leaf0) * bsize;
-    int t = item.y;
-    const int tk = t / (M.ntile[0] * M.ntile[1]);
-    t -= tk * M.ntile[0] * M.ntile[1];
-    const int tj = t / M.ntile[0];
-    const int ti = t - tj * M.ntile[0];
     TileJob<T> J;
-    J.Ub = (stage == 1 ? a.U0 : a.U1) + boff;
-    J.U0b = a.U0 + boff;
-    J.Uoutb = (stage == 1 ? a.U1 : a.U0) + boff;
-    for (int d = 0; d < 3; ++d) {
-      J.nx[d] = M.nx[d];
-      J.S[d] = M.S[d];
+    const int m = batch_job<T>(a, it, STAGE, J);
+    const Member& M = a.mem[m];
+    const int vz0 = (J.leaf - M.leaf0) * NV;
+    const CUtensorMap* tm = TMA ? a.tmaps + 2 * m + (STAGE == 1 ? 0 : 1) : nullptr;
+    double rate;
+    if constexpr (BatchTile<T, TX, TY>::PAIR) {
+      static_assert(TMA, "pair mode stages planes by TMA");
+      if (M.pair)
+        rate = stage_tile_pair<STAGE>(J, member_phys<float>(M), smem, floors, tm, vz0, bars, failed, parity);
+      else
+        rate = stage_tile<float, 16, 16, true, NV, STAGE, PairSmem::NT>(J, member_phys<float>(M), nocap, smem,
+                                                                         floors, tm, vz0, bars, failed, parity);
+    } else {
+      rate = stage_tile<T, TX, TY, TMA>(J, member_phys<T>(M), nocap, smem, floors, tm, vz0, bars, failed, parity);
     }
-    J.i0 = ti * TX;
-    J.j0 = tj * TY;
-    J.k0 = tk * M.KC;
-    J.k1 = min(J.k0 + M.KC, M.nx[2]);
-    J.idx1 = (T)M.idx[0];
-    J.idx2 = (T)M.idx[1];
-    J.idx3 = (T)M.idx[2];
-    J.dt = (T)a.sc[m].dt_next;
-    J.stage = stage;
-    J.want_rate = stage == 2;
-    J.leaf = g;
-    J.nbr27 = a.push ? a.nbr + 27 * g : nullptr;
-    J.pool = (stage == 1 ? a.U1 : a.U0) + M.off;
-    J.bsize = bsize;
-    const CUtensorMap* tm = TMA ? a.tmaps + 2 * m + (stage == 1 ? 0 : 1) : nullptr;
-    const double rate = stage_tile<T, TX, TY, TMA>(J, member_phys<T>(M), nocap, smem, floors, tm,
-                                                   (g - M.leaf0) * NV, bars, failed, parity);
     if (TMA && *(volatile int*)failed) return false;  // every thread saw it after a barrier
-    if (stage == 2) block_max_to(&a.sc[m].wmax_bits, rate, red);
+    if (STAGE == 2) block_max_to(&a.sc[m].wmax_bits, rate, red);
     __syncthreads();  // the next item's priming overwrites the ring
   }
   return true;
@@ -186,9 +233,9 @@ __device__ void batch_ghost_phase(const BatchArgs<T>& a, T* U) {
 }
 
 template <class T, int TX, int TY, bool TMA>
-__global__ void __launch_bounds__(StageSmem<T, TX, TY>::NT, (sizeof(T) == 4 ? 3 : 0))
+__global__ void __launch_bounds__(BatchTile<T, TX, TY>::NT, BatchTile<T, TX, TY>::MINB)
 batch_cycle_kernel(const BatchArgs<T> a) {
-  using SM = StageSmem<T, TX, TY>;
+  using SM = BatchTile<T, TX, TY>;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
@@ -215,8 +262,8 @@ batch_cycle_kernel(const BatchArgs<T> a) {
   // a CTA whose plane wait gave up reports it and leaves; the others give
   // up at the next grid barrier (bounded), so nothing hangs
 #define PH_STAGE_OR_RETURN(st)                                                                \
-  if (!batch_stage_phase<T, TX, TY, TMA>(a, st, nocap, smem_raw, red, floors, bars, &failed,   \
-                                         &parity)) {                                          \
+  if (!batch_stage_phase<T, TX, TY, TMA, st>(a, nocap, smem_raw, red, floors, bars, &failed,   \
+                                             &parity)) {                                      \
     if (threadIdx.x == 0) atomicExch(&a.sc[0].error, 1);                                      \
     return;                                                                                   \
   }
@@ -280,7 +327,7 @@ __global__ void barrier_timeout_kernel(GridBar* gb, unsigned long long spin_limi
 
 template <class T, int TX, int TY>
 size_t batch_smem() {
-  return StageSmem<T, TX, TY>::bytes;
+  return BatchTile<T, TX, TY>::bytes;
 }
 
 }  // namespace ph
@@ -303,7 +350,8 @@ int bfail(int code, const std::string& msg) {
                                                          cudaGetErrorString(_e)); \
   } while (0)
 
-const int kTiles[4][2] = {{8, 8}, {16, 8}, {16, 16}, {32, 8}};
+// autotuner candidates; the last is the paired FP32 tile (pair mode)
+const int kTiles[5][2] = {{8, 8}, {16, 8}, {16, 16}, {32, 8}, {32, 16}};
 
 }  // namespace
 
@@ -361,13 +409,15 @@ int occupancy(int* per_sm) {
   cudaError_t e = set_attr<T, TX, TY, TMA>();
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ph::batch_cycle_kernel<T, TX, TY, TMA>,
-                                                    ph::StageSmem<T, TX, TY>::NT, ph::batch_smem<T, TX, TY>());
+                                                    ph::BatchTile<T, TX, TY>::NT, ph::batch_smem<T, TX, TY>());
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   return PH_OK;
 }
 
 template <class T, bool TMA>
 int occupancy_t(int TX, int TY, int* per_sm) {
+  if constexpr (sizeof(T) == 4 && TMA)
+    if (TX == 32 && TY == 16) return occupancy<T, 32, 16, TMA>(per_sm);
   if (TX == 8 && TY == 8) return occupancy<T, 8, 8, TMA>(per_sm);
   if (TX == 16 && TY == 8) return occupancy<T, 16, 8, TMA>(per_sm);
   if (TX == 16 && TY == 16) return occupancy<T, 16, 16, TMA>(per_sm);
@@ -396,7 +446,7 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   cudaLaunchConfig_t lc;
   std::memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(b->grid);
-  lc.blockDim = dim3(ph::StageSmem<T, TX, TY>::NT);
+  lc.blockDim = dim3(ph::BatchTile<T, TX, TY>::NT);
   lc.dynamicSmemBytes = ph::batch_smem<T, TX, TY>();
   lc.stream = s;
   cudaLaunchAttribute attr[1];
@@ -409,6 +459,8 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
 
 template <class T, bool TMA>
 cudaError_t launch_cycle_tt(ph_batch* b, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4 && TMA)
+    if (b->TX == 32 && b->TY == 16) return launch_cycle<T, 32, 16, TMA>(b, s);
   if (b->TX == 8 && b->TY == 8) return launch_cycle<T, 8, 8, TMA>(b, s);
   if (b->TX == 16 && b->TY == 8) return launch_cycle<T, 16, 8, TMA>(b, s);
   if (b->TX == 16 && b->TY == 16) return launch_cycle<T, 16, 16, TMA>(b, s);
@@ -421,17 +473,17 @@ cudaError_t launch_cycle_t(ph_batch* b, cudaStream_t s) {
   return b->tma ? launch_cycle_tt<T, true>(b, s) : launch_cycle_tt<T, false>(b, s);
 }
 
-// Tensor maps of every member's blocks in both pools for the tile (TX, TY);
+// Tensor maps of every member's blocks in both pools for the member's tile;
 // false if any member's geometry does not admit one (then plain loads).
-bool build_tmaps(ph_batch* b, int TX, int TY) {
+bool build_tmaps(ph_batch* b) {
   if (!ph::stage_tma_wanted() || !b->d_tmaps) return false;
   std::vector<CUtensorMap> maps(2 * (size_t)b->nsim);
   for (int m = 0; m < b->nsim; ++m) {
     const Member& M = b->mem[m];
     const char* u0 = (const char*)b->U0 + (size_t)M.off * b->esize;
     const char* u1 = (const char*)b->U1 + (size_t)M.off * b->esize;
-    if (!ph::make_stage_tmap(&maps[2 * m], u0, b->esize, M.S, M.nleaf, TX, TY) ||
-        !ph::make_stage_tmap(&maps[2 * m + 1], u1, b->esize, M.S, M.nleaf, TX, TY))
+    if (!ph::make_stage_tmap(&maps[2 * m], u0, b->esize, M.S, M.nleaf, M.tile[0], M.tile[1]) ||
+        !ph::make_stage_tmap(&maps[2 * m + 1], u1, b->esize, M.S, M.nleaf, M.tile[0], M.tile[1]))
       return false;
   }
   return cudaMemcpy(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
@@ -452,9 +504,31 @@ void drop_graph(ph_batch* b) {
   }
 }
 
+// Pair mode: FP32 with the launch choice 32 x 16 (paired tile where a member's
+// blocks tile into 32 x 16, one-cell 16 x 16 elsewhere); every member needs
+// blocks of at least 16 x 16 cells.
+bool pair_choice(const ph_batch* b, int TX, int TY) {
+  return b->precision == PH_FP32 && TX == 32 && TY == 16;
+}
+bool pair_possible(const ph_batch* b) {
+  if (b->precision != PH_FP32 || !ph::stage_tma_wanted()) return false;
+  for (const Member& M : b->mem)
+    if (M.nx[0] < 16 || M.nx[1] < 16) return false;
+  return true;
+}
+
 // Apply a launch choice: tiles per member, the cost-ordered work list, grid.
 int configure(ph_batch* b, int TX, int TY, int KC, int ctas) {
-  const bool tma = build_tmaps(b, TX, TY);
+  const bool pair = pair_choice(b, TX, TY);
+  if (pair && !pair_possible(b))
+    return bfail(PH_ERR_INVALID, "batch: the 32 x 16 paired tile needs FP32, TMA and blocks of 16 x 16 or more");
+  for (Member& M : b->mem) {
+    M.pair = pair && M.nx[0] % 32 == 0 && M.nx[1] % 16 == 0;
+    M.tile[0] = pair ? (M.pair ? 32 : 16) : TX;
+    M.tile[1] = pair ? 16 : TY;
+  }
+  const bool tma = build_tmaps(b);
+  if (pair && !tma) return bfail(PH_ERR_INVALID, "batch: the paired tile needs TMA staging");
   int per_sm = 0;
   int rc = b->precision == PH_FP32
                ? (tma ? occupancy_t<float, true>(TX, TY, &per_sm) : occupancy_t<float, false>(TX, TY, &per_sm))
@@ -476,8 +550,8 @@ int configure(ph_batch* b, int TX, int TY, int KC, int ctas) {
   std::vector<std::pair<long long, int2>> items;
   for (int m = 0; m < b->nsim; ++m) {
     Member& M = b->mem[m];
-    M.ntile[0] = (M.nx[0] + TX - 1) / TX;
-    M.ntile[1] = (M.nx[1] + TY - 1) / TY;
+    M.ntile[0] = (M.nx[0] + M.tile[0] - 1) / M.tile[0];
+    M.ntile[1] = (M.nx[1] + M.tile[1] - 1) / M.tile[1];
     M.KC = std::min(KC, M.nx[2]);
     M.ntile[2] = (M.nx[2] + M.KC - 1) / M.KC;
     const int per = M.ntile[0] * M.ntile[1] * M.ntile[2];
@@ -746,9 +820,11 @@ int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch*
     if (e) rc = bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   }
   if (!rc) {
+    // FP32: the paired tile where the members allow it; else 16 x 16 or 8 x 8
     int minn = 1 << 30;
     for (const Member& M : b->mem) minn = std::min(minn, std::min(M.nx[0], M.nx[1]));
-    const int TX = minn >= 16 ? 16 : 8, TY = minn >= 16 ? 16 : 8;
+    const bool pair = pair_possible(b);
+    const int TX = pair ? 32 : (minn >= 16 ? 16 : 8), TY = minn >= 16 ? 16 : 8;
     rc = configure(b, TX, TY, 32, 0);
   }
   if (rc) {
@@ -855,7 +931,8 @@ int ph_batch_get_launch(const ph_batch* b, int32_t choice[4]) {
 
 int ph_batch_set_launch(ph_batch* b, const int32_t choice[4]) {
   if (!b || !choice) return bfail(PH_ERR_INVALID, "ph_batch_set_launch: null argument");
-  if (!ph::stage_tile_supported(choice[0], choice[1]) || choice[2] < 1)
+  if (!(ph::stage_tile_supported(choice[0], choice[1]) || pair_choice(b, choice[0], choice[1])) ||
+      choice[2] < 1)
     return bfail(PH_ERR_INVALID, "ph_batch_set_launch: unsupported tile");
   return configure(b, choice[0], choice[1], choice[2], choice[3]);
 }
@@ -885,12 +962,14 @@ int ph_batch_autotune(ph_batch* b, int32_t trial_cycles, int32_t chosen[4]) {
   float best = 1e30f;
   int bc[4] = {b->TX, b->TY, b->KC, b->ctas_per_sm};
   int rc = PH_OK;
-  for (int t = 0; t < 4 && !rc; ++t) {
+  for (int t = 0; t < 5 && !rc; ++t) {
     const int TX = kTiles[t][0], TY = kTiles[t][1];
-    if (TX > 2 * minn || TY > minn) continue;
+    const bool pair = pair_choice(b, TX, TY);
+    if (pair ? !pair_possible(b) : (t == 4 || TX > 2 * minn || TY > minn)) continue;
     int per_sm = 0;
     // an upper bound for the CTA count; configure() clamps to the variant it picks
-    rc = b->precision == PH_FP32 ? occupancy_t<float, false>(TX, TY, &per_sm)
+    rc = b->precision == PH_FP32 ? (pair ? occupancy_t<float, true>(TX, TY, &per_sm)
+                                         : occupancy_t<float, false>(TX, TY, &per_sm))
                                  : occupancy_t<double, false>(TX, TY, &per_sm);
     if (rc) break;
     const int kcs[3] = {8, 16, 32};

@@ -78,7 +78,9 @@ __device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int fac
   }
 }
 
-template <class T, int TX, int TY, int NVT = NV>
+// NTO: thread count of the CTA when the tile runs inside a kernel of another
+// size (0: the tile's own choice below).
+template <class T, int TX, int TY, int NVT = NV, int NTO = 0>
 struct StageSmem {
   static constexpr int WX = TX + 4, WY = TY + 4;
   // threads.  FP32 (issue-bound): enough for the largest per-plane work list
@@ -87,7 +89,7 @@ struct StageSmem {
   // FP64 (bound by the FP64 pipe): one thread per cell, no cap (the extra warp
   // and the cap cost more FP64 pipe time in spills than the balance saves).
   static constexpr int NT0 = (TX + 2) * TY > TX * (TY + 2) ? (TX + 2) * TY : TX * (TY + 2);
-  static constexpr int NT = sizeof(T) == 4 ? (NT0 + 31) / 32 * 32 : TX * TY;
+  static constexpr int NT = NTO ? NTO : (sizeof(T) == 4 ? (NT0 + 31) / 32 * 32 : TX * TY);
   // resident CTAs per SM the registers are allocated for (FP32: 3; FP64: left
   // to the compiler, which keeps 2 CTAs of 256 threads without spills)
   static constexpr int MINB = sizeof(T) == 4 ? 3 : 0;
@@ -209,15 +211,15 @@ __device__ __forceinline__ void vanleer_all(const T wm[NVT], const T w0[NVT], co
 
 
 // STAGE: 1 or 2 fixes the stage at compile time (its own register
-// allocation); 0 takes it from J.stage.
-template <class T, int TX, int TY, bool TMA, int NVT = NV, int STAGE = 0>
+// allocation); 0 takes it from J.stage.  NTO: see StageSmem.
+template <class T, int TX, int TY, bool TMA, int NVT = NV, int STAGE = 0, int NTO = 0>
 __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>& P,
                                              const StageArgs<T>& a, unsigned char* smem_raw,
                                              unsigned& floors, const CUtensorMap* tmap = nullptr,
                                              int vz0 = 0, uint64_t* bars = nullptr,
                                              int* failed = nullptr,
                                              unsigned* parity_io = nullptr) {
-  using SM = StageSmem<T, TX, TY, NVT>;
+  using SM = StageSmem<T, TX, TY, NVT, NTO>;
   constexpr int NT = SM::NT;        // threads of the CTA
   constexpr int NC = TX * TY;       // threads that own a cell of the tile
   constexpr int FP = SM::FP;

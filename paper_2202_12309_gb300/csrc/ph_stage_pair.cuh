@@ -235,12 +235,13 @@ struct PairSmem {
 // tile's max signal rate when J.want_rate.
 // STAGE (1 or 2) is a template argument: the two stages keep different
 // values live across the plane (stage 2 also U0), and each gets its own
-// register allocation.
+// register allocation.  parity_io (optional): the mbarrier phase bits,
+// carried across calls by a CTA that runs several tiles on the same barriers.
 template <int STAGE>
 __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const Phys<float>& P,
                                                   unsigned char* smem_raw, unsigned& floors,
                                                   const CUtensorMap* tmap, int vz0, uint64_t* bars,
-                                                  int* failed) {
+                                                  int* failed, unsigned* parity_io = nullptr) {
   using SM = PairSmem;
   constexpr int TX = SM::TX, TY = SM::TY, NT = SM::NT, WX = SM::WX, WY = SM::WY, FPX = SM::FPX;
   float* ring = reinterpret_cast<float*>(smem_raw);
@@ -259,7 +260,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
   const size_t vstride = (size_t)J.S[0] * J.S[1] * J.S[2];
 
-  unsigned parity = 0;
+  unsigned parity = parity_io ? *parity_io : 0u;
   auto issue = [&](int p) {
     if (tid == 0) {
       const int sl = (p + 4) & 3;
@@ -482,6 +483,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       }
     }
   }
+  if (parity_io) *parity_io = parity;
   return rate;
 }
 

@@ -55,10 +55,18 @@ def test_batch_matches_single_meshes_bit_exact(precision):
     dts = B.dt()
     t, cyc = B.time()
     assert np.all(cyc == 4)
+    launch = B.launch()
     for s, (cfg, U) in enumerate(zip(cfgs, states)):
-        # the batch runs the one-cell stage kernel; FP32 single meshes default
-        # to the paired one, which rounds differently, so pin the tile
-        cfg.tile[:] = [16, 16, cfg.nx[2]]
+        # FP32 batches run the paired tile for members whose blocks tile into
+        # 32 x 16 and the one-cell 16 x 16 tile for the others (pair mode);
+        # FP64 batches the one-cell tile of the launch choice.  The single
+        # mesh is pinned to the same kernel (the two round differently).
+        if precision == "fp32":
+            assert tuple(launch[:2]) == (32, 16)
+            pair = cfg.nx[0] % 32 == 0 and cfg.nx[1] % 16 == 0
+            cfg.tile[:] = [32 if pair else 16, 16, cfg.nx[2]]
+        else:
+            cfg.tile[:] = [16, 16, cfg.nx[2]]
         m = ph.Mesh(cfg)
         m.set_state(U.astype(dtype))
         m.step(4)
@@ -101,7 +109,10 @@ def test_batch_autotune_keeps_results():
     for s in range(len(cfgs)):
         assert np.array_equal(B.get_state(s), before[s])
     B.step(2)
+    # the same launch choice from the start gives the same bits (the paired
+    # and one-cell FP32 tiles round differently, so the choice matters)
     ref = ph.Batch(cfgs)
+    ref.set_launch(choice)
     for s, U in enumerate(states):
         ref.set_state(s, U.astype(np.float32))
     ref.step(4)
