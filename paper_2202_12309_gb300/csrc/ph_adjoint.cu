@@ -673,13 +673,15 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   T* seg0 = alloc(bytes * ckpt);
   T* seg1 = alloc(bytes * ckpt);
   double* gbar = (double*)alloc(sizeof(double) * 2);
+  double* d_dts = (double*)alloc(sizeof(double) * ncycles);
+  DevScalars* sc_final = (DevScalars*)alloc(sizeof(DevScalars));
   T* packed = alloc(sizeof(T) * (size_t)A.nleaf * NV * A.nx[0] * A.nx[1] * A.nx[2]);
   for (void* p : bufs)
     if (!p) {
       cleanup();
       return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
     }
-  if (bufs.size() != 15) {
+  if (bufs.size() != 17) {
     cleanup();
     return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
   }
@@ -688,20 +690,28 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
     cleanup();
     return code;
   };
-  // ---- forward with checkpoints (records the dt schedule when not given)
+  // ---- forward with checkpoints; the dt schedule (given, or recorded from
+  // the CFL dts) lives in device memory, so no cycle waits for the host
   if ((rc = mesh_set_state(m, U0, on_device))) return fail_clean(rc);
   std::vector<double> dts(ncycles);
+  if (dts_in) {
+    for (int c = 0; c < ncycles; ++c) dts[c] = dts_in[c];
+    PA_CUDA(cudaMemcpyAsync(d_dts, dts.data(), sizeof(double) * ncycles, cudaMemcpyHostToDevice, s));
+  }
   for (int c = 0; c < ncycles; ++c) {
     if (c % ckpt == 0)
       PA_CUDA(cudaMemcpyAsync(ck + (size_t)(c / ckpt) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
-    if (dts_in) {
-      dts[c] = dts_in[c];
-      if ((rc = mesh_cycle_fixed_dt(m, dts[c]))) return fail_clean(rc);
-    } else if ((rc = mesh_cycle_read_dt(m, &dts[c]))) {
-      return fail_clean(rc);
-    }
+    rc = dts_in ? mesh_cycle_device_dt(m, d_dts + c) : mesh_cycle_record_dt(m, d_dts + c);
+    if (rc) return fail_clean(rc);
+  }
+  if (!dts_in) {
+    PA_CUDA(cudaMemcpyAsync(dts.data(), d_dts, sizeof(double) * ncycles, cudaMemcpyDeviceToHost, s));
+    PA_CUDA(cudaStreamSynchronize(s));
   }
   PA_CUDA(cudaMemcpyAsync(ufinal, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+  // the recomputation below advances the mesh's clock again: keep the
+  // forward run's time, cycle count and dts to restore at the end
+  PA_CUDA(cudaMemcpyAsync(sc_final, A.sc, sizeof(DevScalars), cudaMemcpyDeviceToDevice, s));
   // ---- seed: dL/dU_final on interior cells, zero ghosts
   PA_CUDA(cudaMemsetAsync(lam, 0, bytes, s));
   if (on_device) {
@@ -728,7 +738,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
     PA_CUDA(cudaMemcpyAsync(A.U0, ck + (size_t)sg * elems, bytes, cudaMemcpyDeviceToDevice, s));
     for (int c = c0; c < c1; ++c) {
       PA_CUDA(cudaMemcpyAsync(seg0 + (size_t)(c - c0) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
-      if ((rc = mesh_cycle_fixed_dt(m, dts[c]))) return fail_clean(rc);
+      if ((rc = mesh_cycle_device_dt(m, d_dts + c))) return fail_clean(rc);
       PA_CUDA(cudaMemcpyAsync(seg1 + (size_t)(c - c0) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
     }
     for (int c = c1 - 1; c >= c0; --c) {
@@ -759,6 +769,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   double hg = 0.0;
   PA_CUDA(cudaMemcpyAsync(&hg, gbar, sizeof(double), cudaMemcpyDeviceToHost, s));
   PA_CUDA(cudaMemcpyAsync(A.U0, ufinal, bytes, cudaMemcpyDeviceToDevice, s));
+  PA_CUDA(cudaMemcpyAsync(A.sc, sc_final, sizeof(DevScalars), cudaMemcpyDeviceToDevice, s));
   PA_CUDA(cudaStreamSynchronize(s));
   if (dLdgamma) *dLdgamma = hg;
   cleanup();

@@ -960,6 +960,26 @@ int mesh_set_state(ph_mesh* m, const void* U, int on_device) {
 
 int mesh_cycle_fixed_dt(ph_mesh* m, double dt) { return DISPATCH(m, cycle_fixed_dt_t, m, dt); }
 
+// One cycle with the dt read from device memory (stream-ordered, no host
+// synchronisation): the cycle graph runs on the dt the copy leaves in place.
+int mesh_cycle_device_dt(ph_mesh* m, const double* d_dt) {
+  if (!m->gexec) {
+    const int rc = DISPATCH(m, capture_graph, m);
+    if (rc) return rc;
+  }
+  PH_CUDA(cudaMemcpyAsync(&m->sc->dt_next, d_dt, sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  PH_CUDA(cudaGraphLaunch(m->gexec, m->stream));
+  return PH_OK;
+}
+
+// One CFL cycle; its dt is copied to device memory d_dt (stream-ordered).
+int mesh_cycle_record_dt(ph_mesh* m, double* d_dt) {
+  const int rc = DISPATCH(m, step_t, m, 1);
+  if (rc) return rc;
+  PH_CUDA(cudaMemcpyAsync(d_dt, &m->sc->dt_last, sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  return PH_OK;
+}
+
 int mesh_cycle_read_dt(ph_mesh* m, double* dt) {
   int rc = DISPATCH(m, step_t, m, 1);
   if (rc) return rc;

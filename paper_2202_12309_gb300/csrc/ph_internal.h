@@ -29,6 +29,10 @@ int mesh_access(ph_mesh* m, MeshAccess* out);
 int mesh_set_state(ph_mesh* m, const void* U, int on_device);
 int mesh_cycle_fixed_dt(ph_mesh* m, double dt);   // one cycle with a prescribed dt
 int mesh_cycle_read_dt(ph_mesh* m, double* dt);   // one CFL cycle, returns its dt
+// Stream-ordered forms without host synchronisation: one cycle with the dt
+// at device address d_dt; one CFL cycle whose dt is stored at d_dt.
+int mesh_cycle_device_dt(ph_mesh* m, const double* d_dt);
+int mesh_cycle_record_dt(ph_mesh* m, double* d_dt);
 // Device memory from the mesh's allocator (NULL on failure); mesh_free
 // returns it (stream-ordered on the mesh's stream, as the allocator is).
 void* mesh_alloc(ph_mesh* m, size_t bytes);

@@ -222,3 +222,24 @@ def test_adjoint_element_by_element(ckpt):
     assert big.sum() >= U0.size // 2
     assert (err[big] / np.abs(ref[big])).max() <= 1e-8
     assert abs(gg - ref_g) <= 1e-10 * abs(ref_g), (gg, ref_g)
+
+
+def test_adjoint_leaves_the_forward_run_final_state_and_clock():
+    """After ph_adjoint the mesh holds the forward run's final state, time,
+    cycle count and dt (the recomputation inside does not advance them)."""
+    torch, ph = _ph()
+    nx, nb, n = (8, 8, 8), (2, 2, 1), 6
+    cfg = ph.make_config(nx, nb)
+    geo = W.Geometry(nx, nb)
+    U0 = generic_state(geo, ph.Mesh(cfg).tree())
+    ref = ph.Mesh(cfg)
+    ref.set_state(U0)
+    ref.step(n)
+    m = ph.Mesh(cfg)
+    m.adjoint(U0, np.ones_like(U0), n, 4)
+    assert np.array_equal(m.get_state(), ref.get_state())
+    assert m.time() == ref.time()
+    assert m.dt() == ref.dt() and m.next_dt() == ref.next_dt()
+    m.step(2)
+    ref.step(2)
+    assert np.array_equal(m.get_state(), ref.get_state())

@@ -61,15 +61,18 @@ def test_uniform_256cube_one_cycle(oracle_256, precision):
 
 def _cycle_against_oracle(m, om, c):
     """Tree and refinement flags bit for bit, state within 1e-12 per field.
-    The indicator is computed from each side's own state, which agree to
-    rounding, so it agrees to 1e-10 (a flag decided that close to a
-    tolerance would be a near-threshold event, reported as such)."""
+    The indicator, |rho_{+1} - rho_{-1}| / (2 rho), is computed from each
+    side's own state; with densities of order 1 that agree to ~1e-15 the
+    indicators agree to ~1e-15 absolute, whatever their size (a difference
+    quotient of nearly equal densities, ~5e-6 for the sound wave), so the
+    check is absolute: 1e-11.  A flag decided that close to a tolerance would
+    be a near-threshold event, reported as such."""
     assert np.array_equal(m.tree(), om.tree()), "cycle %d: tree" % c
     gf, gmb = m.tag()
     of, omb = om.tag()
     near = np.min(np.abs(omb - 0.05)), np.min(np.abs(omb - 0.0125))
     assert np.array_equal(gf, of), "cycle %d: flags (closest to a tolerance: %.3g, %.3g)" % ((c,) + near)
-    assert np.all(np.abs(gmb - omb) <= 1e-10 * np.abs(omb).max()), "cycle %d: indicator" % c
+    assert np.abs(gmb - omb).max() <= 1e-11, "cycle %d: indicator %.3g" % (c, np.abs(gmb - omb).max())
     err, plain = field_errors(m.get_state(), om.get_state(), with_plain=True)
     assert err.max() <= 1e-12, "cycle %d: %s" % (c, describe(err, plain))
 

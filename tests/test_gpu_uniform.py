@@ -170,7 +170,8 @@ def test_default_chunks_fill_the_gpu_on_small_meshes():
     """Default tiles march 16 planes; a uniform mesh too small to give two
     CTAs per SM gets shorter chunks (down to 4 planes), and the result does
     not depend on the chunk length."""
-    ph = _ph()
+    _torch()
+    import paper_2202_12309_gb300 as ph
     big = ph.Mesh(ph.make_config((32, 32, 32), (4, 4, 4)))
     assert big.tile() == (16, 16, 16)
     small = ph.Mesh(ph.make_config((32, 32, 32), (2, 2, 2)))
