@@ -251,11 +251,13 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   float* sfy = sfx + SM::FXN;
   const int tid = threadIdx.x;
   const int tx = 2 * (tid & 15), ty = tid >> 4;  // own cells (tx, tx+1) of row ty
-  // Work lists that leave a partial second round start on different warps,
-  // so that no warp takes two extra rounds in one barrier interval: the x1
-  // slope and face lists at warp 0, the x2 ones at warp 1, the conversion
-  // of a staged plane at warp 2.
-  const int trot = (tid + NT - 32) % NT, crot = (tid + NT - 64) % NT;
+  // Work lists: every thread's main item in every list is its own pair;
+  // the halo items of a list go to one warp (x1 slopes: warp 0, x2 slopes:
+  // warp 1, x1 faces: warp 2, x2 faces: warp 3, conversion: the last 104
+  // threads), so index arithmetic is shifts of the thread index.
+  constexpr int CEXTRA = 4 * (WX / 2) + 2 * TY;
+  static_assert(CEXTRA <= NT, "conversion halo fits one round");
+  const int warp = tid >> 5, lane = tid & 31;
   const int S1 = J.S[0], S2 = J.S[1];
   const int i0 = J.i0, j0 = J.j0, k0 = J.k0, k1 = J.k1;
   const size_t vstride = (size_t)J.S[0] * J.S[1] * J.S[2];
@@ -273,14 +275,24 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     const bool ok = mbar_wait(bars + sl, (parity >> sl) & 1u, 1u << 22);
     parity ^= 1u << sl;
     float* dst = ring + sl * SM::SLOT;
-    for (int c = crot; c < WY * (WX / 2); c += NT) {
-      const int r = c / (WX / 2), q = 2 * (c - r * (WX / 2));
+    auto conv = [&](int r, int q) {
       F2 w[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v] = ld2(dst + (v * WY + r) * WX + q);
       cons_to_prim2(w, P, floors);
 #pragma unroll
       for (int v = 0; v < NV; ++v) st2(dst + (v * WY + r) * WX + q, w[v]);
+    };
+    conv(ty + 2, tx + 2);  // own pair
+    if (tid >= NT - CEXTRA) {  // plane rows 0, 1, TY+2, TY+3 and the x1 halo columns
+      const int e = tid - (NT - CEXTRA);
+      if (e < 4 * (WX / 2)) {
+        const int rr = e / (WX / 2);
+        conv(rr < 2 ? rr : rr + TY, 2 * (e - rr * (WX / 2)));
+      } else {
+        const int t = e - 4 * (WX / 2);
+        conv(2 + (t >> 1), (t & 1) ? WX - 2 : 0);
+      }
     }
     return ok;
   };
@@ -376,25 +388,26 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       }
     }
     const float* W = ring + ((k + 4) & 3) * SM::SLOT;
-    // (C2) x1 slopes of plane positions (2q, 2q+1), q = 0..WX/2-1 (cells -2..TX+1;
-    // the outermost lanes read clamped neighbours and are never used)
-    for (int c = tid; c < TY * (WX / 2); c += NT) {
-      const int jj = c / (WX / 2), q = 2 * (c - jj * (WX / 2));
+    // (C2) x1 slopes at plane positions (q, q+1): own pair q = tx + 2; the
+    // halo pairs q = 0 and WX-2 of each row (their outermost lanes read
+    // clamped neighbours and are never used)
+    auto x1_slope = [&](int jj, int q, bool edge) {
       F2 a[NV], b[NV], r[NV], h[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const float* row = W + (v * WY + jj + 2) * WX;
         b[v] = ld2(row + q);
-        a[v] = f2(row[q > 0 ? q - 1 : 0], lane0(b[v]));
-        r[v] = f2(lane1(b[v]), row[q + 2 < WX ? q + 2 : WX - 1]);
+        const float lo = edge ? row[q > 0 ? q - 1 : 0] : row[q - 1];
+        const float hi = edge ? row[q + 2 < WX ? q + 2 : WX - 1] : row[q + 2];
+        a[v] = f2(lo, lane0(b[v]));
+        r[v] = f2(lane1(b[v]), hi);
       }
       vanleer_half5_2(a, b, r, h);
 #pragma unroll
       for (int v = 0; v < NV; ++v) st2(sdx + (v * TY + jj) * WX + q, h[v]);
-    }
-    // (C3) x2 slopes of rows -1..TY, column pairs
-    for (int c = trot; c < (TY + 2) * (TX / 2); c += NT) {
-      const int jj = c / (TX / 2), q = 2 * (c - jj * (TX / 2));
+    };
+    // (C3) x2 slopes of rows jj - 1 (jj = 0 .. TY + 1), column pair q
+    auto x2_slope = [&](int jj, int q) {
       F2 a[NV], b[NV], r[NV], h[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -406,11 +419,14 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       vanleer_half5_2(a, b, r, h);
 #pragma unroll
       for (int v = 0; v < NV; ++v) st2(sdy + (v * (TY + 2) + jj) * TX + q, h[v]);
-    }
+    };
+    x1_slope(ty, tx + 2, false);
+    x2_slope(ty + 1, tx);
+    if (warp == 0) x1_slope(lane >> 1, (lane & 1) ? WX - 2 : 0, true);
+    if (warp == 1) x2_slope((lane >> 4) ? TY + 1 : 0, 2 * (lane & 15));
     __syncthreads();
     // (E1) x1 face pairs (f, f+1), f even; face f joins cells f-1 and f
-    for (int c = tid; c < TY * (FPX / 2); c += NT) {
-      const int jj = c / (FPX / 2), f = 2 * (c - jj * (FPX / 2));
+    auto x1_face = [&](int jj, int f) {
       F2 wl[NV], wr[NV], fl[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -424,10 +440,9 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       hlle2<0>(wl, wr, P, fl);
 #pragma unroll
       for (int v = 0; v < NV; ++v) st2(sfx + (v * TY + jj) * FPX + f, fl[v]);
-    }
-    // (E2) x2 faces between rows g-1 and g, column pairs
-    for (int c = trot; c < (TY + 1) * (TX / 2); c += NT) {
-      const int g = c / (TX / 2), q = 2 * (c - g * (TX / 2));
+    };
+    // (E2) x2 faces between rows g-1 and g, column pair q
+    auto x2_face = [&](int g, int q) {
       F2 wl[NV], wr[NV], fl[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
@@ -439,7 +454,11 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       hlle2<1>(wl, wr, P, fl);
 #pragma unroll
       for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + g) * TX + q, fl[v]);
-    }
+    };
+    x1_face(ty, tx);
+    x2_face(ty, tx);
+    if (warp == 2 && lane < TY) x1_face(lane, TX);
+    if (warp == 3 && lane < TX / 2) x2_face(TY, 2 * lane);
     // (F) plane k+3 into the slot of plane k-1; then plane k+4 into the slot of plane k
     {
       const bool ok = k + 3 <= k1 + 1 ? convert(k + 3) : true;
