@@ -307,6 +307,93 @@ int ph_batch_autotune(ph_batch* batch, int32_t trial_cycles, int32_t chosen[4]);
  * still usable. */
 int ph_debug_barrier_timeout(void* stream, int32_t nctas, int64_t spin_limit, int32_t* gave_up);
 
+/* ---------------------------------------------------------------------------
+ * Domain decomposition (Sec. 2.1: MeshBlocks are distributed over ranks as
+ * contiguous ranges of the Z-ordered block list; Sec. 3.7: ghost zones of
+ * blocks whose neighbours live elsewhere are filled by packing buffers on the
+ * sender, sending them and unpacking on the receiver; Sec. 3.10: dt is a
+ * global min-reduction).  Uniform meshes (max_level 0), any boundaries.
+ *
+ * A shard is a mesh holding shard s of nshards: the global leaves
+ * [s N / P, (s + 1) N / P) of the Z-ordered root grid (N blocks, P shards),
+ * in that order.  Its state calls (ph_set_state, ph_get_state, ph_totals,
+ * ph_tree) cover its own leaves only.  Its ghost cells whose source lies on
+ * another shard come from the halo exchange: a per-cell plan, ordered by the
+ * receiving cell's (global leaf, padded cell index) on both sides, so a
+ * sender's slab for a peer and the peer's slab from it list the same cells
+ * in the same order.  Messages hold nvar values per entry (entries x nvar
+ * elements of the mesh's precision).  ph_step, ph_step_dt, ph_adjoint,
+ * ph_save and ph_profile_cycles refuse shards (PH_ERR_STATE / _INVALID).
+ *
+ * One cycle of every shard, as ph_shards_step runs it for shards of one
+ * process and as a caller with its own transport (one process per GPU)
+ * writes it:
+ *   ph_shard_stage(m, 1); ph_shard_pack(m, 1, send); exchange; ph_shard_unpack(m, 1, recv);
+ *   ph_shard_stage(m, 2); ph_shard_pack(m, 0, send); exchange; ph_shard_unpack(m, 0, recv);
+ *   ph_shard_rate(m, 0, r); r = max over shards; ph_shard_finish(m, 0, r);
+ * and after ph_set_state on every shard (whose dt is then its own shard's):
+ *   ph_shard_pack(m, 0, ...); exchange; ph_shard_unpack(m, 0, ...);
+ *   ph_shard_rate(m, 1, r); r = max over shards; ph_shard_finish(m, 1, r).
+ * Every call is stream-ordered on the shard's stream and returns without
+ * waiting; buffers are device pointers.
+ * ------------------------------------------------------------------------- */
+
+/* Create shard `shard` of `nshards` (1 <= nshards <= blocks) of the uniform
+ * mesh `cfg`, on `stream`.  nshards = 1 is ph_create.  Errors as ph_create;
+ * PH_ERR_INVALID for max_level > 0 or a bad shard. */
+int ph_create_shard(const ph_config* cfg, int32_t nshards, int32_t shard, void* stream, ph_mesh** out);
+
+/* Halo of a shard with one peer: entries it sends to / receives from `peer`
+ * and their offsets (in entries) in its send / receive buffers, which hold
+ * every peer's slab in peer order; leaf_range (may be NULL) receives the
+ * shard's global leaves [first, last).  Any output may be NULL. */
+int ph_shard_halo(const ph_mesh* m, int32_t peer, int64_t* send_entries, int64_t* send_offset,
+                  int64_t* recv_entries, int64_t* recv_offset, int64_t leaf_range[2]);
+
+/* Stage `stage` (1 or 2) of the cycle on the shard's leaves, followed by the
+ * ghost cells whose sources are its own leaves (and physical boundaries). */
+int ph_shard_stage(ph_mesh* m, int32_t stage);
+
+/* One launch packing every outgoing halo value of pool (0: the state U0,
+ * after stage 2 or ph_set_state; 1: the stage-1 result) into sendbuf; one
+ * launch unpacking every incoming value from recvbuf into that pool's ghost
+ * cells (the normal momentum negated where the image crossed a reflecting
+ * wall).  Buffers: device, layout of ph_shard_halo. */
+int ph_shard_pack(ph_mesh* m, int32_t pool, void* sendbuf);
+int ph_shard_unpack(ph_mesh* m, int32_t pool, const void* recvbuf);
+
+/* The shard's largest signal rate max (|v_d| + c)/dx_d, as one double at
+ * device address d_rate: recompute = 0 takes the one the last stage 2 folded
+ * in, 1 computes it from the state (after ph_set_state and its exchange). */
+int ph_shard_rate(ph_mesh* m, int32_t recompute, double* d_rate);
+
+/* Time-step bookkeeping with the global rate at device address d_rate (the
+ * max over shards of ph_shard_rate): first = 0 commits the cycle (time, cycle
+ * count) and sets the next dt = cfl / rate; first = 1 sets the first dt of a
+ * fresh state. */
+int ph_shard_finish(ph_mesh* m, int32_t first, const double* d_rate);
+
+/* All shards of one mesh in this process (shards[s] is shard s of n; they
+ * may live on different devices, each on its own stream): the exchange is a
+ * device copy (cudaMemcpyPeerAsync) into each receiver's own buffer and the
+ * dt reduction runs on shard 0's device.  ph_shards_sync after ph_set_state
+ * on every shard (ghost exchange and the global first dt); ph_shards_step
+ * advances ncycles.  Neither waits for the GPU.
+ * Errors: PH_ERR_INVALID (not the n shards of one mesh), PH_ERR_STATE (a
+ * shard without a state), PH_ERR_CUDA. */
+int ph_shards_sync(ph_mesh* const* shards, int32_t n);
+int ph_shards_step(ph_mesh* const* shards, int32_t n, int32_t ncycles);
+
+/* The halo plan of shard `shard` with `peer`, from the configuration alone
+ * (host computation, no device work): the keys (global leaf x padded cells +
+ * padded cell index of the receiving ghost cell) it sends to and receives
+ * from the peer, in message order.  *nsend / *nrecv hold the capacities of
+ * send_keys / recv_keys (either array may be NULL to query the counts) and
+ * receive the counts; leaf_range (may be NULL) the shard's global leaves.
+ * Errors: PH_ERR_INVALID (bad shard or peer, capacity too small). */
+int ph_shard_plan(const ph_config* cfg, int32_t nshards, int32_t shard, int32_t peer, int64_t* send_keys,
+                  int64_t* nsend, int64_t* recv_keys, int64_t* nrecv, int64_t leaf_range[2]);
+
 /* Outputs and restarts (Sec. 3.9: outputs of single or double precision, and
  * a restart type from which a run continues bitwise identically).
  *

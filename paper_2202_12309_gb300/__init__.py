@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Optional, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -34,6 +34,8 @@ EXPORTS = [
     "ph_batch_status", "ph_batch_get_launch", "ph_batch_set_launch", "ph_batch_autotune",
     "ph_debug_barrier_timeout", "ph_step_dt", "ph_adjoint", "ph_debug_math", "ph_debug_fma_rate",
     "ph_save", "ph_load", "ph_set_state_async", "ph_get_state_async",
+    "ph_create_shard", "ph_shard_halo", "ph_shard_stage", "ph_shard_pack", "ph_shard_unpack",
+    "ph_shard_rate", "ph_shard_finish", "ph_shards_sync", "ph_shards_step", "ph_shard_plan",
 ]
 
 
@@ -169,6 +171,18 @@ def lib():
             "ph_set_state_async": [P, P, i64, i32],
             "ph_get_state_async": [P, P, i64, i32],
             "ph_load": [ctypes.c_char_p, P, ctypes.POINTER(P)],
+            "ph_create_shard": [ctypes.POINTER(Config), i32, i32, P, ctypes.POINTER(P)],
+            "ph_shard_halo": [P, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                              ctypes.POINTER(i64), ctypes.POINTER(i64)],
+            "ph_shard_stage": [P, i32],
+            "ph_shard_pack": [P, i32, P],
+            "ph_shard_unpack": [P, i32, P],
+            "ph_shard_rate": [P, i32, P],
+            "ph_shard_finish": [P, i32, P],
+            "ph_shards_sync": [ctypes.POINTER(P), i32],
+            "ph_shards_step": [ctypes.POINTER(P), i32, i32],
+            "ph_shard_plan": [ctypes.POINTER(Config), i32, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                              ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -260,7 +274,8 @@ def _check_buffer(x, count: int, itemsize: int, what: str):
 class Mesh:
     """A GPU mesh (uniform or two-level) with its conserved state."""
 
-    def __init__(self, cfg: Config, stream: Optional[int] = None):
+    def __init__(self, cfg: Config, stream: Optional[int] = None, shard: Optional[Tuple[int, int]] = None):
+        """shard = (nshards, s): shard s of the uniform mesh cfg (ph_create_shard)."""
         if stream is None:
             import torch
             if not torch.cuda.is_available():
@@ -269,7 +284,11 @@ class Mesh:
         self.L = lib()
         self.cfg = cfg
         self.h = ctypes.c_void_p()
-        check(self.L.ph_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(self.h)))
+        if shard is None:
+            check(self.L.ph_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(self.h)))
+        else:
+            check(self.L.ph_create_shard(ctypes.byref(cfg), int(shard[0]), int(shard[1]), ctypes.c_void_p(stream),
+                                         ctypes.byref(self.h)))
         self.nx = tuple(cfg.nx)
         self.nvar = 5 + int(cfg.nscalars)
         self.dtype = np.float32 if cfg.precision == PH_FP32 else np.float64
@@ -655,3 +674,179 @@ def hydro_run(U0, gamma, cfg: Config, ncycles: int, ckpt_every: int = 5):
     if "_HydroRun" not in globals():
         _HydroRun = _hydro_run_function()
     return _HydroRun.apply(U0, gamma, cfg, ncycles, ckpt_every)
+
+
+# ---------------------------------------------------------------------------
+# Domain decomposition (ph_create_shard and the ph_shard_* calls): argument
+# marshalling for shards of one process (ShardedMesh) and for one shard per
+# process over torch.distributed (DistShard).
+# ---------------------------------------------------------------------------
+
+def shard_plan(cfg: Config, nshards: int, shard: int, peer: int):
+    """ph_shard_plan (host only, no GPU needed): the receiving-cell keys that
+    `shard` sends to and receives from `peer`, and its global leaf range."""
+    L = lib()
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    ns, nr = ctypes.c_int64(0), ctypes.c_int64(0)
+    rng = (ctypes.c_int64 * 2)()
+    check(L.ph_shard_plan(ctypes.byref(cfg), nshards, shard, peer, None, ctypes.byref(ns), None,
+                          ctypes.byref(nr), rng))
+    send = np.zeros(ns.value, dtype=np.int64)
+    recv = np.zeros(nr.value, dtype=np.int64)
+    check(L.ph_shard_plan(ctypes.byref(cfg), nshards, shard, peer, send.ctypes.data_as(i64p), ctypes.byref(ns),
+                          recv.ctypes.data_as(i64p), ctypes.byref(nr), rng))
+    return send, recv, (int(rng[0]), int(rng[1]))
+
+
+class Shard(Mesh):
+    """Shard s of nshards of a uniform mesh: a mesh of its own leaves."""
+
+    def __init__(self, cfg: Config, nshards: int, s: int, stream: Optional[int] = None):
+        super().__init__(cfg, stream=stream, shard=(nshards, s))
+        self.nshards, self.shard = int(nshards), int(s)
+
+    def halo(self, peer: int):
+        """(send entries, send offset, recv entries, recv offset) with peer,
+        and the shard's global leaf range."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        rng = (ctypes.c_int64 * 2)()
+        check(self.L.ph_shard_halo(self.h, peer, *[ctypes.byref(x) for x in v], rng))
+        return tuple(x.value for x in v), (int(rng[0]), int(rng[1]))
+
+    def stage(self, stage: int):
+        check(self.L.ph_shard_stage(self.h, stage))
+
+    def pack(self, pool: int, buf):
+        check(self.L.ph_shard_pack(self.h, pool, ctypes.c_void_p(buf.data_ptr())))
+
+    def unpack(self, pool: int, buf):
+        check(self.L.ph_shard_unpack(self.h, pool, ctypes.c_void_p(buf.data_ptr())))
+
+    def rate(self, recompute: int, d_rate):
+        check(self.L.ph_shard_rate(self.h, recompute, ctypes.c_void_p(d_rate.data_ptr())))
+
+    def finish(self, first: int, d_rate):
+        check(self.L.ph_shard_finish(self.h, first, ctypes.c_void_p(d_rate.data_ptr())))
+
+
+class ShardedMesh:
+    """All shards of a uniform mesh in this process (ph_shards_sync /
+    ph_shards_step), with the global state in the layout of Mesh (blocks in
+    Z-order) split by the shards' leaf ranges."""
+
+    def __init__(self, cfg: Config, nshards: int, devices: Optional[Sequence[int]] = None):
+        import torch
+        self.cfg = cfg
+        self.shards: List[Shard] = []
+        self.streams = []
+        for s in range(nshards):
+            dev = devices[s] if devices else torch.cuda.current_device()
+            with torch.cuda.device(dev):
+                st = torch.cuda.Stream(device=dev)
+                self.streams.append(st)
+                self.shards.append(Shard(cfg, nshards, s, stream=st.cuda_stream))
+        self.ranges = [sh.halo(0)[1] for sh in self.shards] if nshards > 1 else [(0, self.shards[0].nblocks)]
+        self._handles = (ctypes.c_void_p * nshards)(*[sh.h.value for sh in self.shards])
+
+    @property
+    def nblocks(self) -> int:
+        return self.ranges[-1][1]
+
+    def tree(self) -> np.ndarray:
+        return np.concatenate([sh.tree() for sh in self.shards])
+
+    def set_state(self, U: np.ndarray):
+        for sh, (a, b) in zip(self.shards, self.ranges):
+            sh.set_state(np.ascontiguousarray(U[a:b]))
+        check(lib().ph_shards_sync(self._handles, len(self.shards)))
+
+    def step(self, n: int = 1):
+        check(lib().ph_shards_step(self._handles, len(self.shards), int(n)))
+
+    def get_state(self) -> np.ndarray:
+        return np.concatenate([sh.get_state() for sh in self.shards])
+
+    def dt(self) -> float:
+        return self.shards[0].dt()
+
+    def time(self):
+        return self.shards[0].time()
+
+    def close(self):
+        for sh in self.shards:
+            sh.close()
+
+
+class DistShard:
+    """One shard per process of a torch.distributed group: shard `rank` of
+    `world` on the current device, with the halo exchange as point-to-point
+    messages (device buffers with NCCL, host-staged with gloo) and the dt as
+    an all-reduce max."""
+
+    def __init__(self, cfg: Config):
+        import torch
+        import torch.distributed as dist
+        self.dist, self.torch = dist, torch
+        self.rank, self.world = dist.get_rank(), dist.get_world_size()
+        self.host = dist.get_backend() == "gloo"
+        self.m = Shard(cfg, self.world, self.rank)
+        self.nvar = self.m.nvar
+        tdt = torch.float32 if cfg.precision == PH_FP32 else torch.float64
+        self.peers = []
+        nsend = nrecv = 0
+        for p in range(self.world):
+            if p == self.rank:
+                continue
+            (ns, so, nr, ro), self.range = self.m.halo(p)
+            self.peers.append((p, ns, so, nr, ro))
+            nsend, nrecv = max(nsend, so + ns), max(nrecv, ro + nr)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.send = torch.empty(max(nsend, 1) * self.nvar, dtype=tdt, device=dev)
+        self.recv = torch.empty(max(nrecv, 1) * self.nvar, dtype=tdt, device=dev)
+        self.rate_d = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def _exchange(self, pool: int):
+        torch, dist, nv = self.torch, self.dist, self.nvar
+        self.m.pack(pool, self.send)
+        torch.cuda.current_stream().synchronize()
+        send = self.send.cpu() if self.host else self.send
+        recv = torch.empty_like(self.recv, device="cpu") if self.host else self.recv
+        ops = []
+        for p, ns, so, nr, ro in self.peers:
+            if ns:
+                ops.append(dist.P2POp(dist.isend, send[so * nv:(so + ns) * nv], p))
+            if nr:
+                ops.append(dist.P2POp(dist.irecv, recv[ro * nv:(ro + nr) * nv], p))
+        if ops:
+            for w in dist.batch_isend_irecv(ops):
+                w.wait()
+        if self.host:
+            self.recv.copy_(recv)
+        self.m.unpack(pool, self.recv)
+
+    def _dt(self, recompute: int, first: int):
+        torch, dist = self.torch, self.dist
+        self.m.rate(recompute, self.rate_d)
+        torch.cuda.current_stream().synchronize()
+        r = self.rate_d.cpu() if self.host else self.rate_d
+        dist.all_reduce(r, op=dist.ReduceOp.MAX)
+        if self.host:
+            self.rate_d.copy_(r)
+        self.m.finish(first, self.rate_d)
+
+    def set_state(self, U_local: np.ndarray):
+        """This shard's blocks (global leaves self.range) of the state."""
+        self.m.set_state(U_local)
+        self._exchange(0)
+        self._dt(1, 1)
+
+    def step(self, n: int = 1):
+        for _ in range(int(n)):
+            self.m.stage(1)
+            self._exchange(1)
+            self.m.stage(2)
+            self._exchange(0)
+            self._dt(0, 0)
+
+    def get_state(self) -> np.ndarray:
+        return self.m.get_state()

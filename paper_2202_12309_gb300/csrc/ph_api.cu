@@ -117,6 +117,20 @@ struct ph_mesh {
   CUtensorMap tm[2];
   bool tma = false;
 
+  // domain decomposition (ph_create_shard): this mesh holds the global
+  // leaves [plan.lo, plan.hi) of a uniform mesh split into plan.nshards
+  int nshards = 1;
+  ph::ShardPlan plan;
+  int device = 0;
+  long long* d_send_src = nullptr;
+  long long* d_recv_dst = nullptr;
+  int8_t* d_recv_flip = nullptr;
+  void* d_sendbuf = nullptr;   // in-process exchange (ph_shards_step / sync)
+  void* d_recvbuf = nullptr;
+  unsigned long long* d_wscratch = nullptr;  // per shard + 1: the dt reduction (shard 0)
+  cudaEvent_t ev = nullptr;       // the shard's pack (or its wmax copy) is done
+  cudaEvent_t ev_done = nullptr;  // the shard's unpack (or dt reduction) is done
+
   std::vector<void*> owned;  // every device allocation, for destroy
 
   void* dalloc(size_t bytes) {
@@ -934,6 +948,7 @@ void mesh_free(ph_mesh* m, void* p) { m->dfree(p); }
 
 int mesh_access(ph_mesh* m, MeshAccess* out) {
   if (m->multi_level) return fail(PH_ERR_INVALID, "adjoint: uniform meshes only");
+  if (m->nshards > 1) return fail(PH_ERR_INVALID, "adjoint: not on a shard of a decomposed mesh");
   if (bc_mask(m)) return fail(PH_ERR_INVALID, "adjoint: periodic meshes only");
   if (m->nvar != ph::NV) return fail(PH_ERR_INVALID, "adjoint: meshes without passive scalars only");
   out->U0 = m->U0;
@@ -1000,6 +1015,7 @@ int ph_step_dt(ph_mesh* m, int32_t ncycles, const double* dts) {
   PH_RANGE("ph_step_dt");
   if (!m || (!dts && ncycles > 0) || ncycles < 0) return fail(PH_ERR_INVALID, "ph_step_dt: bad argument");
   if (m->multi_level) return fail(PH_ERR_INVALID, "ph_step_dt: uniform meshes only");
+  if (m->nshards > 1) return fail(PH_ERR_INVALID, "ph_step_dt: not on a shard of a decomposed mesh");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_step_dt: set the state first");
   for (int c = 0; c < ncycles; ++c) {
     int rc = ph::mesh_cycle_fixed_dt(m, dts[c]);
@@ -1020,9 +1036,49 @@ int ph_set_allocator(ph_alloc_fn alloc, ph_free_fn release, void* ctx) {
 
 const char* ph_last_error(void) { return g_err.c_str(); }
 
+static int create_mesh(const ph_config* cfg, void* stream, int nshards, int shard, ph_mesh** out);
+
 int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
+  return create_mesh(cfg, stream, 1, 0, out);
+}
+
+// Device side of a shard's halo plan: the index lists of the pack and unpack
+// launches, exchange buffers for in-process shards, the dt reduction
+// scratch and an event for cross-stream ordering.
+static int setup_shard(ph_mesh* m) {
+  const ph::ShardPlan& P = m->plan;
+  PH_CUDA(cudaGetDevice(&m->device));
+  const size_t ns = P.send_src.size(), nr = P.recv_dst.size();
+  m->d_send_src = (long long*)m->dalloc(sizeof(long long) * std::max<size_t>(ns, 1));
+  m->d_recv_dst = (long long*)m->dalloc(sizeof(long long) * std::max<size_t>(nr, 1));
+  m->d_recv_flip = (int8_t*)m->dalloc(std::max<size_t>(nr, 1));
+  m->d_sendbuf = m->dalloc(m->esize * m->nvar * std::max<size_t>(ns, 1));
+  m->d_recvbuf = m->dalloc(m->esize * m->nvar * std::max<size_t>(nr, 1));
+  m->d_wscratch = (unsigned long long*)m->dalloc(sizeof(unsigned long long) * (P.nshards + 1));
+  if (!m->d_send_src || !m->d_recv_dst || !m->d_recv_flip || !m->d_sendbuf || !m->d_recvbuf || !m->d_wscratch)
+    return fail(PH_ERR_OOM, "device allocation failed (shard halo plan)");
+  if (ns)
+    PH_CUDA(cudaMemcpyAsync(m->d_send_src, P.send_src.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice,
+                            m->stream));
+  if (nr) {
+    PH_CUDA(cudaMemcpyAsync(m->d_recv_dst, P.recv_dst.data(), sizeof(long long) * nr, cudaMemcpyHostToDevice,
+                            m->stream));
+    PH_CUDA(cudaMemcpyAsync(m->d_recv_flip, P.recv_flip.data(), nr, cudaMemcpyHostToDevice, m->stream));
+  }
+  PH_CUDA(cudaEventCreateWithFlags(&m->ev, cudaEventDisableTiming));
+  PH_CUDA(cudaEventCreateWithFlags(&m->ev_done, cudaEventDisableTiming));
+  return PH_OK;
+}
+
+static int create_mesh(const ph_config* cfg, void* stream, int nshards, int shard, ph_mesh** out) {
   if (!cfg || !out) return fail(PH_ERR_INVALID, "ph_create: null argument");
   *out = nullptr;
+  ph::ShardPlan plan;
+  if (nshards > 1) {
+    std::string err;
+    const int prc = ph::shard_plan(*cfg, nshards, shard, &plan, &err);
+    if (prc) return fail(prc, "ph_create_shard: " + err);
+  }
   for (int d = 0; d < 3; ++d) {
     if (cfg->nx[d] < 2 * ph::NG) return fail(PH_ERR_INVALID, "ph_create: nx must be >= 4");
     if (cfg->nb[d] < 1) return fail(PH_ERR_INVALID, "ph_create: nb must be >= 1");
@@ -1068,7 +1124,8 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     const char* g = std::getenv("PH_GHOSTS");  // "launch": keep the separate exchange launch
     bool periodic = true;
     for (int f = 0; f < 6; ++f) periodic = periodic && cfg->bc[f] == PH_BC_PERIODIC;
-    m->push = !m->multi_level && periodic && !(g && std::strcmp(g, "launch") == 0);
+    // shards exchange ghosts between stages (pack / copy / unpack), never by push
+    m->push = !m->multi_level && periodic && nshards == 1 && !(g && std::strcmp(g, "launch") == 0);
   }
   int t[3] = {cfg->tile[0], cfg->tile[1], cfg->tile[2]};
   const bool default_tile = t[0] == 0 && t[1] == 0 && t[2] == 0;
@@ -1102,9 +1159,16 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
     return cuda_fail(e, "cudaStreamCreateWithFlags");
   }
   // root grid, then static refinement (Sec. 3.8) before any data exists
-  for (int64_t k = 0; k < cfg->nb[2]; ++k)
-    for (int64_t j = 0; j < cfg->nb[1]; ++j)
-      for (int64_t i = 0; i < cfg->nb[0]; ++i) m->leaf.push_back(Leaf{0, {i, j, k}, 0});
+  if (nshards > 1) {  // this shard's range of the Z-ordered root grid
+    m->nshards = nshards;
+    m->plan = plan;
+    for (long long g = plan.lo; g < plan.hi; ++g)
+      m->leaf.push_back(Leaf{0, {plan.loc[g][0], plan.loc[g][1], plan.loc[g][2]}, 0});
+  } else {
+    for (int64_t k = 0; k < cfg->nb[2]; ++k)
+      for (int64_t j = 0; j < cfg->nb[1]; ++j)
+        for (int64_t i = 0; i < cfg->nb[0]; ++i) m->leaf.push_back(Leaf{0, {i, j, k}, 0});
+  }
   index_tree(m);
   // the static region is refined to the finest level, one level at a time
   for (int l = 0; l < cfg->max_level && cfg->static_region; ++l) {
@@ -1138,6 +1202,7 @@ int ph_create(const ph_config* cfg, void* stream, ph_mesh** out) {
   if (!m->sc || !m->d_totals) rc = fail(PH_ERR_OOM, "device allocation failed");
   if (!rc) rc = ensure_pools(m, m->nleaf());
   if (!rc) rc = build_tables(m);
+  if (!rc && nshards > 1) rc = setup_shard(m);
   if (!rc) {
     e = cudaMemsetAsync(m->sc, 0, sizeof(ph::DevScalars), m->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
@@ -1158,6 +1223,8 @@ int ph_destroy(ph_mesh* m) {
   if (!m) return PH_OK;
   cudaStreamSynchronize(m->stream);
   drop_graph(m);
+  if (m->ev) cudaEventDestroy(m->ev);
+  if (m->ev_done) cudaEventDestroy(m->ev_done);
   std::vector<void*> all = m->owned;
   for (void* p : all) m->dfree(p);
   if (m->cap) cudaStreamDestroy(m->cap);
@@ -1224,11 +1291,239 @@ int ph_get_full(ph_mesh* m, void* U, int64_t count, int32_t on_device) {
   return PH_OK;
 }
 
+// ============================================================== shards
+
+int ph_create_shard(const ph_config* cfg, int32_t nshards, int32_t shard, void* stream, ph_mesh** out) {
+  if (nshards < 1) return fail(PH_ERR_INVALID, "ph_create_shard: nshards must be >= 1");
+  return create_mesh(cfg, stream, nshards, shard, out);
+}
+
+int ph_shard_halo(const ph_mesh* m, int32_t peer, int64_t* send_entries, int64_t* send_offset,
+                  int64_t* recv_entries, int64_t* recv_offset, int64_t leaf_range[2]) {
+  if (!m) return fail(PH_ERR_INVALID, "ph_shard_halo: null mesh");
+  if (m->nshards < 2) return fail(PH_ERR_INVALID, "ph_shard_halo: not a shard of a decomposed mesh");
+  if (peer < 0 || peer >= m->nshards) return fail(PH_ERR_INVALID, "ph_shard_halo: peer out of range");
+  const ph::ShardPlan& P = m->plan;
+  if (send_entries) *send_entries = P.send_off[peer + 1] - P.send_off[peer];
+  if (send_offset) *send_offset = P.send_off[peer];
+  if (recv_entries) *recv_entries = P.recv_off[peer + 1] - P.recv_off[peer];
+  if (recv_offset) *recv_offset = P.recv_off[peer];
+  if (leaf_range) {
+    leaf_range[0] = P.lo;
+    leaf_range[1] = P.hi;
+  }
+  return PH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <class T>
+int shard_stage_t(ph_mesh* m, int stage, cudaStream_t s) {
+  const ph::StageArgs<T> a = stage_args<T>(m, stage);
+  PH_CUDA(ph::launch_stage<T>(a, m->tile[0], m->tile[1], s, tmap_for(m, stage)));
+  T* out = (T*)(stage == 1 ? m->U1 : m->U0);
+  PH_CUDA(ph::launch_ghost_uniform<T>(out, m->d_nbr, m->nx, m->nleaf(), s, m->d_leaf_id, m->nb, bc_mask(m),
+                                      m->nvar));
+  return PH_OK;
+}
+
+template <class T>
+int shard_pack_t(ph_mesh* m, int pool, void* buf) {
+  const long long vs = (long long)m->S[0] * m->S[1] * m->S[2];
+  PH_CUDA(ph::launch_shard_pack<T>((const T*)(pool ? m->U1 : m->U0), m->d_send_src,
+                                   (long long)m->plan.send_src.size(), vs, m->nvar, (T*)buf, m->stream));
+  return PH_OK;
+}
+
+template <class T>
+int shard_unpack_t(ph_mesh* m, int pool, const void* buf) {
+  const long long vs = (long long)m->S[0] * m->S[1] * m->S[2];
+  PH_CUDA(ph::launch_shard_unpack<T>((T*)(pool ? m->U1 : m->U0), m->d_recv_dst, m->d_recv_flip,
+                                     (long long)m->plan.recv_dst.size(), vs, m->nvar, (const T*)buf, m->stream));
+  return PH_OK;
+}
+
+int check_shard_set(ph_mesh* const* sh, int n, const char* who) {
+  if (!sh || n < 2) return fail(PH_ERR_INVALID, std::string(who) + ": need the shards of one mesh");
+  for (int s = 0; s < n; ++s) {
+    if (!sh[s] || sh[s]->nshards != n || sh[s]->plan.shard != s)
+      return fail(PH_ERR_INVALID, std::string(who) + ": shards[s] must be shard s of n");
+    if (std::memcmp(&sh[s]->cfg, &sh[0]->cfg, sizeof(ph_config)) != 0)
+      return fail(PH_ERR_INVALID, std::string(who) + ": shards of different meshes");
+    if (!sh[s]->state_set) return fail(PH_ERR_STATE, std::string(who) + ": set every shard's state first");
+  }
+  return PH_OK;
+}
+
+// Ghost exchange of pool (0: U0, 1: U1) between the shards of one process:
+// pack on every shard, copy each peer's slab into the receiver's buffer (a
+// peer copy when the shards live on different devices), unpack.  Events
+// order the streams: a receiver copies after the sender packed, a sender
+// packs again only after every receiver has finished with its buffer.
+template <class T>
+int shards_exchange(ph_mesh* const* sh, int n, int pool) {
+  int rc;
+  for (int s = 0; s < n; ++s) {
+    for (int p = 0; p < n; ++p)
+      if (p != s) PH_CUDA(cudaStreamWaitEvent(sh[s]->stream, sh[p]->ev_done, 0));
+    if ((rc = shard_pack_t<T>(sh[s], pool, sh[s]->d_sendbuf))) return rc;
+    PH_CUDA(cudaEventRecord(sh[s]->ev, sh[s]->stream));
+  }
+  for (int p = 0; p < n; ++p) {
+    ph_mesh* r = sh[p];
+    const size_t per = r->esize * r->nvar;
+    for (int s = 0; s < n; ++s) {
+      if (s == p) continue;
+      const int64_t cnt = r->plan.recv_off[s + 1] - r->plan.recv_off[s];
+      const int64_t scnt = sh[s]->plan.send_off[p + 1] - sh[s]->plan.send_off[p];
+      if (cnt != scnt) return fail(PH_ERR_STATE, "shard exchange: halo plans disagree");
+      if (cnt == 0) continue;
+      PH_CUDA(cudaStreamWaitEvent(r->stream, sh[s]->ev, 0));
+      PH_CUDA(cudaMemcpyPeerAsync((char*)r->d_recvbuf + per * r->plan.recv_off[s], r->device,
+                                  (const char*)sh[s]->d_sendbuf + per * sh[s]->plan.send_off[p], sh[s]->device,
+                                  per * cnt, r->stream));
+    }
+    if ((rc = shard_unpack_t<T>(r, pool, r->d_recvbuf))) return rc;
+    PH_CUDA(cudaEventRecord(r->ev_done, r->stream));
+  }
+  return PH_OK;
+}
+
+// One dt for all shards: the max signal rate over shards (recompute: from
+// U0, else the one the last stage 2 folded), then each shard's bookkeeping
+// (first: the first dt of a fresh state; else commit the cycle and the next dt).
+int shards_dt(ph_mesh* const* sh, int n, int recompute, int first) {
+  ph_mesh* z = sh[0];
+  for (int s = 0; s < n; ++s) {
+    ph_mesh* m = sh[s];
+    if (recompute) {
+      const int rc = m->cfg.precision == PH_FP32
+                         ? (ph::launch_rate<float>((const float*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(),
+                                                   phys<float>(m), m->sc, m->stream, m->nvar) == cudaSuccess ? 0 : 1)
+                         : (ph::launch_rate<double>((const double*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(),
+                                                    phys<double>(m), m->sc, m->stream, m->nvar) == cudaSuccess ? 0 : 1);
+      if (rc) return fail(PH_ERR_CUDA, "shard dt: rate launch failed");
+    }
+    PH_CUDA(cudaStreamWaitEvent(m->stream, z->ev_done, 0));  // shard 0 read the previous cycle's values
+    PH_CUDA(cudaMemcpyPeerAsync(z->d_wscratch + s, z->device, &m->sc->wmax_bits, m->device, sizeof(unsigned long long),
+                                m->stream));
+    PH_CUDA(cudaEventRecord(m->ev, m->stream));
+  }
+  for (int s = 1; s < n; ++s) PH_CUDA(cudaStreamWaitEvent(z->stream, sh[s]->ev, 0));
+  PH_CUDA(ph::launch_shard_wmax(z->d_wscratch, n, z->d_wscratch + n, z->stream));
+  PH_CUDA(cudaEventRecord(z->ev_done, z->stream));
+  for (int s = 0; s < n; ++s) {
+    ph_mesh* m = sh[s];
+    PH_CUDA(cudaStreamWaitEvent(m->stream, z->ev_done, 0));
+    PH_CUDA(cudaMemcpyPeerAsync(&m->sc->wmax_bits, m->device, z->d_wscratch + n, z->device, sizeof(unsigned long long),
+                                m->stream));
+    if (first) {
+      PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 2, m->stream));
+      PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 4, m->stream));
+    } else {
+      PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream));
+    }
+  }
+  // the next exchange's packs wait for every shard's ev_done: make them
+  // cover the copies above
+  for (int s = 0; s < n; ++s) PH_CUDA(cudaEventRecord(sh[s]->ev_done, sh[s]->stream));
+  return PH_OK;
+}
+
+template <class T>
+int shards_step_t(ph_mesh* const* sh, int n, int ncycles) {
+  int rc;
+  for (int c = 0; c < ncycles; ++c) {
+    for (int stage = 1; stage <= 2; ++stage) {
+      for (int s = 0; s < n; ++s)
+        if ((rc = shard_stage_t<T>(sh[s], stage, sh[s]->stream))) return rc;
+      if ((rc = shards_exchange<T>(sh, n, stage == 1 ? 1 : 0))) return rc;
+    }
+    if ((rc = shards_dt(sh, n, 0, 0))) return rc;
+  }
+  return PH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ph_shard_stage(ph_mesh* m, int32_t stage) {
+  if (!m || (stage != 1 && stage != 2)) return fail(PH_ERR_INVALID, "ph_shard_stage: bad argument");
+  if (m->nshards < 2) return fail(PH_ERR_INVALID, "ph_shard_stage: not a shard of a decomposed mesh");
+  if (!m->state_set) return fail(PH_ERR_STATE, "ph_shard_stage: set the state first");
+  return DISPATCH(m, shard_stage_t, m, stage, m->stream);
+}
+
+int ph_shard_pack(ph_mesh* m, int32_t pool, void* sendbuf) {
+  if (!m || (pool != 0 && pool != 1) || !sendbuf) return fail(PH_ERR_INVALID, "ph_shard_pack: bad argument");
+  if (m->nshards < 2) return fail(PH_ERR_INVALID, "ph_shard_pack: not a shard of a decomposed mesh");
+  return DISPATCH(m, shard_pack_t, m, pool, sendbuf);
+}
+
+int ph_shard_unpack(ph_mesh* m, int32_t pool, const void* recvbuf) {
+  if (!m || (pool != 0 && pool != 1) || !recvbuf) return fail(PH_ERR_INVALID, "ph_shard_unpack: bad argument");
+  if (m->nshards < 2) return fail(PH_ERR_INVALID, "ph_shard_unpack: not a shard of a decomposed mesh");
+  return DISPATCH(m, shard_unpack_t, m, pool, recvbuf);
+}
+
+int ph_shard_rate(ph_mesh* m, int32_t recompute, double* d_rate) {
+  if (!m || !d_rate) return fail(PH_ERR_INVALID, "ph_shard_rate: bad argument");
+  if (m->nshards < 2) return fail(PH_ERR_INVALID, "ph_shard_rate: not a shard of a decomposed mesh");
+  if (recompute) {
+    const cudaError_t e =
+        m->cfg.precision == PH_FP32
+            ? ph::launch_rate<float>((const float*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(),
+                                     phys<float>(m), m->sc, m->stream, m->nvar)
+            : ph::launch_rate<double>((const double*)m->U0, m->d_level, level_geom(m), m->nx, m->nleaf(),
+                                      phys<double>(m), m->sc, m->stream, m->nvar);
+    if (e != cudaSuccess) return cuda_fail(e, "ph_shard_rate");
+  }
+  PH_CUDA(cudaMemcpyAsync(d_rate, &m->sc->wmax_bits, sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  return PH_OK;
+}
+
+int ph_shard_finish(ph_mesh* m, int32_t first, const double* d_rate) {
+  if (!m || !d_rate) return fail(PH_ERR_INVALID, "ph_shard_finish: bad argument");
+  if (m->nshards < 2) return fail(PH_ERR_INVALID, "ph_shard_finish: not a shard of a decomposed mesh");
+  PH_CUDA(cudaMemcpyAsync(&m->sc->wmax_bits, d_rate, sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
+  if (first) {
+    PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 2, m->stream));
+    PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 4, m->stream));
+  } else {
+    PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream));
+  }
+  return PH_OK;
+}
+
+int ph_shards_sync(ph_mesh* const* shards, int32_t n) {
+  PH_RANGE("ph_shards_sync");
+  int rc = check_shard_set(shards, n, "ph_shards_sync");
+  if (rc) return rc;
+  rc = shards[0]->cfg.precision == PH_FP32 ? shards_exchange<float>(shards, n, 0)
+                                           : shards_exchange<double>(shards, n, 0);
+  if (rc) return rc;
+  return shards_dt(shards, n, 1, 1);
+}
+
+int ph_shards_step(ph_mesh* const* shards, int32_t n, int32_t ncycles) {
+  PH_RANGE("ph_shards_step");
+  if (ncycles < 0) return fail(PH_ERR_INVALID, "ph_shards_step: negative cycle count");
+  int rc = check_shard_set(shards, n, "ph_shards_step");
+  if (rc) return rc;
+  return shards[0]->cfg.precision == PH_FP32 ? shards_step_t<float>(shards, n, ncycles)
+                                             : shards_step_t<double>(shards, n, ncycles);
+}
+
 int ph_step(ph_mesh* m, int32_t ncycles) {
   PH_RANGE("ph_step");
   if (!m) return fail(PH_ERR_INVALID, "ph_step: null mesh");
   if (ncycles < 0) return fail(PH_ERR_INVALID, "ph_step: negative cycle count");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_step: set the state first");
+  if (m->nshards > 1)
+    return fail(PH_ERR_STATE, "ph_step: a shard steps with ph_shards_step or the ph_shard_* phases");
   if (ncycles == 0) return PH_OK;
   return DISPATCH(m, step_t, m, ncycles);
 }
@@ -1339,6 +1634,7 @@ int ph_profile_cycles(ph_mesh* m, int32_t ncycles, double* ms_out, int32_t nslot
   if (!m || !ms_out || nslots < 0 || nslots > 5 || ncycles < 0)
     return fail(PH_ERR_INVALID, "ph_profile_cycles: bad argument");
   if (m->multi_level) return fail(PH_ERR_INVALID, "ph_profile_cycles: uniform meshes only");
+  if (m->nshards > 1) return fail(PH_ERR_INVALID, "ph_profile_cycles: not on a shard of a decomposed mesh");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_profile_cycles: set the state first");
   return DISPATCH(m, profile_t, m, ncycles, ms_out, nslots);
 }
@@ -1393,6 +1689,7 @@ int ph_save(ph_mesh* m, const char* path, int32_t precision) {
   if (precision != PH_FP64 && precision != PH_FP32)
     return fail(PH_ERR_INVALID, "ph_save: precision must be PH_FP64 or PH_FP32");
   if (!m->state_set) return fail(PH_ERR_STATE, "ph_save: set the state first");
+  if (m->nshards > 1) return fail(PH_ERR_INVALID, "ph_save: not on a shard of a decomposed mesh");
   ph::DevScalars hs;
   int rc = read_scalars(m, &hs);
   if (rc) return rc;

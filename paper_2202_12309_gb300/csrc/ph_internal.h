@@ -5,6 +5,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <string>
+#include <vector>
+
+#include "../../include/ph_hydro.h"
+
 #include "ph_device.cuh"
 
 struct ph_mesh;
@@ -90,7 +96,8 @@ bool stage_scalar_tile(int TX, int TY);
 cudaError_t configure_stage_kernels();
 
 // K1 (uniform mesh): every ghost cell of every leaf copied from the
-// same-level neighbour given by nbr[27 * leaf + region], or, across a
+// same-level neighbour given by nbr[27 * leaf + region] (-1: a neighbour on
+// another shard, whose cells the shard unpack writes), or, across a
 // physical boundary face (bcm: 2 bits per face, x1 inner first; leaf_id and
 // nb give the leaf's place in the root grid), from its image in the block.
 template <class T>
@@ -144,5 +151,35 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
                                 const int nx[3], const int8_t* level, const LevelGeom& g,
                                 double beta, const DevScalars* sc, cudaStream_t s, int nvar = NV);
+
+// Domain decomposition of a uniform mesh (ph_shard.cu).  Shard `shard` of
+// `nshards` owns the global leaves [lo, hi) of the Z-ordered root grid; the
+// halo plan lists, per peer (peers in order, offsets in *_off), the ghost
+// cells it receives (destination: local leaf * padded cells + cell, flips of
+// the normal momentum across reflecting walls) and the interior cells it
+// sends (source: local leaf * padded cells + cell), both in the order of
+// the receiving ghost cell's (global leaf, padded cell) key.  Local
+// positions are element offsets into the state pool (local leaf times
+// nvar x padded cells, plus the padded cell); variable v is v x padded cells
+// further.
+struct ShardPlan {
+  int nshards = 1, shard = 0;
+  long long lo = 0, hi = 0;
+  std::vector<long long> first;            // per shard, its first global leaf (size nshards + 1)
+  std::vector<int> owner;                  // per global leaf
+  std::vector<std::array<int, 3>> loc;     // per global leaf, root-grid location
+  std::vector<int64_t> send_off, recv_off; // per peer, entry offsets (size nshards + 1)
+  std::vector<int64_t> send_key, send_src;
+  std::vector<int64_t> recv_key, recv_dst;
+  std::vector<int8_t> recv_flip;
+};
+int shard_plan(const ph_config& cfg, int nshards, int shard, ShardPlan* out, std::string* err);
+template <class T>
+cudaError_t launch_shard_pack(const T* U, const long long* src, long long n, long long vs, int nvar, T* buf,
+                              cudaStream_t s);
+template <class T>
+cudaError_t launch_shard_unpack(T* U, const long long* dst, const int8_t* flip, long long n, long long vs,
+                                int nvar, const T* buf, cudaStream_t s);
+cudaError_t launch_shard_wmax(const unsigned long long* src, int n, unsigned long long* dst, cudaStream_t s);
 
 }  // namespace ph

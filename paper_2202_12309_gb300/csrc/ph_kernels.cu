@@ -73,6 +73,7 @@ __global__ void ghost_uniform_kernel(T* U, const int* __restrict__ nbr, int3 nx,
       if (bc_image(sk, oz, nx.z, lx[2] == 0, lx[2] == nbl.z - 1, (bcm >> 8) & 3, (bcm >> 10) & 3, f3)) oz = 0;
     }
     const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    if (src < 0) continue;  // source on another shard: filled by the shard unpack
     const T* srcb = U + (size_t)src * NVT * vs;
     const size_t so = ((size_t)(sk - oz * nx.z) * S2 + (sj - oy * nx.y)) * S1 + (si - ox * nx.x);
     const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
@@ -124,6 +125,7 @@ __global__ void ghost_uniform_pairs_kernel(T* U, const int* __restrict__ nbr, in
     const int oy = j < NG ? -1 : (j >= NG + nx.y ? 1 : 0);
     const int oz = k < NG ? -1 : (k >= NG + nx.z ? 1 : 0);
     const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    if (src < 0) continue;  // source on another shard: filled by the shard unpack
     const T* srcb = U + (size_t)src * NVT * vs;
     const size_t so = ((size_t)(k - oz * nx.z) * S2 + (j - oy * nx.y)) * S1 + (i - ox * nx.x);
     const size_t dofs = ((size_t)k * S2 + j) * S1 + i;
