@@ -247,7 +247,8 @@ int ph_step_dt(ph_mesh* mesh, int32_t ncycles, const double* dts);
  *   U0       initial interior state (layout of ph_set_state)
  *   ncycles  cycles of the forward run; ckpt_every: keep every k-th state
  *            and recompute the k cycles in between (memory ~ ncycles/k + 2k
- *            states)
+ *            states; the last k cycles' stage inputs are kept from the
+ *            forward run, so those are not recomputed)
  *   dts      host array of ncycles dts, or NULL to use (and freeze) the CFL
  *            dts of the forward run
  *   dLdU     dL/dU_final (interior layout); dLdU0 receives dL/dU0

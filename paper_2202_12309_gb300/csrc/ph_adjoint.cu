@@ -698,11 +698,18 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
     for (int c = 0; c < ncycles; ++c) dts[c] = dts_in[c];
     PA_CUDA(cudaMemcpyAsync(d_dts, dts.data(), sizeof(double) * ncycles, cudaMemcpyHostToDevice, s));
   }
+  // the last segment's stage inputs are kept as the forward pass makes them,
+  // so the backward pass starts without recomputing it
+  const int clast = (nseg - 1) * ckpt;
   for (int c = 0; c < ncycles; ++c) {
     if (c % ckpt == 0)
       PA_CUDA(cudaMemcpyAsync(ck + (size_t)(c / ckpt) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+    if (c >= clast)
+      PA_CUDA(cudaMemcpyAsync(seg0 + (size_t)(c - clast) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
     rc = dts_in ? mesh_cycle_device_dt(m, d_dts + c) : mesh_cycle_record_dt(m, d_dts + c);
     if (rc) return fail_clean(rc);
+    if (c >= clast)
+      PA_CUDA(cudaMemcpyAsync(seg1 + (size_t)(c - clast) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
   }
   if (!dts_in) {
     PA_CUDA(cudaMemcpyAsync(dts.data(), d_dts, sizeof(double) * ncycles, cudaMemcpyDeviceToHost, s));
@@ -735,8 +742,9 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   // ---- backward, segment by segment
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int c0 = sg * ckpt, c1 = std::min(c0 + ckpt, ncycles);
-    PA_CUDA(cudaMemcpyAsync(A.U0, ck + (size_t)sg * elems, bytes, cudaMemcpyDeviceToDevice, s));
-    for (int c = c0; c < c1; ++c) {
+    if (sg != nseg - 1)  // (the last segment was kept by the forward pass)
+      PA_CUDA(cudaMemcpyAsync(A.U0, ck + (size_t)sg * elems, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int c = c0; c < c1 && sg != nseg - 1; ++c) {
       PA_CUDA(cudaMemcpyAsync(seg0 + (size_t)(c - c0) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
       if ((rc = mesh_cycle_device_dt(m, d_dts + c))) return fail_clean(rc);
       PA_CUDA(cudaMemcpyAsync(seg1 + (size_t)(c - c0) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));

@@ -50,8 +50,11 @@ def _compare_runs(ph, nx, nb, nshards, cycles, precision="fp64", bc=None):
         assert sm.dt() == whole.dt() and sm.time() == whole.time(), "cycle %d" % c
     for sh in sm.shards:
         assert sh.status()[0] == 0
+    # per-shard totals add up to the mesh's (momentum totals are round-off
+    # around zero: compare on the scale of the largest total)
     tot = sum(sh.totals() for sh in sm.shards)
-    assert np.allclose(tot, whole.totals(), rtol=1e-13, atol=0)
+    ref = whole.totals()
+    assert np.all(np.abs(tot - ref) <= 1e-13 * np.abs(ref).max())
     sm.close()
     whole.close()
 
