@@ -106,6 +106,9 @@ struct ph_mesh {
   void* d_fcc = nullptr;
   void* d_fcf = nullptr;
   int nrec = 0, ncorr = 0;
+  // multi-level: ghost cells evaluated through the tree, (leaf, shell index)
+  int2* d_eval = nullptr;
+  int neval = 0;
   // staging for host copies and packed device copies
   void* staging = nullptr;
   size_t staging_bytes = 0;
@@ -344,17 +347,18 @@ bool next_tree(const ph_mesh* m, const std::vector<int8_t>& flags, bool check_ag
 // ---------------------------------------------------------------- device tables
 
 // The device tables of a mesh (rebuilt whenever the tree changes).
-void table_slots(ph_mesh* m, void** (&slot)[13]) {
-  void** ptrs[13] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_node,
-                     (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
-                     (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
-                     (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
-                     (void**)&m->d_fcf};
-  for (int i = 0; i < 13; ++i) slot[i] = ptrs[i];
+constexpr int kTableSlots = 14;
+void table_slots(ph_mesh* m, void** (&slot)[kTableSlots]) {
+  void** ptrs[kTableSlots] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_node,
+                              (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
+                              (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
+                              (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
+                              (void**)&m->d_fcf, (void**)&m->d_eval};
+  for (int i = 0; i < kTableSlots; ++i) slot[i] = ptrs[i];
 }
 
 void free_tables(ph_mesh* m) {
-  void** slot[13];
+  void** slot[kTableSlots];
   table_slots(m, slot);
   for (void** p : slot) {
     m->dfree(*p);
@@ -378,23 +382,24 @@ int build_tables_fresh(ph_mesh* m);
 // tables are made beside the old ones, which are released only when every
 // new one exists: on a failure (PH_ERR_OOM) the mesh keeps its old tables.
 int build_tables(ph_mesh* m) {
-  void** slot[13];
+  void** slot[kTableSlots];
   table_slots(m, slot);
-  void* keep[13];
-  for (int i = 0; i < 13; ++i) {
+  void* keep[kTableSlots];
+  for (int i = 0; i < kTableSlots; ++i) {
     keep[i] = *slot[i];
     *slot[i] = nullptr;
   }
-  const int nrec = m->nrec, ncorr = m->ncorr;
+  const int nrec = m->nrec, ncorr = m->ncorr, neval = m->neval;
   const int rc = build_tables_fresh(m);
   if (rc) {
     free_tables(m);
-    for (int i = 0; i < 13; ++i) *slot[i] = keep[i];
+    for (int i = 0; i < kTableSlots; ++i) *slot[i] = keep[i];
     m->nrec = nrec;
     m->ncorr = ncorr;
+    m->neval = neval;
     return rc;
   }
-  for (int i = 0; i < 13; ++i) m->dfree(keep[i]);
+  for (int i = 0; i < kTableSlots; ++i) m->dfree(keep[i]);
   return PH_OK;
 }
 
@@ -435,6 +440,24 @@ int build_tables_fresh(ph_mesh* m) {
   if ((rc = upload(m, &m->d_level, level))) return rc;
   if ((rc = upload(m, &m->d_leaf_id, leaf_id))) return rc;
   if ((rc = upload(m, &m->d_nbr, nbr))) return rc;
+  // multi-level: the ghost cells of regions without a same-level leaf, which
+  // the exchange evaluates through the tree
+  m->neval = 0;
+  if (m->multi_level) {
+    const ph::Shell sh(m->nx);
+    std::vector<int2> ev;
+    for (int b = 0; b < n; ++b)
+      for (int c = 0; c < sh.count(); ++c) {
+        int i, j, k;
+        sh.cell(c, i, j, k);
+        const int ox = i < ph::NG ? -1 : (i >= ph::NG + m->nx[0] ? 1 : 0);
+        const int oy = j < ph::NG ? -1 : (j >= ph::NG + m->nx[1] ? 1 : 0);
+        const int oz = k < ph::NG ? -1 : (k >= ph::NG + m->nx[2] ? 1 : 0);
+        if (nbr[27 * b + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)] < 0) ev.push_back(make_int2(b, c));
+      }
+    if ((rc = upload(m, &m->d_eval, ev))) return rc;
+    m->neval = (int)ev.size();
+  }
   if ((rc = upload(m, &m->d_node, m->node))) return rc;
   m->d_partial = (double*)m->dalloc(sizeof(double) * m->nvar * std::max(n, 1));
   m->d_mb = (double*)m->dalloc(sizeof(double) * std::max(n, 1));
@@ -594,8 +617,8 @@ ph::LevelGeom level_geom(const ph_mesh* m) {
 template <class T>
 int fill_ghosts_t(ph_mesh* m, T* U) {
   if (m->multi_level) {
-    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->d_nbr, m->nleaf(), m->stream,
-                                          m->nvar));
+    PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->d_nbr, m->nleaf(), m->d_eval,
+                                          m->neval, m->stream, m->nvar));
   } else {
     PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream,
                                         m->d_leaf_id, m->nb, bc_mask(m), m->nvar));

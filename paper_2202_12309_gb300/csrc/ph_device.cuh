@@ -381,18 +381,19 @@ __device__ __forceinline__ void block_max_to(unsigned long long* dst, double v, 
 // Ghost-shell enumeration: the ghost cells of a padded block, flattened as
 // (A) the 4 x3-ghost planes, (B) the 4 x2-ghost rows of each interior plane,
 // (C) the 4 x1-ghost cells of each interior row.  Rows stay contiguous in x1.
+// (Host and device: the host lists the cells a kernel will visit.)
 // --------------------------------------------------------------------------
 struct Shell {
   int n1, n2, n3, S1, S2, nA, nB, nC;
-  __device__ __forceinline__ Shell(const int nx[3]) {
+  __host__ __device__ __forceinline__ Shell(const int nx[3]) {
     n1 = nx[0]; n2 = nx[1]; n3 = nx[2];
     S1 = n1 + 2 * NG; S2 = n2 + 2 * NG;
     nA = 4 * S2 * S1;
     nB = n3 * 4 * S1;
     nC = n3 * n2 * 4;
   }
-  __device__ __forceinline__ int count() const { return nA + nB + nC; }
-  __device__ __forceinline__ void cell(int c, int& i, int& j, int& k) const {
+  __host__ __device__ __forceinline__ int count() const { return nA + nB + nC; }
+  __host__ __device__ __forceinline__ void cell(int c, int& i, int& j, int& k) const {
     if (c < nA) {
       const int kk = c / (S2 * S1), r = c - kk * S2 * S1;
       j = r / S1;

@@ -106,12 +106,14 @@ cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nlea
                                  int bcm = 0, int nvar = NV);
 
 // K1 (multi-level mesh): every ghost cell of every leaf takes the composite
-// field of the mesh (copy / restriction / prolongation), one launch.
+// field of the mesh (copy / restriction / prolongation).
 // nbr[27 * leaf + region]: the same-level leaf covering that neighbour
-// region (its ghost cells are copied directly), or -1.
+// region (its ghost cells are copied directly, one CTA per leaf), or -1;
+// the cells of regions with -1 are eval[0 .. neval) = (leaf, shell index),
+// evaluated through the tree in a second launch, one thread per cell.
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
-                                   int nleaf, cudaStream_t s, int nvar = NV);
+                                   int nleaf, const int2* eval, int neval, cudaStream_t s, int nvar = NV);
 
 // K7: interior of every new leaf from the old mesh's composite field.
 template <class T>

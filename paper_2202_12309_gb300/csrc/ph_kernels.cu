@@ -319,7 +319,11 @@ __device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int
 // location next to leaf b in that neighbour region, or -1 (finer or coarser
 // leaves, or a physical boundary).  Ghost cells of such a region are plain
 // copies of that leaf's interior, the value the composite evaluation gives
-// there, read directly instead of through the tree.
+// there, read directly instead of through the tree; this kernel (one CTA per
+// leaf) does those copies.  The other ghost cells are listed per tree
+// (leaf, shell index) and evaluated by ghost_composite_eval_kernel, one
+// thread each over the whole list, so that the few leaves next to a level
+// jump do not serialise their evaluations in a handful of CTAs.
 template <class T, int NVT>
 __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id,
                                        const int* __restrict__ nbr) {
@@ -340,33 +344,61 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
     const int oy = j < NG ? -1 : (j >= NG + tv.nx[1] ? 1 : 0);
     const int oz = k < NG ? -1 : (k >= NG + tv.nx[2] ? 1 : 0);
     const int src = nb[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+    if (src < 0) continue;  // evaluated through the tree (the evaluation list)
     T val[NVT];
-    if (src >= 0) {
-      const T* s = U + (size_t)src * NVT * vs +
-                   ((size_t)(k - oz * tv.nx[2]) * tv.S[1] + (j - oy * tv.nx[1])) * tv.S[0] + (i - ox * tv.nx[0]);
+    const T* s = U + (size_t)src * NVT * vs +
+                 ((size_t)(k - oz * tv.nx[2]) * tv.S[1] + (j - oy * tv.nx[1])) * tv.S[0] + (i - ox * tv.nx[0]);
 #pragma unroll
-      for (int v = 0; v < NVT; ++v) val[v] = s[v * vs];
-    } else {
-      composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
-    }
+    for (int v = 0; v < NVT; ++v) val[v] = s[v * vs];
     const size_t d = ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
 #pragma unroll
     for (int v = 0; v < NVT; ++v) dst[v * vs + d] = val[v];
   }
 }
 
+// Ghost cells of regions without a same-level leaf: list[e] = (leaf, shell
+// index), one thread each; the composite field through the tree.
+template <class T, int NVT>
+__global__ void ghost_composite_eval_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id,
+                                            const int2* __restrict__ list, int n) {
+  const Shell sh(tv.nx);
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = list[e];
+    const int b = it.x;
+    int i, j, k;
+    sh.cell(it.y, i, j, k);
+    const int lev = leaf_id[4 * b];
+    const long long o1 = (long long)leaf_id[4 * b + 1] * tv.nx[0] - NG;
+    const long long o2 = (long long)leaf_id[4 * b + 2] * tv.nx[1] - NG;
+    const long long o3 = (long long)leaf_id[4 * b + 3] * tv.nx[2] - NG;
+    T val[NVT];
+    composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
+    T* dst = U + (size_t)b * NVT * vs + ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
+#pragma unroll
+    for (int v = 0; v < NVT; ++v) dst[v * vs] = val[v];
+  }
+}
+
+template <class T, int NVT>
+static cudaError_t launch_ghost_composite_n(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
+                                           int nleaf, const int2* eval, int neval, cudaStream_t s) {
+  ghost_composite_kernel<T, NVT><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
+  if (neval > 0) {
+    const int grid = std::min((neval + 127) / 128, 152 * 16);
+    ghost_composite_eval_kernel<T, NVT><<<grid, 128, 0, s>>>(U, tv, leaf_id, eval, neval);
+  }
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
-                                   int nleaf, cudaStream_t s, int nvar) {
+                                   int nleaf, const int2* eval, int neval, cudaStream_t s, int nvar) {
   PH_RANGE("ph ghost exchange (composite)");
   if (nleaf <= 0) return cudaSuccess;
-  if (nvar == NV + 1)
-    ghost_composite_kernel<T, NV + 1><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
-  else if (nvar == NV + 2)
-    ghost_composite_kernel<T, NV + 2><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
-  else
-    ghost_composite_kernel<T, NV><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
-  return cudaGetLastError();
+  if (nvar == NV + 1) return launch_ghost_composite_n<T, NV + 1>(U, tv, leaf_id, nbr, nleaf, eval, neval, s);
+  if (nvar == NV + 2) return launch_ghost_composite_n<T, NV + 2>(U, tv, leaf_id, nbr, nleaf, eval, neval, s);
+  return launch_ghost_composite_n<T, NV>(U, tv, leaf_id, nbr, nleaf, eval, neval, s);
 }
 
 template <class T, int NVT>
@@ -695,7 +727,7 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
   template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t, \
                                               const int*, const int*, int, int);              \
   template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, const int*,  \
-                                                 int, cudaStream_t, int);                       \
+                                                 int, const int2*, int, cudaStream_t, int);     \
   template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
                                         cudaStream_t, int);                                     \
   template cudaError_t launch_rate<T>(const T*, const int8_t*, const LevelGeom&, const int*,   \
