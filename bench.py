@@ -361,6 +361,34 @@ def scalar_variant(ph, torch, steps, warmup, precision="fp64", nscalars=2, block
             "zone_cycles_per_s": MESH ** 3 * steps / (ms / 1e3)}
 
 
+def shard_variant(ph, torch, steps, warmup, nshards=2, precision="fp64", block=32):
+    """The 256^3 wave as `nshards` shards of one process on this GPU
+    (ph_shards_step): the decomposed cycle with its pack / copy / unpack
+    exchange and the dt reduction over shards, against the same mesh in one
+    piece.  Wall-clock around the cycles (the shards run on their own
+    streams), synchronised on both sides."""
+    nb = MESH // block
+    cfg = ph.make_config((block,) * 3, (nb,) * 3, precision=precision)
+    sm = ph.ShardedMesh(cfg, nshards)
+    geo = W.Geometry((block,) * 3, (nb,) * 3)
+    dtype = np.float32 if precision == "fp32" else np.float64
+    sm.set_state(wave_state(geo, sm.tree(), dtype))
+    sm.step(warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sm.step(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    halo = sum(sh.halo(p)[0][2] for sh in sm.shards for p in range(nshards) if p != sh.shard)
+    rcs = [sh.status()[0] for sh in sm.shards]
+    sm.close()
+    return {"workload": "256^3 wave as %d shards of one process on one GPU (%d blocks of %d^3), "
+                        "pack / device copy / unpack exchange, dt reduced over shards" % (nshards, nb ** 3, block),
+            "precision": precision, "nshards": nshards, "ms_per_cycle": dt / steps * 1e3,
+            "zone_cycles_per_s": MESH ** 3 * steps / dt, "halo_cells_per_exchange": int(halo),
+            "status": max(rcs)}
+
+
 def restart_variant(ph, torch, block=32):
     """Write and read a restart file of the 256^3 FP64 benchmark mesh (state,
     tree, scalars) in the system's temporary directory: GB/s of file bytes,
@@ -648,7 +676,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline only: no variants, e2e, CPU leg")
     ap.add_argument("--mesh", type=int, default=256, help="zones per dimension (profiling runs)")
     ap.add_argument("--batch-launch", help="TX,TY,KC,CTAS: skip the batch autotuner (profiling runs)")
-    ap.add_argument("--only", choices=["batch", "two_level", "multilevel", "adjoint", "restart", "scalars", "e2e"],
+    ap.add_argument("--only", choices=["batch", "two_level", "multilevel", "adjoint", "restart", "scalars", "e2e",
+                                       "shards"],
                     help="run one variant workload only and print its record (profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -688,6 +717,8 @@ def main():
             rec = scalar_variant(ph, torch, args.steps, args.warmup, precision=args.precision)
         elif args.only == "e2e":
             rec = e2e_variant(ph, torch, args.block, args.precision, args.steps, args.warmup)
+        elif args.only == "shards":
+            rec = shard_variant(ph, torch, args.steps, args.warmup, precision=args.precision)
         else:
             rec = adjoint_variant(ph, torch, args.precision)
         if rank == 0:
@@ -748,6 +779,11 @@ def main():
             v = scalar_variant(ph, torch, args.steps, args.warmup, precision=prec)
             variants.append(v)
             log("%s with 2 passive scalars: %.3e zone-cycles/s" % (prec, v["zone_cycles_per_s"]))
+        for ns in (2, 4):
+            v = shard_variant(ph, torch, args.steps, args.warmup, nshards=ns)
+            variants.append(v)
+            log("fp64 in %d shards: %.3e zone-cycles/s (%d halo cells per exchange)"
+                % (ns, v["zone_cycles_per_s"], v["halo_cells_per_exchange"]))
         v = restart_variant(ph, torch)
         variants.append(v)
         log("restart: save %.2f GB/s, load %.2f GB/s (%.0f MB)" % (v["save_gbs"], v["load_gbs"], v["bytes"] / 1e6))

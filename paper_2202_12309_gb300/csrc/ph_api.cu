@@ -645,7 +645,7 @@ ph::StageArgs<T> stage_args(ph_mesh* m, int stage) {
   a.KC = m->tile[2];
   a.nleaf = m->nleaf();
   a.stage = stage;
-  a.want_rate = (stage == 2 && !m->multi_level) ? 1 : 0;
+  a.want_rate = stage == 2 ? 1 : 0;
   a.P = phys<T>(m);
   a.sc = m->sc;
   a.nvar = m->nvar;
@@ -720,8 +720,9 @@ int remesh_t(ph_mesh* m, std::vector<Leaf>& nl);
 // One multi-level cycle (host-driven; flux correction after each stage).
 template <class T>
 int multi_level_cycle(ph_mesh* m) {
+  // dt of this cycle: set by set_state, a refinement, a load, the previous
+  // cycle's stage 2 (folded signal rates) or the remesh after it
   int rc;
-  if ((rc = refresh_dt_t<T>(m))) return rc;
   const ph::LevelGeom geom = level_geom(m);
   for (int stage = 1; stage <= 2; ++stage) {
     const ph::StageArgs<T> a = stage_args<T>(m, stage);
@@ -729,10 +730,13 @@ int multi_level_cycle(ph_mesh* m) {
     T* out = (T*)(stage == 1 ? m->U1 : m->U0);
     PH_CUDA(ph::launch_flux_correct<T>(out, m->d_corr_leaf, m->d_rec_beg, m->ncorr, m->d_rec_face,
                                        (const T*)m->d_fcc, (const T*)m->d_fcf, m->nx, m->d_level, geom,
-                                       stage == 1 ? 1.0 : 0.5, m->sc, m->stream, m->nvar));
+                                       stage == 1 ? 1.0 : 0.5, m->sc, m->stream, m->nvar, phys<T>(m),
+                                       stage == 2 ? 1 : 0));
     if ((rc = fill_ghosts_t<T>(m, out))) return rc;
   }
-  PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 1, m->stream));
+  // commit the cycle; the next dt from the rates stage 2 and the correction
+  // folded (recomputed below on the new mesh if the tree changes)
+  PH_CUDA(ph::launch_advance(m->sc, m->cfg.cfl, 3, m->stream));
   for (auto& l : m->leaf) l.age += 1;
   if (m->cfg.adaptive) {
     std::vector<int8_t> flags;
@@ -751,8 +755,10 @@ int multi_level_cycle(ph_mesh* m) {
         flags[b] = -1;
     }
     std::vector<Leaf> nl;
-    if (next_tree(m, flags, true, nl))
+    if (next_tree(m, flags, true, nl)) {
       if ((rc = remesh_t<T>(m, nl))) return rc;
+      if ((rc = refresh_dt_t<T>(m))) return rc;
+    }
   }
   return PH_OK;
 }

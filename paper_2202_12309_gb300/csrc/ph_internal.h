@@ -148,11 +148,14 @@ cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb,
 
 // K4: flux correction at fine-coarse faces, applied after the stage update.
 // One CTA per coarse leaf corr_leaf[c] with records rec_beg[c] .. rec_beg[c+1].
+// want_rate (stage 2): also fold the signal rate of every corrected cell
+// into sc->wmax_bits (the stage skips those cells).
 template <class T>
 cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
                                 const int nx[3], const int8_t* level, const LevelGeom& g,
-                                double beta, const DevScalars* sc, cudaStream_t s, int nvar = NV);
+                                double beta, DevScalars* sc, cudaStream_t s, int nvar, Phys<T> P,
+                                int want_rate);
 
 // Domain decomposition of a uniform mesh (ph_shard.cu).  Shard `shard` of
 // `nshards` owns the global leaves [lo, hi) of the Z-ordered root grid; the

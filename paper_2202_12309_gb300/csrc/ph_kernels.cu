@@ -667,13 +667,16 @@ cudaError_t launch_indicator(const T* U, const int nx[3], int nleaf, double* mb,
 // face, deterministically and without atomics.
 // rec_face: 2*d + side (side 1 = high face).
 // --------------------------------------------------------------------------
+// want_rate (stage 2): afterwards, fold the signal rate of every corrected
+// cell into sc->wmax_bits (the stage skipped those cells).
 template <class T>
 __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
                                     const int* __restrict__ rec_beg,
                                     const int* __restrict__ rec_face, const T* __restrict__ fcc,
                                     const T* __restrict__ fcf, int3 nx,
                                     const int8_t* __restrict__ level, const LevelGeom g,
-                                    double beta, const DevScalars* sc, int nvar) {
+                                    double beta, DevScalars* sc, int nvar, Phys<T> P, int want_rate) {
+  __shared__ double red[32];
   const int leaf = corr_leaf[blockIdx.x];
   const int lev = level[leaf];
   const int n[3] = {nx.x, nx.y, nx.z};
@@ -707,18 +710,45 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
     }
     __syncthreads();
   }
+  if (!want_rate) return;
+  const T i1 = (T)g.idx[lev][0], i2 = (T)g.idx[lev][1], i3 = (T)g.idx[lev][2];
+  unsigned floors = 0;
+  double m = 0.0;
+  for (int r = rec_beg[blockIdx.x]; r < rec_beg[blockIdx.x + 1]; ++r) {
+    const int face = rec_face[r];
+    const int d = face >> 1, side = face & 1;
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const int m1 = n[t1], m2 = n[t2];
+    for (int c = threadIdx.x; c < m1 * m2; c += blockDim.x) {
+      const int a2 = c / m1, a1 = c - a2 * m1;
+      int l[3];
+      l[d] = side ? n[d] - 1 : 0;
+      l[t1] = a1;
+      l[t2] = a2;
+      const size_t o = ((size_t)(l[2] + NG) * S[1] + (l[1] + NG)) * S[0] + (l[0] + NG);
+      T w[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) w[v] = Ub[v * vs + o];
+      cons_to_prim(w, P, floors);
+      const double r8 = (double)wave_rate(w, P, i1, i2, i3);
+      if (!(r8 <= m)) m = r8;
+    }
+  }
+  block_max_to(&sc->wmax_bits, m, red);
+  if (floors) atomicAdd(&sc->floor_hits, (unsigned long long)floors);
 }
 
 template <class T>
 cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, int ncorr,
                                 const int* rec_face, const T* fc_coarse, const T* fc_fine,
                                 const int nx[3], const int8_t* level, const LevelGeom& g,
-                                double beta, const DevScalars* sc, cudaStream_t s, int nvar) {
+                                double beta, DevScalars* sc, cudaStream_t s, int nvar, Phys<T> P,
+                                int want_rate) {
   PH_RANGE("ph flux correction");
   if (ncorr <= 0) return cudaSuccess;
   flux_correct_kernel<T><<<ncorr, 256, 0, s>>>(U, corr_leaf, rec_beg, rec_face, fc_coarse, fc_fine,
                                                 make_int3(nx[0], nx[1], nx[2]), level, g, beta, sc,
-                                                nvar);
+                                                nvar, P, want_rate);
   return cudaGetLastError();
 }
 
@@ -739,8 +769,8 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
                                            int);                                                \
   template cudaError_t launch_flux_correct<T>(T*, const int*, const int*, int, const int*,      \
                                               const T*, const T*, const int*, const int8_t*,    \
-                                              const LevelGeom&, double, const DevScalars*,      \
-                                              cudaStream_t, int);
+                                              const LevelGeom&, double, DevScalars*,            \
+                                              cudaStream_t, int, Phys<T>, int);
 PH_INST(double)
 PH_INST(float)
 #undef PH_INST

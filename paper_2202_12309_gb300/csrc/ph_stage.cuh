@@ -80,6 +80,15 @@ __device__ __forceinline__ void capture(const StageArgs<T>& a, int leaf, int fac
 
 // NTO: thread count of the CTA when the tile runs inside a kernel of another
 // size (0: the tile's own choice below).
+// Cell (i, j, k) of a leaf lies on a face whose flux-correction record has
+// the leaf on its coarse side (fr: the leaf's 6 records, 2 rec on the coarse
+// side, 2 rec + 1 on the fine side, -1 none): the correction changes it.
+__device__ __forceinline__ bool coarse_face_cell(const int* fr, int i, int j, int k, int n1, int n2, int n3) {
+  auto coarse = [](int r) { return r >= 0 && (r & 1) == 0; };
+  return (i == 0 && coarse(fr[0])) || (i == n1 - 1 && coarse(fr[1])) || (j == 0 && coarse(fr[2])) ||
+         (j == n2 - 1 && coarse(fr[3])) || (k == 0 && coarse(fr[4])) || (k == n3 - 1 && coarse(fr[5]));
+}
+
 template <class T, int TX, int TY, int NVT = NV, int NTO = 0>
 struct StageSmem {
   static constexpr int WX = TX + 4, WY = TY + 4;
@@ -566,7 +575,10 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
         if (k == n3 - 1 && fr[5] >= 0)
           for (int v = 0; v < NVT; ++v) capture(a, leaf, 5, i, j, v, fzm[v]);
       }
-      if (J.want_rate) {
+      // the signal rate of the new state for the next dt; on multi-level
+      // meshes, cells next to a fine-coarse face on the coarse side are
+      // skipped here and rated by the flux correction that changes them
+      if (J.want_rate && !(a.face_rec && coarse_face_cell(a.face_rec + 6 * leaf, i, j, k, n1, n2, n3))) {
         cons_to_prim<T, NVT>(unew, P, floors);
         const T r = wave_rate(unew, P, idx1, idx2, idx3);
         const double rd = (double)r;
