@@ -356,7 +356,7 @@ def scalar_variant(ph, torch, steps, warmup, precision="fp64", nscalars=2, block
     ms = e0.elapsed_time(e1)
     tile = list(m.tile())
     m.close()
-    return {"workload": "256^3 wave with %d passive scalars, %d blocks of %d^3" % (nscalars, nb ** 3, block),
+    return {"workload": "%d^3 wave with %d passive scalars, %d blocks of %d^3" % (MESH, nscalars, nb ** 3, block),
             "precision": precision, "tile": tile, "ms_per_cycle": ms / steps,
             "zone_cycles_per_s": MESH ** 3 * steps / (ms / 1e3)}
 
@@ -382,8 +382,8 @@ def shard_variant(ph, torch, steps, warmup, nshards=2, precision="fp64", block=3
     halo = sum(sh.halo(p)[0][2] for sh in sm.shards for p in range(nshards) if p != sh.shard)
     rcs = [sh.status()[0] for sh in sm.shards]
     sm.close()
-    return {"workload": "256^3 wave as %d shards of one process on one GPU (%d blocks of %d^3), "
-                        "pack / device copy / unpack exchange, dt reduced over shards" % (nshards, nb ** 3, block),
+    return {"workload": "%d^3 wave as %d shards of one process on one GPU (%d blocks of %d^3), "
+                        "pack / device copy / unpack exchange, dt reduced over shards" % (MESH, nshards, nb ** 3, block),
             "precision": precision, "nshards": nshards, "ms_per_cycle": dt / steps * 1e3,
             "zone_cycles_per_s": MESH ** 3 * steps / dt, "halo_cells_per_exchange": int(halo),
             "status": max(rcs)}
@@ -414,7 +414,7 @@ def restart_variant(ph, torch, block=32):
         if os.path.exists(path):
             os.remove(path)
     m.close()
-    return {"workload": "restart file of the 256^3 FP64 mesh (%d blocks of %d^3)" % ((MESH // block) ** 3, block),
+    return {"workload": "restart file of the %d^3 FP64 mesh (%d blocks of %d^3)" % (MESH, (MESH // block) ** 3, block),
             "bytes": nbytes, "save_s": t1 - t0, "load_s": t2 - t1,
             "save_gbs": nbytes / (t1 - t0) / 1e9, "load_gbs": nbytes / (t2 - t1) / 1e9,
             "bitwise_state": same}
@@ -624,9 +624,9 @@ def dist_setup(args):
 
 def headline_config(block, precision, nb, world=1):
     """The `config` of the benchmark line: the workload both arms report on."""
-    cfg = {"workload": "uniform 256^3-zone periodic linear sound wave (A=1e-4, k=2pi(1,1,1)), "
+    cfg = {"workload": "uniform %d^3-zone periodic linear sound wave (A=1e-4, k=2pi(1,1,1)), "
                        "%d blocks of %d^3, 2 ghost zones, %s, 1 cycle per step"
-                       % (nb, block, precision.upper()),
+                       % (MESH, nb, block, precision.upper()),
            "zones": MESH ** 3, "block": block, "nblocks": nb,
            "l2": "state %.0f MB > 129 MB L2: no flush needed"
                  % (MESH ** 3 * 5 * (8 if precision == "fp64" else 4) / 1e6 * (1 + 4.0 / block) ** 3),
