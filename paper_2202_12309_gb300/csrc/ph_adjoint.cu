@@ -15,9 +15,11 @@
 // which flows back through HLLE to the face states, through
 // W_L = W_a + h_a, W_R = W_b - h_b to the cells and their half-slopes h, and
 // through each half-slope h_k = vl(W_{k-1}, W_k, W_{k+1}) to three cells;
-// finally W -> U by the transpose of the primitive Jacobian.  Three kernels
-// per direction/stage: faces (HLLE reverse), cells (gather of face and slope
-// contributions), primitives (W -> U).  The transpose of the ghost exchange
+// finally W -> U by the transpose of the primitive Jacobian.  Per stage: the
+// primitives of the stage input once; per direction the faces (HLLE
+// reverse), the slopes (each cell's half-slope differentiated once; FP32
+// fuses this into the gather) and the gather per cell; then the primitives
+// (W -> U).  The transpose of the ghost exchange
 // is a gather: an interior cell next to a block face receives the adjoint of
 // the face-ghost cell that copied it in the neighbouring block.  Everything
 // is a gather with one writer per output, so results are reproducible run to
@@ -25,6 +27,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ph_hydro.h"
@@ -104,192 +107,148 @@ __device__ __forceinline__ T vl_half_d(T wm, T w0, T wp, T& dm, T& d0, T& dp) {
   return prod * is;
 }
 
-// Reverse of the HLLE flux (same formulation as the forward kernel), with
-// Einfeldt's max/min and the Roe sound-speed clip frozen at their forward
-// choices.  Accumulates wlb, wrb (primitive adjoints) and gbar.
+// Reverse of the HLLE flux in the factored form of the stage kernels' hlle()
+// (ph_device.cuh), with the same forward arithmetic:
+//   F = cL F_L + cR F_R + cD (U_R - U_L),  cL = b+/(b+ - b-), cR = -b-/(b+ - b-),
+//   cD = b+ b-/(b+ - b-),  alL = cL v_nL - cD,  alR = cR v_nR + cD,
+//   aL = alL rho_L, aR = alR rho_R:  F_rho = aL + aR,
+//   F_v = aL v_L + aR v_R (+ cL p_L + cR p_R on the normal component),
+//   F_E = alL (rho h)_L + alR (rho h)_R - cD (p_R - p_L).
+// Einfeldt's max / min and the Roe sound-speed clip are frozen at their
+// forward choices.  Accumulates wlb, wrb (primitive adjoints) and gbar
+// (d/d gamma: gamma enters through 1/(gamma-1) in rho h, gamma - 1 in the
+// Roe sound speed and gamma p in the sound speeds).
 template <class T, int DIR>
 __device__ void hlle_rev(const T wl[NV], const T wr[NV], const Phys<T>& P, const T fb[NV], T wlb[NV],
                          T wrb[NV], double& gbar) {
   constexpr int IN = 1 + DIR;
+  constexpr int IB = 1 + (DIR + 1) % 3, IC = 1 + (DIR + 2) % 3;
   // ---- forward
   const T rl = wl[0], pl = wl[4], rr = wr[0], pr = wr[4];
   const T vnl = wl[IN], vnr = wr[IN];
-  const T v2l = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
-  const T v2r = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-  const T el = pl * P.igm1 + T(0.5) * rl * v2l;
-  const T er = pr * P.igm1 + T(0.5) * rr * v2r;
-  const T ql = rsq(rl), qr = rsq(rr);
-  const T sl = rl * ql, sr = rr * qr;
-  const T irl = ql * ql, irr = qr * qr;
-  const T xl = P.gamma * pl * irl, xr = P.gamma * pr * irr;
-  const T cl = sq(xl), cr = sq(xr);
-  const T hl = (el + pl) * irl, hr = (er + pr) * irr;
+  const T kl = fma(wl[IN], wl[IN], fma(wl[IB], wl[IB], wl[IC] * wl[IC]));
+  const T kr = fma(wr[IN], wr[IN], fma(wr[IB], wr[IB], wr[IC] * wr[IC]));
+  const T hl = fma(pl, P.igm1, fma(T(0.5) * rl, kl, pl));  // rho h
+  const T hr = fma(pr, P.igm1, fma(T(0.5) * rr, kr, pr));
+  const T ql = rsq(rl), qr = rsq(rr);                      // 1/sqrt(rho)
+  const T sl = rl * ql, sr = rr * qr;                      // sqrt(rho)
+  const T gl = sq(P.gamma * pl), gr = sq(P.gamma * pr);    // c = g / sqrt(rho)
   const T isum = rcp(sl + sr);
   const T wsl = sl * isum, wsr = sr * isum;
   T u[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = wsl * wl[1 + a] + wsr * wr[1 + a];
-  const T hroe = wsl * hl + wsr * hr;
-  const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-  const T a2raw = P.gm1 * (hroe - T(0.5) * usq);
-  const bool a2pos = a2raw > T(0);
-  const T croe = sq(a2pos ? a2raw : T(0));
+  for (int a = 0; a < 3; ++a) u[a] = fma(wsl, wl[1 + a], wsr * wr[1 + a]);
+  const T t = fma(hl, ql, hr * qr);
+  const T hroe = t * isum;
+  const T usq = fma(u[IN - 1], u[IN - 1], fma(u[IB - 1], u[IB - 1], u[IC - 1] * u[IC - 1]));
+  const T a2 = P.gm1 * fma(T(-0.5), usq, hroe);
+  const bool a2pos = positive(a2);
+  const T croe = a2pos ? sq(a2) : T(0);
   const T un = u[IN - 1];
-  const T A = vnr + cr, B = un + croe, C = vnl - cl, D = un - croe;
-  const bool AgeB = A >= B;
-  const T m1 = AgeB ? A : B;
-  const bool bp0 = T(0) >= m1;
-  const T bp = bp0 ? T(0) : m1;
-  const bool CleD = C <= D;
-  const T m2 = CleD ? C : D;
-  const bool bm0 = T(0) <= m2;
-  const T bm = bm0 ? T(0) : m2;
+  const T A = fma(gr, qr, vnr), B = un + croe;
+  const T C = fma(-gl, ql, vnl), D = un - croe;
+  const T bp = max0(A, B), bm = min0(C, D);
   const T idb = rcp(bp - bm);
-  const T bpbm = bp * bm;
-  const T mfl = rl * vnl, mfr = rr * vnr;
-  T FL[NV], FR[NV], UL[NV], UR[NV];
-  FL[0] = mfl;
-  FR[0] = mfr;
-  UL[0] = rl;
-  UR[0] = rr;
-#pragma unroll
-  for (int a = 1; a <= 3; ++a) {
-    FL[a] = mfl * wl[a] + (a == IN ? pl : T(0));
-    FR[a] = mfr * wr[a] + (a == IN ? pr : T(0));
-    UL[a] = rl * wl[a];
-    UR[a] = rr * wr[a];
-  }
-  FL[4] = (el + pl) * vnl;
-  FR[4] = (er + pr) * vnr;
-  UL[4] = el;
-  UR[4] = er;
+  const T cL = bp * idb, cR = -bm * idb, cD = (bp * bm) * idb;
+  const T alL = fma(cL, vnl, -cD), alR = fma(cR, vnr, cD);
+  const T aL = alL * rl, aR = alR * rr;
   // ---- reverse
-  T bpb = 0, bmb = 0, bpbmb = 0, idbb = 0;
-  T FLb[NV], FRb[NV], ULb[NV], URb[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const T N = bp * FL[v] - bm * FR[v] + bpbm * (UR[v] - UL[v]);
-    idbb += fb[v] * N;
-    const T Nb = fb[v] * idb;
-    bpb += Nb * FL[v];
-    FLb[v] = Nb * bp;
-    bmb -= Nb * FR[v];
-    FRb[v] = -Nb * bm;
-    bpbmb += Nb * (UR[v] - UL[v]);
-    URb[v] = Nb * bpbm;
-    ULb[v] = -Nb * bpbm;
-  }
-  bpb += bpbmb * bm;
-  bmb += bpbmb * bp;
-  {
-    const T diffb = -idb * idb * idbb;
-    bpb += diffb;
-    bmb -= diffb;
-  }
-  T Ab = 0, Bb = 0, Cb = 0, Db = 0;
-  if (!bp0) {
-    if (AgeB) Ab = bpb; else Bb = bpb;
-  }
-  if (!bm0) {
-    if (CleD) Cb = bmb; else Db = bmb;
-  }
-  T vnrb = Ab, crb = Ab, unb = Bb + Db, croeb = Bb - Db, vnlb = Cb, clb = -Cb;
-  // fluxes and conserved states back to primitives
-  T rlb = 0, rrb = 0, plb = 0, prb = 0, elb = 0, erb = 0;
-  T vlb[3] = {0, 0, 0}, vrb[3] = {0, 0, 0};
-  T mflb = FLb[0], mfrb = FRb[0];
-  rlb += ULb[0];
-  rrb += URb[0];
+  T aLb = fb[0], aRb = fb[0];
 #pragma unroll
   for (int a = 1; a <= 3; ++a) {
-    mflb += FLb[a] * wl[a];
-    vlb[a - 1] += FLb[a] * mfl;
-    mfrb += FRb[a] * wr[a];
-    vrb[a - 1] += FRb[a] * mfr;
-    if (a == IN) {
-      plb += FLb[a];
-      prb += FRb[a];
-    }
-    rlb += ULb[a] * wl[a];
-    vlb[a - 1] += ULb[a] * rl;
-    rrb += URb[a] * wr[a];
-    vrb[a - 1] += URb[a] * rr;
+    aLb = fma(fb[a], wl[a], aLb);
+    aRb = fma(fb[a], wr[a], aRb);
+    wlb[a] += fb[a] * aL;
+    wrb[a] += fb[a] * aR;
   }
-  elb += FLb[4] * vnl + ULb[4];
-  plb += FLb[4] * vnl;
-  vnlb += FLb[4] * (el + pl);
-  erb += FRb[4] * vnr + URb[4];
-  prb += FRb[4] * vnr;
-  vnrb += FRb[4] * (er + pr);
-  rlb += mflb * vnl;
-  vnlb += mflb * rl;
-  rrb += mfrb * vnr;
-  vnrb += mfrb * rr;
-  // Roe sound speed
-  T a2b = (a2pos && croe > T(0)) ? croeb * (T(0.5) * rcp(croe)) : T(0);
-  T hroeb = a2b * P.gm1;
-  const T usqb = -T(0.5) * P.gm1 * a2b;
-  gbar += (double)a2b * (double)(hroe - T(0.5) * usq);
+  T cLb = fb[IN] * pl, cRb = fb[IN] * pr;
+  T plb = fma(fb[IN], cL, fb[4] * cD), prb = fma(fb[IN], cR, -fb[4] * cD);
+  T cDb = -fb[4] * (pr - pl);
+  T hlb = fb[4] * alL, hrb = fb[4] * alR;
+  const T alLb = fma(fb[4], hl, aLb * rl), alRb = fma(fb[4], hr, aRb * rr);
+  T rlb = aLb * alL, rrb = aRb * alR;
+  cLb = fma(alLb, vnl, cLb);
+  cRb = fma(alRb, vnr, cRb);
+  cDb += alRb - alLb;
+  T vnlb = alLb * cL, vnrb = alRb * cR;
+  T bpb = fma(cDb, bm, cLb) * idb, bmb = fma(cDb, bp, -cRb) * idb;
+  {
+    const T idbb = fma(cLb, bp, fma(-cRb, bm, cDb * (bp * bm)));
+    const T db = -idb * idb * idbb;  // idb = 1/(b+ - b-)
+    bpb += db;
+    bmb -= db;
+  }
+  T Ab = T(0), Bb = T(0), Cb = T(0), Db = T(0);
+  if (bp > T(0)) {
+    if (A >= B) Ab = bpb; else Bb = bpb;
+  }
+  if (bm < T(0)) {
+    if (C <= D) Cb = bmb; else Db = bmb;
+  }
+  T grb = Ab * qr, qrb = Ab * gr;
+  T glb = -Cb * ql, qlb = -Cb * gl;
+  vnrb += Ab;
+  vnlb += Cb;
+  const T unb = Bb + Db, croeb = Bb - Db;
+  // Roe sound speed croe = sqrt(a2), a2 = (gamma - 1)(hroe - |u|^2 / 2)
+  const T a2b = (a2pos && croe > T(0)) ? croeb * (T(0.5) * rcp(croe)) : T(0);
+  const T hroeb = a2b * P.gm1;
+  const T usqb = T(-0.5) * P.gm1 * a2b;
+  gbar += (double)a2b * (double)fma(T(-0.5), usq, hroe);
   T ub[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) ub[a] = usqb * T(2) * u[a];
+  for (int a = 0; a < 3; ++a) ub[a] = T(2) * usqb * u[a];
   ub[IN - 1] += unb;
-  T wslb = hroeb * hl, wsrb = hroeb * hr;
-  T hlb = hroeb * wsl, hrb = hroeb * wsr;
+  T wslb = T(0), wsrb = T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    wslb += ub[a] * wl[1 + a];
-    vlb[a] += ub[a] * wsl;
-    wsrb += ub[a] * wr[1 + a];
-    vrb[a] += ub[a] * wsr;
+    wslb = fma(ub[a], wl[1 + a], wslb);
+    wsrb = fma(ub[a], wr[1 + a], wsrb);
+    wlb[1 + a] += ub[a] * wsl;
+    wrb[1 + a] += ub[a] * wsr;
   }
+  // hroe = (hl ql + hr qr) isum, wsl = sl isum, wsr = sr isum
+  const T tb = hroeb * isum;
+  const T isumb = fma(hroeb, t, fma(wslb, sl, wsrb * sr));
+  hlb = fma(tb, ql, hlb);
+  hrb = fma(tb, qr, hrb);
+  qlb = fma(tb, hl, qlb);
+  qrb = fma(tb, hr, qrb);
   T slb = wslb * isum, srb = wsrb * isum;
-  const T isumb = wslb * sl + wsrb * sr;
   {
-    const T s_b = -isum * isum * isumb;
-    slb += s_b;
-    srb += s_b;
+    const T sb = -isum * isum * isumb;  // isum = 1/(sl + sr)
+    slb += sb;
+    srb += sb;
   }
-  elb += hlb * irl;
-  plb += hlb * irl;
-  T irlb = hlb * (el + pl);
-  erb += hrb * irr;
-  prb += hrb * irr;
-  T irrb = hrb * (er + pr);
-  {
-    const T xlb = clb * (T(0.5) * rcp(cl)), xrb = crb * (T(0.5) * rcp(cr));
-    gbar += (double)xlb * (double)(pl * irl) + (double)xrb * (double)(pr * irr);
-    plb += xlb * P.gamma * irl;
-    irlb += xlb * P.gamma * pl;
-    prb += xrb * P.gamma * irr;
-    irrb += xrb * P.gamma * pr;
-  }
-  T qlb = irlb * T(2) * ql + slb * rl;
-  rlb += slb * ql;
-  T qrb = irrb * T(2) * qr + srb * rr;
-  rrb += srb * qr;
-  rlb += qlb * (-T(0.5) * ql * ql * ql);
-  rrb += qrb * (-T(0.5) * qr * qr * qr);
-  // el = pl igm1 + rl v2l / 2
-  plb += elb * P.igm1;
-  rlb += elb * T(0.5) * v2l;
-  prb += erb * P.igm1;
-  rrb += erb * T(0.5) * v2r;
-  gbar += -(double)(elb * pl + erb * pr) * (double)(P.igm1 * P.igm1);
+  rlb = fma(slb, ql, rlb);
+  qlb = fma(slb, rl, qlb);
+  rrb = fma(srb, qr, rrb);
+  qrb = fma(srb, rr, qrb);
+  // g = sqrt(gamma p)
+  const T xlb = gl > T(0) ? glb * (T(0.5) * rcp(gl)) : T(0);
+  const T xrb = gr > T(0) ? grb * (T(0.5) * rcp(gr)) : T(0);
+  plb = fma(xlb, P.gamma, plb);
+  prb = fma(xrb, P.gamma, prb);
+  gbar += (double)xlb * (double)pl + (double)xrb * (double)pr;
+  // q = rho^(-1/2)
+  rlb = fma(qlb, T(-0.5) * ql * ql * ql, rlb);
+  rrb = fma(qrb, T(-0.5) * qr * qr * qr, rrb);
+  // rho h = p / (gamma - 1) + rho |v|^2 / 2 + p
+  plb = fma(hlb, P.igm1 + T(1), plb);
+  prb = fma(hrb, P.igm1 + T(1), prb);
+  rlb = fma(hlb, T(0.5) * kl, rlb);
+  rrb = fma(hrb, T(0.5) * kr, rrb);
+  gbar -= ((double)hlb * (double)pl + (double)hrb * (double)pr) * (double)(P.igm1 * P.igm1);
+  const T klb = hlb * (T(0.5) * rl), krb = hrb * (T(0.5) * rr);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    vlb[a] += elb * rl * wl[1 + a];
-    vrb[a] += erb * rr * wr[1 + a];
+  for (int a = 1; a <= 3; ++a) {
+    wlb[a] = fma(T(2) * klb, wl[a], wlb[a]);
+    wrb[a] = fma(T(2) * krb, wr[a], wrb[a]);
   }
-  vlb[IN - 1] += vnlb;
-  vrb[IN - 1] += vnrb;
+  wlb[IN] += vnlb;
+  wrb[IN] += vnrb;
   wlb[0] += rlb;
   wrb[0] += rrb;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    wlb[1 + a] += vlb[a];
-    wrb[1 + a] += vrb[a];
-  }
   wlb[4] += plb;
   wrb[4] += prb;
 }
@@ -397,9 +356,121 @@ __global__ void adj_faces_kernel(const T* __restrict__ Wp, const T* __restrict__
   block_sum_add(gbar, gbar_out);
 }
 
-// Cells along DIR (padded 0..S-1, other axes interior): gather the face and
-// half-slope contributions into Wbar.  Face k+1/2 lives at padded index k+1
-// when 2 <= k+1 <= n+2.
+// Cells along DIR (padded 0..S-1, other axes interior).  Face k+1/2 lives at
+// padded index k+1 when 2 <= k+1 <= n+2.  Two kernels per direction:
+//   adj_slope: for every cell k with both neighbours (1 <= k <= S-2), the
+//     adjoint of its half-slope, hb = FL(face k+1/2) - FR(face k-1/2), times
+//     the slope's partial derivatives: Gm = hb dh/dW_{k-1}, G0 = hb dh/dW_k,
+//     Gp = hb dh/dW_{k+1} (zero elsewhere), each slope differentiated once;
+//   adj_gather: Wbar_p += FL(face p+1/2) + FR(face p-1/2) + Gp_{p-1} + G0_p
+//     + Gm_{p+1}, one writer per cell.
+template <int DIR>
+__device__ __forceinline__ void adj_line_cell(const AdjGeom& g, size_t e, size_t per_leaf, int& leaf, int pos[3]) {
+  leaf = (int)(e / per_leaf);
+  size_t r = e - (size_t)leaf * per_leaf;
+  int dims[3] = {g.nx[0], g.nx[1], g.nx[2]};
+  dims[DIR] = g.S[DIR];
+  int bx[3];
+  bx[0] = (int)(r % dims[0]);
+  r /= dims[0];
+  bx[1] = (int)(r % dims[1]);
+  bx[2] = (int)(r / dims[1]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) pos[d] = (d == DIR) ? bx[d] : bx[d] + NG;
+}
+
+template <int DIR>
+__device__ __forceinline__ size_t adj_at(const AdjGeom& g, const int pos[3], int q) {
+  int qq[3] = {pos[0], pos[1], pos[2]};
+  qq[DIR] = q;
+  return cell_index(g, qq[2], qq[1], qq[0]);
+}
+
+template <class T, int DIR>
+__global__ void adj_slope_kernel(const T* __restrict__ Wp, const T* __restrict__ FLb,
+                                 const T* __restrict__ FRb, T* __restrict__ Gm, T* __restrict__ G0,
+                                 T* __restrict__ Gp, AdjGeom g) {
+  constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
+  const int Sd = g.S[DIR], n = g.nx[DIR];
+  const size_t per_leaf = (size_t)Sd * g.nx[t1] * g.nx[t2];
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_leaf * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int leaf, pos[3];
+    adj_line_cell<DIR>(g, e, per_leaf, leaf, pos);
+    const int k = pos[DIR];
+    const size_t lo = (size_t)leaf * NV * vs;
+    const size_t ck = adj_at<DIR>(g, pos, k);
+    T hb[NV] = {0, 0, 0, 0, 0};
+    bool nz = false;
+    if (k >= 1 && k <= Sd - 2) {
+      const bool up = k + 1 >= NG && k + 1 <= n + NG, dn = k >= NG && k <= n + NG;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        hb[v] = (up ? FLb[lo + v * vs + adj_at<DIR>(g, pos, k + 1)] : T(0)) - (dn ? FRb[lo + v * vs + ck] : T(0));
+        nz |= hb[v] != T(0);
+      }
+    }
+    T m[NV] = {0, 0, 0, 0, 0}, z[NV] = {0, 0, 0, 0, 0}, q[NV] = {0, 0, 0, 0, 0};
+    if (nz) {
+      T wa[NV], wb[NV], wc[NV];
+      load_u(Wp + lo, vs, adj_at<DIR>(g, pos, k - 1), wa);
+      load_u(Wp + lo, vs, ck, wb);
+      load_u(Wp + lo, vs, adj_at<DIR>(g, pos, k + 1), wc);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T dm, d0, dp;
+        vl_half_d(wa[v], wb[v], wc[v], dm, d0, dp);
+        m[v] = hb[v] * dm;
+        z[v] = hb[v] * d0;
+        q[v] = hb[v] * dp;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Gm[lo + v * vs + ck] = m[v];
+      G0[lo + v * vs + ck] = z[v];
+      Gp[lo + v * vs + ck] = q[v];
+    }
+  }
+}
+
+template <class T, int DIR>
+__global__ void adj_gather_kernel(const T* __restrict__ FLb, const T* __restrict__ FRb,
+                                  const T* __restrict__ Gm, const T* __restrict__ G0,
+                                  const T* __restrict__ Gp, T* Wbar, AdjGeom g) {
+  constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
+  const int Sd = g.S[DIR], n = g.nx[DIR];
+  const size_t per_leaf = (size_t)Sd * g.nx[t1] * g.nx[t2];
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_leaf * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int leaf, pos[3];
+    adj_line_cell<DIR>(g, e, per_leaf, leaf, pos);
+    const int p = pos[DIR];
+    const size_t lo = (size_t)leaf * NV * vs;
+    const size_t cp = adj_at<DIR>(g, pos, p);
+    const bool up = p + 1 >= NG && p + 1 <= n + NG, dn = p >= NG && p <= n + NG;
+    const size_t cu = adj_at<DIR>(g, pos, p + 1 < Sd ? p + 1 : p);  // read only if p + 1 < S
+    const size_t cd = adj_at<DIR>(g, pos, p >= 1 ? p - 1 : p);       // read only if p >= 1
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t o = lo + v * vs;
+      T acc = T(0);
+      if (up) acc += FLb[o + cu];  // left state of face p+1/2
+      if (dn) acc += FRb[o + cp];  // right state of face p-1/2
+      if (p >= 1) acc += Gp[o + cd];
+      acc += G0[o + cp];
+      if (p + 1 < Sd) acc += Gm[o + cu];
+      Wbar[o + cp] += acc;
+    }
+  }
+}
+
+// FP32: the same gather in one kernel, each thread differentiating the three
+// half-slopes its cell enters (FP32 arithmetic is cheap here; one launch and
+// no intermediate arrays are not): the sum of the same terms in the same
+// order as adj_slope + adj_gather.
 template <class T, int DIR>
 __global__ void adj_cells_kernel(const T* __restrict__ Wp, const T* __restrict__ FLb,
                                  const T* __restrict__ FRb, T* Wbar, AdjGeom g) {
@@ -607,7 +678,7 @@ namespace ph {
 
 template <class T>
 int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, T* Wbar, T* Wp,
-          double* gbar) {
+          T* Gm, T* G0, T* Gp, double* gbar) {
   AdjGeom g;
   for (int d = 0; d < 3; ++d) {
     g.nx[d] = A.nx[d];
@@ -626,12 +697,23 @@ int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, 
   const size_t ncell = (size_t)(A.nx[0] + 4) * A.nx[1] * A.nx[2] * A.nleaf;
   const size_t all = A.block_elems / NV * A.nleaf;
   adj_wprim_kernel<T><<<grid_for(all), 256, 0, s>>>(U, Wp, g, P);
+  // FP64 (bound by the FP64 pipe): every half-slope differentiated once
+  // (adj_slope), then the gather; FP32: one fused gather (adj_cells)
+  auto cells = [&](auto dir) {
+    constexpr int D = decltype(dir)::value;
+    if constexpr (sizeof(T) == 4) {
+      adj_cells_kernel<T, D><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
+    } else {
+      adj_slope_kernel<T, D><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Gm, G0, Gp, g);
+      adj_gather_kernel<T, D><<<grid_for(ncell), 256, 0, s>>>(FLb, FRb, Gm, G0, Gp, Wbar, g);
+    }
+  };
   adj_faces_kernel<T, 0><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
-  adj_cells_kernel<T, 0><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
+  cells(std::integral_constant<int, 0>());
   adj_faces_kernel<T, 1><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
-  adj_cells_kernel<T, 1><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
+  cells(std::integral_constant<int, 1>());
   adj_faces_kernel<T, 2><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
-  adj_cells_kernel<T, 2><<<grid_for(ncell), 256, 0, s>>>(Wp, FLb, FRb, Wbar, g);
+  cells(std::integral_constant<int, 2>());
   adj_prim_kernel<T><<<grid_for(all), 256, 0, s>>>(U, Wbar, acc, g, P, gbar);
   PA_CUDA(cudaGetLastError());
   return PH_OK;
@@ -669,6 +751,9 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   T* Wbar = alloc(bytes);
   T* ufinal = alloc(bytes);
   T* Wp = alloc(bytes);
+  T* Gm = alloc(bytes);
+  T* G0 = alloc(bytes);
+  T* Gp = alloc(bytes);
   T* ck = alloc(bytes * nseg);
   T* seg0 = alloc(bytes * ckpt);
   T* seg1 = alloc(bytes * ckpt);
@@ -681,7 +766,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
       cleanup();
       return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
     }
-  if (bufs.size() != 17) {
+  if (bufs.size() != 20) {
     cleanup();
     return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
   }
@@ -757,12 +842,12 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, T(0.5), nullptr, T(0), elems);
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc1, lam, T(0.5), nullptr, T(0), elems);
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, lam, T(0.5) * dt, nullptr, T(0), elems);
-      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, Wp, gbar))) return fail_clean(rc);
+      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, Wp, Gm, G0, Gp, gbar))) return fail_clean(rc);
       adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc1, tmp, A.nbr, g);
       // stage 1: U1 = U0 + dt L(U0)
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, acc0, T(1), tmp, T(1), elems);
       adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, tmp, dt, nullptr, T(0), elems);
-      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, Wp, gbar))) return fail_clean(rc);
+      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, Wp, Gm, G0, Gp, gbar))) return fail_clean(rc);
       adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, A.nbr, g);
       PA_CUDA(cudaGetLastError());
     }

@@ -39,7 +39,6 @@ struct Member {
   int nx[3], S[3], nb[3];
   int ntile[3];
   int tile[2];    // the member's tile (TX, TY)
-  int pair;       // 1: the member runs the paired FP32 tile (32 x 16)
   int KC;
   int nleaf, leaf0;
   double idx[3];
@@ -113,30 +112,21 @@ __device__ __forceinline__ Phys<T> member_phys(const Member& M) {
   return P;
 }
 
-// Pair mode (FP32, launch choice 32 x 16): members whose blocks tile into
-// 32 x 16 run the paired tile of ph_stage_pair.cuh, the others the one-cell
-// 16 x 16 tile with the same 256 threads.  Both share the ring at the start
-// of shared memory and the mbarriers and reduction scratch placed after the
-// larger of the two layouts.
-using OneCell16x256 = StageSmem<float, 16, 16, NV, PairSmem::NT>;
-struct PairBatchSmem {
-  static constexpr size_t body = PairSmem::body > OneCell16x256::body ? PairSmem::body : OneCell16x256::body;
-  static constexpr size_t red_off = (body + 15) / 16 * 16;
-  static constexpr size_t bar_off = red_off + 32 * sizeof(double);
-  static constexpr size_t bytes = bar_off + 4 * sizeof(uint64_t) + 128;
-};
-
 // Threads, shared memory and CTAs per SM (register budget) of the batch
-// kernel for a launch choice.
-template <class T, int TX, int TY>
+// kernel for a launch choice.  Pair mode (FP32 with TMA staging, launch
+// choice 32 x 16 or 16 x 16): every member runs the paired tile of
+// ph_stage_pair.cuh of that width (its blocks must tile into it); other
+// choices run the one-cell tile.
+template <class T, int TX, int TY, bool TMA>
 struct BatchTile {
-  static constexpr bool PAIR = sizeof(T) == 4 && TX == 32 && TY == 16;
+  static constexpr bool PAIR = sizeof(T) == 4 && TMA && TY == 16 && (TX == 32 || TX == 16);
+  using PS = PairSmemT<(TX == 16 ? 16 : 32)>;
   using One = StageSmem<T, (PAIR ? 16 : TX), (PAIR ? 16 : TY)>;
-  static constexpr int NT = PAIR ? PairSmem::NT : One::NT;
-  static constexpr size_t bytes = PAIR ? PairBatchSmem::bytes : One::bytes;
-  static constexpr size_t red_off = PAIR ? PairBatchSmem::red_off : One::red_off;
-  static constexpr size_t bar_off = PAIR ? PairBatchSmem::bar_off : One::bar_off;
-  static constexpr int MINB = PAIR ? 2 : (sizeof(T) == 4 ? 3 : 0);
+  static constexpr int NT = PAIR ? PS::NT : One::NT;
+  static constexpr size_t bytes = PAIR ? PS::bytes : One::bytes;
+  static constexpr size_t red_off = PAIR ? PS::red_off : One::red_off;
+  static constexpr size_t bar_off = PAIR ? PS::bar_off : One::bar_off;
+  static constexpr int MINB = PAIR ? PS::MINB : (sizeof(T) == 4 ? 3 : 0);
 };
 
 // The tile job of work item `it` in the given stage; returns the member.
@@ -188,13 +178,8 @@ __device__ bool batch_stage_phase(const BatchArgs<T>& a, const StageArgs<T>& noc
     const int vz0 = (J.leaf - M.leaf0) * NV;
     const CUtensorMap* tm = TMA ? a.tmaps + 2 * m + (STAGE == 1 ? 0 : 1) : nullptr;
     double rate;
-    if constexpr (BatchTile<T, TX, TY>::PAIR) {
-      static_assert(TMA, "pair mode stages planes by TMA");
-      if (M.pair)
-        rate = stage_tile_pair<STAGE>(J, member_phys<float>(M), smem, floors, tm, vz0, bars, failed, parity);
-      else
-        rate = stage_tile<float, 16, 16, true, NV, STAGE, PairSmem::NT>(J, member_phys<float>(M), nocap, smem,
-                                                                         floors, tm, vz0, bars, failed, parity);
+    if constexpr (BatchTile<T, TX, TY, TMA>::PAIR) {
+      rate = stage_tile_pair<TX, STAGE>(J, member_phys<float>(M), smem, floors, tm, vz0, bars, failed, parity);
     } else {
       rate = stage_tile<T, TX, TY, TMA>(J, member_phys<T>(M), nocap, smem, floors, tm, vz0, bars, failed, parity);
     }
@@ -233,9 +218,9 @@ __device__ void batch_ghost_phase(const BatchArgs<T>& a, T* U) {
 }
 
 template <class T, int TX, int TY, bool TMA>
-__global__ void __launch_bounds__(BatchTile<T, TX, TY>::NT, BatchTile<T, TX, TY>::MINB)
+__global__ void __launch_bounds__(BatchTile<T, TX, TY, TMA>::NT, BatchTile<T, TX, TY, TMA>::MINB)
 batch_cycle_kernel(const BatchArgs<T> a) {
-  using SM = BatchTile<T, TX, TY>;
+  using SM = BatchTile<T, TX, TY, TMA>;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
@@ -325,9 +310,9 @@ __global__ void barrier_timeout_kernel(GridBar* gb, unsigned long long spin_limi
   if (threadIdx.x == 0 && !s_ok) atomicAdd(out, 1);
 }
 
-template <class T, int TX, int TY>
+template <class T, int TX, int TY, bool TMA>
 size_t batch_smem() {
-  return BatchTile<T, TX, TY>::bytes;
+  return BatchTile<T, TX, TY, TMA>::bytes;
 }
 
 }  // namespace ph
@@ -350,7 +335,8 @@ int bfail(int code, const std::string& msg) {
                                                          cudaGetErrorString(_e)); \
   } while (0)
 
-// autotuner candidates; the last is the paired FP32 tile (pair mode)
+// autotuner candidates; 16 x 16 is the 16-wide paired tile in pair mode,
+// 32 x 16 exists only there
 const int kTiles[5][2] = {{8, 8}, {16, 8}, {16, 16}, {32, 8}, {32, 16}};
 
 }  // namespace
@@ -401,7 +387,7 @@ template <class T, int TX, int TY, bool TMA>
 cudaError_t set_attr() {
   return cudaFuncSetAttribute(ph::batch_cycle_kernel<T, TX, TY, TMA>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ph::batch_smem<T, TX, TY>());
+                              (int)ph::batch_smem<T, TX, TY, TMA>());
 }
 
 template <class T, int TX, int TY, bool TMA>
@@ -409,7 +395,8 @@ int occupancy(int* per_sm) {
   cudaError_t e = set_attr<T, TX, TY, TMA>();
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ph::batch_cycle_kernel<T, TX, TY, TMA>,
-                                                    ph::BatchTile<T, TX, TY>::NT, ph::batch_smem<T, TX, TY>());
+                                                    ph::BatchTile<T, TX, TY, TMA>::NT,
+                                                    ph::batch_smem<T, TX, TY, TMA>());
   if (e != cudaSuccess) return bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   return PH_OK;
 }
@@ -446,8 +433,8 @@ cudaError_t launch_cycle(ph_batch* b, cudaStream_t s) {
   cudaLaunchConfig_t lc;
   std::memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(b->grid);
-  lc.blockDim = dim3(ph::BatchTile<T, TX, TY>::NT);
-  lc.dynamicSmemBytes = ph::batch_smem<T, TX, TY>();
+  lc.blockDim = dim3(ph::BatchTile<T, TX, TY, TMA>::NT);
+  lc.dynamicSmemBytes = ph::batch_smem<T, TX, TY, TMA>();
   lc.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -504,28 +491,30 @@ void drop_graph(ph_batch* b) {
   }
 }
 
-// Pair mode: FP32 with the launch choice 32 x 16 (paired tile where a member's
-// blocks tile into 32 x 16, one-cell 16 x 16 elsewhere); every member needs
-// blocks of at least 16 x 16 cells.
+// Pair mode: FP32 with TMA staging and the launch choice 32 x 16 or 16 x 16;
+// every member's blocks must tile into the choice (the paired tile of that
+// width runs on all of them).
 bool pair_choice(const ph_batch* b, int TX, int TY) {
-  return b->precision == PH_FP32 && TX == 32 && TY == 16;
+  return b->precision == PH_FP32 && ph::stage_tma_wanted() && TY == 16 && (TX == 32 || TX == 16);
 }
-bool pair_possible(const ph_batch* b) {
+bool pair_possible(const ph_batch* b, int TX) {
   if (b->precision != PH_FP32 || !ph::stage_tma_wanted()) return false;
   for (const Member& M : b->mem)
-    if (M.nx[0] < 16 || M.nx[1] < 16) return false;
+    if (M.nx[0] % TX || M.nx[1] % 16) return false;
   return true;
 }
 
 // Apply a launch choice: tiles per member, the cost-ordered work list, grid.
 int configure(ph_batch* b, int TX, int TY, int KC, int ctas) {
   const bool pair = pair_choice(b, TX, TY);
-  if (pair && !pair_possible(b))
-    return bfail(PH_ERR_INVALID, "batch: the 32 x 16 paired tile needs FP32, TMA and blocks of 16 x 16 or more");
+  if (pair && !pair_possible(b, TX))
+    return bfail(PH_ERR_INVALID, "batch: FP32 tiles of 32 x 16 and 16 x 16 are paired and need TMA staging "
+                                 "and blocks that tile into them");
+  if (TX == 32 && TY == 16 && !pair)
+    return bfail(PH_ERR_INVALID, "batch: the 32 x 16 tile is the paired FP32 tile");
   for (Member& M : b->mem) {
-    M.pair = pair && M.nx[0] % 32 == 0 && M.nx[1] % 16 == 0;
-    M.tile[0] = pair ? (M.pair ? 32 : 16) : TX;
-    M.tile[1] = pair ? 16 : TY;
+    M.tile[0] = TX;
+    M.tile[1] = TY;
   }
   const bool tma = build_tmaps(b);
   if (pair && !tma) return bfail(PH_ERR_INVALID, "batch: the paired tile needs TMA staging");
@@ -820,11 +809,16 @@ int ph_batch_create(const ph_config* cfgs, int32_t nsim, void* stream, ph_batch*
     if (e) rc = bfail(PH_ERR_CUDA, cudaGetErrorString(e));
   }
   if (!rc) {
-    // FP32: the paired tile where the members allow it; else 16 x 16 or 8 x 8
+    // FP32: the widest paired tile every member's blocks tile into; else the
+    // one-cell 16 x 16 (FP64, or FP32 without TMA), 16 x 8 or 8 x 8 tile
     int minn = 1 << 30;
     for (const Member& M : b->mem) minn = std::min(minn, std::min(M.nx[0], M.nx[1]));
-    const bool pair = pair_possible(b);
-    const int TX = pair ? 32 : (minn >= 16 ? 16 : 8), TY = minn >= 16 ? 16 : 8;
+    int TX = minn >= 16 ? 16 : 8, TY = minn >= 16 ? 16 : 8;
+    if (pair_possible(b, 32)) {
+      TX = 32;
+    } else if (!pair_possible(b, 16) && TY == 16 && pair_choice(b, 16, 16)) {
+      TY = 8;  // FP32 with TMA: 16 x 16 is paired, and these blocks do not tile into it
+    }
     rc = configure(b, TX, TY, 32, 0);
   }
   if (rc) {
@@ -965,7 +959,7 @@ int ph_batch_autotune(ph_batch* b, int32_t trial_cycles, int32_t chosen[4]) {
   for (int t = 0; t < 5 && !rc; ++t) {
     const int TX = kTiles[t][0], TY = kTiles[t][1];
     const bool pair = pair_choice(b, TX, TY);
-    if (pair ? !pair_possible(b) : (t == 4 || TX > 2 * minn || TY > minn)) continue;
+    if (pair ? !pair_possible(b, TX) : (t == 4 || TX > 2 * minn || TY > minn)) continue;
     int per_sm = 0;
     // an upper bound for the CTA count; configure() clamps to the variant it picks
     rc = b->precision == PH_FP32 ? (pair ? occupancy_t<float, true>(TX, TY, &per_sm)

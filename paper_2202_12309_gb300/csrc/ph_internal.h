@@ -89,8 +89,16 @@ template <class T>
 size_t stage_smem_bytes(int TX, int TY);
 bool stage_tile_supported(int TX, int TY);
 // 32 x 16: the paired FP32 kernel (FP32 uniform meshes with TMA staging,
-// nx1 a multiple of 32 and nx2 of 16)
+// nx1 a multiple of 32 and nx2 of 16), the only kernel of that tile
 bool stage_pair_tile(int TX, int TY);
+// Whether a mesh's stages run the paired FP32 kernel: FP32, TMA staging,
+// hydro variables only, one level, and tiles 32 x 16 or 16 x 16 that divide
+// the block (16 x 16 tiles of other meshes run the one-cell kernel).
+bool stage_pair_kernel(bool fp32, bool tma, int nvar, bool multi_level, const int tile[3], const int nx[3]);
+// Resident CTAs per SM of the stage kernel for a tile (0 if unknown); the
+// stage kernels' shared-memory attributes must be set (configure_stage_kernels).
+template <class T>
+int stage_ctas_per_sm(int TX, int TY, int nvar, bool pair, bool tma);
 // tiles that meshes with passive scalars can use
 bool stage_scalar_tile(int TX, int TY);
 cudaError_t configure_stage_kernels();

@@ -20,6 +20,12 @@ bool stage_tile_supported(int TX, int TY) {
 
 bool stage_pair_tile(int TX, int TY) { return TX == PairSmem::TX && TY == PairSmem::TY; }
 
+bool stage_pair_kernel(bool fp32, bool tma, int nvar, bool multi_level, const int tile[3], const int nx[3]) {
+  if (!fp32 || !tma || nvar != NV || multi_level || tile[1] != 16) return false;
+  if (tile[0] != 32 && tile[0] != 16) return false;
+  return nx[0] % tile[0] == 0 && nx[1] % tile[1] == 0;
+}
+
 template <class T>
 size_t stage_smem_bytes(int TX, int TY) {
   if (sizeof(T) == 4 && stage_pair_tile(TX, TY)) return PairSmem::bytes;
@@ -68,11 +74,17 @@ cudaError_t configure_stage_kernels() {
   if ((e = configure_tile<float, 16, 16, NV + 2>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 8, 8, NV + 1>()) != cudaSuccess) return e;
   if ((e = configure_tile<float, 8, 8, NV + 2>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(stage_kernel_pair<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(stage_kernel_pair<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)PairSmem::bytes)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(stage_kernel_pair<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)PairSmem::bytes);
+  if ((e = cudaFuncSetAttribute(stage_kernel_pair<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PairSmem::bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(stage_kernel_pair<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PairSmem16::bytes)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(stage_kernel_pair<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PairSmem16::bytes);
 }
 
 template <class T, int TX, int TY, int NVT = NV>
@@ -100,16 +112,55 @@ static cudaError_t launch_scalar_tiles(const StageArgs<T>& a, int TX, int TY, cu
   return cudaErrorInvalidValue;
 }
 
-// The paired FP32 kernel (32 x 16 tiles, TMA staging, uniform meshes).
+// The paired FP32 kernel (TXP x 16 tiles, TMA staging, uniform meshes).
+template <int TXP>
 static cudaError_t launch_pair(const StageArgs<float>& a, const CUtensorMap* tmap, cudaStream_t s) {
-  if (!tmap || a.face_rec) return cudaErrorInvalidValue;
+  using SM = PairSmemT<TXP>;
+  if (!tmap || a.face_rec || a.nx[0] % TXP || a.nx[1] % SM::TY) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)a.nleaf * a.ntile[0] * a.ntile[1] * a.ntile[2];
   if (grid == 0) return cudaSuccess;
   if (a.stage == 1)
-    stage_kernel_pair<1><<<grid, PairSmem::NT, PairSmem::bytes, s>>>(a, *tmap);
+    stage_kernel_pair<TXP, 1><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
   else
-    stage_kernel_pair<2><<<grid, PairSmem::NT, PairSmem::bytes, s>>>(a, *tmap);
+    stage_kernel_pair<TXP, 2><<<grid, SM::NT, SM::bytes, s>>>(a, *tmap);
   return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the stage-2 kernel a launch would run (0 if the
+// query fails); stage 1 has the same shape.
+template <class K>
+static int occupancy_of(K kernel, int nt, size_t smem) {
+  int n = 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, nt, smem) == cudaSuccess ? n : 0;
+}
+
+template <class T, int TX, int TY, int NVT = NV>
+static int tile_occupancy(bool tma) {
+  using SM = StageSmem<T, TX, TY, NVT>;
+  if (!tma) return occupancy_of(stage_kernel<T, TX, TY, NVT>, SM::NT, SM::bytes);
+  if (NVT != NV) return occupancy_of(stage_kernel_tma<T, TX, TY, NVT, 0>, SM::NT, SM::bytes);
+  return occupancy_of(stage_kernel_tma<T, TX, TY, NVT, 2>, SM::NT, SM::bytes);
+}
+
+template <class T>
+int stage_ctas_per_sm(int TX, int TY, int nvar, bool pair, bool tma) {
+  if constexpr (sizeof(T) == 4) {
+    if (pair && TX == 32 && TY == 16) return occupancy_of(stage_kernel_pair<32, 2>, PairSmem::NT, PairSmem::bytes);
+    if (pair && TX == 16 && TY == 16)
+      return occupancy_of(stage_kernel_pair<16, 2>, PairSmem16::NT, PairSmem16::bytes);
+  }
+  if (pair) return 0;
+  if (nvar == NV + 1 || nvar == NV + 2) {
+    const bool one = nvar == NV + 1;
+    if (TX == 16 && TY == 16) return one ? tile_occupancy<T, 16, 16, NV + 1>(tma) : tile_occupancy<T, 16, 16, NV + 2>(tma);
+    if (TX == 8 && TY == 8) return one ? tile_occupancy<T, 8, 8, NV + 1>(tma) : tile_occupancy<T, 8, 8, NV + 2>(tma);
+    return 0;
+  }
+  if (TX == 8 && TY == 8) return tile_occupancy<T, 8, 8>(tma);
+  if (TX == 16 && TY == 8) return tile_occupancy<T, 16, 8>(tma);
+  if (TX == 16 && TY == 16) return tile_occupancy<T, 16, 16>(tma);
+  if (TX == 32 && TY == 8) return tile_occupancy<T, 32, 8>(tma);
+  return 0;
 }
 
 template <class T>
@@ -118,8 +169,11 @@ cudaError_t launch_stage(const StageArgs<T>& a, int TX, int TY, cudaStream_t s, 
   if (a.nvar == NV + 1) return launch_scalar_tiles<T, NV + 1>(a, TX, TY, s, tmap);
   if (a.nvar == NV + 2) return launch_scalar_tiles<T, NV + 2>(a, TX, TY, s, tmap);
   if (a.nvar != NV) return cudaErrorInvalidValue;
-  if (stage_pair_tile(TX, TY)) {
-    if constexpr (sizeof(T) == 4) return launch_pair(a, tmap, s);
+  if (a.pair || stage_pair_tile(TX, TY)) {
+    if constexpr (sizeof(T) == 4) {
+      if (a.pair && TX == 32 && TY == 16) return launch_pair<32>(a, tmap, s);
+      if (a.pair && TX == 16 && TY == 16) return launch_pair<16>(a, tmap, s);
+    }
     return cudaErrorInvalidValue;
   }
   if (TX == 8 && TY == 8) return launch_tile<T, 8, 8>(a, tmap, s);
@@ -185,6 +239,8 @@ template cudaError_t launch_stage<double>(const StageArgs<double>&, int, int, cu
                                           const CUtensorMap*);
 template cudaError_t launch_stage<float>(const StageArgs<float>&, int, int, cudaStream_t,
                                          const CUtensorMap*);
+template int stage_ctas_per_sm<double>(int, int, int, bool, bool);
+template int stage_ctas_per_sm<float>(int, int, int, bool, bool);
 template size_t stage_smem_bytes<double>(int, int);
 template size_t stage_smem_bytes<float>(int, int);
 

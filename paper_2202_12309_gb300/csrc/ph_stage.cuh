@@ -56,6 +56,9 @@ struct StageArgs {
   // value into the ghost zones of Uout that it fills (push exchange), and the
   // separate exchange launch is not needed.
   const int* nbr;
+  // FP32 uniform meshes with TMA staging whose blocks tile into the launch's
+  // 32 x 16 or 16 x 16 tiles: the paired kernel (ph_stage_pair.cuh) runs
+  int pair;
 };
 
 // Store one face flux of a leaf on a fine-coarse face (Sec. 3.7 flux

