@@ -315,89 +315,6 @@ __device__ __noinline__ void composite_value(const T* U, const TreeView& tv, int
   }
 }
 
-// The value of cell (L, I, J, K) when a leaf of level L covers it (after
-// mapping through the domain's boundaries), as composite_value() gives it;
-// false otherwise.
-template <class T, int NVT>
-__device__ __forceinline__ bool composite_direct(const T* U, const TreeView& tv, int L, long long I,
-                                                 long long J, long long K, T* out) {
-  const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
-                  N3 = (long long)tv.nb[2] * tv.nx[2] << L;
-  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
-  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
-  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
-  const long long b1 = I / tv.nx[0], b2 = J / tv.nx[1], b3 = K / tv.nx[2];
-  int lev = 0;
-  const int lf = tree_cover(tv, L, b1, b2, b3, &lev);
-  if (lf < 0 || lev != L) return false;
-  read_cell<T, NVT>(U, tv, lf, (int)(I - b1 * tv.nx[0]), (int)(J - b2 * tv.nx[1]), (int)(K - b3 * tv.nx[2]), out);
-  negate_momenta(out, f1, f2, f3);
-  return true;
-}
-
-// composite_value() for the common ghost cell next to a level jump: one
-// prolongation from 7 cells of level L-1, or one restriction of 8 cells of
-// level L+1, every one of them read from a leaf of its own level (the same
-// operations in the same order, inline).  Returns false, leaving the cell to
-// the general recursive evaluation, when any of them is itself covered by
-// other levels.
-template <class T, int NVT>
-__device__ __forceinline__ bool composite_one_jump(const T* U, const TreeView& tv, int L, long long I,
-                                                   long long J, long long K, T* out) {
-  const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
-                  N3 = (long long)tv.nb[2] * tv.nx[2] << L;
-  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
-  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
-  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
-  const long long b1 = I / tv.nx[0], b2 = J / tv.nx[1], b3 = K / tv.nx[2];
-  int lev = 0;
-  const int lf = tree_cover(tv, L, b1, b2, b3, &lev);
-  if (lf >= 0 && lev == L) {
-    read_cell<T, NVT>(U, tv, lf, (int)(I - b1 * tv.nx[0]), (int)(J - b2 * tv.nx[1]), (int)(K - b3 * tv.nx[2]),
-                      out);
-  } else if (lf >= 0) {  // prolongation from level L-1
-    if (L < 1) return false;
-    const long long C[3] = {I >> 1, J >> 1, K >> 1};
-    const long long F[3] = {I, J, K};
-    T uc[NVT], acc[NVT];
-    if (!composite_direct<T, NVT>(U, tv, L - 1, C[0], C[1], C[2], uc)) return false;
-#pragma unroll
-    for (int v = 0; v < NVT; ++v) acc[v] = uc[v];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      long long cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
-      cm[d] -= 1;
-      cp[d] += 1;
-      T um[NVT], up[NVT];
-      if (!composite_direct<T, NVT>(U, tv, L - 1, cm[0], cm[1], cm[2], um)) return false;
-      if (!composite_direct<T, NVT>(U, tv, L - 1, cp[0], cp[1], cp[2], up)) return false;
-      const T sg = (F[d] & 1) ? T(0.25) : T(-0.25);
-#pragma unroll
-      for (int v = 0; v < NVT; ++v)
-        acc[v] = add_rn(acc[v], mul_rn(sg, minmod_dev(sub_rn(uc[v], um[v]), sub_rn(up[v], uc[v]))));
-    }
-#pragma unroll
-    for (int v = 0; v < NVT; ++v) out[v] = acc[v];
-  } else {  // restriction from level L+1
-    T sum[NVT];
-#pragma unroll
-    for (int v = 0; v < NVT; ++v) sum[v] = T(0);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      T f[NVT];
-      if (!composite_direct<T, NVT>(U, tv, L + 1, 2 * I + (c & 1), 2 * J + ((c >> 1) & 1),
-                                    2 * K + (c >> 2), f))
-        return false;
-#pragma unroll
-      for (int v = 0; v < NVT; ++v) sum[v] = add_rn(sum[v], f[v]);
-    }
-#pragma unroll
-    for (int v = 0; v < NVT; ++v) out[v] = mul_rn(T(0.125), sum[v]);
-  }
-  negate_momenta(out, f1, f2, f3);
-  return true;
-}
-
 // nbr[27 b + region]: the leaf of the same level that covers the block
 // location next to leaf b in that neighbour region, or -1 (finer or coarser
 // leaves, or a physical boundary).  Ghost cells of such a region are plain
@@ -456,8 +373,7 @@ __global__ void ghost_composite_eval_kernel(T* U, const TreeView tv, const int* 
     const long long o2 = (long long)leaf_id[4 * b + 2] * tv.nx[1] - NG;
     const long long o3 = (long long)leaf_id[4 * b + 3] * tv.nx[2] - NG;
     T val[NVT];
-    if (!composite_one_jump<T, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val))
-      composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
+    composite_value<T, COMPOSITE_DEPTH, NVT>(U, tv, lev, o1 + i, o2 + j, o3 + k, val);
     T* dst = U + (size_t)b * NVT * vs + ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
 #pragma unroll
     for (int v = 0; v < NVT; ++v) dst[v * vs] = val[v];
