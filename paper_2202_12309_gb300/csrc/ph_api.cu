@@ -108,6 +108,7 @@ struct ph_mesh {
   int nrec = 0, ncorr = 0;
   // multi-level: ghost cells evaluated through the tree, (leaf, shell index)
   int2* d_eval = nullptr;
+  void* d_recipe = nullptr;  // per evaluated cell: source offsets resolved once per tree
   int neval = 0;
   // staging for host copies and packed device copies
   void* staging = nullptr;
@@ -348,13 +349,13 @@ bool next_tree(const ph_mesh* m, const std::vector<int8_t>& flags, bool check_ag
 // ---------------------------------------------------------------- device tables
 
 // The device tables of a mesh (rebuilt whenever the tree changes).
-constexpr int kTableSlots = 14;
+constexpr int kTableSlots = 15;
 void table_slots(ph_mesh* m, void** (&slot)[kTableSlots]) {
   void** ptrs[kTableSlots] = {(void**)&m->d_nbr, (void**)&m->d_level, (void**)&m->d_node,
                               (void**)&m->d_leaf_id, (void**)&m->d_partial, (void**)&m->d_mb,
                               (void**)&m->d_face_rec, (void**)&m->d_fine_off, (void**)&m->d_corr_leaf,
                               (void**)&m->d_rec_beg, (void**)&m->d_rec_face, (void**)&m->d_fcc,
-                              (void**)&m->d_fcf, (void**)&m->d_eval};
+                              (void**)&m->d_fcf, (void**)&m->d_eval, (void**)&m->d_recipe};
   for (int i = 0; i < kTableSlots; ++i) slot[i] = ptrs[i];
 }
 
@@ -378,6 +379,7 @@ int upload(ph_mesh* m, V** dst, const std::vector<V>& src) {
 }
 
 int build_tables_fresh(ph_mesh* m);
+ph::TreeView tree_view(const ph_mesh* m);
 
 // Build and upload every per-leaf table for the current tree.  The new
 // tables are made beside the old ones, which are released only when every
@@ -460,6 +462,12 @@ int build_tables_fresh(ph_mesh* m) {
     m->neval = (int)ev.size();
   }
   if ((rc = upload(m, &m->d_node, m->node))) return rc;
+  if (m->multi_level) {
+    m->d_recipe = m->dalloc(ph::ghost_recipe_bytes() * (size_t)std::max(m->neval, 1));
+    if (!m->d_recipe) return fail(PH_ERR_OOM, "device allocation failed (tables)");
+    PH_CUDA(ph::launch_ghost_recipes(tree_view(m), m->d_leaf_id, m->d_eval, m->neval, m->d_recipe, m->stream,
+                                     m->nvar));
+  }
   m->d_partial = (double*)m->dalloc(sizeof(double) * m->nvar * std::max(n, 1));
   m->d_mb = (double*)m->dalloc(sizeof(double) * std::max(n, 1));
   if (!m->d_partial || !m->d_mb) return fail(PH_ERR_OOM, "device allocation failed (tables)");
@@ -619,7 +627,7 @@ template <class T>
 int fill_ghosts_t(ph_mesh* m, T* U) {
   if (m->multi_level) {
     PH_CUDA(ph::launch_ghost_composite<T>(U, tree_view(m), m->d_leaf_id, m->d_nbr, m->nleaf(), m->d_eval,
-                                          m->neval, m->stream, m->nvar));
+                                          m->d_recipe, m->neval, m->stream, m->nvar));
   } else {
     PH_CUDA(ph::launch_ghost_uniform<T>(U, m->d_nbr, m->nx, m->nleaf(), m->stream,
                                         m->d_leaf_id, m->nb, bc_mask(m), m->nvar));

@@ -118,10 +118,18 @@ cudaError_t launch_ghost_uniform(T* U, const int* nbr, const int nx[3], int nlea
 // nbr[27 * leaf + region]: the same-level leaf covering that neighbour
 // region (its ghost cells are copied directly, one CTA per leaf), or -1;
 // the cells of regions with -1 are eval[0 .. neval) = (leaf, shell index),
-// evaluated through the tree in a second launch, one thread per cell.
+// evaluated in a second launch, one thread per cell, from recipe[0 .. neval)
+// (launch_ghost_recipes: source offsets resolved once per tree).
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
-                                   int nleaf, const int2* eval, int neval, cudaStream_t s, int nvar = NV);
+                                   int nleaf, const int2* eval, const void* recipe, int neval, cudaStream_t s,
+                                   int nvar = NV);
+// Resolve the evaluation list of a tree into recipes (ghost_recipe_bytes()
+// each): for cells that are one prolongation, restriction or copy of cells in
+// leaves of their own level, the source offsets and sign flips.
+size_t ghost_recipe_bytes();
+cudaError_t launch_ghost_recipes(const TreeView& tv, const int* leaf_id, const int2* eval, int neval,
+                                 void* out, cudaStream_t s, int nvar);
 
 // K7: interior of every new leaf from the old mesh's composite field.
 template <class T>

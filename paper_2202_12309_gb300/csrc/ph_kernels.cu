@@ -357,13 +357,231 @@ __global__ void ghost_composite_kernel(T* U, const TreeView tv, const int* __res
 }
 
 // Ghost cells of regions without a same-level leaf: list[e] = (leaf, shell
-// index), one thread each; the composite field through the tree.
+// index), one thread each.  Most of them are one prolongation from 7 cells
+// of level L-1 or one restriction of 8 cells of level L+1, every source cell
+// in a leaf of its own level (or a copy of a cell of level L through a
+// physical boundary).  For those the tree walks depend on the tree only, so
+// they are done once per tree (ghost_recipe_kernel): the element offsets of
+// the source cells and the momentum sign flips of every image.  Each
+// exchange then reads the sources and combines them with the operations of
+// composite_value(), in its order (ghost_composite_eval_kernel); the other
+// cells take the recursive evaluation through the tree in a second launch
+// (ghost_composite_tree_kernel), which keeps the recursion's stack and
+// registers (212 a thread) out of the first one.
+struct GhostRecipe {
+  long long src[8];  // element offset of variable 0 of each source cell
+  // bits 0-1 kind (0: through the tree, 1: copy, 2: prolongation,
+  // 3: restriction); 2-4 parity of the cell along x1..x3 (prolongation);
+  // 5-7 momentum flips of the ghost cell's own image; 8 + 3 s: flips of
+  // source s
+  unsigned meta;
+  // bit s: source s of a prolongation is covered by finer leaves, its value
+  // the mean of its 8 children (src[s] is the offset of child (0, 0, 0))
+  unsigned mean;
+};
+
+template <int NVT>
+__device__ __forceinline__ bool direct_source(const TreeView& tv, int L, long long I, long long J, long long K,
+                                              long long& off, unsigned& flips) {
+  const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
+                  N3 = (long long)tv.nb[2] * tv.nx[2] << L;
+  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
+  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
+  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
+  const long long b1 = I / tv.nx[0], b2 = J / tv.nx[1], b3 = K / tv.nx[2];
+  int lev = 0;
+  const int lf = tree_cover(tv, L, b1, b2, b3, &lev);
+  if (lf < 0 || lev != L) return false;
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  off = (long long)((size_t)lf * NVT * vs +
+                    ((size_t)(K - b3 * tv.nx[2] + NG) * tv.S[1] + (J - b2 * tv.nx[1] + NG)) * tv.S[0] +
+                    (I - b1 * tv.nx[0] + NG));
+  flips = (f1 ? 1u : 0u) | (f2 ? 2u : 0u) | (f3 ? 4u : 0u);
+  return true;
+}
+
+// A prolongation source: a cell of a leaf of its level, or (mean = true) a
+// cell covered by finer leaves whose 8 children lie in one leaf of the next
+// level (the restriction composite_value() takes there).
+template <int NVT>
+__device__ __forceinline__ bool prolong_source(const TreeView& tv, int L, long long I, long long J, long long K,
+                                               long long& off, unsigned& flips, bool& mean) {
+  mean = false;
+  if (direct_source<NVT>(tv, L, I, J, K, off, flips)) return true;
+  const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
+                  N3 = (long long)tv.nb[2] * tv.nx[2] << L;
+  const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
+  const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
+  const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
+  int lev = 0;
+  if (tree_cover(tv, L, I / tv.nx[0], J / tv.nx[1], K / tv.nx[2], &lev) >= 0) return false;  // coarser
+  const long long c1 = 2 * I, c2 = 2 * J, c3 = 2 * K;  // first child; the 8 share a block (nx even)
+  const long long b1 = c1 / tv.nx[0], b2 = c2 / tv.nx[1], b3 = c3 / tv.nx[2];
+  const int lf = tree_cover(tv, L + 1, b1, b2, b3, &lev);
+  if (lf < 0 || lev != L + 1) return false;
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  off = (long long)((size_t)lf * NVT * vs +
+                    ((size_t)(c3 - b3 * tv.nx[2] + NG) * tv.S[1] + (c2 - b2 * tv.nx[1] + NG)) * tv.S[0] +
+                    (c1 - b1 * tv.nx[0] + NG));
+  flips = (f1 ? 1u : 0u) | (f2 ? 2u : 0u) | (f3 ? 4u : 0u);
+  mean = true;
+  return true;
+}
+
+template <int NVT>
+__global__ void ghost_recipe_kernel(const TreeView tv, const int* __restrict__ leaf_id,
+                                    const int2* __restrict__ list, int n, GhostRecipe* __restrict__ out) {
+  const Shell sh(tv.nx);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = list[e];
+    const int b = it.x;
+    int i, j, k;
+    sh.cell(it.y, i, j, k);
+    const int L = leaf_id[4 * b];
+    long long I = (long long)leaf_id[4 * b + 1] * tv.nx[0] - NG + i;
+    long long J = (long long)leaf_id[4 * b + 2] * tv.nx[1] - NG + j;
+    long long K = (long long)leaf_id[4 * b + 3] * tv.nx[2] - NG + k;
+    GhostRecipe R;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) R.src[q] = 0;
+    R.mean = 0u;
+    bool mn = false;
+    const long long N1 = (long long)tv.nb[0] * tv.nx[0] << L, N2 = (long long)tv.nb[1] * tv.nx[1] << L,
+                    N3 = (long long)tv.nb[2] * tv.nx[2] << L;
+    const bool f1 = domain_image(I, N1, tv.bc[0], tv.bc[1]);
+    const bool f2 = domain_image(J, N2, tv.bc[2], tv.bc[3]);
+    const bool f3 = domain_image(K, N3, tv.bc[4], tv.bc[5]);
+    unsigned meta = ((f1 ? 1u : 0u) | (f2 ? 2u : 0u) | (f3 ? 4u : 0u)) << 5;
+    const long long b1 = I / tv.nx[0], b2 = J / tv.nx[1], b3 = K / tv.nx[2];
+    int lev = 0;
+    const int lf = tree_cover(tv, L, b1, b2, b3, &lev);
+    bool ok = true;
+    unsigned fl = 0;
+    if (lf >= 0 && lev == L) {  // a cell of this level (an image through a boundary)
+      const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+      R.src[0] = (long long)((size_t)lf * NVT * vs +
+                             ((size_t)(K - b3 * tv.nx[2] + NG) * tv.S[1] + (J - b2 * tv.nx[1] + NG)) * tv.S[0] +
+                             (I - b1 * tv.nx[0] + NG));
+      meta |= 1u;
+    } else if (lf >= 0) {  // prolongation: C, then C -+ e_d for d = 1, 2, 3
+      const long long C[3] = {I >> 1, J >> 1, K >> 1};
+      ok = direct_source<NVT>(tv, L - 1, C[0], C[1], C[2], R.src[0], fl);
+      meta |= fl << 8;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        long long cm[3] = {C[0], C[1], C[2]}, cp[3] = {C[0], C[1], C[2]};
+        cm[d] -= 1;
+        cp[d] += 1;
+        ok = ok && prolong_source<NVT>(tv, L - 1, cm[0], cm[1], cm[2], R.src[1 + 2 * d], fl, mn);
+        meta |= ok ? fl << (8 + 3 * (1 + 2 * d)) : 0u;
+        R.mean |= ok && mn ? 1u << (1 + 2 * d) : 0u;
+        ok = ok && prolong_source<NVT>(tv, L - 1, cp[0], cp[1], cp[2], R.src[2 + 2 * d], fl, mn);
+        meta |= ok ? fl << (8 + 3 * (2 + 2 * d)) : 0u;
+        R.mean |= ok && mn ? 1u << (2 + 2 * d) : 0u;
+      }
+      meta |= 2u | (unsigned)(I & 1) << 2 | (unsigned)(J & 1) << 3 | (unsigned)(K & 1) << 4;
+    } else {  // restriction of the 8 children, x1 fastest
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        ok = ok && direct_source<NVT>(tv, L + 1, 2 * I + (c & 1), 2 * J + ((c >> 1) & 1), 2 * K + (c >> 2),
+                                      R.src[c], fl);
+        meta |= ok ? fl << (8 + 3 * c) : 0u;
+      }
+      meta |= 3u;
+    }
+    R.meta = ok ? meta : 0u;
+    out[e] = R;
+  }
+}
+
+template <class T, int NVT>
+__device__ __forceinline__ void recipe_source(const T* U, const TreeView& tv, size_t vs, const GhostRecipe& R,
+                                              int s, T out[NVT]) {
+  if ((R.mean >> s) & 1u) {  // restriction of the 8 children, x1 fastest
+    const size_t p1 = 1, p2 = tv.S[0], p3 = (size_t)tv.S[0] * tv.S[1];
+#pragma unroll
+    for (int v = 0; v < NVT; ++v) out[v] = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const T* q = U + R.src[s] + (c & 1) * p1 + ((c >> 1) & 1) * p2 + (c >> 2) * p3;
+#pragma unroll
+      for (int v = 0; v < NVT; ++v) out[v] = add_rn(out[v], q[v * vs]);
+    }
+#pragma unroll
+    for (int v = 0; v < NVT; ++v) out[v] = mul_rn(T(0.125), out[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NVT; ++v) out[v] = U[R.src[s] + v * vs];
+  }
+  const unsigned f = R.meta >> (8 + 3 * s);
+  negate_momenta(out, f & 1u, (f & 2u) != 0, (f & 4u) != 0);
+}
+
 template <class T, int NVT>
 __global__ void ghost_composite_eval_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id,
-                                            const int2* __restrict__ list, int n) {
+                                            const int2* __restrict__ list, const GhostRecipe* __restrict__ rec,
+                                            int n) {
   const Shell sh(tv.nx);
   const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 it = list[e];
+    const int b = it.x;
+    int i, j, k;
+    sh.cell(it.y, i, j, k);
+    const GhostRecipe R = rec[e];
+    const unsigned kind = R.meta & 3u;
+    T val[NVT];
+    if (kind == 0u) continue;  // ghost_composite_tree_kernel
+    {
+      if (kind == 1u) {
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) val[v] = U[R.src[0] + v * vs];
+      } else if (kind == 2u) {
+        T uc[NVT];
+        recipe_source<T, NVT>(U, tv, vs, R, 0, uc);
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) val[v] = uc[v];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T um[NVT], up[NVT];
+          recipe_source<T, NVT>(U, tv, vs, R, 1 + 2 * d, um);
+          recipe_source<T, NVT>(U, tv, vs, R, 2 + 2 * d, up);
+          const T sg = ((R.meta >> (2 + d)) & 1u) ? T(0.25) : T(-0.25);
+#pragma unroll
+          for (int v = 0; v < NVT; ++v)
+            val[v] = add_rn(val[v], mul_rn(sg, minmod_dev(sub_rn(uc[v], um[v]), sub_rn(up[v], uc[v]))));
+        }
+      } else {
+        T sum[NVT];
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) sum[v] = T(0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          T f[NVT];
+          recipe_source<T, NVT>(U, tv, vs, R, c, f);
+#pragma unroll
+          for (int v = 0; v < NVT; ++v) sum[v] = add_rn(sum[v], f[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) val[v] = mul_rn(T(0.125), sum[v]);
+      }
+      const unsigned f = R.meta >> 5;
+      negate_momenta(val, f & 1u, (f & 2u) != 0, (f & 4u) != 0);
+    }
+    T* dst = U + (size_t)b * NVT * vs + ((size_t)k * tv.S[1] + j) * tv.S[0] + i;
+#pragma unroll
+    for (int v = 0; v < NVT; ++v) dst[v * vs] = val[v];
+  }
+}
+
+template <class T, int NVT>
+__global__ void ghost_composite_tree_kernel(T* U, const TreeView tv, const int* __restrict__ leaf_id,
+                                            const int2* __restrict__ list, const GhostRecipe* __restrict__ rec,
+                                            int n) {
+  const Shell sh(tv.nx);
+  const size_t vs = (size_t)tv.S[0] * tv.S[1] * tv.S[2];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    if (rec[e].meta & 3u) continue;
     const int2 it = list[e];
     const int b = it.x;
     int i, j, k;
@@ -382,23 +600,46 @@ __global__ void ghost_composite_eval_kernel(T* U, const TreeView tv, const int* 
 
 template <class T, int NVT>
 static cudaError_t launch_ghost_composite_n(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
-                                           int nleaf, const int2* eval, int neval, cudaStream_t s) {
+                                           int nleaf, const int2* eval, const void* recipe, int neval,
+                                           cudaStream_t s) {
   ghost_composite_kernel<T, NVT><<<nleaf, 256, 0, s>>>(U, tv, leaf_id, nbr);
   if (neval > 0) {
     const int grid = std::min((neval + 127) / 128, 152 * 16);
-    ghost_composite_eval_kernel<T, NVT><<<grid, 128, 0, s>>>(U, tv, leaf_id, eval, neval);
+    ghost_composite_eval_kernel<T, NVT><<<grid, 128, 0, s>>>(U, tv, leaf_id, eval,
+                                                             (const GhostRecipe*)recipe, neval);
+    ghost_composite_tree_kernel<T, NVT><<<grid, 128, 0, s>>>(U, tv, leaf_id, eval,
+                                                             (const GhostRecipe*)recipe, neval);
   }
+  return cudaGetLastError();
+}
+
+size_t ghost_recipe_bytes() { return sizeof(GhostRecipe); }
+
+cudaError_t launch_ghost_recipes(const TreeView& tv, const int* leaf_id, const int2* eval, int neval,
+                                 void* out, cudaStream_t s, int nvar) {
+  if (neval <= 0) return cudaSuccess;
+  const int grid = std::min((neval + 127) / 128, 152 * 16);
+  GhostRecipe* r = (GhostRecipe*)out;
+  if (nvar == NV + 1)
+    ghost_recipe_kernel<NV + 1><<<grid, 128, 0, s>>>(tv, leaf_id, eval, neval, r);
+  else if (nvar == NV + 2)
+    ghost_recipe_kernel<NV + 2><<<grid, 128, 0, s>>>(tv, leaf_id, eval, neval, r);
+  else
+    ghost_recipe_kernel<NV><<<grid, 128, 0, s>>>(tv, leaf_id, eval, neval, r);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_ghost_composite(T* U, const TreeView& tv, const int* leaf_id, const int* nbr,
-                                   int nleaf, const int2* eval, int neval, cudaStream_t s, int nvar) {
+                                   int nleaf, const int2* eval, const void* recipe, int neval, cudaStream_t s,
+                                   int nvar) {
   PH_RANGE("ph ghost exchange (composite)");
   if (nleaf <= 0) return cudaSuccess;
-  if (nvar == NV + 1) return launch_ghost_composite_n<T, NV + 1>(U, tv, leaf_id, nbr, nleaf, eval, neval, s);
-  if (nvar == NV + 2) return launch_ghost_composite_n<T, NV + 2>(U, tv, leaf_id, nbr, nleaf, eval, neval, s);
-  return launch_ghost_composite_n<T, NV>(U, tv, leaf_id, nbr, nleaf, eval, neval, s);
+  if (nvar == NV + 1)
+    return launch_ghost_composite_n<T, NV + 1>(U, tv, leaf_id, nbr, nleaf, eval, recipe, neval, s);
+  if (nvar == NV + 2)
+    return launch_ghost_composite_n<T, NV + 2>(U, tv, leaf_id, nbr, nleaf, eval, recipe, neval, s);
+  return launch_ghost_composite_n<T, NV>(U, tv, leaf_id, nbr, nleaf, eval, recipe, neval, s);
 }
 
 template <class T, int NVT>
@@ -759,7 +1000,8 @@ cudaError_t launch_flux_correct(T* U, const int* corr_leaf, const int* rec_beg, 
   template cudaError_t launch_ghost_uniform<T>(T*, const int*, const int*, int, cudaStream_t, \
                                               const int*, const int*, int, int);              \
   template cudaError_t launch_ghost_composite<T>(T*, const TreeView&, const int*, const int*,  \
-                                                 int, const int2*, int, cudaStream_t, int);     \
+                                                 int, const int2*, const void*, int, cudaStream_t, \
+                                                 int);                                          \
   template cudaError_t launch_remesh<T>(T*, const int*, int, const T*, const TreeView&,        \
                                         cudaStream_t, int);                                     \
   template cudaError_t launch_rate<T>(const T*, const int8_t*, const LevelGeom&, const int*,   \
