@@ -501,11 +501,23 @@ def adjoint_variant(ph, torch, precision, cycles=20, ckpt=5):
     m.adjoint(U0, dLdU, cycles, ckpt)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    # the same with U0, dL/dU and the gradient resident in device memory
+    U0d = torch.from_numpy(U0).cuda()
+    dLdUd = torch.from_numpy(dLdU).cuda()
+    m.adjoint(U0d, dLdUd, cycles, ckpt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m.adjoint(U0d, dLdUd, cycles, ckpt)
+    torch.cuda.synchronize()
+    dtd = time.perf_counter() - t0
     m.close()
     zones = 64 ** 3
     return {"workload": "adjoint: 64^3 zones (8 blocks of 32^3), %d cycles, checkpoint every %d" % (cycles, ckpt),
             "precision": precision, "seconds_per_gradient": dt,
-            "zone_cycles_per_s": zones * cycles / dt, "note": "forward + recomputation + reverse"}
+            "seconds_per_gradient_device": dtd,
+            "zone_cycles_per_s": zones * cycles / dt,
+            "note": "forward + recomputation + reverse; seconds_per_gradient with host arrays in and out "
+                    "(copies inside), _device with device tensors"}
 
 
 def e2e_variant(ph, torch, block, precision, steps, warmup):
@@ -774,7 +786,8 @@ def main():
         for prec in ("fp64", "fp32"):
             v = adjoint_variant(ph, torch, prec)
             variants.append(v)
-            log("adjoint %s: %.3f s per gradient" % (prec, v["seconds_per_gradient"]))
+            log("adjoint %s: %.4f s per gradient (%.4f s with device-resident inputs)"
+                % (prec, v["seconds_per_gradient"], v["seconds_per_gradient_device"]))
         for prec in ("fp64", "fp32"):
             v = scalar_variant(ph, torch, args.steps, args.warmup, precision=prec)
             variants.append(v)

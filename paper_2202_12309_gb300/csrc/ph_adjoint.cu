@@ -292,8 +292,8 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst) {
 // Writes the adjoints of the face's left and right primitive states at the
 // padded index of the right cell.
 template <class T, int DIR>
-__global__ void adj_faces_kernel(const T* __restrict__ Wp, const T* __restrict__ mu, T* FLb, T* FRb,
-                                 AdjGeom g, Phys<T> P, double* gbar_out) {
+__global__ void adj_faces_kernel(const T* __restrict__ Wp, const T* __restrict__ H, const T* __restrict__ mu,
+                                 T* FLb, T* FRb, AdjGeom g, Phys<T> P, double* gbar_out) {
   constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
   const size_t per_leaf = (size_t)(g.nx[DIR] + 1) * g.nx[t1] * g.nx[t2];
   const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
@@ -333,15 +333,13 @@ __global__ void adj_faces_kernel(const T* __restrict__ Wp, const T* __restrict__
     }
     T wlb[NV] = {0, 0, 0, 0, 0}, wrb[NV] = {0, 0, 0, 0, 0};
     if (any) {
-      T w[4][NV];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) load_u(Wb, vs, c[s], w[s]);
+      // face states from the cells' half-slopes along DIR (adj_hslope_kernel)
+      const T* Hb = H + (size_t)leaf * NV * vs;
       T wl[NV], wr[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T d0, d1, d2;
-        wl[v] = w[1][v] + vl_half_d(w[0][v], w[1][v], w[2][v], d0, d1, d2);
-        wr[v] = w[2][v] - vl_half_d(w[1][v], w[2][v], w[3][v], d0, d1, d2);
+        wl[v] = Wb[v * vs + c[1]] + Hb[v * vs + c[1]];
+        wr[v] = Wb[v * vs + c[2]] - Hb[v * vs + c[2]];
       }
       hlle_rev<T, DIR>(wl, wr, P, fb, wlb, wrb, gbar);
     }
@@ -564,6 +562,33 @@ __global__ void adj_wprim_kernel(const T* __restrict__ U, T* __restrict__ Wp, Ad
   }
 }
 
+// Half van Leer slopes along DIR of the cells the face kernel reads: each
+// cell's once per stage, where the face kernel would compute each twice (one
+// per face of the cell).
+template <class T, int DIR>
+__global__ void adj_hslope_kernel(const T* __restrict__ Wp, T* __restrict__ H, AdjGeom g) {
+  // the cells the face kernel reads: padded 1 .. S-2 along DIR, interior
+  // along the other two axes
+  constexpr int t1 = (DIR + 1) % 3, t2 = (DIR + 2) % 3;
+  const size_t per_leaf = (size_t)g.S[DIR] * g.nx[t1] * g.nx[t2];
+  const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
+  const size_t stride = DIR == 0 ? 1 : (DIR == 1 ? (size_t)g.S[0] : (size_t)g.S[0] * g.S[1]);
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_leaf * g.nleaf;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int leaf, pos[3];
+    adj_line_cell<DIR>(g, e, per_leaf, leaf, pos);
+    const int q = pos[DIR];
+    if (q < 1 || q > g.S[DIR] - 2) continue;
+    const size_t base = (size_t)leaf * NV * vs + cell_index(g, pos[2], pos[1], pos[0]);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T dm, d0, dp;
+      H[base + v * vs] = vl_half_d(Wp[base + v * vs - stride], Wp[base + v * vs], Wp[base + v * vs + stride], dm,
+                                   d0, dp);
+    }
+  }
+}
+
 // W -> U for every padded cell: acc += J^T Wbar; Wbar cleared.
 template <class T>
 __global__ void adj_prim_kernel(const T* __restrict__ U, T* Wbar, T* acc, AdjGeom g, Phys<T> P,
@@ -598,9 +623,11 @@ __global__ void adj_prim_kernel(const T* __restrict__ U, T* Wbar, T* acc, AdjGeo
 
 // Transpose of the uniform ghost exchange: out = in on interior cells plus the
 // adjoints of the face-ghost images in the neighbouring blocks; 0 on ghosts.
-template <class T>
+// ACC (after the reverse of stage 2): instead of storing the result s,
+// acc += s and mu = dt s (the stage-1 seeds), 0 into mu on ghost cells.
+template <class T, bool ACC = false>
 __global__ void adj_ghost_t_kernel(const T* __restrict__ in, T* out, const int* __restrict__ nbr,
-                                   AdjGeom g) {
+                                   AdjGeom g, T* acc = nullptr, T dt = T(0)) {
   const size_t vs = (size_t)g.S[0] * g.S[1] * g.S[2];
   const int n1 = g.nx[0], n2 = g.nx[1], n3 = g.nx[2];
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < vs * g.nleaf;
@@ -614,7 +641,7 @@ __global__ void adj_ghost_t_kernel(const T* __restrict__ in, T* out, const int* 
     T* o = out + (size_t)leaf * NV * vs + c;
     if (!interior) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) o[v * vs] = T(0);
+      for (int v = 0; v < NV; ++v) o[v * vs] = T(0);  // ACC: mu
       continue;
     }
     const T* ib = in + (size_t)leaf * NV * vs + c;
@@ -635,16 +662,31 @@ __global__ void adj_ghost_t_kernel(const T* __restrict__ in, T* out, const int* 
     if (j >= n2) add(1 * 9 + 2 * 3 + 1, i, j - n2, k);
     if (k < NG + 2) add(0 * 9 + 1 * 3 + 1, i, j, k + n3);
     if (k >= n3) add(2 * 9 + 1 * 3 + 1, i, j, k - n3);
+    if (ACC) {
+      T* a = acc + (size_t)leaf * NV * vs + c;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) o[v * vs] = s[v];
+      for (int v = 0; v < NV; ++v) {
+        a[v * vs] = a[v * vs] + s[v];
+        o[v * vs] = dt * s[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) o[v * vs] = s[v];
+    }
   }
 }
 
-// out = alpha * x + beta * y (y may be null)
+// Stage-2 seeds of a reverse cycle from the state adjoint lam:
+// acc0 = lam / 2, acc1 = lam / 2, mu = (dt / 2) lam.
 template <class T>
-__global__ void adj_axpby_kernel(T* out, const T* x, T alpha, const T* y, T beta, size_t n) {
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    out[e] = alpha * x[e] + (y ? beta * y[e] : T(0));
+__global__ void adj_seed_kernel(const T* __restrict__ lam, T* __restrict__ acc0, T* __restrict__ acc1,
+                                T* __restrict__ mu, T hdt, size_t n) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const T l = lam[e];
+    acc0[e] = T(0.5) * l;
+    acc1[e] = T(0.5) * l;
+    mu[e] = hdt * l;
+  }
 }
 
 }  // namespace ph
@@ -678,7 +720,7 @@ namespace ph {
 
 template <class T>
 int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, T* Wbar, T* Wp,
-          T* Gm, T* G0, T* Gp, double* gbar) {
+          T* Gm, T* G0, T* Gp, T* H, double* gbar) {
   AdjGeom g;
   for (int d = 0; d < 3; ++d) {
     g.nx[d] = A.nx[d];
@@ -708,11 +750,14 @@ int vjp_L(const MeshAccess& A, const T* U, const T* mu, T* acc, T* FLb, T* FRb, 
       adj_gather_kernel<T, D><<<grid_for(ncell), 256, 0, s>>>(FLb, FRb, Gm, G0, Gp, Wbar, g);
     }
   };
-  adj_faces_kernel<T, 0><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
+  adj_hslope_kernel<T, 0><<<grid_for(ncell), 256, 0, s>>>(Wp, H, g);
+  adj_faces_kernel<T, 0><<<grid_for(nfaces0), 256, 0, s>>>(Wp, H, mu, FLb, FRb, g, P, gbar);
   cells(std::integral_constant<int, 0>());
-  adj_faces_kernel<T, 1><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
+  adj_hslope_kernel<T, 1><<<grid_for(ncell), 256, 0, s>>>(Wp, H, g);
+  adj_faces_kernel<T, 1><<<grid_for(nfaces0), 256, 0, s>>>(Wp, H, mu, FLb, FRb, g, P, gbar);
   cells(std::integral_constant<int, 1>());
-  adj_faces_kernel<T, 2><<<grid_for(nfaces0), 256, 0, s>>>(Wp, mu, FLb, FRb, g, P, gbar);
+  adj_hslope_kernel<T, 2><<<grid_for(ncell), 256, 0, s>>>(Wp, H, g);
+  adj_faces_kernel<T, 2><<<grid_for(nfaces0), 256, 0, s>>>(Wp, H, mu, FLb, FRb, g, P, gbar);
   cells(std::integral_constant<int, 2>());
   adj_prim_kernel<T><<<grid_for(all), 256, 0, s>>>(U, Wbar, acc, g, P, gbar);
   PA_CUDA(cudaGetLastError());
@@ -744,7 +789,6 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   T* lam = alloc(bytes);
   T* acc0 = alloc(bytes);
   T* acc1 = alloc(bytes);
-  T* tmp = alloc(bytes);
   T* mu = alloc(bytes);
   T* FLb = alloc(bytes);
   T* FRb = alloc(bytes);
@@ -754,6 +798,7 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   T* Gm = alloc(bytes);
   T* G0 = alloc(bytes);
   T* Gp = alloc(bytes);
+  T* H = alloc(bytes);
   T* ck = alloc(bytes * nseg);
   T* seg0 = alloc(bytes * ckpt);
   T* seg1 = alloc(bytes * ckpt);
@@ -839,15 +884,11 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
       const T* U1n = seg1 + (size_t)(c - c0) * elems;
       const T dt = (T)dts[c];
       // stage 2: U = 1/2 U0 + 1/2 (U1 + dt L(U1))
-      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, T(0.5), nullptr, T(0), elems);
-      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc1, lam, T(0.5), nullptr, T(0), elems);
-      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, lam, T(0.5) * dt, nullptr, T(0), elems);
-      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, Wp, Gm, G0, Gp, gbar))) return fail_clean(rc);
-      adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc1, tmp, A.nbr, g);
-      // stage 1: U1 = U0 + dt L(U0)
-      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(acc0, acc0, T(1), tmp, T(1), elems);
-      adj_axpby_kernel<T><<<gE, 256, 0, s>>>(mu, tmp, dt, nullptr, T(0), elems);
-      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, Wp, Gm, G0, Gp, gbar))) return fail_clean(rc);
+      adj_seed_kernel<T><<<gE, 256, 0, s>>>(lam, acc0, acc1, mu, T(0.5) * dt, elems);
+      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, Wp, Gm, G0, Gp, H, gbar))) return fail_clean(rc);
+      // stage 1: U1 = U0 + dt L(U0); its seeds acc0 += G^T acc1, mu = dt G^T acc1
+      adj_ghost_t_kernel<T, true><<<gE, 256, 0, s>>>(acc1, mu, A.nbr, g, acc0, dt);
+      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, Wp, Gm, G0, Gp, H, gbar))) return fail_clean(rc);
       adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, A.nbr, g);
       PA_CUDA(cudaGetLastError());
     }
