@@ -68,6 +68,12 @@ extern "C" {
  *                  (static_lo, static_hi) are refined at creation and pinned
  *   precision      PH_FP64 or PH_FP32 (state and fluxes; dt and totals stay FP64)
  *   tile[3]        fused-stage tile (TX, TY, KC); 0,0,0 = pick a default
+ *                  (KC then follows the leaf count).  TX x TY: 8x8, 16x8,
+ *                  16x16, 32x8, and for FP32 uniform meshes 32x16; on FP32
+ *                  uniform meshes with TMA staging and no passive scalars
+ *                  whose blocks tile into them, 32x16 and 16x16 run the
+ *                  paired kernel (two cells per thread; both widths give the
+ *                  same bits), other tiles the one-cell kernel
  *   bc[6]          physical boundary of each face (PH_BC_*, below); all zero
  *                  = periodic everywhere
  *   nscalars       passive scalars, 0 .. 2 (Sec. 3.4: the hydro package

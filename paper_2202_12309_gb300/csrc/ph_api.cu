@@ -1213,7 +1213,8 @@ static int create_mesh(const ph_config* cfg, void* stream, int nshards, int shar
     t[1] = (cfg->nx[1] >= 16 && t[0] == 16) ? 16 : 8;
     t[2] = cfg->nx[2] >= 32 ? 16 : cfg->nx[2];
     if (cfg->nscalars > 0 && !(t[0] == 16 && t[1] == 16)) t[0] = t[1] = 8;
-    // FP32 uniform meshes: the paired kernel where the blocks tile into 32 x 16
+    // FP32 uniform meshes: the 32 x 16 paired tile where the blocks tile into
+    // it (16 x 16, paired as well where the blocks tile into that, otherwise)
     const int pt[3] = {32, 16, t[2]};
     if (ph::stage_tma_wanted() && valid_tile(cfg, pt)) {
       t[0] = pt[0];
