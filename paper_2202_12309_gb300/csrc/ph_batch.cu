@@ -126,7 +126,10 @@ struct BatchTile {
   static constexpr size_t bytes = PAIR ? PS::bytes : One::bytes;
   static constexpr size_t red_off = PAIR ? PS::red_off : One::red_off;
   static constexpr size_t bar_off = PAIR ? PS::bar_off : One::bar_off;
-  static constexpr int MINB = PAIR ? PS::MINB : (sizeof(T) == 4 ? 3 : 0);
+  // FP64: registers capped for 512 threads per SM (2 CTAs of a 16 x 16 tile),
+  // as the single-mesh stage kernels compile; the cycle kernel holds both
+  // stages and would otherwise take 150 registers (one CTA per SM)
+  static constexpr int MINB = PAIR ? PS::MINB : (sizeof(T) == 4 ? 3 : (512 / NT > 0 ? 512 / NT : 1));
 };
 
 // The tile job of work item `it` in the given stage; returns the member.
