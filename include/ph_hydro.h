@@ -252,8 +252,10 @@ int ph_step_dt(ph_mesh* mesh, int32_t ncycles, const double* dts);
  * branches frozen at their forward values.
  *   U0       initial interior state (layout of ph_set_state)
  *   ncycles  cycles of the forward run; ckpt_every: keep every k-th state
- *            and recompute the k cycles in between (memory ~ ncycles/k + 2k
- *            states; the last k cycles' stage inputs are kept from the
+ *            and recompute the k cycles in between (memory ~ ncycles/k + 4k
+ *            states: two sets of a segment's stage inputs, one read by the
+ *            reverse sweep while the segment before is recomputed into the
+ *            other; the last k cycles' stage inputs are kept from the
  *            forward run, so those are not recomputed)
  *   dts      host array of ncycles dts, or NULL to use (and freeze) the CFL
  *            dts of the forward run

@@ -782,9 +782,17 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
     bufs.push_back(p);
     return (T*)p;
   };
+  // the reverse sweep runs on its own stream, so that the recomputation of
+  // the segment before (on the mesh's stream) overlaps it
+  cudaStream_t rs = nullptr;
+  cudaEvent_t ev_init = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
   auto cleanup = [&]() {
     cudaStreamSynchronize(s);
+    if (rs) cudaStreamSynchronize(rs);
     for (void* p : bufs) mesh_free(m, p);
+    for (cudaEvent_t e : {ev_init, ev_rec[0], ev_rec[1], ev_rev[0], ev_rev[1]})
+      if (e) cudaEventDestroy(e);
+    if (rs) cudaStreamDestroy(rs);
   };
   T* lam = alloc(bytes);
   T* acc0 = alloc(bytes);
@@ -800,8 +808,9 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   T* Gp = alloc(bytes);
   T* H = alloc(bytes);
   T* ck = alloc(bytes * nseg);
-  T* seg0 = alloc(bytes * ckpt);
-  T* seg1 = alloc(bytes * ckpt);
+  // stage inputs of one segment (U^n, U^1 per cycle), two sets: the reverse
+  // sweep reads one while the recomputation fills the other
+  T* segs[2][2] = {{alloc(bytes * ckpt), alloc(bytes * ckpt)}, {alloc(bytes * ckpt), alloc(bytes * ckpt)}};
   double* gbar = (double*)alloc(sizeof(double) * 2);
   double* d_dts = (double*)alloc(sizeof(double) * ncycles);
   DevScalars* sc_final = (DevScalars*)alloc(sizeof(DevScalars));
@@ -811,11 +820,20 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
       cleanup();
       return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
     }
-  if (bufs.size() != 20) {
+  if (bufs.size() != 22) {
     cleanup();
     return afail(PH_ERR_OOM, "device allocation failed (adjoint)");
   }
   const size_t count = (size_t)A.nleaf * NV * A.nx[0] * A.nx[1] * A.nx[2];
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&ev_init, &ev_rec[0], &ev_rec[1], &ev_rev[0], &ev_rev[1]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cleanup();
+      return afail(PH_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
   auto fail_clean = [&](int code) {
     cleanup();
     return code;
@@ -834,12 +852,13 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
   for (int c = 0; c < ncycles; ++c) {
     if (c % ckpt == 0)
       PA_CUDA(cudaMemcpyAsync(ck + (size_t)(c / ckpt) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+    T* const* last = segs[(nseg - 1) % 2];
     if (c >= clast)
-      PA_CUDA(cudaMemcpyAsync(seg0 + (size_t)(c - clast) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+      PA_CUDA(cudaMemcpyAsync(last[0] + (size_t)(c - clast) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
     rc = dts_in ? mesh_cycle_device_dt(m, d_dts + c) : mesh_cycle_record_dt(m, d_dts + c);
     if (rc) return fail_clean(rc);
     if (c >= clast)
-      PA_CUDA(cudaMemcpyAsync(seg1 + (size_t)(c - clast) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
+      PA_CUDA(cudaMemcpyAsync(last[1] + (size_t)(c - clast) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
   }
   if (!dts_in) {
     PA_CUDA(cudaMemcpyAsync(dts.data(), d_dts, sizeof(double) * ncycles, cudaMemcpyDeviceToHost, s));
@@ -869,39 +888,59 @@ int adjoint_t(ph_mesh* m, const void* U0, int ncycles, int ckpt, const double* d
     g.idx[d] = A.idx[d];
   }
   g.nleaf = A.nleaf;
-  // ---- backward, segment by segment
+  // ---- backward, segment by segment: the reverse sweep of segment sg (on
+  // rs) overlaps the recomputation of segment sg - 1 (on the mesh's stream)
+  // into the other set of stage inputs
+  PA_CUDA(cudaEventRecord(ev_init, s));  // seeds, the last segment's inputs, checkpoints
+  PA_CUDA(cudaStreamWaitEvent(rs, ev_init, 0));
+  MeshAccess AR = A;
+  AR.stream = rs;
+  auto recompute = [&](int sgr) -> int {
+    const int r0 = sgr * ckpt, r1 = std::min(r0 + ckpt, ncycles);
+    T* const* set = segs[sgr % 2];
+    // the set's last reader is the reverse sweep of segment sgr + 2
+    if (sgr + 2 <= nseg - 1) PA_CUDA(cudaStreamWaitEvent(s, ev_rev[sgr % 2], 0));
+    PA_CUDA(cudaMemcpyAsync(A.U0, ck + (size_t)sgr * elems, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int c = r0; c < r1; ++c) {
+      PA_CUDA(cudaMemcpyAsync(set[0] + (size_t)(c - r0) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
+      int rr = mesh_cycle_device_dt(m, d_dts + c);
+      if (rr) return rr;
+      PA_CUDA(cudaMemcpyAsync(set[1] + (size_t)(c - r0) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    PA_CUDA(cudaEventRecord(ev_rec[sgr % 2], s));
+    return PH_OK;
+  };
+  // (the last segment's inputs were kept by the forward pass: ev_init covers them)
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int c0 = sg * ckpt, c1 = std::min(c0 + ckpt, ncycles);
-    if (sg != nseg - 1)  // (the last segment was kept by the forward pass)
-      PA_CUDA(cudaMemcpyAsync(A.U0, ck + (size_t)sg * elems, bytes, cudaMemcpyDeviceToDevice, s));
-    for (int c = c0; c < c1 && sg != nseg - 1; ++c) {
-      PA_CUDA(cudaMemcpyAsync(seg0 + (size_t)(c - c0) * elems, A.U0, bytes, cudaMemcpyDeviceToDevice, s));
-      if ((rc = mesh_cycle_device_dt(m, d_dts + c))) return fail_clean(rc);
-      PA_CUDA(cudaMemcpyAsync(seg1 + (size_t)(c - c0) * elems, A.U1, bytes, cudaMemcpyDeviceToDevice, s));
-    }
+    if (sg >= 1 && (rc = recompute(sg - 1))) return fail_clean(rc);
+    if (sg != nseg - 1) PA_CUDA(cudaStreamWaitEvent(rs, ev_rec[sg % 2], 0));
+    T* const* set = segs[sg % 2];
     for (int c = c1 - 1; c >= c0; --c) {
-      const T* Un = seg0 + (size_t)(c - c0) * elems;
-      const T* U1n = seg1 + (size_t)(c - c0) * elems;
+      const T* Un = set[0] + (size_t)(c - c0) * elems;
+      const T* U1n = set[1] + (size_t)(c - c0) * elems;
       const T dt = (T)dts[c];
       // stage 2: U = 1/2 U0 + 1/2 (U1 + dt L(U1))
-      adj_seed_kernel<T><<<gE, 256, 0, s>>>(lam, acc0, acc1, mu, T(0.5) * dt, elems);
-      if ((rc = vjp_L<T>(A, U1n, mu, acc1, FLb, FRb, Wbar, Wp, Gm, G0, Gp, H, gbar))) return fail_clean(rc);
+      adj_seed_kernel<T><<<gE, 256, 0, rs>>>(lam, acc0, acc1, mu, T(0.5) * dt, elems);
+      if ((rc = vjp_L<T>(AR, U1n, mu, acc1, FLb, FRb, Wbar, Wp, Gm, G0, Gp, H, gbar))) return fail_clean(rc);
       // stage 1: U1 = U0 + dt L(U0); its seeds acc0 += G^T acc1, mu = dt G^T acc1
-      adj_ghost_t_kernel<T, true><<<gE, 256, 0, s>>>(acc1, mu, A.nbr, g, acc0, dt);
-      if ((rc = vjp_L<T>(A, Un, mu, acc0, FLb, FRb, Wbar, Wp, Gm, G0, Gp, H, gbar))) return fail_clean(rc);
-      adj_ghost_t_kernel<T><<<gE, 256, 0, s>>>(acc0, lam, A.nbr, g);
+      adj_ghost_t_kernel<T, true><<<gE, 256, 0, rs>>>(acc1, mu, A.nbr, g, acc0, dt);
+      if ((rc = vjp_L<T>(AR, Un, mu, acc0, FLb, FRb, Wbar, Wp, Gm, G0, Gp, H, gbar))) return fail_clean(rc);
+      adj_ghost_t_kernel<T><<<gE, 256, 0, rs>>>(acc0, lam, A.nbr, g);
       PA_CUDA(cudaGetLastError());
     }
+    PA_CUDA(cudaEventRecord(ev_rev[sg % 2], rs));
   }
   // ---- outputs; leave the mesh at the final state of the forward run
   if (on_device) {
-    PA_CUDA(launch_pack<T>(lam, (T*)dLdU0, A.nx, A.nleaf, 1, s));
+    PA_CUDA(launch_pack<T>(lam, (T*)dLdU0, A.nx, A.nleaf, 1, rs));
   } else {
-    PA_CUDA(launch_pack<T>(lam, packed, A.nx, A.nleaf, 1, s));
-    PA_CUDA(cudaMemcpyAsync(dLdU0, packed, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    PA_CUDA(launch_pack<T>(lam, packed, A.nx, A.nleaf, 1, rs));
+    PA_CUDA(cudaMemcpyAsync(dLdU0, packed, count * sizeof(T), cudaMemcpyDeviceToHost, rs));
   }
   double hg = 0.0;
-  PA_CUDA(cudaMemcpyAsync(&hg, gbar, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PA_CUDA(cudaMemcpyAsync(&hg, gbar, sizeof(double), cudaMemcpyDeviceToHost, rs));
+  PA_CUDA(cudaStreamSynchronize(rs));
   PA_CUDA(cudaMemcpyAsync(A.U0, ufinal, bytes, cudaMemcpyDeviceToDevice, s));
   PA_CUDA(cudaMemcpyAsync(A.sc, sc_final, sizeof(DevScalars), cudaMemcpyDeviceToDevice, s));
   PA_CUDA(cudaStreamSynchronize(s));
