@@ -273,6 +273,11 @@ def roofline_for(v, pk, peak_kind, fp64_measured=None):
                "peak_source": peak_kind + " hbm_gbs (copy bandwidth)",
                "algorithmic_bytes_per_zone_launch": words * word,
                "ghost_bytes_per_zone_launch": ghost}
+        # the other roof: FP32 arithmetic (128 lanes per SM, fma = 2 flops)
+        fp32_peak = SMS * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        out["alu"] = {"achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": tflops / fp32_peak,
+                      "flops_per_zone_launch": FLOPS_PER_ZONE_CYCLE * 0.5,
+                      "peak_source": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
         return out
     # FP64: bound by the FP64 pipe
     peak = SMS * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -285,7 +290,7 @@ def roofline_for(v, pk, peak_kind, fp64_measured=None):
         out["peak_measured"] = fp64_measured
         out["frac_of_measured"] = tflops / fp64_measured
         out["peak_measured_source"] = ("measured in this run: ph_debug_fma_rate, FP64 DFMA chains, "
-                                       "%d CTAs x 256 threads, best of 5" % (SMS * 8))
+                                       "%d CTAs x 256 threads, best of 10" % (SMS * 8))
     return out
 
 

@@ -35,6 +35,9 @@ def test_fp32_roofline_counts_algorithmic_bytes_only(bench):
     assert r["frac"] == pytest.approx(r["achieved"] / 1000.0)
     # the pushed ghost shell is overhead, beside the algorithmic bytes
     assert r["ghost_bytes_per_zone_launch"] == pytest.approx(4 * 5 * 13888 / 32768)
+    # the FP32 arithmetic roof beside it
+    assert r["alu"]["peak"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert r["alu"]["frac"] == pytest.approx(bench.FLOPS_PER_ZONE_CYCLE / 2 * zones / 1e-3 / 1e12 / r["alu"]["peak"])
     v["launches_per_cycle"] = 5
     r5 = bench.roofline_for(v, pk, "measured")
     assert r5["ghost_bytes_per_zone_launch"] == 0.0 and r5["frac"] == pytest.approx(r["frac"])
