@@ -525,15 +525,16 @@ def adjoint_variant(ph, torch, precision, cycles=20, ckpt=5):
                     "(copies inside), _device with device tensors"}
 
 
-def e2e_variant(ph, torch, block, precision, steps, warmup):
+def e2e_variant(ph, torch, block, precision, steps, warmup, nbuf=3):
     """Same metric through the public API with pinned host buffers: every step
     copies a state in from the host (ph_set_state_async), runs one cycle and
-    reads the new state back to the host (ph_get_state_async).  Steps
-    alternate between two meshes on two streams; each step's cycle waits for
-    the previous step's cycle (an event), so the cycles run one after the
-    other at full speed while one mesh's transfers overlap the other's
-    cycle.  The timed region ends when both streams have drained."""
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    reads the new state back to the host (ph_get_state_async).  Steps rotate
+    over `nbuf` meshes on as many streams; each step's cycle waits for the
+    previous step's cycle (an event), so the cycles run one after the other
+    at full speed while the other meshes' transfers (the read-back of the
+    state before and the copy-in of the state after) overlap it.  The timed
+    region ends when every stream has drained."""
+    streams = [torch.cuda.Stream() for _ in range(nbuf)]
     meshes = []
     for st in streams:
         n = MESH
@@ -543,20 +544,20 @@ def e2e_variant(ph, torch, block, precision, steps, warmup):
     geo = W.Geometry((block,) * 3, (MESH // block,) * 3)
     dtype = np.float32 if precision == "fp32" else np.float64
     U = wave_state(geo, meshes[0].tree(), dtype)
-    host_in = [torch.from_numpy(U.copy()).pin_memory() for _ in range(2)]
-    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
+    host_in = [torch.from_numpy(U.copy()).pin_memory() for _ in range(nbuf)]
+    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(nbuf)]
 
     def run(nsteps):
         done = None
         for k in range(nsteps):
-            m, st = meshes[k % 2], streams[k % 2]
-            m.set_state(host_in[k % 2].numpy(), sync=False)
+            m, st = meshes[k % nbuf], streams[k % nbuf]
+            m.set_state(host_in[k % nbuf].numpy(), sync=False)
             if done is not None:
                 st.wait_event(done)
             m.step(1)
             done = torch.cuda.Event()
             done.record(st)
-            m.get_state(host_out[k % 2].numpy(), sync=False)
+            m.get_state(host_out[k % nbuf].numpy(), sync=False)
 
     run(max(2, warmup))
     torch.cuda.synchronize()
@@ -570,8 +571,8 @@ def e2e_variant(ph, torch, block, precision, steps, warmup):
         m.close()
     return {"value": MESH ** 3 * steps / dt, "unit": "zone-cycles/s",
             "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes),
-            "note": "two meshes on two streams, cycles in sequence, transfers of one mesh "
-                    "overlapping the other's cycle"}
+            "note": "%d meshes on %d streams, cycles in sequence, the other meshes' transfers "
+                    "overlapping each cycle" % (nbuf, nbuf)}
 
 
 def oracle_rate(block, n_sample, cycles, warmup=0):
