@@ -268,7 +268,11 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   float* sfx = sdy + SM::DYN;
   float* sfy = sfx + SM::FXN;
   const int tid = threadIdx.x;
-  const int tx = 2 * (tid % PR), ty = tid / PR;  // own cells (tx, tx+1) of row ty
+  // own cells (tx, tx+1) of row ty.  16-wide tiles: a half-warp's 16 threads
+  // take rows r and r + 4 (not r and r + 1), 80 floats apart in the planes
+  // and the x1 slopes (rows of 20): the two rows fall on disjoint banks.
+  const int q = tid / PR;
+  const int tx = 2 * (tid % PR), ty = TXP == 16 ? (((q & 1) << 2) | ((q >> 1) & 3) | (q & 8)) : q;
   // Work lists: every thread's main item in every list is its own pair;
   // the halo items of a list go to one warp (x1 slopes: warp 0, x2 slopes:
   // warp 1, x1 faces: warp 2, x2 faces: warp 3, conversion: the last
