@@ -606,6 +606,22 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def host_cpu():
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm
+    implementer / part numbers), and the machine type."""
+    import platform
+    name = ""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        fields = dict(l.split(":", 1) for l in info if ":" in l)
+        fields = {k.strip(): v.strip() for k, v in fields.items()}
+        name = fields.get("model name") or ("Arm implementer %s part %s" % (
+            fields.get("CPU implementer", "?"), fields.get("CPU part", "?")))
+    except OSError:
+        pass
+    return "%s (%s)" % (name or "unknown", platform.machine())
+
+
 def oracle_rate_all_cores(block, n_sample, cycles, warmup=0):
     """The same oracle run as one independent process per host core (each on
     its own copy of the sample, as replicas): aggregate zone-cycles/s over the
@@ -673,7 +689,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": headline_config(args.block, args.precision, nb, world=1),
         "cpu_baseline": {"value": value, "unit": "zone-cycles/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "cpu": host_cpu(), "sample": sample},
         "e2e": {"value": value, "unit": "zone-cycles/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -824,7 +840,7 @@ def main():
         # one process per core
         ncyc = 8
         rate, n, secs, cores = oracle_rate_all_cores(args.block, 128, ncyc)
-        cpu = {"value": rate, "unit": "zone-cycles/s", "cores": cores, "kind": "oracle",
+        cpu = {"value": rate, "unit": "zone-cycles/s", "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                "sample": "%d processes, each %d^3 zones of the same workload (blocks of %d^3), "
                          "%d cycles, %.1f s; %.3g zone-cycles/s per core"
                          % (cores, n, min(args.block, n), ncyc, secs, rate / cores)}
