@@ -233,9 +233,7 @@ struct PairSmemT {
   static constexpr int PLANE = NV * WX * WY;
   static constexpr int SLOT = (PLANE * 4 + 127) / 128 * 128 / 4;
   static constexpr unsigned PLANE_BYTES = PLANE * 4;
-  // x1 face pitch (faces 0..TX, spare); 16-wide tiles: 20, so that rows r
-  // and r + 4 (a half-warp) fall on disjoint banks
-  static constexpr int FPX = TX == 16 ? 20 : TX + 2;
+  static constexpr int FPX = TX + 2;                 // x1 face pitch (faces 0..TX, one spare)
   static constexpr int DXN = NV * TY * WX;           // x1 slopes, indexed by plane position
   static constexpr int DYN = NV * (TY + 2) * TX;     // x2 slopes, rows -1..TY
   static constexpr int FXN = NV * TY * FPX;          // x1 face fluxes
@@ -264,10 +262,6 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
   using SM = PairSmemT<TXP>;
   constexpr int TX = SM::TX, TY = SM::TY, NT = SM::NT, WX = SM::WX, WY = SM::WY, FPX = SM::FPX;
   constexpr int PR = SM::PR;
-  // 16-wide tiles: rows of the x2 slopes and fluxes (16 floats apart) are
-  // stored at row r ^ ((r >> 2) & 1), so that a half-warp's rows r and r + 4
-  // land an odd number of rows, 16 floats mod 32, apart (disjoint banks)
-  auto yrow = [](int r) { return TXP == 16 ? r ^ ((r >> 2) & 1) : r; };
   float* ring = reinterpret_cast<float*>(smem_raw);
   float* sdx = ring + 4 * SM::SLOT;
   float* sdy = sdx + SM::DXN;
@@ -451,7 +445,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       }
       vanleer_half5_2(a, b, r, h);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) st2(sdy + (v * (TY + 2) + yrow(jj)) * TX + q, h[v]);
+      for (int v = 0; v < NV; ++v) st2(sdy + (v * (TY + 2) + jj) * TX + q, h[v]);
     };
     x1_slope(ty, tx + 2, false);
     x2_slope(ty + 1, tx);
@@ -480,14 +474,13 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const float* p = W + (v * WY + g + 1) * WX + q + 2;
-        const float* s0 = sdy + (v * (TY + 2) + yrow(g)) * TX + q;
-        const float* s1 = sdy + (v * (TY + 2) + yrow(g + 1)) * TX + q;
-        wl[v] = ld2(p) + ld2(s0);
-        wr[v] = ld2(p + WX) - ld2(s1);
+        const float* s = sdy + (v * (TY + 2) + g) * TX + q;
+        wl[v] = ld2(p) + ld2(s);
+        wr[v] = ld2(p + WX) - ld2(s + TX);
       }
       hlle2<1>(wl, wr, P, fl);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + yrow(g)) * TX + q, fl[v]);
+      for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + g) * TX + q, fl[v]);
     };
     x1_face(ty, tx);
     x2_face(ty, tx);
@@ -509,7 +502,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         const F2 fa = ld2(fr);
         const F2 fb = f2(lane1(fa), fr[2]);
         const F2 dfx = fb - fa;
-        const F2 dfy = ld2(sfy + (v * (TY + 1) + yrow(ty + 1)) * TX + tx) - ld2(sfy + (v * (TY + 1) + yrow(ty)) * TX + tx);
+        const F2 dfy = ld2(sfy + (v * (TY + 1) + ty + 1) * TX + tx) - ld2(sfy + (v * (TY + 1) + ty) * TX + tx);
         const F2 L = -fma2(dfx, idx1, fma2(dfy, idx2, (fzm[v] - fzlo[v]) * idx3));
         if (STAGE == 1) {
           unew[v] = fma2(tdt, L, ucur[v]);
