@@ -11,9 +11,11 @@ benchmark times.
 * derefinement on the same 960-leaf mesh: 64 refined parents carrying a
   smooth state merge as soon as their children reach the derefinement age,
   against the oracle every cycle;
-* the 64-member batch as the benchmark autotunes it: a member of every size
-  matches its own single-mesh run bit for bit (single meshes are pinned to
-  the oracle above and in test_gpu_uniform)."""
+* the 256^3 wave in 4096 blocks of 16^3, FP32 on the 16-wide paired tile:
+  one cycle against the oracle, cell by cell over the domain;
+* the 64-member batch as the benchmark autotunes it, FP64 and FP32: a member
+  of every size matches its own single-mesh run bit for bit (single meshes
+  are pinned to the oracle above and in test_gpu_uniform)."""
 import numpy as np
 import pytest
 
@@ -56,6 +58,38 @@ def test_uniform_256cube_one_cycle(oracle_256, precision):
     tol = 1e-12 if precision == "fp64" else 2e-6
     assert err.max() <= tol, describe(err)
     assert abs(m.dt() - odt) <= (1e-12 if precision == "fp64" else 1e-6) * odt
+    assert m.status()[0] == 0
+
+
+def _global(U, tree, n):
+    """Blocks U[b][v][k][j][i] of a uniform tree (rows: level, l1, l2, l3)
+    assembled into one array [v][k][j][i]."""
+    nb = [int(tree[:, 1 + d].max()) + 1 for d in range(3)]
+    G = np.zeros((U.shape[1], nb[2] * n, nb[1] * n, nb[0] * n), dtype=np.float64)
+    for b, (lev, l1, l2, l3) in enumerate(tree[:, :4]):
+        G[:, l3 * n:(l3 + 1) * n, l2 * n:(l2 + 1) * n, l1 * n:(l1 + 1) * n] = U[b]
+    return G
+
+
+def test_uniform_256cube_16blocks_fp32_paired_16_wide(oracle_256):
+    """The 256^3 benchmark wave in 4096 blocks of 16^3, FP32: the default
+    tile is the 16-wide paired kernel; one cycle against the oracle's (run
+    on 32^3 blocks: on a periodic uniform mesh the blocking does not change
+    the method), compared cell by cell on the whole domain."""
+    ph = _ph()
+    U0, ref, odt, tree = oracle_256
+    m = ph.Mesh(ph.make_config((16, 16, 16), (16, 16, 16), precision="fp32"))
+    assert m.tile()[:2] == (16, 16)
+    geo = W.Geometry((16, 16, 16), (16, 16, 16))
+    U16 = W.linear_wave(geo, m.tree(), seed=0, amp=1e-4, kvec=(1, 1, 1))
+    assert np.array_equal(_global(U16, m.tree(), 16), _global(U0, tree, 32))
+    m.set_state(U16.astype(np.float32))
+    m.step(1)
+    G = _global(m.get_state().astype(np.float64), m.tree(), 16)
+    R = _global(ref, tree, 32)
+    err = field_errors(G[None], R[None])
+    assert err.max() <= 2e-6, describe(err)
+    assert abs(m.dt() - odt) <= 1e-6 * odt
     assert m.status()[0] == 0
 
 
@@ -155,20 +189,25 @@ def test_derefinement_full_size():
     _indicator_on_oracle_state(m, om)
 
 
-def test_batch_full_members_match_single_meshes():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_full_members_match_single_meshes(precision):
+    """FP32: the autotuned launch is the paired tile on every member; single
+    meshes pinned to the same tile shape run the same kernel arithmetic."""
     ph = _ph()
     mem = W.batch_members(seed=0, nsim=64)
+    dtype = np.float32 if precision == "fp32" else np.float64
     cfgs, states = [], []
     for mb in mem:
         nb = mb.n // mb.block
-        cfg = ph.make_config((mb.block,) * 3, (nb,) * 3, precision="fp64")
+        cfg = ph.make_config((mb.block,) * 3, (nb,) * 3, precision=precision)
         cfgs.append(cfg)
         geo = W.Geometry((mb.block,) * 3, (nb,) * 3)
-        states.append(W.blast(geo, ph.Mesh(cfg).tree(), seed=mb.seed, center=mb.center, p_in=mb.p_in))
+        states.append(W.blast(geo, ph.Mesh(cfg).tree(), seed=mb.seed, center=mb.center,
+                              p_in=mb.p_in).astype(dtype))
     B = ph.Batch(cfgs)
     for s, U in enumerate(states):
         B.set_state(s, U)
-    B.autotune(1)
+    launch = B.autotune(1)
     B.step(3)
     seen = set()
     for s, mb in enumerate(mem):
@@ -176,6 +215,8 @@ def test_batch_full_members_match_single_meshes():
         if key in seen:
             continue
         seen.add(key)
+        if precision == "fp32":
+            cfgs[s].tile[:] = [launch[0], launch[1], cfgs[s].nx[2]]
         m = ph.Mesh(cfgs[s])
         m.set_state(states[s])
         m.step(3)
