@@ -72,6 +72,13 @@ def test_shards_match_one_mesh_fp32_paired_kernel():
     _compare_runs(ph, (32, 32, 32), (2, 2, 2), 2, 6, precision="fp32")
 
 
+def test_shards_match_one_mesh_fp32_16_wide_paired_kernel():
+    ph = _ph()
+    cfg = ph.make_config((16, 16, 16), (4, 2, 2), precision="fp32")
+    assert tuple(ph.Shard(cfg, 3, 0).tile())[:2] == (16, 16)
+    _compare_runs(ph, (16, 16, 16), (4, 2, 2), 3, 6, precision="fp32")
+
+
 def test_shards_match_one_mesh_with_walls():
     ph = _ph()
     bc = ("reflect", "outflow", "periodic", "periodic", "outflow", "reflect")
