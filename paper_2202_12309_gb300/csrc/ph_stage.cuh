@@ -399,7 +399,9 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
   const int stg = STAGE ? STAGE : J.stage;
   const T hs = stg == 1 ? T(1) : T(0.5);
   const T c1 = hs * J.dt * idx1, c2 = hs * J.dt * idx2, c3 = hs * J.dt * idx3;
-  double rate = 0.0;
+  // running max in the data precision (FP32: no FP64 conversion or compare
+  // per cell; widening is exact and monotonic, so the max is the same)
+  T rate = T(0);
 
   for (int k = k0; k < k1; ++k) {
     // (C) slopes; own x3 flux (planes k, k+1, k+2 are in the ring)
@@ -584,13 +586,12 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       if (J.want_rate && !(a.face_rec && coarse_face_cell(a.face_rec + 6 * leaf, i, j, k, n1, n2, n3))) {
         cons_to_prim<T, NVT>(unew, P, floors);
         const T r = wave_rate(unew, P, idx1, idx2, idx3);
-        const double rd = (double)r;
-        if (!(rd <= rate)) rate = rd;
+        if (!(r <= rate)) rate = r;
       }
     }
   }
   if (parity_io) *parity_io = parity;
-  return rate;
+  return (double)rate;
 }
 
 template <class T, int TX, int TY, int NVT = NV>

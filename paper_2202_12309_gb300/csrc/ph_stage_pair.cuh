@@ -366,7 +366,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
 
   const int i = i0 + tx, j = j0 + ty;
   const F2 tdt = f2(J.dt);
-  double rate = 0.0;
+  float rate = 0.f;  // running max in FP32 (widened once at the end: the same value)
   const F2 idx1 = f2(J.idx1), idx2 = f2(J.idx2), idx3 = f2(J.idx3);
 
   for (int k = k0; k < k1; ++k) {
@@ -391,10 +391,94 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
 #pragma unroll
       for (int v = 0; v < NV; ++v) u0[v] = ld2(J.U0b + cell + v * vstride);
     }
-    F2 fzlo[NV];
-    {  // (C1) own x3 slope and flux
-      F2 wa[NV], wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], dr[NV], f[NV];
-      col(k, wa);
+    // the own pair's primitives at plane k, loaded once: both slopes, both
+    // faces and the x3 face below take them from registers
+    F2 fzlo[NV], wk[NV];
+    col(k, wk);
+    const float* W = ring + ((k + 4) & 3) * SM::SLOT;
+    // (C2) x1 slopes at plane positions (q, q+1): own pair q = tx + 2 (its
+    // values from wk; its left neighbours kept in lo_own for the x1 faces);
+    // the halo pairs q = 0 and WX-2 of each row (their outermost lanes read
+    // clamped neighbours and are never used)
+    float lo_own[NV];
+    auto x1_slope = [&](int jj, int q, bool edge, const F2* own) {
+      F2 a[NV], b[NV], r[NV], h[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* row = W + (v * WY + jj + 2) * WX;
+        b[v] = own ? own[v] : ld2(row + q);
+        const float lo = edge ? row[q > 0 ? q - 1 : 0] : row[q - 1];
+        const float hi = edge ? row[q + 2 < WX ? q + 2 : WX - 1] : row[q + 2];
+        if (own) lo_own[v] = lo;
+        a[v] = f2(lo, lane0(b[v]));
+        r[v] = f2(lane1(b[v]), hi);
+      }
+      vanleer_half5_2(a, b, r, h);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sdx + (v * TY + jj) * WX + q, h[v]);
+    };
+    // (C3) x2 slopes of rows jj - 1 (jj = 0 .. TY + 1), column pair q; the
+    // own pair's (own = wk) also kept in hy_own for its x2 face
+    F2 hy_own[NV];
+    auto x2_slope = [&](int jj, int q, const F2* own) {
+      F2 a[NV], b[NV], r[NV], h[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* p = W + (v * WY + jj) * WX + q + 2;
+        a[v] = ld2(p);
+        b[v] = own ? own[v] : ld2(p + WX);
+        r[v] = ld2(p + 2 * WX);
+      }
+      vanleer_half5_2(a, b, r, h);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (own) hy_own[v] = h[v];
+        st2(sdy + (v * (TY + 2) + jj) * TX + q, h[v]);
+      }
+    };
+    x1_slope(ty, tx + 2, false, wk);
+    x2_slope(ty + 1, tx, wk);
+    if (warp == 0) x1_slope(lane >> 1, (lane & 1) ? WX - 2 : 0, true, nullptr);
+    if (warp == 1 && lane < 2 * PR) x2_slope(lane >= PR ? TY + 1 : 0, 2 * (lane % PR), nullptr);
+    __syncthreads();
+    // (E1) x1 face pairs (f, f+1), f even; face f joins cells f-1 and f
+    auto x1_face = [&](int jj, int f, const F2* own) {
+      F2 wl[NV], wr[NV], fl[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* row = W + (v * WY + jj + 2) * WX;
+        const float* srow = sdx + (v * TY + jj) * WX;
+        const F2 R = own ? own[v] : ld2(row + f + 2), SR = ld2(srow + f + 2);
+        const F2 L = f2(own ? lo_own[v] : row[f + 1], lane0(R)), SL = f2(srow[f + 1], lane0(SR));
+        wl[v] = L + SL;
+        wr[v] = R - SR;
+      }
+      hlle2<0>(wl, wr, P, fl);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sfx + (v * TY + jj) * FPX + f, fl[v]);
+    };
+    // (E2) x2 faces between rows g-1 and g, column pair q
+    auto x2_face = [&](int g, int q, const F2* own) {
+      F2 wl[NV], wr[NV], fl[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* p = W + (v * WY + g + 1) * WX + q + 2;
+        const float* s = sdy + (v * (TY + 2) + g) * TX + q;
+        wl[v] = ld2(p) + ld2(s);
+        wr[v] = (own ? own[v] : ld2(p + WX)) - (own ? hy_own[v] : ld2(s + TX));
+      }
+      hlle2<1>(wl, wr, P, fl);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + g) * TX + q, fl[v]);
+    };
+    x1_face(ty, tx, wk);
+    x2_face(ty, tx, wk);
+    if (warp == 2 && lane < TY) x1_face(lane, TX, nullptr);
+    if (warp == 3 && lane < TX / 2) x2_face(TY, 2 * lane, nullptr);
+    // (C1) own x3 slope and flux (after the x1 / x2 faces: the flux below,
+    // fzlo, is not live across them)
+    {
+      F2 wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], dr[NV], f[NV];
       col(k + 1, wb);
       col(k + 2, wc);
 #pragma unroll
@@ -402,7 +486,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       vanleer_half5_2d(dzr, dr, d1);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        wl[v] = wa[v] + dz[v];
+        wl[v] = wk[v] + dz[v];
         wr[v] = wb[v] - d1[v];
         dz[v] = d1[v];
         dzr[v] = dr[v];
@@ -414,78 +498,6 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         fzm[v] = f[v];
       }
     }
-    const float* W = ring + ((k + 4) & 3) * SM::SLOT;
-    // (C2) x1 slopes at plane positions (q, q+1): own pair q = tx + 2; the
-    // halo pairs q = 0 and WX-2 of each row (their outermost lanes read
-    // clamped neighbours and are never used)
-    auto x1_slope = [&](int jj, int q, bool edge) {
-      F2 a[NV], b[NV], r[NV], h[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float* row = W + (v * WY + jj + 2) * WX;
-        b[v] = ld2(row + q);
-        const float lo = edge ? row[q > 0 ? q - 1 : 0] : row[q - 1];
-        const float hi = edge ? row[q + 2 < WX ? q + 2 : WX - 1] : row[q + 2];
-        a[v] = f2(lo, lane0(b[v]));
-        r[v] = f2(lane1(b[v]), hi);
-      }
-      vanleer_half5_2(a, b, r, h);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) st2(sdx + (v * TY + jj) * WX + q, h[v]);
-    };
-    // (C3) x2 slopes of rows jj - 1 (jj = 0 .. TY + 1), column pair q
-    auto x2_slope = [&](int jj, int q) {
-      F2 a[NV], b[NV], r[NV], h[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float* p = W + (v * WY + jj) * WX + q + 2;
-        a[v] = ld2(p);
-        b[v] = ld2(p + WX);
-        r[v] = ld2(p + 2 * WX);
-      }
-      vanleer_half5_2(a, b, r, h);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) st2(sdy + (v * (TY + 2) + jj) * TX + q, h[v]);
-    };
-    x1_slope(ty, tx + 2, false);
-    x2_slope(ty + 1, tx);
-    if (warp == 0) x1_slope(lane >> 1, (lane & 1) ? WX - 2 : 0, true);
-    if (warp == 1 && lane < 2 * PR) x2_slope(lane >= PR ? TY + 1 : 0, 2 * (lane % PR));
-    __syncthreads();
-    // (E1) x1 face pairs (f, f+1), f even; face f joins cells f-1 and f
-    auto x1_face = [&](int jj, int f) {
-      F2 wl[NV], wr[NV], fl[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float* row = W + (v * WY + jj + 2) * WX;
-        const float* srow = sdx + (v * TY + jj) * WX;
-        const F2 R = ld2(row + f + 2), SR = ld2(srow + f + 2);
-        const F2 L = f2(row[f + 1], lane0(R)), SL = f2(srow[f + 1], lane0(SR));
-        wl[v] = L + SL;
-        wr[v] = R - SR;
-      }
-      hlle2<0>(wl, wr, P, fl);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) st2(sfx + (v * TY + jj) * FPX + f, fl[v]);
-    };
-    // (E2) x2 faces between rows g-1 and g, column pair q
-    auto x2_face = [&](int g, int q) {
-      F2 wl[NV], wr[NV], fl[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float* p = W + (v * WY + g + 1) * WX + q + 2;
-        const float* s = sdy + (v * (TY + 2) + g) * TX + q;
-        wl[v] = ld2(p) + ld2(s);
-        wr[v] = ld2(p + WX) - ld2(s + TX);
-      }
-      hlle2<1>(wl, wr, P, fl);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + g) * TX + q, fl[v]);
-    };
-    x1_face(ty, tx);
-    x2_face(ty, tx);
-    if (warp == 2 && lane < TY) x1_face(lane, TX);
-    if (warp == 3 && lane < TX / 2) x2_face(TY, 2 * lane);
     // (F) plane k+3 into the slot of plane k-1; then plane k+4 into the slot of plane k
     {
       const bool ok = k + 3 <= k1 + 1 ? convert(k + 3) : true;
@@ -524,13 +536,13 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         cons_to_prim2(w, P, floors);
         float ra, rb;
         wave_rate2(w, P, J.idx1, J.idx2, J.idx3, ra, rb);
-        if (!((double)ra <= rate)) rate = (double)ra;
-        if (!((double)rb <= rate)) rate = (double)rb;
+        if (!(ra <= rate)) rate = ra;
+        if (!(rb <= rate)) rate = rb;
       }
     }
   }
   if (parity_io) *parity_io = parity;
-  return rate;
+  return (double)rate;
 }
 
 template <int TXP, int STAGE>
