@@ -182,7 +182,7 @@ __device__ bool batch_stage_phase(const BatchArgs<T>& a, const StageArgs<T>& noc
     const CUtensorMap* tm = TMA ? a.tmaps + 2 * m + (STAGE == 1 ? 0 : 1) : nullptr;
     double rate;
     if constexpr (BatchTile<T, TX, TY, TMA>::PAIR) {
-      rate = stage_tile_pair<TX, STAGE>(J, member_phys<float>(M), smem, floors, tm, vz0, bars, failed, parity);
+      rate = stage_tile_pair<TX, STAGE, true>(J, member_phys<float>(M), smem, floors, tm, vz0, bars, failed, parity);
     } else {
       rate = stage_tile<T, TX, TY, TMA>(J, member_phys<T>(M), nocap, smem, floors, tm, vz0, bars, failed, parity);
     }

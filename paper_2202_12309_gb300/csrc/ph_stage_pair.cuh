@@ -254,7 +254,11 @@ using PairSmem16 = PairSmemT<16>;
 // values live across the plane (stage 2 also U0), and each gets its own
 // register allocation.  parity_io (optional): the mbarrier phase bits,
 // carried across calls by a CTA that runs several tiles on the same barriers.
-template <int TXP, int STAGE>
+// LEAN: the own pair's values are read from shared memory at every use and
+// the x3 face comes first (fewer registers live across the plane step, for
+// a kernel that holds more state besides); otherwise they are loaded once
+// and kept in registers.  Both give the same bits.
+template <int TXP, int STAGE, bool LEAN = false>
 __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const Phys<float>& P,
                                                   unsigned char* smem_raw, unsigned& floors,
                                                   const CUtensorMap* tmap, int vz0, uint64_t* bars,
@@ -392,9 +396,35 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
       for (int v = 0; v < NV; ++v) u0[v] = ld2(J.U0b + cell + v * vstride);
     }
     // the own pair's primitives at plane k, loaded once: both slopes, both
-    // faces and the x3 face below take them from registers
+    // faces and the x3 face take them from registers (own = nullptr: LEAN)
     F2 fzlo[NV], wk[NV];
-    col(k, wk);
+    if constexpr (!LEAN) col(k, wk);
+    const F2* own = LEAN ? nullptr : wk;
+    // (C1) own x3 slope and flux: first in LEAN mode, else after the x1 / x2
+    // faces (the flux below, fzlo, then is not live across them)
+    auto x3_face = [&]() {
+      F2 wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], dr[NV], f[NV];
+      col(k + 1, wb);
+      col(k + 2, wc);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dr[v] = wc[v] - wb[v];
+      vanleer_half5_2d(dzr, dr, d1);
+      if constexpr (LEAN) col(k, wl);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        wl[v] = (LEAN ? wl[v] : wk[v]) + dz[v];
+        wr[v] = wb[v] - d1[v];
+        dz[v] = d1[v];
+        dzr[v] = dr[v];
+      }
+      hlle2<2>(wl, wr, P, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        fzlo[v] = fzm[v];
+        fzm[v] = f[v];
+      }
+    };
+    if constexpr (LEAN) x3_face();
     const float* W = ring + ((k + 4) & 3) * SM::SLOT;
     // (C2) x1 slopes at plane positions (q, q+1): own pair q = tx + 2 (its
     // values from wk; its left neighbours kept in lo_own for the x1 faces);
@@ -436,8 +466,8 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         st2(sdy + (v * (TY + 2) + jj) * TX + q, h[v]);
       }
     };
-    x1_slope(ty, tx + 2, false, wk);
-    x2_slope(ty + 1, tx, wk);
+    x1_slope(ty, tx + 2, false, own);
+    x2_slope(ty + 1, tx, own);
     if (warp == 0) x1_slope(lane >> 1, (lane & 1) ? WX - 2 : 0, true, nullptr);
     if (warp == 1 && lane < 2 * PR) x2_slope(lane >= PR ? TY + 1 : 0, 2 * (lane % PR), nullptr);
     __syncthreads();
@@ -471,33 +501,11 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
 #pragma unroll
       for (int v = 0; v < NV; ++v) st2(sfy + (v * (TY + 1) + g) * TX + q, fl[v]);
     };
-    x1_face(ty, tx, wk);
-    x2_face(ty, tx, wk);
+    x1_face(ty, tx, own);
+    x2_face(ty, tx, own);
     if (warp == 2 && lane < TY) x1_face(lane, TX, nullptr);
     if (warp == 3 && lane < TX / 2) x2_face(TY, 2 * lane, nullptr);
-    // (C1) own x3 slope and flux (after the x1 / x2 faces: the flux below,
-    // fzlo, is not live across them)
-    {
-      F2 wb[NV], wc[NV], wl[NV], wr[NV], d1[NV], dr[NV], f[NV];
-      col(k + 1, wb);
-      col(k + 2, wc);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) dr[v] = wc[v] - wb[v];
-      vanleer_half5_2d(dzr, dr, d1);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        wl[v] = wk[v] + dz[v];
-        wr[v] = wb[v] - d1[v];
-        dz[v] = d1[v];
-        dzr[v] = dr[v];
-      }
-      hlle2<2>(wl, wr, P, f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        fzlo[v] = fzm[v];
-        fzm[v] = f[v];
-      }
-    }
+    if constexpr (!LEAN) x3_face();
     // (F) plane k+3 into the slot of plane k-1; then plane k+4 into the slot of plane k
     {
       const bool ok = k + 3 <= k1 + 1 ? convert(k + 3) : true;
