@@ -681,30 +681,58 @@ cudaError_t launch_remesh(T* Unew, const int* new_leaf_id, int nnew, const T* Uo
 // --------------------------------------------------------------------------
 // K5: signal-speed max for the CFL dt (Sec. 3.10), from interior cells.
 // --------------------------------------------------------------------------
+// SMs of the current device (read once; 1 if the query fails), for grid sizes.
+static int device_sms() {
+  static int nsm = 0;
+  if (nsm <= 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      nsm = n;
+    else
+      return 1;
+  }
+  return nsm;
+}
+
+// One CTA per (leaf, slab of kper planes): the (j, i) cells of a plane in
+// steps of the block size (positions advanced without a division per cell).
 template <class T>
-__global__ void rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
-                            const LevelGeom g, int3 nx, Phys<T> P, DevScalars* sc, int nvar) {
+__global__ void __launch_bounds__(256) rate_kernel(const T* __restrict__ U, const int8_t* __restrict__ level,
+                                                   const LevelGeom g, int3 nx, Phys<T> P, DevScalars* sc,
+                                                   int nvar, int nsplit, int kper) {
   __shared__ double red[32];
-  const int b = blockIdx.x;
+  const int b = blockIdx.x / nsplit;
+  const int ka = (blockIdx.x - b * nsplit) * kper, kb = min(nx.z, ka + kper);
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
   const size_t vs = (size_t)S1 * S2 * S3;
   const T* Ub = U + (size_t)b * nvar * vs;
   const int lev = level ? (int)level[b] : 0;
   const T i1 = (T)g.idx[lev][0], i2 = (T)g.idx[lev][1], i3 = (T)g.idx[lev][2];
   unsigned floors = 0;
-  double m = 0.0;
-  const int total = nx.x * nx.y * nx.z;
-  for (int c = threadIdx.x; c < total; c += blockDim.x) {
-    const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
-    const size_t o = ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
-    T w[NV];
+  T m = T(0);  // running max in the data precision (widening is exact and monotonic)
+  const int plane = nx.x * nx.y;
+  const int dj = blockDim.x / nx.x, di = blockDim.x - dj * nx.x;
+  const int jt = threadIdx.x / nx.x, it = threadIdx.x - jt * nx.x;
+  for (int k = ka; k < kb; ++k) {
+    int i = it, j = jt;
+    for (int c = threadIdx.x; c < plane; c += blockDim.x) {
+      const size_t o = ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
+      T w[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = Ub[v * vs + o];
-    cons_to_prim(w, P, floors);
-    const double r8 = (double)wave_rate(w, P, i1, i2, i3);
-    if (!(r8 <= m)) m = r8;
+      for (int v = 0; v < NV; ++v) w[v] = Ub[v * vs + o];
+      cons_to_prim(w, P, floors);
+      const T r = wave_rate(w, P, i1, i2, i3);
+      if (!(r <= m)) m = r;
+      i += di;
+      j += dj;
+      if (i >= nx.x) {
+        i -= nx.x;
+        ++j;
+      }
+    }
   }
-  block_max_to(&sc->wmax_bits, m, red);
+  block_max_to(&sc->wmax_bits, (double)m, red);
   if (floors) atomicAdd(&sc->floor_hits, (unsigned long long)floors);
 }
 
@@ -713,7 +741,14 @@ cudaError_t launch_rate(const T* U, const int8_t* level, const LevelGeom& g, con
                         int nleaf, Phys<T> P, DevScalars* sc, cudaStream_t s, int nvar) {
   PH_RANGE("ph dt rate");
   if (nleaf <= 0) return cudaSuccess;
-  rate_kernel<T><<<nleaf, 256, 0, s>>>(U, level, g, make_int3(nx[0], nx[1], nx[2]), P, sc, nvar);
+  // at least ~4 CTAs per SM: split the leaves' planes into slabs when there
+  // are few leaves
+  const long long want = 4LL * device_sms();
+  int nsplit = (int)std::min<long long>(nx[2], std::max<long long>(1, (want + nleaf - 1) / nleaf));
+  const int kper = (nx[2] + nsplit - 1) / nsplit;
+  nsplit = (nx[2] + kper - 1) / kper;
+  rate_kernel<T><<<(unsigned)((long long)nleaf * nsplit), 256, 0, s>>>(
+      U, level, g, make_int3(nx[0], nx[1], nx[2]), P, sc, nvar, nsplit, kper);
   return cudaGetLastError();
 }
 
@@ -742,24 +777,36 @@ cudaError_t launch_advance(DevScalars* sc, double cfl, int mode, cudaStream_t s)
 // --------------------------------------------------------------------------
 // Interior <-> padded copies
 // --------------------------------------------------------------------------
+// One CTA per (leaf, variable, slab of kper planes): a plane is contiguous in
+// the packed layout; its padded position advances without a division per cell.
 template <class T>
-__global__ void pack_kernel(T* padded, T* packed, int3 nx, int dir, int nvar) {
-  const int b = blockIdx.y;
+__global__ void __launch_bounds__(256) pack_kernel(T* padded, T* packed, int3 nx, int dir, int nvar,
+                                                   int nsplit, int kper) {
+  const int bv = blockIdx.x / nsplit;          // leaf * nvar + variable
+  const int ka = (blockIdx.x - bv * nsplit) * kper, kb = min(nx.z, ka + kper);
   const int S1 = nx.x + 2 * NG, S2 = nx.y + 2 * NG, S3 = nx.z + 2 * NG;
-  const size_t per = (size_t)nvar * nx.x * nx.y * nx.z;
-  const size_t vs = (size_t)S1 * S2 * S3;
-  const int cells = nx.x * nx.y * nx.z;
-  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < per;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int v = (int)(e / cells);
-    const int c = (int)(e - (size_t)v * cells);
-    const int k = c / (nx.x * nx.y), r = c - k * nx.x * nx.y, j = r / nx.x, i = r - j * nx.x;
-    T* pp = padded + (size_t)b * nvar * vs + v * vs + ((size_t)(k + NG) * S2 + (j + NG)) * S1 + (i + NG);
-    T* qq = packed + (size_t)b * per + e;
-    if (dir == 0)
-      *pp = *qq;
-    else
-      *qq = *pp;
+  const int plane = nx.x * nx.y;
+  T* pv = padded + (size_t)bv * S1 * S2 * S3;  // variables of a leaf are consecutive in both layouts
+  T* qv = packed + (size_t)bv * plane * nx.z;
+  const int dj = blockDim.x / nx.x, di = blockDim.x - dj * nx.x;
+  const int jt = threadIdx.x / nx.x, it = threadIdx.x - jt * nx.x;
+  for (int k = ka; k < kb; ++k) {
+    T* pk = pv + ((size_t)(k + NG) * S2 + NG) * S1 + NG;
+    T* qk = qv + (size_t)k * plane;
+    int i = it, j = jt;
+    for (int c = threadIdx.x; c < plane; c += blockDim.x) {
+      T* pp = pk + (size_t)j * S1 + i;
+      if (dir == 0)
+        *pp = qk[c];
+      else
+        qk[c] = *pp;
+      i += di;
+      j += dj;
+      if (i >= nx.x) {
+        i -= nx.x;
+        ++j;
+      }
+    }
   }
 }
 
@@ -768,11 +815,15 @@ cudaError_t launch_pack(T* padded, T* packed, const int nx[3], int nleaf, int di
                         int nvar) {
   PH_RANGE("ph pack");
   if (nleaf <= 0) return cudaSuccess;
-  const size_t per = (size_t)nvar * nx[0] * nx[1] * nx[2];
-  int gx = (int)((per + 255) / 256);
-  if (gx > 64) gx = 64;
-  pack_kernel<T><<<dim3(gx, nleaf), 256, 0, s>>>(padded, packed, make_int3(nx[0], nx[1], nx[2]), dir,
-                                                  nvar);
+  // at least ~8 CTAs per SM: split the planes into slabs when there are
+  // few leaves
+  const long long units = (long long)nleaf * nvar;
+  const long long want = 8LL * device_sms();
+  int nsplit = (int)std::min<long long>(nx[2], std::max<long long>(1, (want + units - 1) / units));
+  const int kper = (nx[2] + nsplit - 1) / nsplit;
+  nsplit = (nx[2] + kper - 1) / kper;
+  pack_kernel<T><<<(unsigned)(units * nsplit), 256, 0, s>>>(padded, packed, make_int3(nx[0], nx[1], nx[2]),
+                                                             dir, nvar, nsplit, kper);
   return cudaGetLastError();
 }
 
