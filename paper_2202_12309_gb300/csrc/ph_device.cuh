@@ -336,6 +336,18 @@ __device__ __forceinline__ void hlle(const T wl[NVT], const T wr[NVT], const Phy
   for (int v = NV; v < NVT; ++v) f[v] = fma(aL, wl[v], aR * wr[v]);
 }
 
+// Max of two signal rates (non-negative numbers or NaN) on their bit
+// patterns, unsigned: for non-negative numbers that is the numeric max, and
+// a NaN of either sign lands above every number, so a NaN rate is never
+// replaced by a later finite one (integer instructions, not FP64 compares).
+__device__ __forceinline__ double rate_max(double a, double b) {
+  const unsigned long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double((long long)(x > y ? x : y));
+}
+__device__ __forceinline__ float rate_max(float a, float b) {
+  return __uint_as_float(max(__float_as_uint(a), __float_as_uint(b)));
+}
+
 // Largest signal speed over cell width of one primitive state:
 // max_d (|v_d| + c) / dx_d.  dt = cfl / (max over cells).
 template <class T>
@@ -359,10 +371,7 @@ __device__ __forceinline__ T wave_rate(const T w[NV], const Phys<T>& P, T idx1, 
   const T a = add_rn(fabs(w[1]), c) * idx1;
   const T b = add_rn(fabs(w[2]), c) * idx2;
   const T d = add_rn(fabs(w[3]), c) * idx3;
-  T m = a;
-  if (!(b <= m)) m = b;   // NaN-propagating max
-  if (!(d <= m)) m = d;
-  return m;
+  return rate_max(a, rate_max(b, d));  // a NaN in any direction propagates
 }
 
 // Block-wide NaN-propagating max of a non-negative double, then one atomic

@@ -722,8 +722,7 @@ __global__ void __launch_bounds__(256) rate_kernel(const T* __restrict__ U, cons
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v] = Ub[v * vs + o];
       cons_to_prim(w, P, floors);
-      const T r = wave_rate(w, P, i1, i2, i3);
-      if (!(r <= m)) m = r;
+      m = rate_max(m, wave_rate(w, P, i1, i2, i3));
       i += di;
       j += dj;
       if (i >= nx.x) {
@@ -1024,8 +1023,7 @@ __global__ void flux_correct_kernel(T* U, const int* __restrict__ corr_leaf,
 #pragma unroll
       for (int v = 0; v < NV; ++v) w[v] = Ub[v * vs + o];
       cons_to_prim(w, P, floors);
-      const double r8 = (double)wave_rate(w, P, i1, i2, i3);
-      if (!(r8 <= m)) m = r8;
+      m = rate_max(m, (double)wave_rate(w, P, i1, i2, i3));
     }
   }
   block_max_to(&sc->wmax_bits, m, red);

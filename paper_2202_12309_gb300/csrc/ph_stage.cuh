@@ -585,8 +585,7 @@ __device__ __forceinline__ double stage_tile(const TileJob<T>& J, const Phys<T>&
       // skipped here and rated by the flux correction that changes them
       if (J.want_rate && !(a.face_rec && coarse_face_cell(a.face_rec + 6 * leaf, i, j, k, n1, n2, n3))) {
         cons_to_prim<T, NVT>(unew, P, floors);
-        const T r = wave_rate(unew, P, idx1, idx2, idx3);
-        if (!(r <= rate)) rate = r;
+        rate = rate_max(rate, wave_rate(unew, P, idx1, idx2, idx3));
       }
     }
   }

@@ -130,8 +130,8 @@ __device__ __forceinline__ void cons_to_prim2(F2 w[NV], const Phys<float>& P, un
 }
 
 // Signal rate max_d (|v_d| + c)/dx_d of a primitive state on both lanes
-// (the arithmetic of wave_rate() in ph_device.cuh); the NaN-propagating max
-// over directions per lane.
+// (the arithmetic of wave_rate() in ph_device.cuh); the max over directions
+// per lane on the bit patterns (rate_max: a NaN propagates).
 __device__ __forceinline__ F2 abs2(F2 x) {
   F2 o;
   o.r = x.r & 0x7fffffff7fffffffull;
@@ -148,12 +148,8 @@ __device__ __forceinline__ void wave_rate2(const F2 w[NV], const Phys<float>& P,
   split(a, a0, a1);
   split(b, b0, b1);
   split(d, d0, d1);
-  ra = a0;
-  if (!(b0 <= ra)) ra = b0;
-  if (!(d0 <= ra)) ra = d0;
-  rb = a1;
-  if (!(b1 <= rb)) rb = b1;
-  if (!(d1 <= rb)) rb = d1;
+  ra = rate_max(a0, rate_max(b0, d0));
+  rb = rate_max(a1, rate_max(b1, d1));
 }
 
 // Half van Leer slopes of the five variables on both lanes, from the
@@ -544,8 +540,7 @@ __device__ __forceinline__ double stage_tile_pair(const TileJob<float>& J, const
         cons_to_prim2(w, P, floors);
         float ra, rb;
         wave_rate2(w, P, J.idx1, J.idx2, J.idx3, ra, rb);
-        if (!(ra <= rate)) rate = ra;
-        if (!(rb <= rate)) rate = rb;
+        rate = rate_max(rate, rate_max(ra, rb));
       }
     }
   }

@@ -53,6 +53,23 @@ def test_non_finite_state_is_reported():
     assert rc == -3 and nonfinite == 1
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_one_nan_cell_makes_the_first_dt_non_finite(precision):
+    """A NaN density in one cell, in the middle of the cells one thread of
+    the dt reduction visits (32^3 block: 1024-cell planes, 4 cells a thread),
+    must survive the running max: the first dt is not finite and the status
+    says so before any cycle."""
+    torch, ph = _ph()
+    m = ph.Mesh(ph.make_config((32, 32, 32), (1, 1, 1), precision=precision))
+    geo = W.Geometry((32, 32, 32), (1, 1, 1))
+    U = W.blast(geo, m.tree(), seed=0).astype(np.float32 if precision == "fp32" else np.float64)
+    U[0, 0, 5, 0, 0] = np.nan   # plane 5, the first cell a thread visits there
+    m.set_state(U)
+    rc, floors, nonfinite = m.status()
+    assert nonfinite == 1 and rc == -3
+    assert not np.isfinite(m.dt())
+
+
 def test_vacuum_region_hits_floors_and_is_counted():
     torch, ph = _ph()
     m = ph.Mesh(ph.make_config((8, 8, 8), (2, 2, 2)))
