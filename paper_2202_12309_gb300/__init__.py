@@ -777,6 +777,18 @@ class ShardedMesh:
             sh.close()
 
 
+def reduce_rate_max(r, dist):
+    """Max of one signal rate (a one-element float64 tensor) over the ranks
+    of the default process group, in place.  A NaN rate (a non-finite state
+    on some rank) becomes +inf first: the max of floating-point values with
+    a NaN among them depends on the backend, +inf wins on all of them, and
+    dt = cfl / inf = 0 is reported as non-finite by the dt bookkeeping."""
+    import torch
+    r.copy_(torch.where(torch.isnan(r), torch.full_like(r, float("inf")), r))
+    dist.all_reduce(r, op=dist.ReduceOp.MAX)
+    return r
+
+
 class DistShard:
     """One shard per process of a torch.distributed group: shard `rank` of
     `world` on the current device, with the halo exchange as point-to-point
@@ -829,7 +841,7 @@ class DistShard:
         self.m.rate(recompute, self.rate_d)
         torch.cuda.current_stream().synchronize()
         r = self.rate_d.cpu() if self.host else self.rate_d
-        dist.all_reduce(r, op=dist.ReduceOp.MAX)
+        reduce_rate_max(r, dist)
         if self.host:
             self.rate_d.copy_(r)
         self.m.finish(first, self.rate_d)
