@@ -70,6 +70,34 @@ def test_one_nan_cell_makes_the_first_dt_non_finite(precision):
     assert not np.isfinite(m.dt())
 
 
+@pytest.mark.parametrize("precision,nx,nb,kw", [
+    ("fp64", (16, 16, 16), (2, 2, 2), {}),                      # cubic cells
+    ("fp64", (24, 16, 8), (1, 2, 3), {}),                       # dx1 = dx3 != dx2
+    ("fp32", (32, 32, 32), (2, 2, 2), {}),                      # 32x16 paired tiles
+    ("fp32", (16, 16, 16), (2, 2, 2), {}),                      # 16x16 paired tiles
+    ("fp64", (8, 8, 8), (2, 2, 2),                              # two levels: flux correction
+     dict(max_level=1, static_region=1, static_lo=(-0.3, -0.3, -0.3), static_hi=(-0.1, -0.1, -0.1))),
+])
+def test_rate_kernel_gives_the_dt_the_stage_epilogue_folded(precision, nx, nb, kw):
+    """The dt a cycle's stage 2 folds into its epilogue (and, on two levels,
+    the flux correction for the cells it changes) is the dt the rate kernel
+    computes from the same state, bit for bit."""
+    torch, ph = _ph()
+    cfg = ph.make_config(nx, nb, precision=precision, **kw)
+    m = ph.Mesh(cfg)
+    geo = W.Geometry(nx, nb)
+    U = W.blast(geo, m.tree(), seed=3).astype(np.float32 if precision == "fp32" else np.float64)
+    m.set_state(U)
+    m.step(2)
+    folded = m.next_dt()
+    state = m.get_state()
+    m2 = ph.Mesh(cfg)
+    assert np.array_equal(m2.tree(), m.tree())
+    m2.set_state(state)
+    assert m2.dt() == folded and m2.next_dt() == folded
+    assert m.status()[0] == 0 and m2.status()[0] == 0
+
+
 def test_vacuum_region_hits_floors_and_is_counted():
     torch, ph = _ph()
     m = ph.Mesh(ph.make_config((8, 8, 8), (2, 2, 2)))
