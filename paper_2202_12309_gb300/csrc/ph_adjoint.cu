@@ -55,7 +55,8 @@ __device__ __forceinline__ T prim_fwd(const T u[NV], const Phys<T>& P, T w[NV], 
   w[1] = u[1] * ir;
   w[2] = u[2] * ir;
   w[3] = u[3] * ir;
-  T p = P.gm1 * (u[4] - T(0.5) * (u[1] * w[1] + u[2] * w[2] + u[3] * w[3]));
+  // the stage kernels' conversion, fma for fma (cons_to_prim)
+  T p = P.gm1 * fma(T(-0.5), fma(u[3], w[3], fma(u[2], w[2], u[1] * w[1])), u[4]);
   pf = p < P.pfloor;
   if (pf) p = P.pfloor;
   w[4] = p;

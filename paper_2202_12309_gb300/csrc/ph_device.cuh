@@ -183,7 +183,10 @@ __device__ __forceinline__ void cons_to_prim(T w[NVT], const Phys<T>& P, unsigne
   if (below_floor(rho, P.dfloor)) { rho = P.dfloor; ++floors; }
   const T ir = rcp(rho);
   const T v1 = w[1] * ir, v2 = w[2] * ir, v3 = w[3] * ir;
-  T p = P.gm1 * (w[4] - T(0.5) * (w[1] * v1 + w[2] * v2 + w[3] * v3));
+  // explicit fmas in a fixed order (the paired FP32 conversion uses the
+  // same), so that every kernel converts a state to the same bits
+  const T ke = fma(w[3], v3, fma(w[2], v2, w[1] * v1));
+  T p = P.gm1 * fma(T(-0.5), ke, w[4]);
   if (below_floor(p, P.pfloor)) { p = P.pfloor; ++floors; }
   w[0] = rho;
   w[1] = v1;

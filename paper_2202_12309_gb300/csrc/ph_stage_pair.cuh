@@ -116,7 +116,7 @@ __device__ __forceinline__ void cons_to_prim2(F2 w[NV], const Phys<float>& P, un
   const F2 rho = f2(r0, r1);
   const F2 ir = rcp2(rho);
   const F2 v1 = w[1] * ir, v2 = w[2] * ir, v3 = w[3] * ir;
-  const F2 ke = fma2(w[1], v1, fma2(w[2], v2, w[3] * v3));
+  const F2 ke = fma2(w[3], v3, fma2(w[2], v2, w[1] * v1));  // the order of cons_to_prim()
   F2 p = f2(P.gm1) * fma2(f2(-0.5f), ke, w[4]);
   float p0, p1;
   split(p, p0, p1);
