@@ -214,8 +214,11 @@ int ph_refine_where(ph_mesh* mesh, const int8_t* flags, int32_t n, int32_t check
 int ph_refine_by_density(ph_mesh* mesh, int32_t* changed);
 
 /* Health of the state since creation: number of floor applications and 1 if
- * a non-finite dt was produced.  Returns PH_ERR_NONPHYSICAL when either is
- * non-zero (outputs are still written). */
+ * a non-finite dt was produced.  The dt comes from the max signal rate over
+ * every interior cell (after a state is set or loaded, after a remesh and
+ * after each cycle's stage 2); a NaN rate in any cell wins that max, so one
+ * non-finite cell makes the dt non-finite.  Returns PH_ERR_NONPHYSICAL when
+ * either is non-zero (outputs are still written). */
 int ph_status(ph_mesh* mesh, int64_t* floor_hits, int32_t* nonfinite);
 
 /* Kernel-level entry points used by tests and benchmarks ------------------ */
